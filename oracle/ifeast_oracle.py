@@ -1,0 +1,408 @@
+"""CPU oracle for FEAST / IFEAST (Gavin & Polizzi, arXiv 1706.00692).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline legs of ``bench.py`` may import this module. The CUDA library and
+its Python binding never call it, and it imports nothing from them.
+
+Plain, slow, obviously-correct float64 numpy/scipy code. Library primitives
+(sparse mat-vec, dense LU, Cholesky, symmetric eigensolver, least squares) are
+used as single steps; nothing is blocked, fused or reordered beyond what the
+cited definitions state.
+
+Map to the paper:
+  contour_nodes / filter_rho ......... Eq. (contour_int_quad), Eq. (rhoh), the
+                                        half-contour symmetry of Section 4.1
+  feast .............................. Algorithm 1 (direct shifted solves)
+  ifeast ............................. Algorithm 2 (iterative shifted solves,
+                                        stopping rule ||x-(zI-A)y|| <= alpha*||R_F||)
+  gmres .............................. GMRES of Section 2.2 (zero initial guess,
+                                        modified Gram-Schmidt Arnoldi, Givens)
+  gmres_shared_basis ................. Section 3, Eqs. (yz)-(contint_krylov):
+                                        the Krylov basis does not depend on z
+  rayleigh_ritz ...................... Algorithm 1/2 step 3
+  eigen_residuals .................... Algorithm 1/2 step 4
+  convergence_bound .................. Eq. (upperbound), Eq. (deltadef)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+GL_HALF = "gl_half"
+TRAP_HALF = "trap_half"
+TRAP_FULL = "trap_full"
+
+
+# ---------------------------------------------------------------------------
+# Contour and quadrature (Eq. contour_int_quad; half-contour symmetry, Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def contour_nodes(rule: str, nc: int, emin: float, emax: float):
+    """Quadrature nodes z_k and weights w_k for (1/2 pi i) \\oint (zI-A)^{-1} dz
+    on the circle with centre c=(emin+emax)/2 and radius r=(emax-emin)/2.
+
+    Parametrise z = c + r e^{i theta}; then dz/(2 pi i) = r e^{i theta} d theta/(2 pi).
+    * TRAP_FULL: nc points theta_j = 2 pi (j - 1/2)/nc, w_j = r e^{i theta_j}/nc;
+      the filter is the plain sum sum_j w_j/(z_j - lambda).
+    * TRAP_HALF / GL_HALF (real symmetric A): the lower half of the circle
+      contributes the complex conjugate of the upper half, so only nc nodes on
+      the upper half are used and the filter is 2 Re of their sum. The factor 2
+      is folded into the weights, so filter = Re sum_k w_k/(z_k - lambda):
+        TRAP_HALF: theta_j = pi (j - 1/2)/nc, w_j = r e^{i theta_j}/nc
+        GL_HALF:   Gauss-Legendre (x_e, g_e) on (-1,1), theta_e = (pi/2)(1 - x_e),
+                   w_e = (g_e/2) r e^{i theta_e}
+    Returns (z, w) as complex128 arrays of length nc.
+    """
+    c = 0.5 * (emin + emax)
+    r = 0.5 * (emax - emin)
+    if rule == TRAP_FULL:
+        th = 2.0 * math.pi * (np.arange(1, nc + 1) - 0.5) / nc
+        return c + r * np.exp(1j * th), r * np.exp(1j * th) / nc
+    if rule == TRAP_HALF:
+        th = math.pi * (np.arange(1, nc + 1) - 0.5) / nc
+        return c + r * np.exp(1j * th), r * np.exp(1j * th) / nc
+    if rule == GL_HALF:
+        x, g = np.polynomial.legendre.leggauss(nc)
+        th = 0.5 * math.pi * (1.0 - x)
+        return c + r * np.exp(1j * th), 0.5 * g * r * np.exp(1j * th)
+    raise ValueError(rule)
+
+
+def is_half_rule(rule: str) -> bool:
+    return rule in (GL_HALF, TRAP_HALF)
+
+
+def filter_rho(lam, z, w, half: bool):
+    """Rational filter rho_hat(lambda) = sum_k w_k (z_k - lambda)^{-1} (Eq. rhoh),
+    taking the real part for a half contour."""
+    lam = np.asarray(lam, dtype=np.float64)
+    s = np.sum(w[None, :] / (z[None, :] - lam.reshape(-1, 1)), axis=1).reshape(lam.shape)
+    return s.real if half else s
+
+
+# ---------------------------------------------------------------------------
+# Sparse operator (the method touches A only through products, Section 1.2)
+# ---------------------------------------------------------------------------
+
+def csr_to_scipy(rowptr, colidx, val, n):
+    return sp.csr_matrix((np.asarray(val, np.float64), np.asarray(colidx), np.asarray(rowptr)),
+                         shape=(n, n))
+
+
+def shifted_apply(A, z, V):
+    """W = (z I - A) V  (one column block of Algorithm 2 step 1's operator)."""
+    return z * V - A @ V
+
+
+# ---------------------------------------------------------------------------
+# GMRES (Section 2.2): zero initial guess, MGS Arnoldi, Givens least squares
+# ---------------------------------------------------------------------------
+
+def givens_params(a, b):
+    """Unitary rotation G = [[conj(c), conj(s)], [-s, c]] with G [a; b] = [rho; 0],
+    rho = sqrt(|a|^2 + |b|^2) >= 0."""
+    rho = math.hypot(abs(a), abs(b))
+    if rho == 0.0:
+        return 1.0 + 0j, 0j, 0.0
+    return a / rho, b / rho, rho
+
+
+def gmres(matvec, b, k, tol_rel=0.0, breakdown_rel=1e-14):
+    """GMRES for M y = b with y_0 = 0, at most k Arnoldi steps, stopping as soon
+    as the least-squares residual |g_{s+1}| <= tol_rel * ||b|| (tol_rel <= 0:
+    run all k).
+
+    Returns dict(y, steps, res_est, V, H) where V is (steps+1, n) and H the
+    (steps+1) x steps Hessenberg matrix of the Arnoldi relation
+    M V[:steps].T = V.T H (for inspection by tests)."""
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    beta = np.linalg.norm(b)
+    V = np.zeros((k + 1, n), np.complex128)
+    H = np.zeros((k + 1, k), np.complex128)
+    R = np.zeros((k, k), np.complex128)
+    cs = np.zeros(k, np.complex128)
+    sn = np.zeros(k, np.complex128)
+    g = np.zeros(k + 1, np.complex128)
+    if beta == 0.0:
+        return dict(y=np.zeros(n, np.complex128), steps=0, res_est=0.0, V=V[:1], H=H[:1, :0])
+    V[0] = b / beta
+    g[0] = beta
+    steps = 0
+    for s in range(k):
+        w = matvec(V[s])
+        for l in range(s + 1):                      # modified Gram-Schmidt
+            H[l, s] = np.vdot(V[l], w)
+            w = w - H[l, s] * V[l]
+        H[s + 1, s] = np.linalg.norm(w)
+        happy = H[s + 1, s].real <= breakdown_rel * beta
+        if not happy:
+            V[s + 1] = w / H[s + 1, s]
+        col = H[: s + 2, s].copy()
+        for l in range(s):                          # previous rotations
+            a, bb = col[l], col[l + 1]
+            col[l] = np.conj(cs[l]) * a + np.conj(sn[l]) * bb
+            col[l + 1] = -sn[l] * a + cs[l] * bb
+        cs[s], sn[s], rho = givens_params(col[s], col[s + 1])
+        col[s], col[s + 1] = rho, 0.0
+        R[: s + 1, s] = col[: s + 1]
+        g[s + 1] = -sn[s] * g[s]
+        g[s] = np.conj(cs[s]) * g[s]
+        steps = s + 1
+        if happy or (tol_rel > 0.0 and abs(g[s + 1]) <= tol_rel * beta):
+            break
+    y_small = sla.solve_triangular(R[:steps, :steps], g[:steps], lower=False)
+    y = V[:steps].T @ y_small
+    return dict(y=y, steps=steps, res_est=abs(g[steps]), V=V[: steps + 1], H=H[: steps + 1, :steps],
+                y_small=y_small)
+
+
+def arnoldi_real(A, x, k, breakdown_rel=1e-14):
+    """Arnoldi on the real matrix A from x (MGS). Returns V (steps+1, n), the
+    (steps+1) x steps Hessenberg H, beta = ||x||, steps."""
+    n = x.shape[0]
+    beta = np.linalg.norm(x)
+    V = np.zeros((k + 1, n))
+    H = np.zeros((k + 1, k))
+    V[0] = x / beta
+    steps = 0
+    for s in range(k):
+        w = A @ V[s]
+        for l in range(s + 1):
+            H[l, s] = V[l] @ w
+            w = w - H[l, s] * V[l]
+        H[s + 1, s] = np.linalg.norm(w)
+        steps = s + 1
+        if H[s + 1, s] <= breakdown_rel * beta:
+            break
+        V[s + 1] = w / H[s + 1, s]
+    return V[: steps + 1], H[: steps + 1, :steps], beta, steps
+
+
+def gmres_shared_basis(A, x, z, k, tol_rel=0.0):
+    """GMRES for (z I - A) y = x using the basis of K(A, x) (Section 3: the
+    Krylov basis V is the same for every shift z). With A V_s = V_{s+1} Hbar,
+    (z I - A) V_s = V_{s+1} (z Ibar - Hbar); the small least-squares problem is
+    min || beta e_1 - (z Ibar - Hbar) y ||, solved here with lstsq at every s
+    until the residual drops to tol_rel * ||x|| (or all k steps)."""
+    V, H, beta, steps = arnoldi_real(A, x, k)
+    for s in range(1, steps + 1):
+        Hz = -H[: s + 1, :s].astype(np.complex128)
+        Hz[np.arange(s), np.arange(s)] += z
+        rhs = np.zeros(s + 1, np.complex128)
+        rhs[0] = beta
+        ys = np.linalg.lstsq(Hz, rhs, rcond=None)[0]
+        res = np.linalg.norm(rhs - Hz @ ys)
+        if (tol_rel > 0.0 and res <= tol_rel * beta) or s == steps:
+            return dict(y=V[:s].T @ ys, steps=s, res_est=res)
+    raise AssertionError("unreachable")
+
+
+# ---------------------------------------------------------------------------
+# Rayleigh-Ritz and residuals (Algorithm 1/2 steps 3 and 4)
+# ---------------------------------------------------------------------------
+
+def cholesky_shifted(Bq):
+    """Cholesky of the reduced Gram matrix; if it is not numerically positive
+    definite, retry once with the shift 11 (n m0 + m0 (m0+1)) u ||B_Q||_2 of
+    shifted CholeskyQR (Fukaya et al., 2020); n is taken as m0 here since only
+    the m0 x m0 matrix is factored. Returns (L, shifted_flag)."""
+    try:
+        return np.linalg.cholesky(Bq), False
+    except np.linalg.LinAlgError:
+        m = Bq.shape[0]
+        shift = 11.0 * (m * m + m * (m + 1)) * np.finfo(float).eps * np.linalg.norm(Bq, 2)
+        return np.linalg.cholesky(Bq + shift * np.eye(m)), True
+
+
+def rayleigh_ritz(Q, AQ):
+    """Solve A_Q X_Q = B_Q X_Q Lambda with A_Q = Q^H A Q, B_Q = Q^H Q through
+    B_Q = L L^H, C = L^{-1} A_Q L^{-H}, C = U Lambda U^H, X_Q = L^{-H} U.
+    Returns (lam ascending, X_Q) with X_Q^H B_Q X_Q = I."""
+    Aq = Q.conj().T @ AQ
+    Bq = Q.conj().T @ Q
+    Aq = 0.5 * (Aq + Aq.conj().T)
+    Bq = 0.5 * (Bq + Bq.conj().T)
+    L, _ = cholesky_shifted(Bq)
+    Li_Aq = sla.solve_triangular(L, Aq, lower=True)
+    C = sla.solve_triangular(L, Li_Aq.conj().T, lower=True).conj().T
+    C = 0.5 * (C + C.conj().T)
+    lam, U = np.linalg.eigh(C)
+    XQ = sla.solve_triangular(L.conj().T, U, lower=False)
+    return lam, XQ
+
+
+def eigen_residuals(AX, X, lam):
+    """Relative eigenpair residuals ||A x_j - lam_j x_j|| / ||A x_j||."""
+    num = np.linalg.norm(AX - X * lam[None, :], axis=0)
+    den = np.linalg.norm(AX, axis=0)
+    return num / np.where(den > 0, den, 1.0)
+
+
+def in_interval(lam, emin, emax):
+    return (lam > emin) & (lam < emax)
+
+
+# ---------------------------------------------------------------------------
+# FEAST (Algorithm 1) and IFEAST (Algorithm 2)
+# ---------------------------------------------------------------------------
+
+def _filtered_subspace_exact(A_dense, X, z, w, half):
+    n = X.shape[0]
+    Q = np.zeros(X.shape, np.complex128)
+    for zk, wk in zip(z, w):
+        lu = sla.lu_factor(zk * np.eye(n) - A_dense)
+        Q += wk * sla.lu_solve(lu, X.astype(np.complex128))
+    return Q.real if half else Q
+
+
+def _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats):
+    n, m0 = X.shape
+    Q = np.zeros(X.shape, np.complex128)
+    for zk, wk in zip(z, w):
+        for j in range(m0):
+            out = gmres(lambda v: shifted_apply(A, zk, v), X[:, j], k, tol_rel)
+            stats["inner_steps"].append(out["steps"])
+            Q[:, j] += wk * out["y"]
+    return Q.real if half else Q
+
+
+def _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats):
+    n, m0 = X.shape
+    Q = np.zeros(X.shape, np.complex128)
+    for zk, wk in zip(z, w):
+        for j in range(m0):
+            out = gmres_shared_basis(A, X[:, j], zk, k, tol_rel)
+            stats["inner_steps"].append(out["steps"])
+            Q[:, j] += wk * out["y"]
+    return Q.real if half else Q
+
+
+def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0,
+           tol=1e-10, max_outer=100, callback=None):
+    """Algorithm 2 (and, with inner="exact", Algorithm 1) for a real symmetric
+    standard problem A x = lambda x.
+
+    inner: "exact" dense LU per node (Alg. 1 step 1),
+           "gmres" per-node complex GMRES (Alg. 2 step 1),
+           "shared" GMRES on the shift-independent Krylov basis (Section 3).
+    k: maximum inner steps. alpha > 0: stop each inner solve once
+    ||x_j - (z_k I - A) y|| <= alpha * ||R_F|| * ||x_j|| (Alg. 2 step 1 with the
+    residual measured relative to the right-hand side, ||R_F|| = 1 at the
+    start); alpha <= 0: run exactly k steps.
+    ||R_F|| is the largest relative residual ||A x_j - lam_j x_j||/||A x_j||
+    over Ritz values strictly inside (emin, emax).
+
+    Returns dict(lam, X, res, inside, iters, history, converged).
+    """
+    A = A.tocsr() if sp.issparse(A) else A
+    X = np.asarray(X0, dtype=np.float64).copy()
+    RF = 1.0
+    history = []
+    A_dense = None
+    for it in range(1, max_outer + 1):
+        stats = {"inner_steps": []}
+        tol_rel = alpha * RF if alpha > 0 else 0.0
+        if inner == "exact":
+            if A_dense is None:
+                A_dense = A.toarray() if sp.issparse(A) else np.asarray(A)
+            Q = _filtered_subspace_exact(A_dense, X, z, w, half)
+        elif inner == "gmres":
+            Q = _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats)
+        elif inner == "shared":
+            Q = _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats)
+        else:
+            raise ValueError(inner)
+        AQ = A @ Q
+        lam, XQ = rayleigh_ritz(Q, AQ)
+        X = Q @ XQ
+        AX = AQ @ XQ
+        res = eigen_residuals(AX, X, lam)
+        inside = in_interval(lam, emin, emax)
+        RF = float(res[inside].max()) if inside.any() else 1.0
+        history.append(dict(RF=RF, count=int(inside.sum()),
+                            max_inner=max(stats["inner_steps"], default=0),
+                            total_inner=int(sum(stats["inner_steps"]))))
+        if callback is not None:
+            callback(it, lam, X, res, inside)
+        if inside.any() and RF <= tol:
+            return dict(lam=lam, X=X, res=res, inside=inside, iters=it, history=history,
+                        converged=True)
+    return dict(lam=lam, X=X, res=res, inside=inside, iters=max_outer, history=history,
+                converged=False)
+
+
+def feast(A, X0, emin, emax, z, w, *, half=True, tol=1e-10, max_outer=100):
+    """Algorithm 1: FEAST with direct (dense LU) shifted solves."""
+    return ifeast(A, X0, emin, emax, z, w, half=half, inner="exact", tol=tol, max_outer=max_outer)
+
+
+# ---------------------------------------------------------------------------
+# One filtering step from the spectral definition (Eq. rhoh), for pins
+# ---------------------------------------------------------------------------
+
+def filter_step_spectral(A_dense, X, z, w, half=True):
+    """rho_hat(A) X = U rho_hat(Lambda) U^H X with A = U Lambda U^H (Eq. rhoh)."""
+    lam, U = np.linalg.eigh(A_dense)
+    r = filter_rho(lam, z, w, half)
+    return U @ (r[:, None] * (U.conj().T @ X))
+
+
+def convergence_bound_delta(lam_all, z, w, half=True):
+    """Delta = sum_k ||w_k (z_k I - A)^{-1}|| (Eq. deltadef) for normal A with
+    spectrum lam_all; for a half contour the mirrored lower-half nodes are
+    counted too, since the filter uses both halves."""
+    d = 0.0
+    for zk, wk in zip(z, w):
+        t = abs(wk) / np.min(np.abs(zk - lam_all))
+        d += 2.0 * t if half else t
+    return d
+
+
+# ---------------------------------------------------------------------------
+# Step-level references for kernel parity (same maths as the steps above)
+# ---------------------------------------------------------------------------
+
+def ref_spmm_shift(A, V, zcol):
+    """W[:, c] = zcol[c] V[:, c] - A V[:, c] (Alg. 2 step 1 operator on a block)."""
+    return V * zcol[None, :] - A @ V
+
+
+def ref_arnoldi_step(V_basis, W):
+    """Orthogonalise W (n x C) against V_basis (s+1, n, C) column by column
+    with MGS; returns (h (s+2, C), V_next (n, C))."""
+    sp1 = V_basis.shape[0]
+    C = W.shape[1]
+    h = np.zeros((sp1 + 1, C), np.complex128)
+    Vn = np.zeros_like(W)
+    for c in range(C):
+        w = W[:, c].copy()
+        for l in range(sp1):
+            h[l, c] = np.vdot(V_basis[l, :, c], w)
+            w = w - h[l, c] * V_basis[l, :, c]
+        nr = np.linalg.norm(w)
+        h[sp1, c] = nr
+        Vn[:, c] = w / nr
+    return h, Vn
+
+
+def ref_gram(Q, AQ):
+    return Q.conj().T @ AQ, Q.conj().T @ Q
+
+
+# ---------------------------------------------------------------------------
+# Textbook closed form used as a pin (not part of the method)
+# ---------------------------------------------------------------------------
+
+def laplacian_closed_form_eigs(grid):
+    """Eigenvalues of the unit-spacing Dirichlet finite-difference Laplacian on
+    a d-dimensional grid: sum over dimensions of 2 - 2 cos(p pi/(N+1)),
+    p = 1..N. Ascending."""
+    ev = np.zeros(1)
+    for N in grid:
+        mu = 2.0 - 2.0 * np.cos(np.arange(1, N + 1) * math.pi / (N + 1))
+        ev = (ev[:, None] + mu[None, :]).ravel()
+    return np.sort(ev)

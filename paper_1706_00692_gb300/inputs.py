@@ -1,0 +1,193 @@
+"""Seeded synthetic inputs for the IFEAST hot path.
+
+This module is shared by the CUDA path's callers (tests, bench) and by the
+CPU oracle's tests. It holds no arithmetic of the eigensolver itself: it only
+builds the sparse test matrices, the random potential and the random initial
+subspace, and names the workloads.
+
+The paper measures on PARSEC Hamiltonians (Si2, n=769; Na5, n=5832; Section 4)
+that are not available here. Seeded finite-difference Laplacians (a real
+symmetric, sparse, Hamiltonian-like operator: kinetic term plus an optional
+random diagonal potential) stand in for them.
+
+CSR convention used everywhere: ``rowptr`` int32 (n+1), ``colidx`` int32
+(nnz, ascending within a row), ``val`` float64 (nnz). Dense blocks are numpy
+float64 arrays of shape (n, m0), C-contiguous (row i holds m0 entries).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class CSR:
+    n: int
+    rowptr: np.ndarray
+    colidx: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.shape[0])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.val, self.colidx, self.rowptr), shape=(self.n, self.n))
+
+
+def _csr_from_coo(n, rows, cols, vals) -> CSR:
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    counts = np.bincount(rows, minlength=n)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals.astype(np.float64))
+
+
+def laplacian(grid: tuple[int, ...]) -> CSR:
+    """Dirichlet finite-difference Laplacian (unit spacing) on a d-dimensional
+    grid: 2d on the diagonal, -1 for each of the 2d nearest neighbours inside
+    the grid (5-point in 2D, 7-point in 3D). Unknowns are numbered with the
+    last grid index fastest."""
+    grid = tuple(int(g) for g in grid)
+    d = len(grid)
+    n = int(np.prod(grid))
+    idx = np.arange(n, dtype=np.int64).reshape(grid)
+    rows = [idx.ravel()]
+    cols = [idx.ravel()]
+    vals = [np.full(n, 2.0 * d)]
+    for ax in range(d):
+        lo = [slice(None)] * d
+        hi = [slice(None)] * d
+        lo[ax] = slice(0, grid[ax] - 1)
+        hi[ax] = slice(1, grid[ax])
+        a = idx[tuple(lo)].ravel()
+        b = idx[tuple(hi)].ravel()
+        rows += [a, b]
+        cols += [b, a]
+        vals += [np.full(a.size, -1.0), np.full(a.size, -1.0)]
+    return _csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def add_diagonal(A: CSR, d: np.ndarray) -> CSR:
+    """A + diag(d); every row of A already holds its diagonal entry."""
+    val = A.val.copy()
+    for i in range(A.n):
+        lo, hi = A.rowptr[i], A.rowptr[i + 1]
+        k = lo + int(np.searchsorted(A.colidx[lo:hi], i))
+        assert A.colidx[k] == i
+        val[k] += d[i]
+    return CSR(A.n, A.rowptr.copy(), A.colidx.copy(), val)
+
+
+def add_diagonal_fast(A: CSR, d: np.ndarray) -> CSR:
+    """Vectorised add_diagonal for large stencils (same result)."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    val = A.val.copy()
+    diag = rows == A.colidx
+    assert int(diag.sum()) == A.n
+    val[diag] += d[rows[diag]]
+    return CSR(A.n, A.rowptr.copy(), A.colidx.copy(), val)
+
+
+def random_potential(n: int, seed: int) -> np.ndarray:
+    """Diagonal potential, i.i.d. uniform on [0, 1), numpy PCG64(seed)."""
+    return np.random.Generator(np.random.PCG64(seed)).uniform(0.0, 1.0, n)
+
+
+def initial_subspace(n: int, m0: int, seed: int) -> np.ndarray:
+    """Random initial search subspace X^(0): i.i.d. N(0,1), n x m0, PCG64(seed)."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal((n, m0))
+
+
+def random_sparse_symmetric(n: int, nnz_per_row: int, seed: int) -> CSR:
+    """Random real symmetric sparse matrix with a ragged row-length mix
+    (1 .. 2*nnz_per_row off-diagonals per row before symmetrisation), values
+    N(0,1), diagonal uniform on [0, 4). Used for SpMM edge cases."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    rows, cols = [], []
+    for i in range(n):
+        k = int(g.integers(0, 2 * nnz_per_row + 1))
+        c = g.integers(0, n, size=k)
+        rows.append(np.full(k, i))
+        cols.append(c)
+    r = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    c = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    keep = r != c
+    r, c = r[keep], c[keep]
+    v = g.standard_normal(r.size)
+    rr = np.concatenate([r, c, np.arange(n)])
+    cc = np.concatenate([c, r, np.arange(n)])
+    vv = np.concatenate([v, v, g.uniform(0.0, 4.0, n)])
+    # merge duplicates
+    key = rr.astype(np.int64) * n + cc
+    uk, inv = np.unique(key, return_inverse=True)
+    vals = np.zeros(uk.size)
+    np.add.at(vals, inv, vv)
+    return _csr_from_coo(n, (uk // n).astype(np.int64), (uk % n).astype(np.int64), vals)
+
+
+# ---------------------------------------------------------------------------
+# Closed-form spectra of the stencils (used to place interval endpoints in
+# spectral gaps and as test pins).
+# ---------------------------------------------------------------------------
+
+def laplacian_1d_eigs(N: int) -> np.ndarray:
+    p = np.arange(1, N + 1)
+    return 2.0 - 2.0 * np.cos(p * math.pi / (N + 1))
+
+
+def laplacian_eigs(grid: tuple[int, ...]) -> np.ndarray:
+    """All eigenvalues of laplacian(grid), ascending (sum of 1D spectra)."""
+    ev = np.zeros(1)
+    for N in grid:
+        ev = (ev[:, None] + laplacian_1d_eigs(N)[None, :]).ravel()
+    return np.sort(ev)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    A: CSR
+    emin: float
+    emax: float
+    m0: int
+    nc: int
+    rule: str
+    inner_iters: int
+    alpha: float
+    seed: int
+    expected_count: int | None = None
+
+    def X0(self) -> np.ndarray:
+        return initial_subspace(self.A.n, self.m0, self.seed)
+
+
+def workload_lap2d_50(seed: int = 0) -> Workload:
+    """2D 5-point Dirichlet Laplacian on a 50x50 grid (n=2500), interval
+    enclosing the 10 lowest eigenvalues, m0=20, 8 Gauss-Legendre nodes on the
+    upper half circle, GMRES fixed at 10 iterations."""
+    ev = laplacian_eigs((50, 50))
+    emin, emax = 0.0, 0.5 * (ev[9] + ev[10])
+    return Workload("lap2d_50x50_m0_20_gl8_gmres10", laplacian((50, 50)), emin, emax,
+                    m0=20, nc=8, rule="gl_half", inner_iters=10, alpha=0.0, seed=seed,
+                    expected_count=10)
+
+
+def workload_lap3d_pot(N: int = 64, seed: int = 0, m0: int = 80, first: int = 1000,
+                       count: int = 50, nc: int = 8, inner_iters: int = 400,
+                       alpha: float = 1e-3) -> Workload:
+    """3D 7-point Dirichlet Laplacian on N^3 plus a U[0,1) diagonal potential.
+    The interior window is placed from the pure-Laplacian spectrum shifted by
+    the potential's mean 0.5: (lam_L[first] + 0.5, lam_L[first+count] + 0.5)
+    (0-based indices into the ascending closed-form spectrum, endpoints taken
+    half way between neighbours)."""
+    ev = laplacian_eigs((N, N, N))
+    emin = 0.5 * (ev[first - 1] + ev[first]) + 0.5
+    emax = 0.5 * (ev[first + count - 1] + ev[first + count]) + 0.5
+    A = add_diagonal_fast(laplacian((N, N, N)), random_potential(N ** 3, seed + 1))
+    return Workload(f"lap3d_{N}^3_pot_interior_m0_{m0}_gl{nc}", A, emin, emax, m0=m0, nc=nc,
+                    rule="gl_half", inner_iters=inner_iters, alpha=alpha, seed=seed)

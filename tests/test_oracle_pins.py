@@ -1,0 +1,277 @@
+"""Pins for the CPU oracle: each checks it against something other than itself
+(closed forms, brute force, the spectral definition, library solvers)."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import ifeast_oracle as orc
+from paper_1706_00692_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- contour / filter
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+@pytest.mark.parametrize("t", [0.0, 0.3, 0.9, 1.2, 2.0, -0.7, -1.5])
+def test_trapezoid_filter_closed_form(N, t):
+    """N offset trapezoid nodes on the full circle give rho(t) = 1/(1+t^N),
+    t=(lambda-c)/r; the half-contour form with N/2 upper nodes is identical."""
+    emin, emax = -1.0, 3.0
+    c, r = 1.0, 2.0
+    lam = c + t * r
+    z, w = orc.contour_nodes(orc.TRAP_FULL, N, emin, emax)
+    full = orc.filter_rho(np.array([lam]), z, w, half=False)[0]
+    assert abs(full - 1.0 / (1.0 + t ** N)) < 1e-13
+    zh, wh = orc.contour_nodes(orc.TRAP_HALF, N // 2, emin, emax)
+    half = orc.filter_rho(np.array([lam]), zh, wh, half=True)[0]
+    assert abs(half - 1.0 / (1.0 + t ** N)) < 1e-13
+
+
+def test_trapezoid_value_16_nodes():
+    z, w = orc.contour_nodes(orc.TRAP_HALF, 8, 0.0, 2.0)
+    assert abs(orc.filter_rho(np.array([1.0 + 1.2]), z, w, True)[0] - 1 / (1 + 1.2 ** 16)) < 1e-14
+
+
+@pytest.mark.parametrize("nc", [4, 8, 12])
+def test_gl_half_centre_is_one(nc):
+    """At the centre every term is w_k/(r e^{i theta_k}) = g_k/2 and the
+    Gauss-Legendre weights sum to 2."""
+    z, w = orc.contour_nodes(orc.GL_HALF, nc, 2.0, 5.0)
+    assert abs(orc.filter_rho(np.array([3.5]), z, w, True)[0] - 1.0) < 1e-14
+
+
+def test_gl_half_tends_to_indicator():
+    """Exact contour integral of 1/(z-lambda) is 1 inside, 0 outside."""
+    z, w = orc.contour_nodes(orc.GL_HALF, 48, -1.0, 1.0)
+    inside = orc.filter_rho(np.linspace(-0.6, 0.6, 13), z, w, True)
+    outside = orc.filter_rho(np.concatenate([np.linspace(-5, -1.6, 7), np.linspace(1.6, 5, 7)]), z, w, True)
+    assert np.abs(inside - 1).max() < 1e-9
+    assert np.abs(outside).max() < 1e-9
+
+
+def test_half_contour_equals_full_circle_gl():
+    """Half contour with its folded weights equals the full-circle Gauss-Legendre
+    sum obtained by mirroring the nodes into the lower half plane."""
+    z, w = orc.contour_nodes(orc.GL_HALF, 8, 0.5, 2.5)
+    zf = np.concatenate([z, z.conj()])
+    wf = np.concatenate([w, w.conj()]) / 2.0
+    lam = np.linspace(-2, 5, 31)
+    a = orc.filter_rho(lam, z, w, True)
+    b = orc.filter_rho(lam, zf, wf, False)
+    assert np.abs(b.imag).max() < 1e-13
+    assert np.abs(a - b.real).max() < 1e-13
+
+
+# ---------------------------------------------------------------- stencils
+
+@pytest.mark.parametrize("grid", [(7,), (7, 5), (4, 5, 3)])
+def test_laplacian_generator_closed_form(grid):
+    A = inputs.laplacian(grid).to_scipy().toarray()
+    assert np.allclose(A, A.T)
+    ev = np.linalg.eigvalsh(A)
+    assert np.abs(ev - orc.laplacian_closed_form_eigs(grid)).max() < 1e-12
+    assert np.abs(ev - inputs.laplacian_eigs(grid)).max() < 1e-12
+
+
+def test_golden_lap2d_50():
+    vals = np.loadtxt(os.path.join(GOLDEN, "lap2d_50x50_lowest11.txt"))
+    A = inputs.laplacian((50, 50)).to_scipy().toarray()
+    ev = np.linalg.eigvalsh(A)[:11]
+    assert np.abs(ev - vals).max() < 1e-12
+    wl = inputs.workload_lap2d_50()
+    assert abs(wl.emax - 0.5 * (vals[9] + vals[10])) < 1e-15
+
+
+def test_potential_weyl_bounds():
+    """lam_j(L) <= lam_j(L + diag(U[0,1))) <= lam_j(L) + 1."""
+    L = inputs.laplacian((6, 5, 4))
+    A = inputs.add_diagonal(L, inputs.random_potential(L.n, 3))
+    el = np.linalg.eigvalsh(L.to_scipy().toarray())
+    ea = np.linalg.eigvalsh(A.to_scipy().toarray())
+    assert np.all(ea >= el - 1e-12) and np.all(ea <= el + 1 + 1e-12)
+    B = inputs.add_diagonal_fast(L, inputs.random_potential(L.n, 3))
+    assert np.array_equal(A.val, B.val)
+
+
+# ---------------------------------------------------------------- GMRES
+
+def _rand_complex_matrix(n, seed):
+    g = np.random.default_rng(seed)
+    return g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)) + 4 * np.eye(n)
+
+
+def test_gmres_full_dimension_is_exact():
+    n = 12
+    M = _rand_complex_matrix(n, 1)
+    b = np.random.default_rng(2).standard_normal(n)
+    out = orc.gmres(lambda v: M @ v, b, n)
+    assert np.abs(out["y"] - np.linalg.solve(M, b)).max() < 1e-10
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_gmres_minimal_residual_brute_force(k):
+    """GMRES returns the minimiser of ||b - M y|| over K_k(M, b): compare with
+    lstsq on an orthonormalised explicit Krylov matrix."""
+    n = 15
+    M = _rand_complex_matrix(n, 5)
+    b = np.random.default_rng(6).standard_normal(n).astype(np.complex128)
+    K = np.zeros((n, k), np.complex128)
+    v = b.copy()
+    for j in range(k):
+        K[:, j] = v
+        v = M @ v
+    Qk, _ = np.linalg.qr(K)
+    c = np.linalg.lstsq(M @ Qk, b, rcond=None)[0]
+    y_bf = Qk @ c
+    out = orc.gmres(lambda x: M @ x, b, k)
+    assert out["steps"] == k
+    assert np.abs(out["y"] - y_bf).max() < 1e-9 * np.abs(y_bf).max()
+    true_res = np.linalg.norm(b - M @ out["y"])
+    assert abs(out["res_est"] - true_res) < 1e-10 * np.linalg.norm(b)
+
+
+def test_gmres_tolerance_stop_is_first_step_below():
+    n = 30
+    M = _rand_complex_matrix(n, 8)
+    b = np.random.default_rng(9).standard_normal(n)
+    full = [orc.gmres(lambda x: M @ x, b, s)["res_est"] for s in range(1, 20)]
+    tol = 0.5 * (full[6] + full[7]) / np.linalg.norm(b)
+    out = orc.gmres(lambda x: M @ x, b, 19, tol_rel=tol)
+    first = next(i for i, r in enumerate(full) if r <= tol * np.linalg.norm(b)) + 1
+    assert out["steps"] == first
+
+
+def test_shifted_gmres_shared_basis_equals_per_shift():
+    """Section 3: the Krylov basis of (zI - A) does not depend on z, so GMRES on
+    the real basis of K(A, x) with the shifted Hessenberg gives the same y."""
+    A = inputs.add_diagonal(inputs.laplacian((8, 7)), inputs.random_potential(56, 1)).to_scipy()
+    x = np.random.default_rng(4).standard_normal(56)
+    for z in [0.3 + 0.2j, 1.7 + 0.05j, 4.0 + 1.0j]:
+        a = orc.gmres(lambda v: orc.shifted_apply(A, z, v), x, 10)
+        b = orc.gmres_shared_basis(A, x, z, 10)
+        assert np.abs(a["y"] - b["y"]).max() < 1e-10 * np.abs(a["y"]).max()
+        assert abs(a["res_est"] - b["res_est"]) < 1e-10 * np.linalg.norm(x)
+
+
+# ---------------------------------------------------------------- FEAST / IFEAST
+
+def _small_problem():
+    A = inputs.laplacian((12, 12))
+    ev = orc.laplacian_closed_form_eigs((12, 12))
+    emin, emax = 0.0, 0.5 * (ev[5] + ev[6])
+    return A, ev, emin, emax
+
+
+def test_exact_filter_step_matches_spectral_definition():
+    """Alg. 1 steps 1-2 with dense LU equal U rho(Lambda) U^T X (Eq. rhoh)."""
+    A, ev, emin, emax = _small_problem()
+    Ad = A.to_scipy().toarray()
+    z, w = orc.contour_nodes(orc.GL_HALF, 8, emin, emax)
+    X = inputs.initial_subspace(A.n, 9, 0)
+    Q_lu = orc._filtered_subspace_exact(Ad, X, z, w, True)
+    Q_sp = orc.filter_step_spectral(Ad, X, z, w, True)
+    assert np.abs(Q_lu - Q_sp).max() < 1e-11 * np.abs(Q_sp).max()
+
+
+def test_feast_exact_matches_brute_force():
+    A, ev, emin, emax = _small_problem()
+    z, w = orc.contour_nodes(orc.GL_HALF, 8, emin, emax)
+    out = orc.feast(A.to_scipy(), inputs.initial_subspace(A.n, 10, 1), emin, emax, z, w)
+    assert out["converged"]
+    lam = out["lam"][out["inside"]]
+    assert lam.size == 6
+    assert np.abs(lam - ev[:6]).max() < 1e-12
+    # spectral projector of the wanted cluster
+    Ad = A.to_scipy().toarray()
+    e, U = np.linalg.eigh(Ad)
+    P_ref = U[:, :6] @ U[:, :6].T
+    Xi = out["X"][:, out["inside"]]
+    P = Xi @ Xi.T
+    assert np.abs(P - P_ref).max() < 1e-9
+
+
+def test_ifeast_exact_inner_reproduces_feast():
+    """Solving the shifted systems to full accuracy turns Algorithm 2 into
+    Algorithm 1: compare Ritz values iterate by iterate."""
+    A, ev, emin, emax = _small_problem()
+    z, w = orc.contour_nodes(orc.GL_HALF, 6, emin, emax)
+    X0 = inputs.initial_subspace(A.n, 9, 2)
+    h1, h2 = [], []
+    orc.ifeast(A.to_scipy(), X0, emin, emax, z, w, inner="exact", max_outer=3, tol=0.0,
+               callback=lambda it, lam, X, res, ins: h1.append(lam.copy()))
+    orc.ifeast(A.to_scipy(), X0, emin, emax, z, w, inner="gmres", k=A.n, max_outer=3, tol=0.0,
+               callback=lambda it, lam, X, res, ins: h2.append(lam.copy()))
+    assert len(h1) == len(h2) == 3
+    for a, b in zip(h1, h2):
+        # wanted Ritz values (inside the interval) to 1e-10; the unwanted ones,
+        # which the filter damps, carry the rounding of the 144-step Krylov run
+        ins = (a > emin) & (a < emax)
+        assert np.abs(a[ins] - b[ins]).max() < 1e-10 * np.abs(a).max()
+        assert np.abs(a - b).max() < 1e-7 * np.abs(a).max()
+
+
+def test_rayleigh_ritz_recovers_exact_pairs():
+    A, ev, emin, emax = _small_problem()
+    Ad = A.to_scipy().toarray()
+    e, U = np.linalg.eigh(Ad)
+    g = np.random.default_rng(3)
+    Msix = g.standard_normal((6, 6))
+    Q = U[:, [0, 3, 7, 9, 20, 40]] @ Msix
+    lam, XQ = orc.rayleigh_ritz(Q, Ad @ Q)
+    assert np.abs(lam - e[[0, 3, 7, 9, 20, 40]]).max() < 1e-9  # cond(Msix) ~ 1e2
+    Bq = Q.T @ Q
+    assert np.abs(XQ.T @ Bq @ XQ - np.eye(6)).max() < 1e-10
+
+
+def test_residual_definition():
+    lam = np.array([1.0, 2.0])
+    X = np.eye(3)[:, :2]
+    AX = np.array([[1.0, 0.0], [0.0, 2.0], [0.0, 0.5]])
+    r = orc.eigen_residuals(AX, X, lam)
+    assert abs(r[0]) < 1e-16 and abs(r[1] - 0.5 / math.hypot(2.0, 0.5)) < 1e-15
+
+
+@pytest.mark.slow
+def test_ifeast_gmres10_lap2d_50_converges_to_closed_form():
+    """The 50x50 workload: 8 Gauss-Legendre half-circle nodes, m0=20, GMRES
+    fixed at 10 steps, converges to relative residual <= 1e-10 and the 10
+    eigenvalues equal the closed form to 1e-10 relative."""
+    wl = inputs.workload_lap2d_50()
+    z, w = orc.contour_nodes(orc.GL_HALF, 8, wl.emin, wl.emax)
+    out = orc.ifeast(wl.A.to_scipy(), wl.X0(), wl.emin, wl.emax, z, w, inner="gmres", k=10,
+                     alpha=0.0, tol=1e-10, max_outer=60)
+    assert out["converged"]
+    lam = out["lam"][out["inside"]]
+    ref = np.loadtxt(os.path.join(GOLDEN, "lap2d_50x50_lowest11.txt"))[:10]
+    assert lam.size == 10
+    assert np.abs(lam - ref).max() / np.abs(ref).max() < 1e-10
+    assert out["res"][out["inside"]].max() <= 1e-10
+
+
+def test_convergence_rate_bound_exact_solves():
+    """With exact solves (alpha_j = 0) Eq. (upperbound) reduces to the subspace
+    iteration rate |gamma_{m0+1}|/|gamma_j|: the error of the wanted subspace
+    (sine of the largest principal angle) shrinks at least that fast."""
+    A, ev, emin, emax = _small_problem()
+    Ad = A.to_scipy().toarray()
+    e, U = np.linalg.eigh(Ad)
+    z, w = orc.contour_nodes(orc.GL_HALF, 4, emin, emax)
+    m0 = 8
+    gam = np.sort(np.abs(orc.filter_rho(e, z, w, True)))[::-1]
+    rate = gam[m0] / gam[5]
+    errs = []
+
+    def cb(it, lam, X, res, ins):
+        Xq, _ = np.linalg.qr(X)
+        s = sla.subspace_angles(U[:, :6], Xq)
+        errs.append(np.sin(s.max()))
+
+    orc.ifeast(A.to_scipy(), inputs.initial_subspace(A.n, m0, 7), emin, emax, z, w, inner="exact",
+               max_outer=4, tol=0.0, callback=cb)
+    for a, b in zip(errs[:-1], errs[1:]):
+        if a > 1e-12:
+            assert b <= 1.5 * rate * a + 1e-13
