@@ -1,0 +1,198 @@
+/*
+ * ifeast.h -- C ABI of the GB300 (sm_103a) IFEAST hot path.
+ *
+ * IFEAST (Gavin & Polizzi, arXiv 1706.00692, Algorithm 2) finds the eigenpairs
+ * (lambda, x) of a real symmetric sparse matrix A whose eigenvalues lie in an
+ * interval (emin, emax). Each outer (subspace) iteration
+ *   1. solves the shifted systems (z_k I - A) Y_k = X for every contour node z_k
+ *      and every one of the m0 columns of X, inexactly, with a few Krylov
+ *      (GMRES) steps                                         [Alg. 2 step 1]
+ *   2. forms the filtered subspace Q = sum_k w_k Y_k         [Alg. 2 step 2]
+ *   3. Rayleigh-Ritz: A_Q X_Q = B_Q X_Q Lambda, A_Q = Q^T A Q, B_Q = Q^T Q,
+ *      X <- Q X_Q                                            [Alg. 2 step 3]
+ *   4. stops once the largest relative residual ||A x_j - lambda_j x_j|| /
+ *      ||A x_j|| over lambda_j in (emin, emax) is <= tol    [Alg. 2 step 4]
+ * All four steps run in CUDA kernels of this library on one GPU. The host only
+ * validates arguments, launches kernels and reads back one small status record
+ * per outer iteration.
+ *
+ * Conventions
+ *   - Every function returns an ifeast_status code (0 = success) unless noted.
+ *   - Dense blocks are row-major: an n x m0 block stores row i at [i*m0, i*m0+m0).
+ *   - CSR: rowptr int32[n+1] (rowptr[0] = 0, non-decreasing), colidx int32[nnz]
+ *     in [0, n), val float64[nnz]. Pointers in ifeast_csr are HOST pointers;
+ *     ifeast_create copies the matrix to device memory owned by the handle, so
+ *     the caller may free its arrays when ifeast_create returns.
+ *   - "stream" arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).
+ *   - A handle is not thread-safe; distinct handles may run on distinct streams.
+ */
+#ifndef IFEAST_H
+#define IFEAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IFEAST_OK = 0,
+  IFEAST_ERR_INVALID_ARG = 1,    /* bad CSR, m0 <= 0, emin >= emax, nc < 1, ...   */
+  IFEAST_ERR_OOM = 2,            /* workspace larger than given / device memory  */
+  IFEAST_ERR_CUDA = 3,           /* a CUDA runtime call failed                   */
+  IFEAST_ERR_NOT_CONVERGED = 4,  /* max_outer reached; best pairs retrievable    */
+  IFEAST_ERR_M0_TOO_SMALL = 5,   /* m0 Ritz values inside the interval: m0 <= m  */
+  IFEAST_STATUS_NO_EIGENVALUES = 6, /* no Ritz value inside the interval         */
+  IFEAST_ERR_BREAKDOWN = 7,      /* B_Q not positive definite even after a shift */
+  IFEAST_ERR_TIMEOUT = 8,        /* a bounded device-side wait ran out           */
+  IFEAST_ERR_STATE = 9,          /* call out of order (e.g. eigenpairs before solve) */
+  IFEAST_ERR_UNSUPPORTED = 10    /* option combination not built                 */
+} ifeast_status;
+
+/* Quadrature rules on the circle centred at c = (emin+emax)/2 with radius
+ * r = (emax-emin)/2 (Eq. contour_int_quad; half-contour symmetry of Sec. 4.1):
+ *   GL_HALF   nc Gauss-Legendre nodes on the upper half circle, filter taken
+ *             as 2 Re of the upper-half sum (real symmetric A only)
+ *   TRAP_HALF nc trapezoid nodes theta_j = pi (j-1/2)/nc on the upper half
+ *   TRAP_FULL nc trapezoid nodes theta_j = 2 pi (j-1/2)/nc on the full circle
+ *             (needs complex Q; reserved for the non-Hermitian extension)   */
+typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } ifeast_rule;
+
+/* Inner solver for Alg. 2 step 1.
+ *   GMRES:  one complex GMRES per (node, column) pair, zero initial guess,
+ *           classical Gram-Schmidt applied twice, Givens least squares
+ *           (Sec. 2.2). inner_max_iters <= 32.                               */
+typedef enum { IFEAST_INNER_GMRES = 0 } ifeast_inner;
+
+/* Arithmetic of the inner solve (Krylov vectors and their products). The
+ * reduced eigenproblem, Rayleigh-Ritz products and residual check are FP64. */
+typedef enum { IFEAST_FP64 = 0 } ifeast_precision;
+
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  const double *val;
+} ifeast_csr;
+
+typedef struct {
+  int rule;       /* ifeast_rule                        */
+  int nc;         /* number of nodes (upper half for *_HALF rules) */
+  double emin;    /* interval (emin, emax), open         */
+  double emax;
+} ifeast_contour;
+
+typedef struct {
+  int inner_solver;     /* ifeast_inner                                         */
+  int inner_max_iters;  /* k: Krylov steps per shifted system                   */
+  double alpha;         /* > 0: stop a shifted solve once ||x_j - (z_k I - A) y||
+                           <= alpha * ||R_F|| * ||x_j|| (Alg. 2 step 1; ||R_F||=1
+                           before the first iteration); <= 0: always k steps      */
+  int max_outer;        /* outer iteration cap (default 100)                     */
+  double tol;           /* stop when ||R_F|| <= tol (default 1e-10)              */
+  int precision;        /* ifeast_precision                                      */
+} ifeast_opts;
+
+typedef struct {
+  int outer_iters;            /* outer iterations run by the last solve        */
+  int found;                  /* Ritz values inside (emin, emax)               */
+  double RF;                  /* last ||R_F|| (max relative residual inside)   */
+  int64_t total_matvecs;      /* sum over iterations of all (node, column) Krylov steps */
+  int64_t seq_matvecs;        /* sum over iterations of the max steps of any (node, column) */
+  int max_inner;              /* largest per-(node, column) step count seen    */
+  int shifted_cholesky;       /* times B_Q needed the diagonal shift           */
+  double solve_ms;            /* wall time of the last ifeast_solve (host clock) */
+} ifeast_stats;
+
+/* Fills *o with the defaults: GMRES, k = 10, alpha = 0 (fixed k), max_outer =
+ * 100, tol = 1e-10, FP64. */
+void ifeast_default_opts(ifeast_opts *o);
+
+/* Contour nodes and weights (Eq. contour_int_quad with the rules above) on the
+ * host: zw[4*k + {0,1,2,3}] = {Re z_k, Im z_k, Re w_k, Im w_k}, k < c->nc. For
+ * *_HALF rules the weights already include the factor 2 of the conjugate
+ * lower half, so the filter is rho(lambda) = Re sum_k w_k / (z_k - lambda). */
+int ifeast_contour_nodes(const ifeast_contour *c, double *zw);
+
+/* Device bytes a handle needs for (n, nnz, m0, contour, opts). */
+int ifeast_workspace_bytes(int64_t n, int64_t nnz, int m0, const ifeast_contour *c,
+                           const ifeast_opts *o, size_t *bytes);
+
+typedef struct ifeast_ctx *ifeast_t;
+
+/* Validates A (square, rowptr[0] = 0, non-decreasing rowptr, rowptr[n] = nnz,
+ * colidx in range), computes the contour on the host, lays out the workspace
+ * and copies A into it.
+ *   B          must be NULL (standard problem B = I); otherwise UNSUPPORTED.
+ *   workspace  device buffer of ws_bytes >= ifeast_workspace_bytes(...) that
+ *              the caller keeps alive until ifeast_destroy; NULL makes the
+ *              library cudaMalloc (and later cudaFree) its own.
+ *   stream     cudaStream_t (as void*) for every later call on this handle.
+ * On error *out is NULL and nothing stays allocated. */
+int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour *c, int m0,
+                  const ifeast_opts *o, void *workspace, size_t ws_bytes, void *stream,
+                  ifeast_t *out);
+
+/* Runs Algorithm 2 from the initial subspace X0 (n x m0, row-major float64;
+ * x0_on_device != 0: device pointer, else host pointer, copied in). Returns
+ * OK on convergence, NOT_CONVERGED after max_outer iterations (the last
+ * iterate is kept), M0_TOO_SMALL if all m0 Ritz values fall inside the
+ * interval, NO_EIGENVALUES if none does, BREAKDOWN if B_Q cannot be factored.
+ * Blocks the calling host thread until the solve ends. */
+int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device);
+
+/* Copies the Ritz pairs with lambda inside (emin, emax), ascending:
+ * evals[m], evecs (n x cap row-major: column j of the block is the j-th pair,
+ * row i at evecs[i*cap + j]), resid[m] relative residuals. Any output pointer
+ * may be NULL. *m_found gets the number inside (may exceed cap; then only the
+ * first cap are copied). out_on_device != 0: outputs are device pointers. */
+int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *evecs,
+                      double *resid, int out_on_device);
+
+/* All m0 Ritz values of the last iterate (ascending) and their residuals;
+ * device or host pointers as flagged. */
+int ifeast_ritz_all(ifeast_t h, double *lam, double *resid, int out_on_device);
+
+int ifeast_get_stats(ifeast_t h, ifeast_stats *s);
+
+/* Human-readable name of a status code (static storage). */
+const char *ifeast_strerror(int code);
+
+/* Frees every device buffer the handle allocated; NULL is allowed. */
+void ifeast_destroy(ifeast_t h);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points. Each runs one step of the outer iteration on the
+ * handle's stream with the handle's matrix and options, on caller-owned DEVICE
+ * buffers, and returns after the work is enqueued and has finished (the
+ * stream is synchronised). They are the same kernels ifeast_solve launches.
+ * ------------------------------------------------------------------------- */
+
+/* Alg. 2 steps 1-2: Q = Re sum_k w_k Y_k with (z_k I - A) Y_k ~= X solved by the
+ * configured inner solver, using tolerance alpha * RF (RF >= 0 given here).
+ * X, Q: n x m0 float64 device. steps (optional, device int32[nc*m0], column
+ * c = k*m0 + j) receives the Krylov steps taken by each (node, column). */
+int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32_t *steps);
+
+/* Alg. 2 steps 3-4 on a given Q (n x m0 float64 device): Rayleigh-Ritz with
+ * B_Q = Q^T Q, A_Q = Q^T A Q, then X = Q X_Q (n x m0 device, B-orthonormal
+ * Ritz vectors), lam[m0] ascending, resid[m0] relative residuals (device).
+ * Returns BREAKDOWN if B_Q cannot be factored. */
+int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, double *resid);
+
+/* One sparse product with a per-column complex shift (the operator of Alg. 2
+ * step 1): W[:, c] = z[c / m0] V[:, c] - A V[:, c] for c < ncols, where V and W
+ * are n x ncols complex float64 blocks (row-major, real and imaginary parts
+ * interleaved: element (i, c) at [2*(i*ncols + c)]), z holds nc = ncols / m0
+ * complex values interleaved (device). Uses the handle's A. ncols must be a
+ * multiple of m0 with ncols / m0 <= 64. */
+int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0,
+                      const double *z);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,15 @@
+"""GB300 (sm_103a) implementation of the IFEAST hot path (Gavin & Polizzi,
+arXiv 1706.00692): batched inexact shifted solves, quadrature and
+Rayleigh-Ritz in hand-written CUDA kernels behind the C ABI of
+include/ifeast.h.
+
+    from paper_1706_00692_gb300 import Solver, inputs
+"""
+from . import inputs  # noqa: F401  (seeded synthetic workloads; no solver arithmetic)
+
+
+def __getattr__(name):
+    if name in ("Solver", "IFEASTError", "contour_nodes"):
+        from . import solver
+        return getattr(solver, name)
+    raise AttributeError(name)

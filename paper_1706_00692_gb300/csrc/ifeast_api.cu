@@ -1,0 +1,620 @@
+// Host side of libifeast: argument validation, contour quadrature, workspace
+// layout, the outer iteration of Algorithm 2 and the C ABI of ifeast.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ifeast;
+
+struct ifeast_ctx {
+  int64_t n = 0, nnz = 0;
+  int m0 = 0, nc = 0, C = 0, K = 0;
+  ifeast_opts opts{};
+  ifeast_contour contour{};
+  std::vector<double2> zh, wh;  // host copies of nodes and weights
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  RowTiling tl{};
+  int Pg = 0, Pr = 0;
+  // workspace
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = false;
+  // device buffers (carved from ws)
+  int32_t *rowptr = nullptr, *colidx = nullptr;
+  double *val = nullptr;
+  double2 *z = nullptr, *w = nullptr;
+  double2 *V = nullptr, *W = nullptr, *part = nullptr, *H1 = nullptr, *H2 = nullptr;
+  double *inv_h = nullptr;
+  double2 *CS = nullptr, *SN = nullptr, *R = nullptr, *G = nullptr, *Y = nullptr;
+  int *steps = nullptr, *done = nullptr;
+  double *X = nullptr, *Q = nullptr, *AQ = nullptr, *beta = nullptr;
+  double *gram_part = nullptr, *Aq = nullptr, *Bq = nullptr, *L = nullptr, *Cm = nullptr,
+         *U = nullptr, *XQ = nullptr, *lam = nullptr, *res_part = nullptr, *res = nullptr;
+  DevStatus *status = nullptr;
+  DevStatus *status_host = nullptr;  // pinned
+  // results
+  bool solved = false;
+  ifeast_stats stats{};
+};
+
+namespace {
+
+struct Layout {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    off = (off + 255) / 256 * 256;
+    const size_t o = off;
+    off += count * sizeof(T);
+    return o;
+  }
+};
+
+struct Offsets {
+  size_t rowptr, colidx, val, z, w, V, W, part, H1, H2, inv_h, CS, SN, R, G, Y, steps, done, X, Q,
+      AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
+};
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 152;
+  return sms > 0 ? sms : 152;
+}
+
+Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr) {
+  Layout L;
+  Offsets o{};
+  const size_t C = (size_t)nc * m0;
+  const size_t mp = (size_t)(m0 + 3) / 4 * 4;
+  o.rowptr = L.take<int32_t>(n + 1);
+  o.colidx = L.take<int32_t>(nnz > 0 ? nnz : 1);
+  o.val = L.take<double>(nnz > 0 ? nnz : 1);
+  o.z = L.take<double2>(nc);
+  o.w = L.take<double2>(nc);
+  o.V = L.take<double2>((size_t)(K + 1) * n * C);
+  o.W = L.take<double2>((size_t)n * C);
+  o.part = L.take<double2>((size_t)tl.P * (K + 2) * C);
+  o.H1 = L.take<double2>((size_t)(K + 2) * C);
+  o.H2 = L.take<double2>((size_t)(K + 2) * C);
+  o.inv_h = L.take<double>(C);
+  o.CS = L.take<double2>((size_t)K * C);
+  o.SN = L.take<double2>((size_t)K * C);
+  o.R = L.take<double2>((size_t)K * K * C);
+  o.G = L.take<double2>((size_t)(K + 1) * C);
+  o.Y = L.take<double2>((size_t)K * C);
+  o.steps = L.take<int>(C);
+  o.done = L.take<int>(C);
+  o.X = L.take<double>((size_t)n * m0);
+  o.Q = L.take<double>((size_t)n * m0);
+  o.AQ = L.take<double>((size_t)n * m0);
+  o.beta = L.take<double>(m0);
+  o.gram_part = L.take<double>((size_t)Pg * 2 * mp * mp);
+  o.Aq = L.take<double>((size_t)m0 * m0);
+  o.Bq = L.take<double>((size_t)m0 * m0);
+  o.L = L.take<double>((size_t)m0 * m0);
+  o.Cm = L.take<double>((size_t)m0 * m0);
+  o.U = L.take<double>((size_t)m0 * m0);
+  o.XQ = L.take<double>((size_t)m0 * m0);
+  o.lam = L.take<double>(m0);
+  o.res_part = L.take<double>((size_t)Pr * 3 * m0);
+  o.res = L.take<double>(m0);
+  o.status = L.take<DevStatus>(1);
+  o.total = (L.off + 255) / 256 * 256;
+  return o;
+}
+
+int validate_contour(const ifeast_contour *c) {
+  if (!c) return IFEAST_ERR_INVALID_ARG;
+  if (c->nc < 1 || c->nc > kMaxNodes) return IFEAST_ERR_INVALID_ARG;
+  if (!(c->emin < c->emax) || !std::isfinite(c->emin) || !std::isfinite(c->emax))
+    return IFEAST_ERR_INVALID_ARG;
+  if (c->rule == IFEAST_TRAP_FULL) return IFEAST_ERR_UNSUPPORTED;
+  if (c->rule != IFEAST_GL_HALF && c->rule != IFEAST_TRAP_HALF) return IFEAST_ERR_INVALID_ARG;
+  return IFEAST_OK;
+}
+
+int validate_opts(const ifeast_opts *o) {
+  if (!o) return IFEAST_ERR_INVALID_ARG;
+  if (o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
+  if (o->precision != IFEAST_FP64) return IFEAST_ERR_UNSUPPORTED;
+  if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxInner) return IFEAST_ERR_INVALID_ARG;
+  if (o->max_outer < 1 || !(o->tol >= 0.0) || !std::isfinite(o->alpha))
+    return IFEAST_ERR_INVALID_ARG;
+  return IFEAST_OK;
+}
+
+// Gauss-Legendre nodes/weights on (-1, 1) by Newton iteration on P_n (Golub &
+// Welsch would also do; Newton from the Chebyshev-like initial guess
+// cos(pi (i - 1/4)/(n + 1/2)) converges to machine precision in a few steps).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &wgt) {
+  x.assign(n, 0.0);
+  wgt.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pn = (n == 1) ? t : p1;
+      const double pnm1 = (n == 1) ? 1.0 : p0;
+      dp = n * (t * pn - pnm1) / (t * t - 1.0);
+      const double dt = pn / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    // recompute derivative at the converged point
+    double p0 = 1.0, p1 = t;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    const double pn = (n == 1) ? t : p1;
+    const double pnm1 = (n == 1) ? 1.0 : p0;
+    dp = n * (t * pn - pnm1) / (t * t - 1.0);
+    x[i] = t;
+    wgt[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+  // ascending nodes
+  std::reverse(x.begin(), x.end());
+  std::reverse(wgt.begin(), wgt.end());
+}
+
+void contour_host(const ifeast_contour *c, std::vector<double2> &z, std::vector<double2> &w) {
+  const double ctr = 0.5 * (c->emin + c->emax), r = 0.5 * (c->emax - c->emin);
+  z.resize(c->nc);
+  w.resize(c->nc);
+  if (c->rule == IFEAST_GL_HALF) {
+    std::vector<double> x, g;
+    gauss_legendre(c->nc, x, g);
+    for (int k = 0; k < c->nc; ++k) {
+      const double th = 0.5 * M_PI * (1.0 - x[k]);
+      z[k] = make_double2(ctr + r * std::cos(th), r * std::sin(th));
+      w[k] = make_double2(0.5 * g[k] * r * std::cos(th), 0.5 * g[k] * r * std::sin(th));
+    }
+  } else {
+    const double full = (c->rule == IFEAST_TRAP_FULL) ? 2.0 : 1.0;
+    for (int k = 0; k < c->nc; ++k) {
+      const double th = full * M_PI * (k + 0.5) / c->nc;
+      z[k] = make_double2(ctr + r * std::cos(th), r * std::sin(th));
+      w[k] = make_double2(r * std::cos(th) / c->nc, r * std::sin(th) / c->nc);
+    }
+  }
+}
+
+std::mutex g_init_mu;
+bool g_init_done[64] = {false};
+
+int ensure_device_init() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IFEAST_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (dev >= 0 && dev < 64 && !g_init_done[dev]) {
+    if (rr_init() != cudaSuccess) return IFEAST_ERR_CUDA;
+    g_init_done[dev] = true;
+  }
+  return IFEAST_OK;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    if ((call) != cudaSuccess) {                  \
+      return IFEAST_ERR_CUDA;                     \
+    }                                             \
+  } while (0)
+
+GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q) {
+  GmresArgs a{};
+  a.n = (int)h->n;
+  a.m0 = h->m0;
+  a.nc = h->nc;
+  a.C = h->C;
+  a.K = h->K;
+  a.rowptr = h->rowptr;
+  a.colidx = h->colidx;
+  a.val = h->val;
+  a.z = h->z;
+  a.w = h->w;
+  a.X = X;
+  a.V = h->V;
+  a.W = h->W;
+  a.part = h->part;
+  a.H1 = h->H1;
+  a.H2 = h->H2;
+  a.inv_h = h->inv_h;
+  a.CS = h->CS;
+  a.SN = h->SN;
+  a.R = h->R;
+  a.G = h->G;
+  a.Y = h->Y;
+  a.beta = h->beta;
+  a.steps = h->steps;
+  a.done = h->done;
+  a.Q = Q;
+  a.status = h->status;
+  a.tl = h->tl;
+  return a;
+}
+
+RRArgs rr_args(ifeast_ctx *h, const double *Q, double *X) {
+  RRArgs a{};
+  a.n = (int)h->n;
+  a.m0 = h->m0;
+  a.rowptr = h->rowptr;
+  a.colidx = h->colidx;
+  a.val = h->val;
+  a.Q = Q;
+  a.AQ = h->AQ;
+  a.gram_part = h->gram_part;
+  a.Pg = h->Pg;
+  a.Aq = h->Aq;
+  a.Bq = h->Bq;
+  a.L = h->L;
+  a.Cm = h->Cm;
+  a.U = h->U;
+  a.XQ = h->XQ;
+  a.lam = h->lam;
+  a.X = X;
+  a.res_part = h->res_part;
+  a.Pr = h->Pr;
+  a.res = h->res;
+  a.beta = h->beta;
+  a.emin = h->contour.emin;
+  a.emax = h->contour.emax;
+  a.alpha = h->opts.alpha;
+  a.status = h->status;
+  return a;
+}
+
+int set_tolerance(ifeast_ctx *h, double RF) {
+  // status->tol_rel = alpha * RF; step counters cleared
+  DevStatus s{};
+  s.RF = RF;
+  s.tol_rel = h->opts.alpha > 0.0 ? h->opts.alpha * RF : 0.0;
+  *h->status_host = s;
+  CK(cudaMemcpyAsync(h->status, h->status_host, sizeof(DevStatus), cudaMemcpyHostToDevice,
+                     h->stream));
+  return IFEAST_OK;
+}
+
+int clear_step_counters(ifeast_ctx *h) {
+  CK(cudaMemsetAsync(&h->status->max_steps, 0, sizeof(int), h->stream));
+  CK(cudaMemsetAsync(&h->status->total_steps, 0, sizeof(long long), h->stream));
+  return IFEAST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ifeast_default_opts(ifeast_opts *o) {
+  if (!o) return;
+  o->inner_solver = IFEAST_INNER_GMRES;
+  o->inner_max_iters = 10;
+  o->alpha = 0.0;
+  o->max_outer = 100;
+  o->tol = 1e-10;
+  o->precision = IFEAST_FP64;
+}
+
+const char *ifeast_strerror(int code) {
+  switch (code) {
+    case IFEAST_OK: return "ok";
+    case IFEAST_ERR_INVALID_ARG: return "invalid argument";
+    case IFEAST_ERR_OOM: return "out of memory (workspace too small or device allocation failed)";
+    case IFEAST_ERR_CUDA: return "CUDA runtime error";
+    case IFEAST_ERR_NOT_CONVERGED: return "not converged within max_outer iterations";
+    case IFEAST_ERR_M0_TOO_SMALL: return "subspace size m0 too small for the interval";
+    case IFEAST_STATUS_NO_EIGENVALUES: return "no eigenvalue found in the interval";
+    case IFEAST_ERR_BREAKDOWN: return "reduced Gram matrix B_Q not positive definite";
+    case IFEAST_ERR_TIMEOUT: return "bounded device wait timed out";
+    case IFEAST_ERR_STATE: return "call out of order";
+    case IFEAST_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+int ifeast_contour_nodes(const ifeast_contour *c, double *zw) {
+  if (!c || !zw) return IFEAST_ERR_INVALID_ARG;
+  if (c->nc < 1 || c->nc > kMaxNodes || !(c->emin < c->emax)) return IFEAST_ERR_INVALID_ARG;
+  if (c->rule != IFEAST_GL_HALF && c->rule != IFEAST_TRAP_HALF && c->rule != IFEAST_TRAP_FULL)
+    return IFEAST_ERR_INVALID_ARG;
+  std::vector<double2> z, w;
+  contour_host(c, z, w);
+  for (int k = 0; k < c->nc; ++k) {
+    zw[4 * k + 0] = z[k].x;
+    zw[4 * k + 1] = z[k].y;
+    zw[4 * k + 2] = w[k].x;
+    zw[4 * k + 3] = w[k].y;
+  }
+  return IFEAST_OK;
+}
+
+int ifeast_workspace_bytes(int64_t n, int64_t nnz, int m0, const ifeast_contour *c,
+                           const ifeast_opts *o, size_t *bytes) {
+  if (!bytes || n < 1 || nnz < 0 || m0 < 1 || m0 > kMaxM0 || m0 > n) return IFEAST_ERR_INVALID_ARG;
+  if (n > (int64_t)INT32_MAX - 1 || nnz > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
+  int rc = validate_contour(c);
+  if (rc) return rc;
+  rc = validate_opts(o);
+  if (rc) return rc;
+  const int sms = device_sms();
+  const RowTiling tl = make_tiling(n, c->nc * m0, sms);
+  const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
+  const int Pr = Pg;
+  *bytes = plan(n, nnz, m0, c->nc, o->inner_max_iters, tl, Pg, Pr).total;
+  return IFEAST_OK;
+}
+
+int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour *c, int m0,
+                  const ifeast_opts *o, void *workspace, size_t ws_bytes, void *stream,
+                  ifeast_t *out) {
+  if (!out) return IFEAST_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (B) return IFEAST_ERR_UNSUPPORTED;
+  if (!A || !A->rowptr || (A->nnz > 0 && (!A->colidx || !A->val))) return IFEAST_ERR_INVALID_ARG;
+  const int64_t n = A->n, nnz = A->nnz;
+  if (n < 1 || nnz < 0) return IFEAST_ERR_INVALID_ARG;
+  size_t need = 0;
+  int rc = ifeast_workspace_bytes(n, nnz, m0, c, o, &need);
+  if (rc) return rc;
+  // CSR structure checks on the host
+  if (A->rowptr[0] != 0 || A->rowptr[n] != nnz) return IFEAST_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (A->rowptr[i + 1] < A->rowptr[i]) return IFEAST_ERR_INVALID_ARG;
+  for (int64_t p = 0; p < nnz; ++p)
+    if (A->colidx[p] < 0 || A->colidx[p] >= n || !std::isfinite(A->val[p]))
+      return IFEAST_ERR_INVALID_ARG;
+  if (workspace && ws_bytes < need) return IFEAST_ERR_OOM;
+  rc = ensure_device_init();
+  if (rc) return rc;
+
+  ifeast_ctx *h = new (std::nothrow) ifeast_ctx();
+  if (!h) return IFEAST_ERR_OOM;
+  h->n = n;
+  h->nnz = nnz;
+  h->m0 = m0;
+  h->nc = c->nc;
+  h->C = c->nc * m0;
+  h->K = o->inner_max_iters;
+  h->opts = *o;
+  h->contour = *c;
+  h->stream = (cudaStream_t)stream;
+  h->num_sms = device_sms();
+  h->tl = make_tiling(n, h->C, h->num_sms);
+  h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
+  h->Pr = h->Pg;
+  contour_host(c, h->zh, h->wh);
+  const Offsets off = plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr);
+  if (workspace) {
+    h->ws = (char *)workspace;
+    h->ws_bytes = ws_bytes;
+  } else {
+    if (cudaMalloc(&h->ws, off.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return IFEAST_ERR_OOM;
+    }
+    h->owns_ws = true;
+    h->ws_bytes = off.total;
+  }
+  if (cudaMallocHost(&h->status_host, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->owns_ws) cudaFree(h->ws);
+    delete h;
+    return IFEAST_ERR_OOM;
+  }
+  char *b = h->ws;
+  h->rowptr = (int32_t *)(b + off.rowptr);
+  h->colidx = (int32_t *)(b + off.colidx);
+  h->val = (double *)(b + off.val);
+  h->z = (double2 *)(b + off.z);
+  h->w = (double2 *)(b + off.w);
+  h->V = (double2 *)(b + off.V);
+  h->W = (double2 *)(b + off.W);
+  h->part = (double2 *)(b + off.part);
+  h->H1 = (double2 *)(b + off.H1);
+  h->H2 = (double2 *)(b + off.H2);
+  h->inv_h = (double *)(b + off.inv_h);
+  h->CS = (double2 *)(b + off.CS);
+  h->SN = (double2 *)(b + off.SN);
+  h->R = (double2 *)(b + off.R);
+  h->G = (double2 *)(b + off.G);
+  h->Y = (double2 *)(b + off.Y);
+  h->steps = (int *)(b + off.steps);
+  h->done = (int *)(b + off.done);
+  h->X = (double *)(b + off.X);
+  h->Q = (double *)(b + off.Q);
+  h->AQ = (double *)(b + off.AQ);
+  h->beta = (double *)(b + off.beta);
+  h->gram_part = (double *)(b + off.gram_part);
+  h->Aq = (double *)(b + off.Aq);
+  h->Bq = (double *)(b + off.Bq);
+  h->L = (double *)(b + off.L);
+  h->Cm = (double *)(b + off.Cm);
+  h->U = (double *)(b + off.U);
+  h->XQ = (double *)(b + off.XQ);
+  h->lam = (double *)(b + off.lam);
+  h->res_part = (double *)(b + off.res_part);
+  h->res = (double *)(b + off.res);
+  h->status = (DevStatus *)(b + off.status);
+  bool ok = cudaMemcpyAsync(h->rowptr, A->rowptr, (n + 1) * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+  if (nnz > 0) {
+    ok = ok && cudaMemcpyAsync(h->colidx, A->colidx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               h->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(h->val, A->val, nnz * sizeof(double), cudaMemcpyHostToDevice,
+                               h->stream) == cudaSuccess;
+  }
+  ok = ok && cudaMemcpyAsync(h->z, h->zh.data(), h->nc * sizeof(double2), cudaMemcpyHostToDevice,
+                             h->stream) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->w, h->wh.data(), h->nc * sizeof(double2), cudaMemcpyHostToDevice,
+                             h->stream) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ifeast_destroy(h);
+    return IFEAST_ERR_CUDA;
+  }
+  *out = h;
+  return IFEAST_OK;
+}
+
+void ifeast_destroy(ifeast_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->owns_ws && h->ws) cudaFree(h->ws);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  delete h;
+}
+
+int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
+  if (!h || !X0) return IFEAST_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  h->solved = false;
+  h->stats = ifeast_stats{};
+  const size_t xbytes = (size_t)h->n * h->m0 * sizeof(double);
+  CK(cudaMemcpyAsync(h->X, X0, xbytes,
+                     x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  CK(column_norms((int)h->n, h->m0, h->X, h->res_part, h->Pr, h->beta, h->stream));
+  int rc = set_tolerance(h, 1.0);
+  if (rc) return rc;
+  int result = IFEAST_ERR_NOT_CONVERGED;
+  for (int it = 1; it <= h->opts.max_outer; ++it) {
+    rc = clear_step_counters(h);
+    if (rc) return rc;
+    CK(gmres_filter(gmres_args(h, h->X, h->Q), h->stream));
+    CK(rayleigh_ritz(rr_args(h, h->Q, h->X), h->stream));
+    CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const DevStatus s = *h->status_host;
+    h->stats.outer_iters = it;
+    h->stats.found = s.count;
+    h->stats.RF = s.RF;
+    h->stats.total_matvecs += s.total_steps;
+    h->stats.seq_matvecs += s.max_steps;
+    h->stats.max_inner = std::max(h->stats.max_inner, s.max_steps);
+    h->stats.shifted_cholesky += s.shifted;
+    h->solved = true;
+    if (s.breakdown) {
+      result = IFEAST_ERR_BREAKDOWN;
+      h->solved = false;
+      break;
+    }
+    if (s.count > 0 && s.RF <= h->opts.tol) {
+      result = IFEAST_OK;
+      break;
+    }
+  }
+  if (result == IFEAST_OK || result == IFEAST_ERR_NOT_CONVERGED) {
+    if (h->stats.found >= h->m0) result = IFEAST_ERR_M0_TOO_SMALL;
+    else if (h->stats.found == 0) result = IFEAST_STATUS_NO_EIGENVALUES;
+  }
+  h->stats.solve_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return result;
+}
+
+int ifeast_get_stats(ifeast_t h, ifeast_stats *s) {
+  if (!h || !s) return IFEAST_ERR_INVALID_ARG;
+  *s = h->stats;
+  return IFEAST_OK;
+}
+
+int ifeast_ritz_all(ifeast_t h, double *lam, double *resid, int out_on_device) {
+  if (!h) return IFEAST_ERR_INVALID_ARG;
+  if (!h->solved) return IFEAST_ERR_STATE;
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (lam) CK(cudaMemcpyAsync(lam, h->lam, h->m0 * sizeof(double), kind, h->stream));
+  if (resid) CK(cudaMemcpyAsync(resid, h->res, h->m0 * sizeof(double), kind, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return IFEAST_OK;
+}
+
+int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *evecs,
+                      double *resid, int out_on_device) {
+  if (!h || cap < 0) return IFEAST_ERR_INVALID_ARG;
+  if (!h->solved) return IFEAST_ERR_STATE;
+  std::vector<double> lam(h->m0), res(h->m0);
+  CK(cudaMemcpyAsync(lam.data(), h->lam, h->m0 * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(res.data(), h->res, h->m0 * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<int> idx;
+  for (int j = 0; j < h->m0; ++j)
+    if (lam[j] > h->contour.emin && lam[j] < h->contour.emax) idx.push_back(j);
+  const int m = (int)idx.size();
+  if (m_found) *m_found = m;
+  const int cnt = std::min(m, cap);
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  std::vector<double> ev(cnt), rs(cnt);
+  for (int q = 0; q < cnt; ++q) {
+    ev[q] = lam[idx[q]];
+    rs[q] = res[idx[q]];
+  }
+  if (evals && cnt) CK(cudaMemcpy(evals, ev.data(), cnt * sizeof(double), kind));
+  if (resid && cnt) CK(cudaMemcpy(resid, rs.data(), cnt * sizeof(double), kind));
+  if (evecs && cnt) {
+    // the in-interval columns are contiguous in the ascending order: idx[0]..idx[cnt-1]
+    const cudaMemcpyKind k2 = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpy2DAsync(evecs, (size_t)cap * sizeof(double), h->X + idx[0],
+                         (size_t)h->m0 * sizeof(double), cnt * sizeof(double), (size_t)h->n, k2,
+                         h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return IFEAST_OK;
+}
+
+int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32_t *steps) {
+  if (!h || !X || !Q || !(RF >= 0.0)) return IFEAST_ERR_INVALID_ARG;
+  CK(column_norms((int)h->n, h->m0, X, h->res_part, h->Pr, h->beta, h->stream));
+  int rc = set_tolerance(h, RF);
+  if (rc) return rc;
+  CK(gmres_filter(gmres_args(h, X, Q), h->stream));
+  if (steps)
+    CK(cudaMemcpyAsync(steps, h->steps, h->C * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return IFEAST_OK;
+}
+
+int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, double *resid) {
+  if (!h || !Q || !X) return IFEAST_ERR_INVALID_ARG;
+  int rc = set_tolerance(h, 1.0);
+  if (rc) return rc;
+  CK(rayleigh_ritz(rr_args(h, Q, X), h->stream));
+  CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                     h->stream));
+  if (lam) CK(cudaMemcpyAsync(lam, h->lam, h->m0 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (resid)
+    CK(cudaMemcpyAsync(resid, h->res, h->m0 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->status_host->breakdown) return IFEAST_ERR_BREAKDOWN;
+  return IFEAST_OK;
+}
+
+int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0, const double *z) {
+  if (!h || !V || !W || !z || ncols < 1 || m0 < 1 || ncols % m0 != 0 || ncols / m0 > kMaxNodes)
+    return IFEAST_ERR_INVALID_ARG;
+  const RowTiling tl = make_tiling(h->n, ncols, h->num_sms);
+  CK(spmm_shift_only((int)h->n, h->rowptr, h->colidx, h->val, (const double2 *)V, (double2 *)W,
+                     ncols, m0, (const double2 *)z, tl, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return IFEAST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal declarations shared by the CUDA translation units of libifeast.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/ifeast.h"
+
+namespace ifeast {
+
+constexpr int kThreads = 256;       // threads per block of the row-tiled kernels
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxInner = 32;       // per-node GMRES basis cap (register-held dots)
+constexpr int kMaxNodes = 64;
+constexpr int kMaxM0 = 256;         // reduced problem solved in one CTA
+
+// Device-side record read back by the host once per outer iteration.
+struct DevStatus {
+  double RF;            // max relative residual over Ritz values inside the interval
+  double tol_rel;       // alpha * RF for the next inner solve (0: fixed-k)
+  int count;            // Ritz values inside (emin, emax)
+  int breakdown;        // reduced eigensolver: 1 = B_Q not factorable
+  int shifted;          // reduced eigensolver: 1 = B_Q needed the diagonal shift
+  int max_steps;        // max Krylov steps over (node, column) in the last filter
+  long long total_steps;// sum of Krylov steps over (node, column) in the last filter
+  int nonfinite;        // a NaN/Inf was seen in the residuals
+  int pad;
+};
+
+// Row-tiled launch geometry for n x C blocks: grid (P, tiles), warp w of a
+// block handles rows r0 + w, r0 + w + kWarps, ... of its chunk of rows.
+struct RowTiling {
+  int P;            // row chunks
+  int rows;         // rows per chunk
+  int tiles;        // 32-column tiles
+};
+RowTiling make_tiling(int64_t n, int ncols, int num_sms);
+
+// ---- inner solve (per-node complex GMRES, FP64) ---------------------------
+struct GmresArgs {
+  int n, m0, nc, C, K;
+  const int32_t *rowptr, *colidx;
+  const double *val;
+  const double2 *z;         // [nc]
+  const double2 *w;         // [nc] quadrature weights
+  const double *X;          // n x m0 right-hand sides (real)
+  double2 *V;               // (K+1) x n x C basis
+  double2 *W;               // n x C work vector
+  double2 *part;            // P x (K+2) x C block partials
+  double2 *H1;              // (K+1) x C first-pass coefficients of the current step
+  double2 *H2;              // (K+1) x C second-pass coefficients of the current step
+  double *inv_h;            // C     1 / h_{s+1,s}
+  double2 *CS, *SN;         // K x C Givens rotations
+  double2 *R;               // K x K x C triangular factor, R[(l*K + s)*C + c]
+  double2 *G;               // (K+1) x C rotated right-hand side
+  double2 *Y;               // K x C w_k-scaled least-squares solutions
+  double *beta;             // m0 column norms of X
+  int *steps;               // C   Krylov steps taken
+  int *done;                // C   column finished (tolerance met or breakdown)
+  double *Q;                // n x m0 output
+  DevStatus *status;        // tol_rel read from here, step counts written here
+  RowTiling tl;
+};
+cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st);
+cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
+                            const double *val, const double2 *V, double2 *W, int ncols,
+                            int m0, const double2 *z, RowTiling tl, cudaStream_t st);
+
+// ---- Rayleigh-Ritz and residual -------------------------------------------
+struct RRArgs {
+  int n, m0;
+  const int32_t *rowptr, *colidx;
+  const double *val;
+  const double *Q;          // n x m0
+  double *AQ;               // n x m0
+  double *gram_part;        // Pg x 2 x m0p x m0p
+  int Pg;
+  double *Aq, *Bq;          // m0 x m0
+  double *L;                // m0 x m0 scratch (Cholesky factor)
+  double *Cm;               // m0 x m0 scratch (reduced standard matrix / Jacobi)
+  double *U;                // m0 x m0 scratch (Jacobi eigenvectors)
+  double *XQ;               // m0 x m0 B_Q-orthonormal eigenvectors
+  double *lam;              // m0 ascending
+  double *X;                // n x m0 new subspace
+  double *res_part;         // Pr x 3 x m0
+  int Pr;
+  double *res;              // m0
+  double *beta;             // m0 norms of the new X columns
+  double emin, emax, alpha;
+  DevStatus *status;
+};
+cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
+cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st);
+cudaError_t column_norms(int n, int m0, const double *X, double *part, int Pr, double *beta,
+                         cudaStream_t st);
+
+}  // namespace ifeast

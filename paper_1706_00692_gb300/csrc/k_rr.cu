@@ -1,0 +1,560 @@
+// Rayleigh-Ritz and residual check of IFEAST (Algorithm 2, steps 3-4), FP64.
+//   spmm_real      AQ = A Q                                   (n x m0)
+//   gram           block partials of A_Q = Q^T AQ, B_Q = Q^T Q (upper triangles,
+//                  4x4 register tiles over a shared-memory chunk of rows)
+//   reduce_gram    fixed-order sum of the partials, mirrored to full matrices
+//   reduced_eig    one CTA: B_Q = L L^T (shifted on breakdown), C = L^-1 A_Q L^-T,
+//                  cyclic Jacobi C = U diag(lam) U^T, X_Q = L^-T U, ascending sort
+//   update_resid   X = Q X_Q, AX = AQ X_Q (AX never stored) and block partials
+//                  of ||AX_j - lam_j X_j||^2, ||AX_j||^2, ||X_j||^2
+//   reduce_resid   residuals, interval count, ||R_F||, next inner tolerance
+#include <cfloat>
+
+#include "internal.h"
+
+namespace ifeast {
+
+namespace {
+
+constexpr int kGramRows = 32;  // rows of Q / AQ staged in shared memory at a time
+
+// AQ = A Q: warp per row, lane per column (32-column tiles).
+__global__ void __launch_bounds__(kThreads)
+k_spmm_real(int n, int m, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+            const double *__restrict__ val, const double *__restrict__ Q, double *__restrict__ AQ,
+            int rows) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.y * 32 + lane;
+  if (j >= m) return;
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(n, r0 + rows);
+  for (int r = r0 + warp; r < r1; r += kWarps) {
+    double acc = 0.0;
+    const int jb = rowptr[r], je = rowptr[r + 1];
+#pragma unroll 4
+    for (int p = jb; p < je; ++p) acc = fma(val[p], Q[(size_t)colidx[p] * m + j], acc);
+    AQ[(size_t)r * m + j] = acc;
+  }
+}
+
+// Partials of Q^T AQ and Q^T Q over this block's rows. Thread t of block
+// (bx, by) owns the 4x4 output tile number by*256 + t of the upper triangle
+// of tiles (m0 padded to mp = multiple of 4).
+__global__ void __launch_bounds__(kThreads)
+k_gram(int n, int m, int mp, const double *__restrict__ Q, const double *__restrict__ AQ,
+       double *__restrict__ part, int rows) {
+  extern __shared__ double sm[];
+  double *Qs = sm;                       // kGramRows x mp
+  double *As = sm + kGramRows * mp;      // kGramRows x mp
+  const int nt = mp / 4;
+  const int ntiles = nt * (nt + 1) / 2;
+  const int tile = blockIdx.y * kThreads + threadIdx.x;
+  int ti = 0, tj = 0;
+  const bool own = tile < ntiles;
+  if (own) {  // tile -> (ti, tj), ti <= tj, row-major over the upper triangle
+    int t = tile, r = 0;
+    while (t >= nt - r) {
+      t -= nt - r;
+      ++r;
+    }
+    ti = r;
+    tj = r + t;
+  }
+  double a[4][4], b[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[p][q] = b[p][q] = 0.0;
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(n, r0 + rows);
+  for (int rb = r0; rb < r1; rb += kGramRows) {
+    const int nr = min(kGramRows, r1 - rb);
+    for (int e = threadIdx.x; e < kGramRows * mp; e += kThreads) {
+      const int rr = e / mp, jj = e % mp;
+      const bool in = rr < nr && jj < m;
+      Qs[e] = in ? Q[(size_t)(rb + rr) * m + jj] : 0.0;
+      As[e] = in ? AQ[(size_t)(rb + rr) * m + jj] : 0.0;
+    }
+    __syncthreads();
+    if (own) {
+      for (int rr = 0; rr < nr; ++rr) {
+        const double *qr = Qs + rr * mp;
+        const double *ar = As + rr * mp;
+        double qi[4], qj[4], aj[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          qi[p] = qr[4 * ti + p];
+          qj[p] = qr[4 * tj + p];
+          aj[p] = ar[4 * tj + p];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            a[p][q] = fma(qi[p], aj[q], a[p][q]);
+            b[p][q] = fma(qi[p], qj[q], b[p][q]);
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (own) {
+    double *pa = part + (size_t)blockIdx.x * 2 * mp * mp;
+    double *pb = pa + (size_t)mp * mp;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        pa[(size_t)(4 * ti + p) * mp + 4 * tj + q] = a[p][q];
+        pb[(size_t)(4 * ti + p) * mp + 4 * tj + q] = b[p][q];
+      }
+  }
+}
+
+// Sum of the gram partials over blocks (fixed order), for i <= j within the
+// computed tiles; mirrored into full m x m matrices. A_Q is symmetrised as
+// (A_Q + A_Q^T)/2 on the diagonal tiles, where both (i, j) and (j, i) exist.
+__global__ void k_reduce_gram(int Pg, int m, int mp, const double *__restrict__ part,
+                              double *__restrict__ Aq, double *__restrict__ Bq) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  const int i = idx / m, j = idx % m;
+  if (i > j) return;
+  const bool same_tile = (i / 4) == (j / 4);
+  double sa = 0.0, sb = 0.0, sa2 = 0.0;
+  for (int b = 0; b < Pg; ++b) {
+    const double *pa = part + (size_t)b * 2 * mp * mp;
+    const double *pb = pa + (size_t)mp * mp;
+    sa += pa[(size_t)i * mp + j];
+    sb += pb[(size_t)i * mp + j];
+    if (same_tile) sa2 += pa[(size_t)j * mp + i];
+  }
+  if (same_tile) sa = 0.5 * (sa + sa2);
+  Aq[(size_t)i * m + j] = sa;
+  Aq[(size_t)j * m + i] = sa;
+  Bq[(size_t)i * m + j] = sb;
+  Bq[(size_t)j * m + i] = sb;
+}
+
+__device__ double block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+// Right-looking Cholesky of the m x m matrix in L (lower part used). Returns
+// 0 on success, 1 if a pivot was not positive.
+__device__ int cholesky_inplace(double *L, int m, int *flag) {
+  for (int j = 0; j < m; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = L[(size_t)j * m + j];
+      if (!(d > 0.0)) {
+        *flag = 1;
+      } else {
+        L[(size_t)j * m + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (*flag) return 1;
+    const double d = L[(size_t)j * m + j];
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[(size_t)i * m + j] /= d;
+    __syncthreads();
+    const int nt = m - j - 1;
+    for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+      const int i = j + 1 + e / nt, k = j + 1 + e % nt;
+      if (k <= i) L[(size_t)i * m + k] -= L[(size_t)i * m + j] * L[(size_t)k * m + j];
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// Generalised symmetric eigenproblem A_Q X = B_Q X Lambda in one CTA.
+__global__ void __launch_bounds__(512)
+k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ Bq,
+              double *__restrict__ L, double *__restrict__ Cg, double *__restrict__ U,
+              double *__restrict__ XQ, double *__restrict__ lam, DevStatus *__restrict__ status,
+              int use_smem) {
+  extern __shared__ double smem[];
+  __shared__ double red[32];
+  __shared__ int flag;
+  __shared__ double rot_c[kMaxM0 / 2], rot_s[kMaxM0 / 2];
+  __shared__ int rot_a[kMaxM0 / 2], rot_b[kMaxM0 / 2];
+  __shared__ double evals[kMaxM0];
+  __shared__ int rank[kMaxM0];
+  double *Cm = use_smem ? smem : Cg;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const size_t mm = (size_t)m * m;
+
+  // ---- Cholesky of B_Q, with one shifted retry --------------------------
+  double fro2 = 0.0;
+  for (size_t e = tid; e < mm; e += nth) fro2 += Bq[e] * Bq[e];
+  fro2 = block_sum(fro2, red);
+  int shifted = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const double shift =
+        attempt ? 11.0 * ((double)m * m + (double)m * (m + 1)) * DBL_EPSILON * sqrt(fro2) : 0.0;
+    for (size_t e = tid; e < mm; e += nth) {
+      const int i = (int)(e / m), k = (int)(e % m);
+      L[e] = (k <= i) ? Bq[e] + (i == k ? shift : 0.0) : 0.0;
+    }
+    if (tid == 0) flag = 0;
+    __syncthreads();
+    if (cholesky_inplace(L, m, &flag) == 0) break;
+    __syncthreads();
+    if (attempt == 1) {
+      if (tid == 0) status->breakdown = 1;
+      return;
+    }
+    shifted = 1;
+  }
+  if (tid == 0) {
+    status->breakdown = 0;
+    status->shifted = shifted;
+  }
+  __syncthreads();
+
+  // ---- C = L^-1 A_Q L^-T ---------------------------------------------------
+  // Y = L^-1 A_Q into U (thread per column), then C = L^-1 Y^T.
+  for (int col = tid; col < m; col += nth) {
+    for (int i = 0; i < m; ++i) {
+      double t = Aq[(size_t)i * m + col];
+      for (int k = 0; k < i; ++k) t -= L[(size_t)i * m + k] * U[(size_t)k * m + col];
+      U[(size_t)i * m + col] = t / L[(size_t)i * m + i];
+    }
+  }
+  __syncthreads();
+  for (int col = tid; col < m; col += nth) {
+    for (int i = 0; i < m; ++i) {
+      double t = U[(size_t)col * m + i];
+      for (int k = 0; k < i; ++k) t -= L[(size_t)i * m + k] * Cm[(size_t)k * m + col];
+      Cm[(size_t)i * m + col] = t / L[(size_t)i * m + i];
+    }
+  }
+  __syncthreads();
+  for (size_t e = tid; e < mm; e += nth) {
+    const int i = (int)(e / m), k = (int)(e % m);
+    if (i < k) {
+      const double v = 0.5 * (Cm[e] + Cm[(size_t)k * m + i]);
+      Cm[e] = v;
+      Cm[(size_t)k * m + i] = v;
+    }
+  }
+  for (size_t e = tid; e < mm; e += nth) U[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
+  __syncthreads();
+
+  // ---- cyclic Jacobi, round-robin pairing (parallel rotations) -----------
+  const int mp = m + (m & 1);
+  const int npairs = mp / 2;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (size_t e = tid; e < mm; e += nth) {
+      const double v = Cm[e] * Cm[e];
+      tot += v;
+      if ((e / m) != (e % m)) off += v;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (!(off > 1e-32 * tot)) break;
+    for (int round = 0; round < mp - 1; ++round) {
+      for (int p = tid; p < npairs; p += nth) {
+        const int pa = p, pb = mp - 1 - p;
+        int a = pa == 0 ? 0 : 1 + (pa - 1 + round) % (mp - 1);
+        int b = pb == 0 ? 0 : 1 + (pb - 1 + round) % (mp - 1);
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+        }
+        double c = 1.0, s = 0.0;
+        if (b < m) {
+          const double apq = Cm[(size_t)a * m + b];
+          const double app = Cm[(size_t)a * m + a], aqq = Cm[(size_t)b * m + b];
+          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) /
+                             (fabs(tau) + (fabs(tau) < 1e150 ? sqrt(1.0 + tau * tau) : fabs(tau)));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        rot_a[p] = a;
+        rot_b[p] = b < m ? b : a;
+        rot_c[p] = c;
+        rot_s[p] = (b < m) ? s : 0.0;
+      }
+      __syncthreads();
+      // rows: C <- J^T C
+      for (int e = tid; e < npairs * m; e += nth) {
+        const int p = e / m, k = e % m;
+        const int a = rot_a[p], b = rot_b[p];
+        if (a == b || rot_s[p] == 0.0) continue;
+        const double c = rot_c[p], s = rot_s[p];
+        const double x = Cm[(size_t)a * m + k], y = Cm[(size_t)b * m + k];
+        Cm[(size_t)a * m + k] = c * x - s * y;
+        Cm[(size_t)b * m + k] = s * x + c * y;
+      }
+      __syncthreads();
+      // columns: C <- C J, U <- U J
+      for (int e = tid; e < npairs * m; e += nth) {
+        const int p = e / m, k = e % m;
+        const int a = rot_a[p], b = rot_b[p];
+        if (a == b || rot_s[p] == 0.0) continue;
+        const double c = rot_c[p], s = rot_s[p];
+        const double x = Cm[(size_t)k * m + a], y = Cm[(size_t)k * m + b];
+        Cm[(size_t)k * m + a] = c * x - s * y;
+        Cm[(size_t)k * m + b] = s * x + c * y;
+        const double u = U[(size_t)k * m + a], v = U[(size_t)k * m + b];
+        U[(size_t)k * m + a] = c * u - s * v;
+        U[(size_t)k * m + b] = s * u + c * v;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < m; i += nth) evals[i] = Cm[(size_t)i * m + i];
+  __syncthreads();
+  // ---- X_Q = L^-T U (back substitution per column), ascending order -------
+  for (int i = tid; i < m; i += nth) {
+    int r = 0;
+    const double v = evals[i];
+    for (int k = 0; k < m; ++k) r += (evals[k] < v) || (evals[k] == v && k < i);
+    rank[i] = r;
+  }
+  __syncthreads();
+  for (int col = tid; col < m; col += nth) {
+    const int dst = rank[col];
+    for (int i = m - 1; i >= 0; --i) {
+      double t = U[(size_t)i * m + col];
+      for (int k = i + 1; k < m; ++k) t -= L[(size_t)k * m + i] * XQ[(size_t)k * m + dst];
+      XQ[(size_t)i * m + dst] = t / L[(size_t)i * m + i];
+    }
+    lam[dst] = evals[col];
+  }
+}
+
+// X = Q X_Q, AX = AQ X_Q on this block's rows; partials per column j of
+// ||AX_j - lam_j X_j||^2, ||AX_j||^2, ||X_j||^2. blockDim = (32, 8): x over
+// columns j = tx + 32 q, y over rows.
+template <int QMAX>
+__global__ void __launch_bounds__(256)
+k_update_resid(int n, int m, const double *__restrict__ Q, const double *__restrict__ AQ,
+               const double *__restrict__ XQ, const double *__restrict__ lam,
+               double *__restrict__ X, double *__restrict__ part, int rows) {
+  extern __shared__ double sm[];
+  const int RB = 8;
+  double *Qs = sm;            // RB x m
+  double *As = sm + RB * m;   // RB x m
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  double e2[QMAX], a2[QMAX], x2[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) e2[q] = a2[q] = x2[q] = 0.0;
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(n, r0 + rows);
+  for (int rb = r0; rb < r1; rb += RB) {
+    const int nr = min(RB, r1 - rb);
+    for (int e = tid; e < RB * m; e += 256) {
+      const int rr = e / m, jj = e % m;
+      Qs[e] = rr < nr ? Q[(size_t)(rb + rr) * m + jj] : 0.0;
+      As[e] = rr < nr ? AQ[(size_t)(rb + rr) * m + jj] : 0.0;
+    }
+    __syncthreads();
+    if (ty < nr) {
+      const double *qr = Qs + ty * m;
+      const double *ar = As + ty * m;
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) {
+        const int j = tx + 32 * q;
+        if (j < m) {
+          double x = 0.0, ax = 0.0;
+          for (int i = 0; i < m; ++i) {
+            const double xq = XQ[(size_t)i * m + j];
+            x = fma(qr[i], xq, x);
+            ax = fma(ar[i], xq, ax);
+          }
+          X[(size_t)(rb + ty) * m + j] = x;
+          const double d = ax - lam[j] * x;
+          e2[q] = fma(d, d, e2[q]);
+          a2[q] = fma(ax, ax, a2[q]);
+          x2[q] = fma(x, x, x2[q]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // reduce over ty (fixed order) and store this block's partials
+  __shared__ double red[8][32];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+    for (int which = 0; which < 3; ++which) {
+      red[ty][tx] = which == 0 ? e2[q] : (which == 1 ? a2[q] : x2[q]);
+      __syncthreads();
+      if (ty == 0) {
+        double t = 0.0;
+        for (int y = 0; y < 8; ++y) t += red[y][tx];
+        const int j = tx + 32 * q;
+        if (j < m) part[((size_t)blockIdx.x * 3 + which) * m + j] = t;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Column norms of X only (first iteration): partial slot 2 as in update_resid.
+__global__ void k_colnorm_part(int n, int m, const double *__restrict__ X, double *__restrict__ part,
+                               int rows) {
+  const int j = blockIdx.y * 32 + (threadIdx.x & 31);
+  const int w = threadIdx.x >> 5;
+  __shared__ double red[kWarps][32];
+  double t = 0.0;
+  if (j < m) {
+    const int r0 = blockIdx.x * rows, r1 = min(n, r0 + rows);
+    for (int r = r0 + w; r < r1; r += kWarps) {
+      const double x = X[(size_t)r * m + j];
+      t = fma(x, x, t);
+    }
+  }
+  red[w][threadIdx.x & 31] = t;
+  __syncthreads();
+  if (w == 0 && j < m) {
+    double u = 0.0;
+    for (int q = 0; q < kWarps; ++q) u += red[q][threadIdx.x];
+    part[((size_t)blockIdx.x * 3 + 2) * m + j] = u;
+  }
+}
+
+__global__ void k_reduce_norms(int Pr, int m, const double *__restrict__ part, double *__restrict__ beta) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double t = 0.0;
+  for (int b = 0; b < Pr; ++b) t += part[((size_t)b * 3 + 2) * m + j];
+  beta[j] = sqrt(t);
+}
+
+// Residuals, interval count, ||R_F|| and the next inner tolerance (one block).
+__global__ void k_reduce_resid(int Pr, int m, const double *__restrict__ part,
+                               const double *__restrict__ lam, double emin, double emax,
+                               double alpha, double *__restrict__ res, double *__restrict__ beta,
+                               DevStatus *__restrict__ status) {
+  __shared__ double smax[256];
+  __shared__ int scnt[256], snan[256];
+  double mx = 0.0;
+  int cnt = 0, bad = 0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double e = 0.0, a = 0.0, x = 0.0;
+    for (int b = 0; b < Pr; ++b) {
+      e += part[((size_t)b * 3 + 0) * m + j];
+      a += part[((size_t)b * 3 + 1) * m + j];
+      x += part[((size_t)b * 3 + 2) * m + j];
+    }
+    const double r = sqrt(e) / (a > 0.0 ? sqrt(a) : 1.0);
+    res[j] = r;
+    beta[j] = sqrt(x);
+    const double l = lam[j];
+    if (!isfinite(r) || !isfinite(l)) bad = 1;
+    if (l > emin && l < emax) {
+      ++cnt;
+      mx = fmax(mx, r);
+    }
+  }
+  smax[threadIdx.x] = mx;
+  scnt[threadIdx.x] = cnt;
+  snan[threadIdx.x] = bad;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double M = 0.0;
+    int N = 0, B = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      M = fmax(M, smax[t]);
+      N += scnt[t];
+      B |= snan[t];
+    }
+    const double RF = N > 0 ? M : 1.0;
+    status->RF = RF;
+    status->count = N;
+    status->nonfinite = B;
+    status->tol_rel = alpha > 0.0 ? alpha * RF : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t rr_init() {
+  cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       2 * kGramRows * kMaxM0 * (int)sizeof(double));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              160 * 1024);
+}
+
+cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
+  const int m = a.m0;
+  if (m < 1 || m > kMaxM0) return cudaErrorInvalidValue;
+  const int mp = (m + 3) / 4 * 4;
+  // AQ = A Q
+  {
+    const int tiles = (m + 31) / 32;
+    const int rows = (a.n + a.Pg - 1) / a.Pg;
+    k_spmm_real<<<dim3((a.n + rows - 1) / rows, tiles), kThreads, 0, st>>>(
+        a.n, m, a.rowptr, a.colidx, a.val, a.Q, a.AQ, rows);
+  }
+  // Gram partials
+  {
+    const int nt = mp / 4;
+    const int ntiles = nt * (nt + 1) / 2;
+    const int gy = (ntiles + kThreads - 1) / kThreads;
+    const int rows = (a.n + a.Pg - 1) / a.Pg;
+    const size_t smem = 2 * (size_t)kGramRows * mp * sizeof(double);
+    k_gram<<<dim3((a.n + rows - 1) / rows, gy), kThreads, smem, st>>>(a.n, m, mp, a.Q, a.AQ,
+                                                                     a.gram_part, rows);
+    const int pg_used = (a.n + rows - 1) / rows;
+    k_reduce_gram<<<(m * m + 255) / 256, 256, 0, st>>>(pg_used, m, mp, a.gram_part, a.Aq, a.Bq);
+  }
+  // reduced eigenproblem
+  {
+    const size_t need = (size_t)m * m * sizeof(double);
+    const int use_smem = need <= 160 * 1024;
+    k_reduced_eig<<<1, 512, use_smem ? need : 0, st>>>(m, a.Aq, a.Bq, a.L, a.Cm, a.U, a.XQ,
+                                                       a.lam, a.status, use_smem);
+  }
+  // X = Q X_Q and residual partials
+  {
+    const int rows = (a.n + a.Pr - 1) / a.Pr;
+    const int pr_used = (a.n + rows - 1) / rows;
+    const size_t smem = 2 * 8 * (size_t)m * sizeof(double);
+    const dim3 blk(32, 8);
+    const int qm = (m + 31) / 32;
+    if (qm <= 1)
+      k_update_resid<1><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
+                                                     a.res_part, rows);
+    else if (qm <= 2)
+      k_update_resid<2><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
+                                                     a.res_part, rows);
+    else if (qm <= 4)
+      k_update_resid<4><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
+                                                     a.res_part, rows);
+    else
+      k_update_resid<8><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
+                                                     a.res_part, rows);
+    k_reduce_resid<<<1, 256, 0, st>>>(pr_used, m, a.res_part, a.lam, a.emin, a.emax, a.alpha,
+                                      a.res, a.beta, a.status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t column_norms(int n, int m, const double *X, double *part, int Pr, double *beta,
+                         cudaStream_t st) {
+  const int rows = (n + Pr - 1) / Pr;
+  const int pr_used = (n + rows - 1) / rows;
+  k_colnorm_part<<<dim3(pr_used, (m + 31) / 32), kThreads, 0, st>>>(n, m, X, part, rows);
+  k_reduce_norms<<<(m + 127) / 128, 128, 0, st>>>(pr_used, m, part, beta);
+  return cudaGetLastError();
+}
+
+}  // namespace ifeast

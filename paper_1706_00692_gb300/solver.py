@@ -1,0 +1,188 @@
+"""Python binding of libifeast: argument marshalling over the C ABI only.
+
+Device memory (the handle's workspace, inputs and outputs) comes from PyTorch
+tensors and kernels run on the current PyTorch CUDA stream; every step of
+the computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+
+from . import _lib
+from .inputs import CSR
+
+
+class IFEASTError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.load().ifeast_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libifeast needs a CUDA device; none is available")
+    return torch
+
+
+def contour_nodes(rule: str, nc: int, emin: float, emax: float):
+    """Nodes z_k and weights w_k computed by the library (complex numpy arrays)."""
+    lib = _lib.load()
+    c = _lib.Contour(_lib.RULES[rule], nc, emin, emax)
+    zw = np.zeros(4 * nc)
+    rc = lib.ifeast_contour_nodes(ct.byref(c), zw.ctypes.data)
+    if rc:
+        raise IFEASTError(rc, "ifeast_contour_nodes")
+    zw = zw.reshape(nc, 4)
+    return zw[:, 0] + 1j * zw[:, 1], zw[:, 2] + 1j * zw[:, 3]
+
+
+class Solver:
+    """One IFEAST problem (A, interval, m0, contour, options) bound to a handle."""
+
+    def __init__(self, A: CSR, emin: float, emax: float, m0: int, *, nc: int = 8,
+                 rule: str = "gl_half", inner_iters: int = 10, alpha: float = 0.0,
+                 max_outer: int = 100, tol: float = 1e-10, precision: int = _lib.FP64,
+                 device: str | int = "cuda", torch_workspace: bool = True):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n, self.m0, self.nc = int(A.n), int(m0), int(nc)
+        self.emin, self.emax = float(emin), float(emax)
+        self.contour = _lib.Contour(_lib.RULES[rule], nc, emin, emax)
+        self.opts = _lib.Opts()
+        self.lib.ifeast_default_opts(ct.byref(self.opts))
+        self.opts.inner_max_iters = inner_iters
+        self.opts.alpha = alpha
+        self.opts.max_outer = max_outer
+        self.opts.tol = tol
+        self.opts.precision = precision
+        nbytes = ct.c_size_t(0)
+        rc = self.lib.ifeast_workspace_bytes(self.n, A.nnz, self.m0, ct.byref(self.contour),
+                                             ct.byref(self.opts), ct.byref(nbytes))
+        if rc:
+            raise IFEASTError(rc, "ifeast_workspace_bytes")
+        self.workspace_bytes = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            if torch_workspace:
+                self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+                ws_ptr, ws_len = self._ws.data_ptr(), self.workspace_bytes
+            else:
+                self._ws, ws_ptr, ws_len = None, None, 0
+            self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+            self._colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
+            self._val = np.ascontiguousarray(A.val, dtype=np.float64)
+            csr = _lib.Csr(self.n, A.nnz, self._rowptr.ctypes.data, self._colidx.ctypes.data,
+                           self._val.ctypes.data)
+            h = ct.c_void_p()
+            rc = self.lib.ifeast_create(ct.byref(csr), None, ct.byref(self.contour), self.m0,
+                                        ct.byref(self.opts), ws_ptr, ws_len,
+                                        ct.c_void_p(self.stream.cuda_stream), ct.byref(h))
+            if rc:
+                raise IFEASTError(rc, "ifeast_create")
+            self.h = h
+
+    # ------------------------------------------------------------------ full solve
+    def solve(self, X0) -> int:
+        """Algorithm 2 from X0 (numpy (n, m0) float64 on the host, or a CUDA
+        float64 tensor). Returns the library status (0 = converged)."""
+        torch = self.torch
+        if isinstance(X0, np.ndarray):
+            x = np.ascontiguousarray(X0, dtype=np.float64)
+            assert x.shape == (self.n, self.m0)
+            return int(self.lib.ifeast_solve(self.h, x.ctypes.data, 0))
+        assert X0.is_cuda and X0.dtype == torch.float64 and X0.shape == (self.n, self.m0)
+        X0 = X0.contiguous()
+        return int(self.lib.ifeast_solve(self.h, X0.data_ptr(), 1))
+
+    def eigenpairs(self, on_device: bool = False):
+        """(lam, X, res) for the Ritz pairs inside the interval, ascending."""
+        torch = self.torch
+        m = ct.c_int(0)
+        rc = self.lib.ifeast_eigenpairs(self.h, 0, ct.byref(m), None, None, None, 0)
+        if rc:
+            raise IFEASTError(rc, "ifeast_eigenpairs")
+        cnt = m.value
+        if on_device:
+            lam = torch.empty(cnt, dtype=torch.float64, device=self.device)
+            X = torch.empty((self.n, cnt), dtype=torch.float64, device=self.device)
+            res = torch.empty(cnt, dtype=torch.float64, device=self.device)
+            ptrs = (lam.data_ptr(), X.data_ptr(), res.data_ptr()) if cnt else (None, None, None)
+        else:
+            lam, X, res = np.zeros(cnt), np.zeros((self.n, cnt)), np.zeros(cnt)
+            ptrs = (lam.ctypes.data, X.ctypes.data, res.ctypes.data) if cnt else (None, None, None)
+        rc = self.lib.ifeast_eigenpairs(self.h, cnt, ct.byref(m), *ptrs, 1 if on_device else 0)
+        if rc:
+            raise IFEASTError(rc, "ifeast_eigenpairs")
+        return lam, X, res
+
+    def ritz_all(self):
+        lam, res = np.zeros(self.m0), np.zeros(self.m0)
+        rc = self.lib.ifeast_ritz_all(self.h, lam.ctypes.data, res.ctypes.data, 0)
+        if rc:
+            raise IFEASTError(rc, "ifeast_ritz_all")
+        return lam, res
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        rc = self.lib.ifeast_get_stats(self.h, ct.byref(s))
+        if rc:
+            raise IFEASTError(rc, "ifeast_get_stats")
+        return {f: getattr(s, f) for f, _ in _lib.Stats._fields_}
+
+    # ------------------------------------------------------------------ steps
+    def apply_filter(self, X, RF: float = 1.0):
+        """Alg. 2 steps 1-2 on a CUDA float64 (n, m0) tensor: returns (Q, steps)."""
+        torch = self.torch
+        X = X.contiguous()
+        Q = torch.empty_like(X)
+        steps = torch.empty(self.nc * self.m0, dtype=torch.int32, device=self.device)
+        rc = self.lib.ifeast_apply_filter(self.h, X.data_ptr(), Q.data_ptr(), float(RF),
+                                          steps.data_ptr())
+        if rc:
+            raise IFEASTError(rc, "ifeast_apply_filter")
+        return Q, steps
+
+    def rayleigh_ritz(self, Q):
+        """Alg. 2 steps 3-4 on a CUDA float64 (n, m0) tensor: returns (X, lam, res)."""
+        torch = self.torch
+        Q = Q.contiguous()
+        X = torch.empty_like(Q)
+        lam = torch.empty(self.m0, dtype=torch.float64, device=self.device)
+        res = torch.empty(self.m0, dtype=torch.float64, device=self.device)
+        rc = self.lib.ifeast_rayleigh_ritz(self.h, Q.data_ptr(), X.data_ptr(), lam.data_ptr(),
+                                           res.data_ptr())
+        if rc:
+            raise IFEASTError(rc, "ifeast_rayleigh_ritz")
+        return X, lam, res
+
+    def spmm_shift(self, V, z):
+        """W[:, c] = z[c // m0] V[:, c] - A V[:, c] for a CUDA complex128 (n, C) V."""
+        torch = self.torch
+        V = V.contiguous()
+        assert V.dtype == torch.complex128 and V.shape[0] == self.n
+        C = V.shape[1]
+        zt = torch.as_tensor(np.asarray(z, dtype=np.complex128), device=self.device)
+        W = torch.empty_like(V)
+        rc = self.lib.ifeast_spmm_shift(self.h, V.data_ptr(), W.data_ptr(), C, C // zt.numel(),
+                                        zt.data_ptr())
+        if rc:
+            raise IFEASTError(rc, "ifeast_spmm_shift")
+        return W
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ifeast_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,141 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+declared in include/*.h, computes the contour like the oracle, and rejects
+malformed input on the host before touching a device."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import ifeast_oracle as orc
+from paper_1706_00692_gb300 import _lib, inputs
+from paper_1706_00692_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def _declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(ifeast_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 12
+    for nm in names:
+        assert hasattr(lib, nm), nm
+        assert nm in _lib.SIGNATURES, f"{nm} has no ctypes signature"
+
+
+@pytest.mark.parametrize("rule,nc,emin,emax", [("gl_half", 8, 0.0, 0.066), ("gl_half", 1, -2.0, 3.0),
+                                                ("gl_half", 24, 0.8968, 0.9104),
+                                                ("trap_half", 4, 1.0, 5.0), ("trap_full", 16, 0.0, 629.7)])
+def test_contour_nodes_match_oracle(lib, rule, nc, emin, emax):
+    c = _lib.Contour(_lib.RULES[rule], nc, emin, emax)
+    zw = np.zeros(4 * nc)
+    assert lib.ifeast_contour_nodes(ct.byref(c), zw.ctypes.data) == 0
+    zw = zw.reshape(nc, 4)
+    z, w = orc.contour_nodes(rule, nc, emin, emax)
+    scale = max(abs(emin), abs(emax), emax - emin)
+    assert np.abs(zw[:, 0] + 1j * zw[:, 1] - z).max() <= 4e-16 * scale * 4
+    assert np.abs(zw[:, 2] + 1j * zw[:, 3] - w).max() <= 4e-16 * (emax - emin) * 4
+
+
+def test_contour_rejects_bad_interval(lib):
+    zw = np.zeros(8)
+    for c in [_lib.Contour(0, 2, 1.0, 1.0), _lib.Contour(0, 0, 0.0, 1.0), _lib.Contour(7, 2, 0.0, 1.0)]:
+        assert lib.ifeast_contour_nodes(ct.byref(c), zw.ctypes.data) == _lib.IFEAST_ERR_INVALID_ARG
+
+
+def _opts(lib, **kw):
+    o = _lib.Opts()
+    lib.ifeast_default_opts(ct.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def test_default_opts(lib):
+    o = _opts(lib)
+    assert (o.inner_solver, o.inner_max_iters, o.alpha, o.max_outer, o.tol, o.precision) == \
+        (0, 10, 0.0, 100, 1e-10, 0)
+
+
+def test_workspace_bytes_grows_with_basis(lib):
+    c = _lib.Contour(0, 8, 0.0, 1.0)
+    b1, b2 = ct.c_size_t(), ct.c_size_t()
+    assert lib.ifeast_workspace_bytes(2500, 12300, 20, ct.byref(c), ct.byref(_opts(lib)), ct.byref(b1)) == 0
+    assert lib.ifeast_workspace_bytes(2500, 12300, 20, ct.byref(c),
+                                      ct.byref(_opts(lib, inner_max_iters=20)), ct.byref(b2)) == 0
+    # the (k+1) x n x C complex basis dominates: 10 more vectors of 2500 x 160 x 16 bytes
+    assert b2.value - b1.value >= 10 * 2500 * 160 * 16
+
+
+def _create(lib, A, m0=4, opts=None, contour=None, B=None):
+    rp = np.ascontiguousarray(A.rowptr, np.int32)
+    ci = np.ascontiguousarray(A.colidx, np.int32)
+    v = np.ascontiguousarray(A.val, np.float64)
+    csr = _lib.Csr(A.n, A.nnz, rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+    h = ct.c_void_p()
+    c = contour or _lib.Contour(0, 4, 0.0, 1.0)
+    rc = lib.ifeast_create(ct.byref(csr), B, ct.byref(c), m0, ct.byref(opts or _opts(lib)), None, 0,
+                           None, ct.byref(h))
+    return rc, h
+
+
+def test_create_rejects_malformed_csr(lib):
+    A = inputs.laplacian((5, 4))
+    bad_col = inputs.CSR(A.n, A.rowptr.copy(), A.colidx.copy(), A.val.copy())
+    bad_col.colidx[3] = A.n
+    assert _create(lib, bad_col)[0] == _lib.IFEAST_ERR_INVALID_ARG
+    bad_ptr = inputs.CSR(A.n, A.rowptr.copy(), A.colidx.copy(), A.val.copy())
+    bad_ptr.rowptr[5], bad_ptr.rowptr[6] = bad_ptr.rowptr[6], bad_ptr.rowptr[5]
+    assert _create(lib, bad_ptr)[0] == _lib.IFEAST_ERR_INVALID_ARG
+    nan_val = inputs.CSR(A.n, A.rowptr.copy(), A.colidx.copy(), A.val.copy())
+    nan_val.val[0] = np.nan
+    assert _create(lib, nan_val)[0] == _lib.IFEAST_ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_options(lib):
+    A = inputs.laplacian((5, 4))
+    assert _create(lib, A, m0=0)[0] == _lib.IFEAST_ERR_INVALID_ARG
+    assert _create(lib, A, m0=A.n + 1)[0] == _lib.IFEAST_ERR_INVALID_ARG
+    assert _create(lib, A, opts=_opts(lib, inner_max_iters=0))[0] == _lib.IFEAST_ERR_INVALID_ARG
+    assert _create(lib, A, opts=_opts(lib, inner_max_iters=33))[0] == _lib.IFEAST_ERR_INVALID_ARG
+    assert _create(lib, A, opts=_opts(lib, max_outer=0))[0] == _lib.IFEAST_ERR_INVALID_ARG
+    assert _create(lib, A, opts=_opts(lib, inner_solver=9))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, contour=_lib.Contour(0, 4, 1.0, 0.5))[0] == _lib.IFEAST_ERR_INVALID_ARG
+    assert _create(lib, A, contour=_lib.Contour(2, 4, 0.0, 0.5))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, B=ct.c_void_p(1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+
+
+def test_strerror_and_null_handles(lib):
+    for code in range(11):
+        assert lib.ifeast_strerror(code)
+    assert lib.ifeast_solve(None, None, 0) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_get_stats(None, None) == _lib.IFEAST_ERR_INVALID_ARG
+    lib.ifeast_destroy(None)
+
+
+def test_product_path_has_no_oracle_import():
+    pkg = os.path.join(ROOT, "paper_1706_00692_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                text = open(os.path.join(dp, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", text, re.M), os.path.join(dp, f)
+                assert "ifeast_oracle" not in text, os.path.join(dp, f)
