@@ -63,12 +63,24 @@ typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } 
 /* Inner solver for Alg. 2 step 1.
  *   GMRES:  one complex GMRES per (node, column) pair, zero initial guess,
  *           classical Gram-Schmidt applied twice, Givens least squares
- *           (Sec. 2.2). inner_max_iters <= 32.                               */
-typedef enum { IFEAST_INNER_GMRES = 0 } ifeast_inner;
+ *           (Sec. 2.2). inner_max_iters <= 32. FP64 only.
+ *   MINRES: one real Lanczos basis per column of X, shared by all nc shifts
+ *           (Sec. 3: the Krylov basis of (z I - A) does not depend on z); each
+ *           (node, column) pair takes the minimal-residual solution on it
+ *           (MINRES for the shifted Hermitian systems, Sec. 2) and stops on
+ *           its own tolerance. From the second outer iteration on, each shifted
+ *           system is solved in residual form: with r_j = A x_j - lambda_j x_j,
+ *           (z I - A)^{-1} x_j = (x_j + (z I - A)^{-1} r_j) / (z - lambda_j),
+ *           an identity, so the same Alg. 2 stop test applies while the Krylov
+ *           solve only has to resolve r_j (this lets FP32 inner arithmetic
+ *           reach FP64 eigenpair accuracy). inner_max_iters <= 4096.        */
+typedef enum { IFEAST_INNER_GMRES = 0, IFEAST_INNER_MINRES = 1 } ifeast_inner;
 
-/* Arithmetic of the inner solve (Krylov vectors and their products). The
- * reduced eigenproblem, Rayleigh-Ritz products and residual check are FP64. */
-typedef enum { IFEAST_FP64 = 0 } ifeast_precision;
+/* Arithmetic of the inner solve (Krylov vectors, sparse products and their
+ * inner products; FP32 is accepted with IFEAST_INNER_MINRES only). The
+ * quadrature weights, least-squares updates, reduced eigenproblem,
+ * Rayleigh-Ritz products and residual check are FP64 in every mode. */
+typedef enum { IFEAST_FP64 = 0, IFEAST_FP32 = 1 } ifeast_precision;
 
 typedef struct {
   int64_t n;
@@ -94,6 +106,7 @@ typedef struct {
   int max_outer;        /* outer iteration cap (default 100)                     */
   double tol;           /* stop when ||R_F|| <= tol (default 1e-10)              */
   int precision;        /* ifeast_precision                                      */
+  int verbose;          /* 1: one line per outer iteration on stderr             */
 } ifeast_opts;
 
 typedef struct {
@@ -108,7 +121,7 @@ typedef struct {
 } ifeast_stats;
 
 /* Fills *o with the defaults: GMRES, k = 10, alpha = 0 (fixed k), max_outer =
- * 100, tol = 1e-10, FP64. */
+ * 100, tol = 1e-10, FP64, verbose = 0. */
 void ifeast_default_opts(ifeast_opts *o);
 
 /* Contour nodes and weights (Eq. contour_int_quad with the rules above) on the

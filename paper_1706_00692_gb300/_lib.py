@@ -20,8 +20,10 @@ IFEAST_ERR_STATE = 9
 IFEAST_ERR_UNSUPPORTED = 10
 
 GL_HALF, TRAP_HALF, TRAP_FULL = 0, 1, 2
-INNER_GMRES = 0
-FP64 = 0
+INNER_GMRES, INNER_MINRES = 0, 1
+FP64, FP32 = 0, 1
+INNERS = {"gmres": INNER_GMRES, "minres": INNER_MINRES}
+PRECISIONS = {"fp64": FP64, "fp32": FP32}
 
 RULES = {"gl_half": GL_HALF, "trap_half": TRAP_HALF, "trap_full": TRAP_FULL}
 
@@ -37,7 +39,8 @@ class Contour(ct.Structure):
 
 class Opts(ct.Structure):
     _fields_ = [("inner_solver", ct.c_int), ("inner_max_iters", ct.c_int), ("alpha", ct.c_double),
-                ("max_outer", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int)]
+                ("max_outer", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
+                ("verbose", ct.c_int)]
 
 
 class Stats(ct.Structure):

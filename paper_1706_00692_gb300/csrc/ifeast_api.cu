@@ -40,6 +40,15 @@ struct ifeast_ctx {
          *U = nullptr, *XQ = nullptr, *lam = nullptr, *res_part = nullptr, *res = nullptr;
   DevStatus *status = nullptr;
   DevStatus *status_host = nullptr;  // pinned
+  // shared-basis (MINRES) mode
+  bool minres = false, fp32 = false;
+  float *val32 = nullptr;
+  void *LV = nullptr, *LW0 = nullptr, *LW1 = nullptr;
+  double *lpart = nullptr, *lalpha = nullptr, *lbeta = nullptr, *ltol = nullptr;
+  double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
+  int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
+  double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
+  int *active_host = nullptr;  // pinned
   // results
   bool solved = false;
   ifeast_stats stats{};
@@ -61,6 +70,8 @@ struct Layout {
 struct Offsets {
   size_t rowptr, colidx, val, z, w, V, W, part, H1, H2, inv_h, CS, SN, R, G, Y, steps, done, X, Q,
       AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
+  size_t val32, LV, LW0, LW1, lpart, lalpha, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
+      lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm;
 };
 
 int device_sms() {
@@ -70,7 +81,8 @@ int device_sms() {
   return sms > 0 ? sms : 152;
 }
 
-Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr) {
+Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr,
+             bool minres, bool fp32) {
   Layout L;
   Offsets o{};
   const size_t C = (size_t)nc * m0;
@@ -80,19 +92,44 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
   o.val = L.take<double>(nnz > 0 ? nnz : 1);
   o.z = L.take<double2>(nc);
   o.w = L.take<double2>(nc);
-  o.V = L.take<double2>((size_t)(K + 1) * n * C);
-  o.W = L.take<double2>((size_t)n * C);
-  o.part = L.take<double2>((size_t)tl.P * (K + 2) * C);
-  o.H1 = L.take<double2>((size_t)(K + 2) * C);
-  o.H2 = L.take<double2>((size_t)(K + 2) * C);
-  o.inv_h = L.take<double>(C);
-  o.CS = L.take<double2>((size_t)K * C);
-  o.SN = L.take<double2>((size_t)K * C);
-  o.R = L.take<double2>((size_t)K * K * C);
-  o.G = L.take<double2>((size_t)(K + 1) * C);
-  o.Y = L.take<double2>((size_t)K * C);
-  o.steps = L.take<int>(C);
-  o.done = L.take<int>(C);
+  if (!minres) {  // per-node complex GMRES
+    o.V = L.take<double2>((size_t)(K + 1) * n * C);
+    o.W = L.take<double2>((size_t)n * C);
+    o.part = L.take<double2>((size_t)tl.P * (K + 2) * C);
+    o.H1 = L.take<double2>((size_t)(K + 2) * C);
+    o.H2 = L.take<double2>((size_t)(K + 2) * C);
+    o.inv_h = L.take<double>(C);
+    o.CS = L.take<double2>((size_t)K * C);
+    o.SN = L.take<double2>((size_t)K * C);
+    o.R = L.take<double2>((size_t)K * K * C);
+    o.G = L.take<double2>((size_t)(K + 1) * C);
+    o.Y = L.take<double2>((size_t)K * C);
+    o.steps = L.take<int>(C);
+    o.done = L.take<int>(C);
+  } else {  // shared Lanczos basis, tl tiles the n x m0 block
+    const size_t es = fp32 ? sizeof(float) : sizeof(double);
+    if (fp32) o.val32 = L.take<float>(nnz > 0 ? nnz : 1);
+    o.LV = L.take<char>((size_t)(K + 1) * n * m0 * es);
+    o.LW0 = L.take<char>((size_t)n * m0 * es);
+    o.LW1 = L.take<char>((size_t)n * m0 * es);
+    o.lpart = L.take<double>((size_t)tl.P * 3 * m0);
+    o.lalpha = L.take<double>((size_t)K * m0);
+    o.lbeta = L.take<double>((size_t)(K + 1) * m0);
+    o.ltol = L.take<double>(C);
+    o.lg = L.take<double2>(C * (K + 1));
+    o.lR = L.take<double2>(C * K * 3);
+    o.lrot = L.take<double2>(C * 4);
+    o.lYc = L.take<double2>(C * K);
+    o.lsteps = L.take<int>(C);
+    o.ldone = L.take<int>(C);
+    o.lcoldone = L.take<int>(m0);
+    o.lactive = L.take<int>(1);
+    o.lSj = L.take<int>(m0);
+    o.lcoef = L.take<double>((size_t)K * m0);
+    o.lcx = L.take<double>(m0);
+    o.Rres = L.take<double>((size_t)n * m0);
+    o.rnorm = L.take<double>(m0);
+  }
   o.X = L.take<double>((size_t)n * m0);
   o.Q = L.take<double>((size_t)n * m0);
   o.AQ = L.take<double>((size_t)n * m0);
@@ -124,9 +161,15 @@ int validate_contour(const ifeast_contour *c) {
 
 int validate_opts(const ifeast_opts *o) {
   if (!o) return IFEAST_ERR_INVALID_ARG;
-  if (o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
-  if (o->precision != IFEAST_FP64) return IFEAST_ERR_UNSUPPORTED;
-  if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxInner) return IFEAST_ERR_INVALID_ARG;
+  if (o->inner_solver == IFEAST_INNER_GMRES) {
+    if (o->precision != IFEAST_FP64) return IFEAST_ERR_UNSUPPORTED;
+    if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxInner) return IFEAST_ERR_INVALID_ARG;
+  } else if (o->inner_solver == IFEAST_INNER_MINRES) {
+    if (o->precision != IFEAST_FP64 && o->precision != IFEAST_FP32) return IFEAST_ERR_UNSUPPORTED;
+    if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxLanczos) return IFEAST_ERR_INVALID_ARG;
+  } else {
+    return IFEAST_ERR_UNSUPPORTED;
+  }
   if (o->max_outer < 1 || !(o->tol >= 0.0) || !std::isfinite(o->alpha))
     return IFEAST_ERR_INVALID_ARG;
   return IFEAST_OK;
@@ -276,6 +319,56 @@ RRArgs rr_args(ifeast_ctx *h, const double *Q, double *X) {
   a.emax = h->contour.emax;
   a.alpha = h->opts.alpha;
   a.status = h->status;
+  a.Rres = h->minres ? h->Rres : nullptr;
+  a.rnorm = h->minres ? h->rnorm : nullptr;
+  return a;
+}
+
+// Shared-basis inner solve. correction = 0: right-hand sides X (norms in
+// h->beta); correction = 1: right-hand sides h->Rres = A X - X Lambda of the
+// current X (norms h->rnorm, Ritz values h->lam, ||x_j|| in h->beta).
+MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction) {
+  MinresArgs a{};
+  a.n = (int)h->n;
+  a.m0 = h->m0;
+  a.nc = h->nc;
+  a.K = h->K;
+  a.fp32 = h->fp32 ? 1 : 0;
+  a.rowptr = h->rowptr;
+  a.colidx = h->colidx;
+  a.val_t = h->fp32 ? (const void *)h->val32 : (const void *)h->val;
+  a.rhs = correction ? h->Rres : X;
+  a.rnorm = correction ? h->rnorm : h->beta;
+  a.X = X;
+  a.V = h->LV;
+  a.W0 = h->LW0;
+  a.W1 = h->LW1;
+  a.part = h->lpart;
+  a.alpha = h->lalpha;
+  a.beta = h->lbeta;
+  a.Yc = h->lYc;
+  a.coef = h->lcoef;
+  a.cx = h->lcx;
+  a.Sj = h->lSj;
+  a.Q = Q;
+  a.tl = h->tl;
+  a.check_every = 16;
+  a.active_host = h->active_host;
+  MinresState &m = a.ms;
+  m.z = h->z;
+  m.w = h->w;
+  m.lam = h->lam;
+  m.xnorm = h->beta;
+  m.correction = correction;
+  m.g = h->lg;
+  m.R = h->lR;
+  m.rot = h->lrot;
+  m.tol = h->ltol;
+  m.steps = h->lsteps;
+  m.done = h->ldone;
+  m.coldone = h->lcoldone;
+  m.active = h->lactive;
+  m.status = h->status;
   return a;
 }
 
@@ -308,6 +401,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->max_outer = 100;
   o->tol = 1e-10;
   o->precision = IFEAST_FP64;
+  o->verbose = 0;
 }
 
 const char *ifeast_strerror(int code) {
@@ -352,10 +446,12 @@ int ifeast_workspace_bytes(int64_t n, int64_t nnz, int m0, const ifeast_contour 
   rc = validate_opts(o);
   if (rc) return rc;
   const int sms = device_sms();
-  const RowTiling tl = make_tiling(n, c->nc * m0, sms);
+  const bool minres = o->inner_solver == IFEAST_INNER_MINRES;
+  const RowTiling tl = make_tiling(n, minres ? m0 : c->nc * m0, sms);
   const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
   const int Pr = Pg;
-  *bytes = plan(n, nnz, m0, c->nc, o->inner_max_iters, tl, Pg, Pr).total;
+  *bytes = plan(n, nnz, m0, c->nc, o->inner_max_iters, tl, Pg, Pr, minres,
+                o->precision == IFEAST_FP32).total;
   return IFEAST_OK;
 }
 
@@ -394,11 +490,13 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->contour = *c;
   h->stream = (cudaStream_t)stream;
   h->num_sms = device_sms();
-  h->tl = make_tiling(n, h->C, h->num_sms);
+  h->minres = o->inner_solver == IFEAST_INNER_MINRES;
+  h->fp32 = o->precision == IFEAST_FP32;
+  h->tl = make_tiling(n, h->minres ? m0 : h->C, h->num_sms);
   h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
   h->Pr = h->Pg;
   contour_host(c, h->zh, h->wh);
-  const Offsets off = plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr);
+  const Offsets off = plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, h->fp32);
   if (workspace) {
     h->ws = (char *)workspace;
     h->ws_bytes = ws_bytes;
@@ -411,8 +509,10 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->owns_ws = true;
     h->ws_bytes = off.total;
   }
-  if (cudaMallocHost(&h->status_host, sizeof(DevStatus)) != cudaSuccess) {
+  if (cudaMallocHost(&h->status_host, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&h->active_host, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
+    if (h->status_host) cudaFreeHost(h->status_host);
     if (h->owns_ws) cudaFree(h->ws);
     delete h;
     return IFEAST_ERR_OOM;
@@ -451,6 +551,29 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->res_part = (double *)(b + off.res_part);
   h->res = (double *)(b + off.res);
   h->status = (DevStatus *)(b + off.status);
+  if (h->minres) {
+    if (h->fp32) h->val32 = (float *)(b + off.val32);
+    h->LV = b + off.LV;
+    h->LW0 = b + off.LW0;
+    h->LW1 = b + off.LW1;
+    h->lpart = (double *)(b + off.lpart);
+    h->lalpha = (double *)(b + off.lalpha);
+    h->lbeta = (double *)(b + off.lbeta);
+    h->ltol = (double *)(b + off.ltol);
+    h->lg = (double2 *)(b + off.lg);
+    h->lR = (double2 *)(b + off.lR);
+    h->lrot = (double2 *)(b + off.lrot);
+    h->lYc = (double2 *)(b + off.lYc);
+    h->lsteps = (int *)(b + off.lsteps);
+    h->ldone = (int *)(b + off.ldone);
+    h->lcoldone = (int *)(b + off.lcoldone);
+    h->lactive = (int *)(b + off.lactive);
+    h->lSj = (int *)(b + off.lSj);
+    h->lcoef = (double *)(b + off.lcoef);
+    h->lcx = (double *)(b + off.lcx);
+    h->Rres = (double *)(b + off.Rres);
+    h->rnorm = (double *)(b + off.rnorm);
+  }
   bool ok = cudaMemcpyAsync(h->rowptr, A->rowptr, (n + 1) * sizeof(int32_t),
                             cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
   if (nnz > 0) {
@@ -463,6 +586,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
                              h->stream) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(h->w, h->wh.data(), h->nc * sizeof(double2), cudaMemcpyHostToDevice,
                              h->stream) == cudaSuccess;
+  if (h->fp32 && nnz > 0) ok = ok && convert_to_float(h->val, h->val32, nnz, h->stream) == cudaSuccess;
   ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -478,6 +602,7 @@ void ifeast_destroy(ifeast_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->owns_ws && h->ws) cudaFree(h->ws);
   if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->active_host) cudaFreeHost(h->active_host);
   delete h;
 }
 
@@ -496,7 +621,10 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
   for (int it = 1; it <= h->opts.max_outer; ++it) {
     rc = clear_step_counters(h);
     if (rc) return rc;
-    CK(gmres_filter(gmres_args(h, h->X, h->Q), h->stream));
+    if (h->minres)
+      CK(minres_filter(minres_args(h, h->X, h->Q, it > 1 ? 1 : 0), h->stream));
+    else
+      CK(gmres_filter(gmres_args(h, h->X, h->Q), h->stream));
     CK(rayleigh_ritz(rr_args(h, h->Q, h->X), h->stream));
     CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                        h->stream));
@@ -510,6 +638,11 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
     h->stats.max_inner = std::max(h->stats.max_inner, s.max_steps);
     h->stats.shifted_cholesky += s.shifted;
     h->solved = true;
+    if (h->opts.verbose)
+      std::fprintf(stderr, "ifeast: iter %3d  inside %4d  RF %.3e  inner max %5d total %9lld  %.1f ms\n",
+                   it, s.count, s.RF, s.max_steps, s.total_steps,
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                       .count());
     if (s.breakdown) {
       result = IFEAST_ERR_BREAKDOWN;
       h->solved = false;
@@ -585,9 +718,13 @@ int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32
   CK(column_norms((int)h->n, h->m0, X, h->res_part, h->Pr, h->beta, h->stream));
   int rc = set_tolerance(h, RF);
   if (rc) return rc;
-  CK(gmres_filter(gmres_args(h, X, Q), h->stream));
+  if (h->minres)
+    CK(minres_filter(minres_args(h, X, Q, 0), h->stream));
+  else
+    CK(gmres_filter(gmres_args(h, X, Q), h->stream));
   if (steps)
-    CK(cudaMemcpyAsync(steps, h->steps, h->C * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(steps, h->minres ? h->lsteps : h->steps, h->C * sizeof(int),
+                       cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return IFEAST_OK;
 }

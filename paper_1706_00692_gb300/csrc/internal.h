@@ -12,6 +12,7 @@ namespace ifeast {
 constexpr int kThreads = 256;       // threads per block of the row-tiled kernels
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxInner = 32;       // per-node GMRES basis cap (register-held dots)
+constexpr int kMaxLanczos = 4096;   // shared-basis (MINRES) step cap
 constexpr int kMaxNodes = 64;
 constexpr int kMaxM0 = 256;         // reduced problem solved in one CTA
 
@@ -67,6 +68,44 @@ cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
                             const double *val, const double2 *V, double2 *W, int ncols,
                             int m0, const double2 *z, RowTiling tl, cudaStream_t st);
 
+// ---- inner solve on one shared Lanczos basis per column (FP32 or FP64) ----
+struct MinresState {
+  const double2 *z, *w;     // [nc] nodes and weights
+  const double *lam;        // [m0] Ritz values (residual form)
+  const double *xnorm;      // [m0] ||x_j||
+  int correction;           // 1: right-hand side is A x_j - lambda_j x_j
+  double2 *g;               // [nc*m0][K+1] rotated right-hand sides
+  double2 *R;               // [nc*m0][K][3] band of the triangular factor
+  double2 *rot;             // [nc*m0][4] last two Givens rotations
+  double *tol;              // [nc*m0] bound on |g_{s+1}|
+  int *steps, *done;        // [nc*m0]
+  int *coldone;             // [m0]
+  int *active;              // [1] columns still running at the last checked step
+  DevStatus *status;
+};
+struct MinresArgs {
+  int n, m0, nc, K;
+  int fp32;
+  const int32_t *rowptr, *colidx;
+  const void *val_t;        // float or double values of A
+  const double *rhs;        // n x m0 right-hand sides (X or A X - X Lambda)
+  const double *rnorm;      // [m0] their norms
+  const double *X;          // n x m0 current subspace (residual-form term)
+  void *V, *W0, *W1;        // basis and double-buffered work vectors (T)
+  double *part;             // P x 3 x m0
+  double *alpha, *beta;     // [K][m0], [K+1][m0]
+  double2 *Yc;              // [nc][K][m0]
+  double *coef, *cx;        // [K][m0], [m0]
+  int *Sj;                  // [m0]
+  double *Q;
+  RowTiling tl;
+  MinresState ms;
+  int check_every;          // steps between early-exit checks (0: never)
+  int *active_host;         // pinned
+};
+cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st);
+cudaError_t convert_to_float(const double *a, float *b, size_t n, cudaStream_t st);
+
 // ---- Rayleigh-Ritz and residual -------------------------------------------
 struct RRArgs {
   int n, m0;
@@ -87,6 +126,8 @@ struct RRArgs {
   int Pr;
   double *res;              // m0
   double *beta;             // m0 norms of the new X columns
+  double *Rres;             // n x m0 A X - X Lambda of the new X (nullptr: not stored)
+  double *rnorm;            // m0 ||A x_j - lambda_j x_j|| (nullptr: not stored)
   double emin, emax, alpha;
   DevStatus *status;
 };

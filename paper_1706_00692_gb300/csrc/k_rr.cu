@@ -345,7 +345,8 @@ template <int QMAX>
 __global__ void __launch_bounds__(256)
 k_update_resid(int n, int m, const double *__restrict__ Q, const double *__restrict__ AQ,
                const double *__restrict__ XQ, const double *__restrict__ lam,
-               double *__restrict__ X, double *__restrict__ part, int rows) {
+               double *__restrict__ X, double *__restrict__ Rres, double *__restrict__ part,
+               int rows) {
   extern __shared__ double sm[];
   const int RB = 8;
   double *Qs = sm;            // RB x m
@@ -380,6 +381,7 @@ k_update_resid(int n, int m, const double *__restrict__ Q, const double *__restr
           }
           X[(size_t)(rb + ty) * m + j] = x;
           const double d = ax - lam[j] * x;
+          if (Rres) Rres[(size_t)(rb + ty) * m + j] = d;
           e2[q] = fma(d, d, e2[q]);
           a2[q] = fma(ax, ax, a2[q]);
           x2[q] = fma(x, x, x2[q]);
@@ -441,7 +443,7 @@ __global__ void k_reduce_norms(int Pr, int m, const double *__restrict__ part, d
 __global__ void k_reduce_resid(int Pr, int m, const double *__restrict__ part,
                                const double *__restrict__ lam, double emin, double emax,
                                double alpha, double *__restrict__ res, double *__restrict__ beta,
-                               DevStatus *__restrict__ status) {
+                               double *__restrict__ rnorm, DevStatus *__restrict__ status) {
   __shared__ double smax[256];
   __shared__ int scnt[256], snan[256];
   double mx = 0.0;
@@ -456,6 +458,7 @@ __global__ void k_reduce_resid(int Pr, int m, const double *__restrict__ part,
     const double r = sqrt(e) / (a > 0.0 ? sqrt(a) : 1.0);
     res[j] = r;
     beta[j] = sqrt(x);
+    if (rnorm) rnorm[j] = sqrt(e);
     const double l = lam[j];
     if (!isfinite(r) || !isfinite(l)) bad = 1;
     if (l > emin && l < emax) {
@@ -532,18 +535,18 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
     const int qm = (m + 31) / 32;
     if (qm <= 1)
       k_update_resid<1><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.res_part, rows);
+                                                     a.Rres, a.res_part, rows);
     else if (qm <= 2)
       k_update_resid<2><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.res_part, rows);
+                                                     a.Rres, a.res_part, rows);
     else if (qm <= 4)
       k_update_resid<4><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.res_part, rows);
+                                                     a.Rres, a.res_part, rows);
     else
       k_update_resid<8><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.res_part, rows);
+                                                     a.Rres, a.res_part, rows);
     k_reduce_resid<<<1, 256, 0, st>>>(pr_used, m, a.res_part, a.lam, a.emin, a.emax, a.alpha,
-                                      a.res, a.beta, a.status);
+                                      a.res, a.beta, a.rnorm, a.status);
   }
   return cudaGetLastError();
 }

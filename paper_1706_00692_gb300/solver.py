@@ -44,9 +44,10 @@ class Solver:
     """One IFEAST problem (A, interval, m0, contour, options) bound to a handle."""
 
     def __init__(self, A: CSR, emin: float, emax: float, m0: int, *, nc: int = 8,
-                 rule: str = "gl_half", inner_iters: int = 10, alpha: float = 0.0,
-                 max_outer: int = 100, tol: float = 1e-10, precision: int = _lib.FP64,
-                 device: str | int = "cuda", torch_workspace: bool = True):
+                 rule: str = "gl_half", inner: str = "gmres", inner_iters: int = 10,
+                 alpha: float = 0.0, max_outer: int = 100, tol: float = 1e-10,
+                 precision: str = "fp64", device: str | int = "cuda",
+                 torch_workspace: bool = True, verbose: bool = False):
         torch = _torch()
         self.lib = _lib.load()
         self.torch = torch
@@ -60,7 +61,9 @@ class Solver:
         self.opts.alpha = alpha
         self.opts.max_outer = max_outer
         self.opts.tol = tol
-        self.opts.precision = precision
+        self.opts.inner_solver = _lib.INNERS[inner]
+        self.opts.precision = _lib.PRECISIONS[precision]
+        self.opts.verbose = 1 if verbose else 0
         nbytes = ct.c_size_t(0)
         rc = self.lib.ifeast_workspace_bytes(self.n, A.nnz, self.m0, ct.byref(self.contour),
                                              ct.byref(self.opts), ct.byref(nbytes))

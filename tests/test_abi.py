@@ -71,8 +71,8 @@ def _opts(lib, **kw):
 
 def test_default_opts(lib):
     o = _opts(lib)
-    assert (o.inner_solver, o.inner_max_iters, o.alpha, o.max_outer, o.tol, o.precision) == \
-        (0, 10, 0.0, 100, 1e-10, 0)
+    assert (o.inner_solver, o.inner_max_iters, o.alpha, o.max_outer, o.tol, o.precision,
+            o.verbose) == (0, 10, 0.0, 100, 1e-10, 0, 0)
 
 
 def test_workspace_bytes_grows_with_basis(lib):
@@ -118,6 +118,9 @@ def test_create_rejects_bad_options(lib):
     assert _create(lib, A, opts=_opts(lib, inner_max_iters=33))[0] == _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, opts=_opts(lib, max_outer=0))[0] == _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, opts=_opts(lib, inner_solver=9))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, opts=_opts(lib, precision=1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, opts=_opts(lib, inner_solver=1, inner_max_iters=5000))[0] == \
+        _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, contour=_lib.Contour(0, 4, 1.0, 0.5))[0] == _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, contour=_lib.Contour(2, 4, 0.0, 0.5))[0] == _lib.IFEAST_ERR_UNSUPPORTED
     assert _create(lib, A, B=ct.c_void_p(1))[0] == _lib.IFEAST_ERR_UNSUPPORTED

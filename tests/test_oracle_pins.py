@@ -275,3 +275,18 @@ def test_convergence_rate_bound_exact_solves():
     for a, b in zip(errs[:-1], errs[1:]):
         if a > 1e-12:
             assert b <= 1.5 * rate * a + 1e-13
+
+
+def test_residual_form_identity_exact_solves():
+    """(zI - A)^{-1} x = (x + (zI - A)^{-1}(A x - lam x)) / (z - lam) for any
+    scalar lam: the right-hand side the shared-basis inner solver uses after
+    the first outer iteration. Checked with dense LU on a random Ritz pair."""
+    A = inputs.add_diagonal(inputs.laplacian((7, 6)), inputs.random_potential(42, 9))
+    Ad = A.to_scipy().toarray()
+    x = inputs.initial_subspace(42, 1, 3)[:, 0]
+    lam = x @ Ad @ x / (x @ x)
+    for z in [0.5 + 0.3j, 3.0 + 0.01j]:
+        M = z * np.eye(42) - Ad
+        lhs = np.linalg.solve(M, x)
+        rhs = (x + np.linalg.solve(M, Ad @ x - lam * x)) / (z - lam)
+        assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(lhs).max()
