@@ -5,6 +5,9 @@
 
 One step = one full IFEAST solve (Algorithm 2 from the seeded initial subspace
 until ||R_F|| <= 1e-10) of the workload, inputs resident on the device. The
+default workload is the 3D 7-point Laplacian on 64^3 plus a U[0,1) potential
+(n = 262,144), interior window with 52 eigenvalues, m0 = 80, 8 contour nodes,
+shared-basis MINRES inner solves in FP32 with the FP64 outer iteration. The
 metric is converged eigenpairs per second (pairs inside the interval with
 relative residual <= 1e-10, times steps, over the device time of the steps).
 Under torchrun every rank solves its own replica of the workload (no data
@@ -37,10 +40,11 @@ METRIC = "converged eigenpairs/s at residual<=1e-10"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="lap2d_50", choices=["lap2d_50"])
+    p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp64",
+                                                                 "lap2d_50"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -49,7 +53,31 @@ def make_workload(name):
     from paper_1706_00692_gb300 import inputs
     if name == "lap2d_50":
         return inputs.workload_lap2d_50(seed=0)
+    if name == "lap3d_64":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp32")
+    if name == "lap3d_64_fp64":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp64")
     raise ValueError(name)
+
+
+def measured_peaks():
+    """HBM copy bandwidth from MEASURED_PEAKS.json next to this script, else
+    the 6.8 TB/s fallback; FP64 FMA peak from the same file or 1.2 TFLOP/s."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def step_bytes(wl, elem):
+    """Algorithmic bytes of one Lanczos step launch (s > 0): read w_{s-1} and
+    v_{s-1} (the gathered rows counted once), write v_s and w_s, read the CSR
+    structure and values once."""
+    n, m0, nnz = wl.A.n, wl.m0, wl.A.nnz
+    return 4 * n * m0 * elem + 4 * (n + 1) + nnz * (4 + elem)
 
 
 class ClockSampler:
@@ -117,12 +145,34 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
-def oracle_sample(wl, budget_s=20.0):
-    """Times the CPU oracle (Algorithm 2, per-node GMRES) on the workload until
-    it converges or the time budget runs out; returns (pairs/s, sample text)."""
+def oracle_sample(wl, budget_s=20.0, gpu_stats=None):
+    """Times the CPU oracle on the workload. For the 50x50 workload it runs the
+    oracle's Algorithm 2 to convergence. For the 64^3 workload a full oracle
+    solve takes hours, so it times the oracle's shared-basis GMRES
+    (gmres_shared_basis: Arnoldi with MGS + least squares, Section 3) on a
+    bounded number of (node, column) pairs and Krylov steps, and scales the
+    time per Krylov step to the Krylov steps a full solve takes (the workload's
+    recorded count from a GPU solve). Returns (pairs/s, text)."""
     from oracle import ifeast_oracle as orc
     z, w = orc.contour_nodes(wl.rule, wl.nc, wl.emin, wl.emax)
     A = wl.A.to_scipy()
+    if wl.A.n > 100000:
+        X = wl.X0()
+        steps, pairs_done, t0 = 60, 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s and pairs_done < 64:
+            k = pairs_done % wl.nc
+            j = pairs_done // wl.nc
+            orc.gmres_shared_basis(A, X[:, j], z[k], steps)
+            pairs_done += 1
+        dt = time.perf_counter() - t0
+        per_step = dt / (pairs_done * steps)
+        total_steps = wl.krylov_steps_full_solve or 16 * 1500 * wl.nc * wl.m0
+        est = per_step * total_steps
+        pairs = wl.expected_count or 0
+        return pairs / est, (f"oracle gmres_shared_basis on {wl.name}: {pairs_done} (node, column) "
+                             f"pairs x {steps} Krylov steps in {dt:.1f} s = {per_step*1e3:.2f} ms "
+                             f"per step; scaled to {total_steps} Krylov steps of a full solve "
+                             f"({est/3600:.1f} h) for {pairs} pairs")
     t0 = time.perf_counter()
     iters = [0]
 
@@ -150,9 +200,9 @@ def run_reference(args):
     vals = []
     sample = ""
     for _ in range(args.warmup):
-        oracle_sample(wl, budget_s=5.0)
+        oracle_sample(wl, budget_s=3.0)
     for _ in range(args.steps):
-        v, sample = oracle_sample(wl, budget_s=30.0)
+        v, sample = oracle_sample(wl, budget_s=15.0)
         vals.append(v)
     value = float(np.mean(vals))
     cores = cpu_threads()
@@ -160,7 +210,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name, "n": wl.A.n, "m0": wl.m0,
-                                             "nc": wl.nc, "inner_iters": wl.inner_iters},
+                                             "nc": wl.nc, "contour": wl.rule,
+                                             "inner": wl.inner, "inner_iters": wl.inner_iters},
             "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0,
@@ -184,8 +235,9 @@ def run_ours(args):
     wl = make_workload(args.workload)
     dev = torch.device("cuda", torch.cuda.current_device())
     X0 = torch.as_tensor(wl.X0(), device=dev)
-    S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner_iters=wl.inner_iters,
-               alpha=wl.alpha, device=dev)
+    skw = dict(nc=wl.nc, rule=wl.rule, inner=wl.inner, inner_iters=wl.inner_iters,
+               alpha=wl.alpha, precision=wl.precision, device=dev)
+    S = Solver(wl.A, wl.emin, wl.emax, wl.m0, **skw)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -201,6 +253,8 @@ def run_ours(args):
         torch.distributed.barrier()
     times = []
     stats = []
+    S.set_profiling(True)
+    S.kernel_times(reset=True)
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flushed between timed steps (outside the events)
@@ -213,6 +267,8 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1))
             stats.append(S.stats())
     torch.cuda.synchronize()
+    ktimes = S.kernel_times(reset=True)
+    S.set_profiling(False)
     total_ms = float(sum(times))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -230,8 +286,7 @@ def run_ours(args):
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S2 = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule,
-                    inner_iters=wl.inner_iters, alpha=wl.alpha, device=dev)
+        S2 = Solver(wl.A, wl.emin, wl.emax, wl.m0, **skw)
         rc = S2.solve(X0h)
         l2, x2, r2 = S2.eigenpairs()
         S2.close()
@@ -241,6 +296,21 @@ def run_ours(args):
     e2e_value = e2e_pairs * world / statistics.mean(e2e_times)
     d2h = l2.nbytes + x2.nbytes + r2.nbytes
 
+    # roofline of the dominant kernel class, from the live event timings
+    peak, peak_kind = measured_peaks()
+    top = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
+    roofline = None
+    if top is not None and top[0] == "lanczos_step":
+        elem = 4 if wl.precision == "fp32" else 8
+        launches, ms = top[1]
+        nbytes = step_bytes(wl, elem)
+        achieved = nbytes / (ms / launches * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_lanczos_step", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"{peak_kind} copy bandwidth", "traffic": None,
+                    "bytes_per_launch": nbytes, "launches": launches,
+                    "us_per_launch": 1e3 * ms / launches}
+    gpu_launches = int(sum(c for c, _ in ktimes.values()))
     if rank == 0:
         st = stats[-1]
         line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world,
@@ -248,17 +318,21 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "n": wl.A.n, "nnz": wl.A.nnz, "m0": wl.m0,
-                           "nc": wl.nc, "contour": wl.rule, "inner": "gmres",
-                           "inner_iters": wl.inner_iters, "alpha": wl.alpha,
-                           "l2": "flushed between steps (256 MB write)",
-                           "outer_iters": st["outer_iters"], "pairs": pairs},
+                           "nc": wl.nc, "contour": wl.rule, "inner": wl.inner,
+                           "inner_precision": wl.precision, "inner_iters": wl.inner_iters,
+                           "alpha": wl.alpha, "l2": "flushed between steps (256 MB write)",
+                           "outer_iters": st["outer_iters"], "pairs": pairs,
+                           "krylov_steps_total": st["total_matvecs"],
+                           "krylov_steps_seq": st["seq_matvecs"]},
                 "e2e": {"value": e2e_value, "unit": "eigenpairs/s",
                         "h2d_bytes_per_step": int(csr_bytes + X0h.nbytes),
                         "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": None,
+                "gpu_launches": gpu_launches,
+                "roofline": roofline,
+                "kernel_ms": {k: {"launches": c, "ms": round(t, 3)} for k, (c, t) in ktimes.items()},
                 "clocks": clk.summary()}
         if not args.no_cpu_baseline and world == 1:
-            v, sample = oracle_sample(wl, budget_s=30.0)
+            v, sample = oracle_sample(wl, budget_s=20.0, gpu_stats=st)
             line["cpu_baseline"] = {"value": v, "unit": "eigenpairs/s", "cores": cpu_threads(),
                                     "kind": "oracle", "sample": sample}
         print(json.dumps(line), flush=True)

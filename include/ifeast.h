@@ -205,6 +205,24 @@ int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, do
 int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0,
                       const double *z);
 
+/* ---------------------------------------------------------------------------
+ * Kernel timing. When on, every kernel launch of the handle is bracketed by
+ * CUDA events on the handle's stream (a few microseconds of overhead per
+ * launch); the durations are summed per kernel class when the library next
+ * synchronises its stream.
+ * ------------------------------------------------------------------------- */
+int ifeast_set_profiling(ifeast_t h, int on);
+
+/* Copies the summed milliseconds and launch counts of the first cap kernel
+ * classes (device time between the bracketing events) into ms[] and
+ * launches[] (either may be NULL); reset != 0 clears them afterwards.
+ * Returns the number of kernel classes (21; each class is one kernel) on success; a NULL handle or a
+ * negative cap returns IFEAST_ERR_INVALID_ARG (1). */
+int ifeast_kernel_times(ifeast_t h, int cap, double *ms, int64_t *launches, int reset);
+
+/* Name of kernel class k (static storage), "unknown" out of range. */
+const char *ifeast_kernel_name(int k);
+
 #ifdef __cplusplus
 }
 #endif

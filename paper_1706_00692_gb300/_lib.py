@@ -71,6 +71,9 @@ SIGNATURES = {
                                         ct.c_void_p]),
     "ifeast_spmm_shift": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int,
                                      ct.c_void_p]),
+    "ifeast_set_profiling": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "ifeast_kernel_times": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "ifeast_kernel_name": (ct.c_char_p, [ct.c_int]),
 }
 
 _lib = None

@@ -1,0 +1,62 @@
+"""Run one IFEAST solve of a named synthetic workload and report the result.
+
+    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp64|lap2d_50]
+                                         [--max-outer M] [--inner-iters K] [--verbose]
+
+Prints one JSON line: status, eigenpairs found, largest residual, outer
+iterations, Krylov steps and wall time. Exit status 0 whenever the library
+calls succeed (a solve stopped by --max-outer before convergence included).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+from . import inputs
+from .solver import Solver
+
+
+def workload(name: str):
+    if name == "lap2d_50":
+        return inputs.workload_lap2d_50(seed=0)
+    if name == "lap3d_64":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp32")
+    if name == "lap3d_64_fp64":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp64")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def main(argv=None) -> int:
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", default="lap3d_64")
+    p.add_argument("--max-outer", type=int, default=100)
+    p.add_argument("--inner-iters", type=int, default=0, help="override the workload's cap")
+    p.add_argument("--verbose", action="store_true")
+    a = p.parse_args(argv)
+    import torch
+    wl = workload(a.workload)
+    k = a.inner_iters or wl.inner_iters
+    S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
+               inner_iters=k, alpha=wl.alpha, precision=wl.precision, max_outer=a.max_outer,
+               verbose=a.verbose)
+    X0 = torch.as_tensor(wl.X0(), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = S.solve(X0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    st = S.stats()
+    out = {"workload": wl.name, "status": rc, "seconds": dt, "outer_iters": st["outer_iters"],
+           "found": st["found"], "RF": st["RF"], "krylov_steps_total": st["total_matvecs"],
+           "krylov_steps_seq": st["seq_matvecs"]}
+    if rc in (0, 4):
+        lam, X, res = S.eigenpairs()
+        out["max_residual"] = float(res.max()) if res.size else None
+    S.close()
+    print(json.dumps(out), flush=True)
+    return 0 if rc in (0, 4) else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -49,6 +49,8 @@ struct ifeast_ctx {
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
   double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
   int *active_host = nullptr;  // pinned
+  Profiler prof;
+  bool profiling = false;
   // results
   bool solved = false;
   ifeast_stats stats{};
@@ -82,7 +84,7 @@ int device_sms() {
 }
 
 Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr,
-             bool minres, bool fp32) {
+             bool minres, bool fp32, int sms_for_plan) {
   Layout L;
   Offsets o{};
   const size_t C = (size_t)nc * m0;
@@ -112,7 +114,8 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.LV = L.take<char>((size_t)(K + 1) * n * m0 * es);
     o.LW0 = L.take<char>((size_t)n * m0 * es);
     o.LW1 = L.take<char>((size_t)n * m0 * es);
-    o.lpart = L.take<double>((size_t)tl.P * 3 * m0);
+    // partials of the step kernels: tl.P blocks (generic) or up to 2 per SM (FP32)
+    o.lpart = L.take<double>((size_t)std::max(std::max(tl.P, 2 * sms_for_plan), 4) * 3 * m0);
     o.lalpha = L.take<double>((size_t)K * m0);
     o.lbeta = L.take<double>((size_t)(K + 1) * m0);
     o.ltol = L.take<double>(C);
@@ -246,7 +249,7 @@ int ensure_device_init() {
   if (cudaGetDevice(&dev) != cudaSuccess) return IFEAST_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_init_mu);
   if (dev >= 0 && dev < 64 && !g_init_done[dev]) {
-    if (rr_init() != cudaSuccess) return IFEAST_ERR_CUDA;
+    if (rr_init() != cudaSuccess || minres_init() != cudaSuccess) return IFEAST_ERR_CUDA;
     g_init_done[dev] = true;
   }
   return IFEAST_OK;
@@ -289,6 +292,7 @@ GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q) {
   a.Q = Q;
   a.status = h->status;
   a.tl = h->tl;
+  a.prof = h->profiling ? &h->prof : nullptr;
   return a;
 }
 
@@ -321,6 +325,7 @@ RRArgs rr_args(ifeast_ctx *h, const double *Q, double *X) {
   a.status = h->status;
   a.Rres = h->minres ? h->Rres : nullptr;
   a.rnorm = h->minres ? h->rnorm : nullptr;
+  a.prof = h->profiling ? &h->prof : nullptr;
   return a;
 }
 
@@ -354,6 +359,8 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.tl = h->tl;
   a.check_every = 16;
   a.active_host = h->active_host;
+  a.P_async = 2 * h->num_sms;  // two resident blocks per SM
+  a.prof = h->profiling ? &h->prof : nullptr;
   MinresState &m = a.ms;
   m.z = h->z;
   m.w = h->w;
@@ -447,11 +454,12 @@ int ifeast_workspace_bytes(int64_t n, int64_t nnz, int m0, const ifeast_contour 
   if (rc) return rc;
   const int sms = device_sms();
   const bool minres = o->inner_solver == IFEAST_INNER_MINRES;
-  const RowTiling tl = make_tiling(n, minres ? m0 : c->nc * m0, sms);
+  RowTiling tl = make_tiling(n, minres ? 32 : c->nc * m0, sms);
+  if (minres) tl.tiles = (m0 + 31) / 32;  // row blocks cover every column
   const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
   const int Pr = Pg;
   *bytes = plan(n, nnz, m0, c->nc, o->inner_max_iters, tl, Pg, Pr, minres,
-                o->precision == IFEAST_FP32).total;
+                o->precision == IFEAST_FP32, sms).total;
   return IFEAST_OK;
 }
 
@@ -492,11 +500,13 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->num_sms = device_sms();
   h->minres = o->inner_solver == IFEAST_INNER_MINRES;
   h->fp32 = o->precision == IFEAST_FP32;
-  h->tl = make_tiling(n, h->minres ? m0 : h->C, h->num_sms);
+  h->tl = make_tiling(n, h->minres ? 32 : h->C, h->num_sms);
+  if (h->minres) h->tl.tiles = (m0 + 31) / 32;
   h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
   h->Pr = h->Pg;
   contour_host(c, h->zh, h->wh);
-  const Offsets off = plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, h->fp32);
+  const Offsets off =
+      plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, h->fp32, h->num_sms);
   if (workspace) {
     h->ws = (char *)workspace;
     h->ws_bytes = ws_bytes;
@@ -603,6 +613,11 @@ void ifeast_destroy(ifeast_t h) {
   if (h->owns_ws && h->ws) cudaFree(h->ws);
   if (h->status_host) cudaFreeHost(h->status_host);
   if (h->active_host) cudaFreeHost(h->active_host);
+  if (h->prof.events) {
+    for (int i = 0; i < 2 * h->prof.cap; ++i) cudaEventDestroy(h->prof.events[i]);
+    delete[] h->prof.events;
+    delete[] h->prof.kid;
+  }
   delete h;
 }
 
@@ -614,7 +629,8 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
   const size_t xbytes = (size_t)h->n * h->m0 * sizeof(double);
   CK(cudaMemcpyAsync(h->X, X0, xbytes,
                      x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-  CK(column_norms((int)h->n, h->m0, h->X, h->res_part, h->Pr, h->beta, h->stream));
+  CK(column_norms((int)h->n, h->m0, h->X, h->res_part, h->Pr, h->beta, h->stream,
+                  h->profiling ? &h->prof : nullptr));
   int rc = set_tolerance(h, 1.0);
   if (rc) return rc;
   int result = IFEAST_ERR_NOT_CONVERGED;
@@ -629,6 +645,7 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
     CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (h->profiling && h->prof.collect()) return IFEAST_ERR_CUDA;
     const DevStatus s = *h->status_host;
     h->stats.outer_iters = it;
     h->stats.found = s.count;
@@ -715,7 +732,8 @@ int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *
 
 int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32_t *steps) {
   if (!h || !X || !Q || !(RF >= 0.0)) return IFEAST_ERR_INVALID_ARG;
-  CK(column_norms((int)h->n, h->m0, X, h->res_part, h->Pr, h->beta, h->stream));
+  CK(column_norms((int)h->n, h->m0, X, h->res_part, h->Pr, h->beta, h->stream,
+                  h->profiling ? &h->prof : nullptr));
   int rc = set_tolerance(h, RF);
   if (rc) return rc;
   if (h->minres)
@@ -726,6 +744,7 @@ int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32
     CK(cudaMemcpyAsync(steps, h->minres ? h->lsteps : h->steps, h->C * sizeof(int),
                        cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->profiling && h->prof.collect()) return IFEAST_ERR_CUDA;
   return IFEAST_OK;
 }
 
@@ -740,6 +759,7 @@ int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, do
   if (resid)
     CK(cudaMemcpyAsync(resid, h->res, h->m0 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->profiling && h->prof.collect()) return IFEAST_ERR_CUDA;
   if (h->status_host->breakdown) return IFEAST_ERR_BREAKDOWN;
   return IFEAST_OK;
 }
@@ -752,6 +772,55 @@ int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0,
                      ncols, m0, (const double2 *)z, tl, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return IFEAST_OK;
+}
+
+int ifeast_set_profiling(ifeast_t h, int on) {
+  if (!h) return IFEAST_ERR_INVALID_ARG;
+  if (on && !h->prof.events) {
+    const int cap = 4096;
+    h->prof.events = new (std::nothrow) cudaEvent_t[2 * cap];
+    h->prof.kid = new (std::nothrow) int[cap];
+    if (!h->prof.events || !h->prof.kid) return IFEAST_ERR_OOM;
+    for (int i = 0; i < 2 * cap; ++i)
+      if (cudaEventCreate(&h->prof.events[i]) != cudaSuccess) {
+        for (int k = 0; k < i; ++k) cudaEventDestroy(h->prof.events[k]);
+        delete[] h->prof.events;
+        delete[] h->prof.kid;
+        h->prof.events = nullptr;
+        h->prof.kid = nullptr;
+        return IFEAST_ERR_CUDA;
+      }
+    h->prof.cap = cap;
+  }
+  h->prof.stream = h->stream;
+  h->prof.used = 0;
+  h->profiling = on != 0;
+  return IFEAST_OK;
+}
+
+int ifeast_kernel_times(ifeast_t h, int cap, double *ms, int64_t *launches, int reset) {
+  if (!h || cap < 0) return IFEAST_ERR_INVALID_ARG;
+  for (int k = 0; k < K_COUNT && k < cap; ++k) {
+    if (ms) ms[k] = h->prof.ms[k];
+    if (launches) launches[k] = h->prof.count[k];
+  }
+  if (reset)
+    for (int k = 0; k < K_COUNT; ++k) {
+      h->prof.ms[k] = 0.0;
+      h->prof.count[k] = 0;
+    }
+  return K_COUNT;
+}
+
+const char *ifeast_kernel_name(int k) {
+  static const char *names[K_COUNT] = {
+      "prep",           "colnorm",          "colnorm_reduce", "gmres_spmm_dot",
+      "gmres_reduce",   "gmres_orth",       "gmres_givens",   "gmres_finish",
+      "gmres_solve",    "gmres_quadrature", "lanczos_step",   "lanczos_givens",
+      "lanczos_solve",  "lanczos_coef",     "lanczos_quadrature", "rr_spmm",
+      "rr_gram",        "rr_gram_reduce",   "rr_eig",         "rr_update_resid",
+      "rr_resid_reduce"};
+  return (k >= 0 && k < K_COUNT) ? names[k] : "unknown";
 }
 
 }  // extern "C"

@@ -16,6 +16,52 @@ constexpr int kMaxLanczos = 4096;   // shared-basis (MINRES) step cap
 constexpr int kMaxNodes = 64;
 constexpr int kMaxM0 = 256;         // reduced problem solved in one CTA
 
+// Kernel classes timed by the optional profiler (CUDA events around launches).
+enum KernelId {
+  K_PREP = 0,      // basis start and least-squares state reset
+  K_NORMS,         // column-norm partials
+  K_NORMS_REDUCE,  // column-norm reduction
+  K_GM_SPMM,       // per-node GMRES: shifted SpMM + first-pass dots
+  K_GM_REDUCE,     // per-node GMRES: fixed-order partial reductions
+  K_GM_ORTH,       // per-node GMRES: Gram-Schmidt update + second-pass dots
+  K_GM_GIVENS,     // per-node GMRES: Hessenberg column, Givens, stop test
+  K_GM_FINISH,     // per-node GMRES: next basis vector
+  K_GM_SOLVE,      // per-node GMRES: back substitution
+  K_GM_QUAD,       // per-node GMRES: quadrature sum
+  K_LZ_STEP,       // shared basis: Lanczos step (SpMM + dots)
+  K_LZ_GIVENS,     // shared basis: reduction + per-node Givens
+  K_LZ_SOLVE,      // shared basis: back substitution
+  K_LZ_COEF,       // shared basis: quadrature coefficients
+  K_LZ_QUAD,       // shared basis: quadrature sum over the basis
+  K_RR_SPMM,       // Rayleigh-Ritz: A Q
+  K_RR_GRAM,       // Rayleigh-Ritz: Q^T A Q, Q^T Q partials
+  K_RR_GRAM_REDUCE,// Rayleigh-Ritz: partial reduction
+  K_RR_EIG,        // reduced generalised eigenproblem (one CTA)
+  K_RR_UPDATE,     // X = Q X_Q and residual partials
+  K_RR_RESID,      // residuals, interval count, ||R_F||
+  K_COUNT
+};
+
+struct Profiler {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t *events = nullptr;  // pool of 2 * cap events
+  int cap = 0, used = 0;
+  int *kid = nullptr;             // kernel class of each pending pair
+  double ms[K_COUNT] = {0};
+  long long count[K_COUNT] = {0};
+  void begin(int k);
+  void end();
+  int collect();                  // after a stream synchronisation
+};
+#define IFEAST_PROF_BEGIN(p, k) \
+  do {                          \
+    if (p) (p)->begin(k);       \
+  } while (0)
+#define IFEAST_PROF_END(p) \
+  do {                     \
+    if (p) (p)->end();     \
+  } while (0)
+
 // Device-side record read back by the host once per outer iteration.
 struct DevStatus {
   double RF;            // max relative residual over Ritz values inside the interval
@@ -62,6 +108,7 @@ struct GmresArgs {
   double *Q;                // n x m0 output
   DevStatus *status;        // tol_rel read from here, step counts written here
   RowTiling tl;
+  Profiler *prof;
 };
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st);
 cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
@@ -102,7 +149,10 @@ struct MinresArgs {
   MinresState ms;
   int check_every;          // steps between early-exit checks (0: never)
   int *active_host;         // pinned
+  Profiler *prof;
+  int P_async;              // max blocks of the FP32 (row, quad) step kernel
 };
+cudaError_t minres_init();  // once per device: opt-in shared-memory sizes
 cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st);
 cudaError_t convert_to_float(const double *a, float *b, size_t n, cudaStream_t st);
 
@@ -130,10 +180,11 @@ struct RRArgs {
   double *rnorm;            // m0 ||A x_j - lambda_j x_j|| (nullptr: not stored)
   double emin, emax, alpha;
   DevStatus *status;
+  Profiler *prof;
 };
 cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
 cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st);
 cudaError_t column_norms(int n, int m0, const double *X, double *part, int Pr, double *beta,
-                         cudaStream_t st);
+                         cudaStream_t st, Profiler *prof);
 
 }  // namespace ifeast

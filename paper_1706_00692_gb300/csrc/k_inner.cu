@@ -346,18 +346,31 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
   const dim3 grid(a.tl.P, a.tl.tiles);
   const size_t vstride = (size_t)a.n * a.C;
   const int K2 = a.K + 2;
+  IFEAST_PROF_BEGIN(a.prof, K_GM_SPMM);
   k_spmm_shift_dot<LMAX, true><<<grid, kThreads, 0, st>>>(
       a.n, a.C, a.m0, a.rowptr, a.colidx, a.val, a.V, vstride, s, a.z, a.done, a.W, a.part,
       a.tl.rows, K2);
+  IFEAST_PROF_END(a.prof);
+  IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 1, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H1);
+  IFEAST_PROF_END(a.prof);
+  IFEAST_PROF_BEGIN(a.prof, K_GM_ORTH);
   k_orth_update_dot<LMAX><<<grid, kThreads, 0, st>>>(a.n, a.C, a.V, vstride, s, a.H1, a.done,
                                                      a.W, a.part, a.tl.rows, K2);
+  IFEAST_PROF_END(a.prof);
+  IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 2, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H2);
+  IFEAST_PROF_END(a.prof);
+  IFEAST_PROF_BEGIN(a.prof, K_GM_GIVENS);
   k_givens<<<(a.C + 127) / 128, 128, 0, st>>>(a.C, a.m0, a.K, s, a.H1, a.H2, a.beta, a.inv_h,
                                               a.CS, a.SN, a.R, a.G, a.steps, a.done, a.status);
-  if (s + 1 < a.K)  // the last step's basis vector is never used
+  IFEAST_PROF_END(a.prof);
+  if (s + 1 < a.K) {  // the last step's basis vector is never used
+    IFEAST_PROF_BEGIN(a.prof, K_GM_FINISH);
     k_orth_finish<LMAX><<<grid, kThreads, 0, st>>>(a.n, a.C, a.V, vstride, s, a.H2, a.inv_h,
                                                    a.done, a.W, a.tl.rows);
+    IFEAST_PROF_END(a.prof);
+  }
   return cudaGetLastError();
 }
 
@@ -380,8 +393,10 @@ RowTiling make_tiling(int64_t n, int ncols, int num_sms) {
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
   if (a.K < 1 || a.K > kMaxInner) return cudaErrorInvalidValue;
   const size_t total = (size_t)a.n * a.C;
+  IFEAST_PROF_BEGIN(a.prof, K_PREP);
   k_prep<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.C, a.K, a.X, a.beta, a.V,
                                                            a.G, a.steps, a.done);
+  IFEAST_PROF_END(a.prof);
   cudaError_t e = cudaGetLastError();
   for (int s = 0; s < a.K && e == cudaSuccess; ++s) {
     if (s + 1 <= 8)
@@ -392,11 +407,15 @@ cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
       e = launch_step<32>(a, s, st);
   }
   if (e != cudaSuccess) return e;
+  IFEAST_PROF_BEGIN(a.prof, K_GM_SOLVE);
   k_solve_y<<<(a.C + 127) / 128, 128, 0, st>>>(a.C, a.m0, a.K, a.R, a.G, a.w, a.steps, a.Y,
                                                a.status);
+  IFEAST_PROF_END(a.prof);
+  IFEAST_PROF_BEGIN(a.prof, K_GM_QUAD);
   const size_t nq = (size_t)a.n * a.m0;
   k_quadrature<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.nc, a.C, a.V,
                                                              (size_t)a.n * a.C, a.Y, a.steps, a.Q);
+  IFEAST_PROF_END(a.prof);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,8 @@
 // <v,w>^2/<v,v> (the squared norm of w_s - alpha_s v_s, using the actual
 // <v,v> so that rounding in earlier normalisations does not feed back), and
 // advances every node's Givens QR.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace ifeast {
@@ -76,68 +78,311 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
 }
 
 // One Lanczos step s on every column still running.
-template <typename T>
+//
+// A warp owns a contiguous segment of rows; lane l handles the columns
+// j = l + 32 q (q < NJ) of every row. Rows are taken in packs whose non-zeros
+// (at most 32) are loaded one per lane, then the gathers of 8 non-zeros are
+// issued back to back before they are consumed, so that many independent
+// loads are in flight per warp. The values of the row itself (w_{s-1}[r],
+// v_{s-1}[r]) come from the gather of its diagonal entry when it has one.
+template <typename T, int NJ, bool FIRST>
 __global__ void __launch_bounds__(kThreads)
 k_lanczos_step(int n, int m0, int s, const int32_t *__restrict__ rowptr,
                const int32_t *__restrict__ colidx, const T *__restrict__ val,
                T *__restrict__ V, const T *__restrict__ Wprev, T *__restrict__ Wout,
                const double *__restrict__ alpha, const double *__restrict__ beta,
                const int *__restrict__ coldone, double *__restrict__ part, int rows) {
+  constexpr unsigned FULL = 0xffffffffu;
+  // non-zeros gathered per batch (all issued before use), sized to the registers
+  constexpr int EB = sizeof(T) == 4 ? (NJ <= 3 ? 8 : (NJ <= 5 ? 4 : 2))
+                                    : (NJ <= 2 ? 8 : (NJ <= 4 ? 4 : 2));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = blockIdx.y * 32 + lane;
   const size_t vs = (size_t)n * m0;
-  const bool act = j < m0 && coldone[j] == 0;
-  T a_prev = 0, inv_b = 1, b_s = 0;
-  if (act && s > 0) {
-    a_prev = (T)alpha[(size_t)(s - 1) * m0 + j];
-    b_s = (T)beta[(size_t)s * m0 + j];
-    inv_b = (T)(1.0 / beta[(size_t)s * m0 + j]);
-  }
   T *__restrict__ Vs = V + (size_t)s * vs;
-  const T *__restrict__ Vp = s > 0 ? V + (size_t)(s - 1) * vs : V;
-  T vv = 0, vw = 0, ww = 0;
-  if (act) {
-    const int r0 = blockIdx.x * rows, r1 = min(n, r0 + rows);
-    for (int r = r0 + warp; r < r1; r += kWarps) {
-      const size_t rj = (size_t)r * m0 + j;
-      T v, vprev = 0;
-      if (s == 0) {
-        v = Vs[rj];
+  // FIRST: gather v_0 = V[0] only; else gather w_{s-1} and v_{s-1}
+  const T *__restrict__ G1 = FIRST ? Vs : Wprev;
+  const T *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
+  bool aq[NJ];
+  T ap[NJ], ib[NJ], bs[NJ], vv[NJ], vw[NJ], ww[NJ];
+#pragma unroll
+  for (int q = 0; q < NJ; ++q) {
+    const int j = lane + 32 * q;
+    aq[q] = j < m0 && coldone[j] == 0;
+    ap[q] = 0;
+    ib[q] = 1;
+    bs[q] = 0;
+    if (!FIRST && aq[q]) {
+      ap[q] = (T)alpha[(size_t)(s - 1) * m0 + j];
+      bs[q] = (T)beta[(size_t)s * m0 + j];
+      ib[q] = (T)(1.0 / beta[(size_t)s * m0 + j]);
+    }
+    vv[q] = vw[q] = ww[q] = 0;
+  }
+  const int b0 = blockIdx.x * rows, b1 = min(n, b0 + rows);
+  const int seg = (rows + kWarps - 1) / kWarps;
+  const int rs = min(b1, b0 + warp * seg), re = min(b1, rs + seg);
+
+  // finishes row r: v_s[r], w_s[r] from the accumulated products and the
+  // row's own w_{s-1}, v_{s-1} values (o1, o2)
+  auto finish = [&](int r, const T (&acc1)[NJ], const T (&acc2)[NJ], const T (&o1)[NJ],
+                    const T (&o2)[NJ]) {
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+      if (!aq[q]) continue;
+      const size_t rj = (size_t)r * m0 + lane + 32 * q;
+      T v, w;
+      if (FIRST) {
+        v = o1[q];
+        w = acc1[q];
       } else {
-        vprev = Vp[rj];
-        v = (Wprev[rj] - a_prev * vprev) * inv_b;
+        v = (o1[q] - ap[q] * o2[q]) * ib[q];
+        w = (acc1[q] - ap[q] * acc2[q]) * ib[q] - bs[q] * o2[q];
         Vs[rj] = v;
       }
-      T w = -b_s * vprev;
-      const int pb = rowptr[r], pe = rowptr[r + 1];
-      if (s == 0) {
-#pragma unroll 4
-        for (int p = pb; p < pe; ++p) w += val[p] * Vs[(size_t)colidx[p] * m0 + j];
-      } else {
-        T acc = 0;
-#pragma unroll 4
-        for (int p = pb; p < pe; ++p) {
-          const size_t cj = (size_t)colidx[p] * m0 + j;
-          acc += val[p] * (Wprev[cj] - a_prev * Vp[cj]);
-        }
-        w += acc * inv_b;
-      }
       Wout[rj] = w;
-      vv += v * v;
-      vw += v * w;
-      ww += w * w;
+      vv[q] += v * v;
+      vw[q] += v * w;
+      ww[q] += w * w;
+    }
+  };
+  auto load_own = [&](int r, T (&o1)[NJ], T (&o2)[NJ]) {
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+      const size_t rj = (size_t)r * m0 + lane + 32 * q;
+      o1[q] = aq[q] ? G1[rj] : (T)0;
+      o2[q] = (aq[q] && !FIRST) ? G2[rj] : (T)0;
+    }
+  };
+
+  int r = rs;
+  while (r < re) {
+    const int lim = re - r;  // rows left in the segment (>= 1)
+    const int rp = lane <= lim ? rowptr[r + lane] : 0x7fffffff;
+    const int base = __shfl_sync(FULL, rp, 0);
+    const unsigned okm = __ballot_sync(FULL, lane <= lim && rp - base <= 32);
+    int R = __popc(okm) - 1;  // rows [r, r+R) hold at most 32 non-zeros
+    if (R < 1) R = 1;         // a single row with more than 32: done in chunks
+    const int nz_end = __shfl_sync(FULL, rp, R);
+    int row = 0;
+    int row_end = __shfl_sync(FULL, rp, 1);
+    T acc1[NJ], acc2[NJ], o1[NJ], o2[NJ];
+    bool have_own = false;
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) acc1[q] = acc2[q] = o1[q] = o2[q] = 0;
+    while (row < R && row_end == base) {  // empty rows at the start of the pack
+      load_own(r + row, o1, o2);
+      finish(r + row, acc1, acc2, o1, o2);
+      ++row;
+      row_end = row < R ? __shfl_sync(FULL, rp, row + 1) : 0x7fffffff;
+    }
+    for (int cb = base; cb < nz_end; cb += 32) {
+      const int cnt = min(32, nz_end - cb);
+      int ci = 0;
+      T cv = 0;
+      if (lane < cnt) {
+        ci = colidx[cb + lane];
+        cv = val[cb + lane];
+      }
+#pragma unroll
+      for (int e0 = 0; e0 < 32; e0 += EB) {
+        if (e0 >= cnt) break;
+        T g1[EB][NJ], g2[EB][NJ];
+        int cs[EB];
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+          const int c = __shfl_sync(FULL, ci, e0 + e);
+          cs[e] = c;
+#pragma unroll
+          for (int q = 0; q < NJ; ++q) {
+            const size_t cj = (size_t)c * m0 + lane + 32 * q;
+            const bool ld = e0 + e < cnt && aq[q];
+            g1[e][q] = ld ? G1[cj] : (T)0;
+            g2[e][q] = (ld && !FIRST) ? G2[cj] : (T)0;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+          const T a = __shfl_sync(FULL, cv, e0 + e);
+          if (e0 + e < cnt) {
+            const int gr = r + row;
+#pragma unroll
+            for (int q = 0; q < NJ; ++q) {
+              acc1[q] += a * g1[e][q];
+              if (!FIRST) acc2[q] += a * g2[e][q];
+            }
+            if (cs[e] == gr) {
+              have_own = true;
+#pragma unroll
+              for (int q = 0; q < NJ; ++q) {
+                o1[q] = g1[e][q];
+                o2[q] = g2[e][q];
+              }
+            }
+            while (cb + e0 + e + 1 == row_end) {  // last non-zero of row gr (and empty rows after it)
+              if (!have_own) load_own(r + row, o1, o2);
+              finish(r + row, acc1, acc2, o1, o2);
+#pragma unroll
+              for (int q = 0; q < NJ; ++q) acc1[q] = acc2[q] = 0;
+              have_own = false;
+              ++row;
+              row_end = row < R ? __shfl_sync(FULL, rp, row + 1) : 0x7fffffff;
+            }
+          }
+        }
+      }
+    }
+    r += R;
+  }
+  __shared__ double red[3][kWarps][32 * NJ];
+#pragma unroll
+  for (int q = 0; q < NJ; ++q) {
+    red[0][warp][lane + 32 * q] = (double)vv[q];
+    red[1][warp][lane + 32 * q] = (double)vw[q];
+    red[2][warp][lane + 32 * q] = (double)ww[q];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 3 * 32 * NJ; t += kThreads) {
+    const int which = t / (32 * NJ), j = t % (32 * NJ);
+    if (j < m0) {
+      double acc = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) acc += red[which][w][j];
+      part[((size_t)blockIdx.x * 3 + which) * m0 + j] = acc;
     }
   }
-  __shared__ double red[3][kWarps][32];
-  red[0][warp][lane] = (double)vv;
-  red[1][warp][lane] = (double)vw;
-  red[2][warp][lane] = (double)ww;
-  __syncthreads();
-  if (warp < 3 && j < m0) {
-    double t = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 Lanczos step for m0 % 4 == 0: one thread per (row, four-column quad).
+// Threads walk the rows grid-stride, so at any moment the whole grid works on
+// one window of consecutive rows and the neighbour rows a stencil-like matrix
+// gathers (near and far diagonals) are still in L2 from the previous window.
+// Each row's non-zeros are taken in groups of kVG: the group's indices and
+// values are loaded together, then all of its float4 gathers are issued before
+// they are used. Same recurrence as k_lanczos_step.
+// ---------------------------------------------------------------------------
+constexpr int kVG = 8;        // non-zeros per gather group
+constexpr int kVThreads = 256;
+
+__device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+template <bool FIRST>
+__global__ void __launch_bounds__(kVThreads, 2)
+k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
+                   const int32_t *__restrict__ colidx, const float *__restrict__ val,
+                   float *__restrict__ V, const float *__restrict__ Wprev,
+                   float *__restrict__ Wout, const double *__restrict__ alpha,
+                   const double *__restrict__ beta, const int *__restrict__ coldone,
+                   double *__restrict__ part, int stride_items) {
+  const int MQ = m0 >> 2;
+  const size_t vs = (size_t)n * m0;
+  float *__restrict__ Vs = V + (size_t)s * vs;
+  const float *__restrict__ G1 = FIRST ? Vs : Wprev;
+  const float *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
+  const int gt = blockIdx.x * kVThreads + threadIdx.x;
+  const bool thr = gt < stride_items;
+  const int q = thr ? gt % MQ : 0;
+  const int rstep = stride_items / MQ;
+  bool act[4];
+  bool qact = false;
+  float ap[4] = {0.f, 0.f, 0.f, 0.f}, ib[4] = {1.f, 1.f, 1.f, 1.f}, bs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) t += red[warp][w][lane];
-    part[((size_t)blockIdx.x * 3 + warp) * m0 + j] = t;
+  for (int i = 0; i < 4; ++i) {
+    const int j = 4 * q + i;
+    act[i] = thr && coldone[j] == 0;
+    qact = qact || act[i];
+    if (!FIRST && act[i]) {
+      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
+      bs[i] = (float)beta[(size_t)s * m0 + j];
+      ib[i] = (float)(1.0 / beta[(size_t)s * m0 + j]);
+    }
+  }
+  const bool all4 = act[0] && act[1] && act[2] && act[3];
+  float vv[4] = {0.f, 0.f, 0.f, 0.f}, vw[4] = {0.f, 0.f, 0.f, 0.f}, ww[4] = {0.f, 0.f, 0.f, 0.f};
+  if (qact) {
+    for (int r = gt / MQ; r < n; r += rstep) {
+      const size_t off = (size_t)r * m0 + 4 * q;
+      const int pb = rowptr[r], pe = rowptr[r + 1];
+      const float4 o1 = *reinterpret_cast<const float4 *>(G1 + off);
+      float4 o2 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!FIRST) o2 = *reinterpret_cast<const float4 *>(G2 + off);
+      float4 acc1 = make_float4(0.f, 0.f, 0.f, 0.f), acc2 = acc1;
+      for (int p0 = pb; p0 < pe; p0 += kVG) {
+        int c[kVG];
+        float a[kVG];
+#pragma unroll
+        for (int u = 0; u < kVG; ++u) {
+          const bool in = p0 + u < pe;
+          c[u] = in ? colidx[p0 + u] : r;
+          a[u] = in ? val[p0 + u] : 0.f;
+        }
+        float4 g1[kVG], g2[kVG];
+#pragma unroll
+        for (int u = 0; u < kVG; ++u) {
+          const bool in = p0 + u < pe;
+          const size_t co = (size_t)c[u] * m0 + 4 * q;
+          g1[u] = in ? *reinterpret_cast<const float4 *>(G1 + co) : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (!FIRST)
+            g2[u] = in ? *reinterpret_cast<const float4 *>(G2 + co) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kVG; ++u) {
+          acc1 = f4fma(a[u], g1[u], acc1);
+          if (!FIRST) acc2 = f4fma(a[u], g2[u], acc2);
+        }
+      }
+      const float o1a[4] = {o1.x, o1.y, o1.z, o1.w}, o2a[4] = {o2.x, o2.y, o2.z, o2.w};
+      const float a1a[4] = {acc1.x, acc1.y, acc1.z, acc1.w}, a2a[4] = {acc2.x, acc2.y, acc2.z, acc2.w};
+      float v[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (FIRST) {
+          v[i] = o1a[i];
+          w[i] = a1a[i];
+        } else {
+          v[i] = (o1a[i] - ap[i] * o2a[i]) * ib[i];
+          w[i] = (a1a[i] - ap[i] * a2a[i]) * ib[i] - bs[i] * o2a[i];
+        }
+        if (act[i]) {
+          vv[i] = fmaf(v[i], v[i], vv[i]);
+          vw[i] = fmaf(v[i], w[i], vw[i]);
+          ww[i] = fmaf(w[i], w[i], ww[i]);
+        }
+      }
+      if (all4) {
+        if (!FIRST) *reinterpret_cast<float4 *>(Vs + off) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(Wout + off) = make_float4(w[0], w[1], w[2], w[3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (act[i]) {
+            if (!FIRST) Vs[off + i] = v[i];
+            Wout[off + i] = w[i];
+          }
+      }
+    }
+  }
+  // block partials per column: thread t holds columns 4 q(t) .. 4 q(t) + 3;
+  // summed over the block's threads in thread order (fixed order)
+  __shared__ float red[kVThreads][13];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    red[threadIdx.x][3 * i + 0] = vv[i];
+    red[threadIdx.x][3 * i + 1] = vw[i];
+    red[threadIdx.x][3 * i + 2] = ww[i];
+  }
+  __syncthreads();
+  const int base_q = (blockIdx.x * kVThreads) % MQ;
+  for (int t = threadIdx.x; t < 3 * m0; t += kVThreads) {
+    const int k = t / m0, j = t % m0;
+    const int qj = j >> 2, ij = j & 3;
+    // threads of this block with q == qj: local index l with (base_q + l) % MQ == qj
+    double acc = 0.0;
+    for (int l = (qj - base_q + MQ) % MQ; l < kVThreads; l += MQ)
+      if (blockIdx.x * kVThreads + l < stride_items) acc += (double)red[l][3 * ij + k];
+    part[((size_t)blockIdx.x * 3 + k) * m0 + j] = acc;
   }
 }
 
@@ -341,9 +586,118 @@ __global__ void k_lz_quadrature(int n, int m0, const T *__restrict__ V, const do
   Q[idx] = cx[j] * X[idx] + (double)acc;
 }
 
+// FP32 basis, m0 % 4 == 0: four columns per thread, eight basis vectors in
+// flight. A column only takes the basis vectors its own solves built
+// (l < Sj[j]); later ones were not written for it and are never multiplied.
+__global__ void __launch_bounds__(256)
+k_lz_quadrature4(int n, int m0, const float *__restrict__ V, const double *__restrict__ coef,
+                 const double *__restrict__ cx, const int *__restrict__ Sj,
+                 const double *__restrict__ X, double *__restrict__ Q) {
+  const size_t i4 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nq = (size_t)n * m0 / 4;
+  if (i4 >= nq) return;
+  const int j0 = (int)((i4 * 4) % m0);
+  const int s0 = Sj[j0], s1 = Sj[j0 + 1], s2 = Sj[j0 + 2], s3 = Sj[j0 + 3];
+  const int S = max(max(s0, s1), max(s2, s3));
+  const size_t vq = (size_t)n * m0 / 4;  // basis stride in float4
+  const float4 *__restrict__ V4 = reinterpret_cast<const float4 *>(V) + i4;
+  float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+  int l = 0;
+  for (; l + 8 <= S; l += 8) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = V4[(size_t)(l + u) * vq];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int ll = l + u;
+      const double *c = coef + (size_t)ll * m0 + j0;
+      ax = ll < s0 ? fmaf((float)c[0], v[u].x, ax) : ax;
+      ay = ll < s1 ? fmaf((float)c[1], v[u].y, ay) : ay;
+      az = ll < s2 ? fmaf((float)c[2], v[u].z, az) : az;
+      aw = ll < s3 ? fmaf((float)c[3], v[u].w, aw) : aw;
+    }
+  }
+  for (; l < S; ++l) {
+    const float4 v = V4[(size_t)l * vq];
+    const double *c = coef + (size_t)l * m0 + j0;
+    ax = l < s0 ? fmaf((float)c[0], v.x, ax) : ax;
+    ay = l < s1 ? fmaf((float)c[1], v.y, ay) : ay;
+    az = l < s2 ? fmaf((float)c[2], v.z, az) : az;
+    aw = l < s3 ? fmaf((float)c[3], v.w, aw) : aw;
+  }
+  const size_t e = i4 * 4;
+  Q[e + 0] = cx[j0 + 0] * X[e + 0] + (double)ax;
+  Q[e + 1] = cx[j0 + 1] * X[e + 1] + (double)ay;
+  Q[e + 2] = cx[j0 + 2] * X[e + 2] + (double)az;
+  Q[e + 3] = cx[j0 + 3] * X[e + 3] + (double)aw;
+}
+
 __global__ void k_to_float(size_t n, const double *__restrict__ a, float *__restrict__ b) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
+}
+
+template <typename T, int NJ>
+void launch_step_nj(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo, const T *val,
+                    cudaStream_t st) {
+  if (s == 0)
+    k_lanczos_step<T, NJ, true><<<a.tl.P, kThreads, 0, st>>>(a.n, a.m0, s, a.rowptr, a.colidx,
+                                                            val, V, Wp, Wo, a.alpha, a.beta,
+                                                            a.ms.coldone, a.part, a.tl.rows);
+  else
+    k_lanczos_step<T, NJ, false><<<a.tl.P, kThreads, 0, st>>>(a.n, a.m0, s, a.rowptr, a.colidx,
+                                                             val, V, Wp, Wo, a.alpha, a.beta,
+                                                             a.ms.coldone, a.part, a.tl.rows);
+}
+
+bool use_vec_step(const MinresArgs &a) { return a.fp32 && a.m0 % 4 == 0 && a.m0 <= 1024; }
+
+// Blocks of k_lanczos_step_vec and the number of (row, quad) items the grid
+// covers per sweep (a multiple of m0 / 4).
+void vec_grid(const MinresArgs &a, int &blocks, int &stride_items) {
+  const int MQ = a.m0 / 4;
+  const long long need = (long long)a.n * MQ;
+  long long b = std::min<long long>((need + kVThreads - 1) / kVThreads, (long long)a.P_async);
+  if (b < 1) b = 1;
+  blocks = (int)b;
+  stride_items = (int)((b * kVThreads) / MQ * MQ);
+  if (stride_items < MQ) {  // fewer threads than one row needs: one more block
+    blocks = (MQ + kVThreads - 1) / kVThreads;
+    stride_items = (blocks * kVThreads) / MQ * MQ;
+  }
+}
+
+template <typename T>
+cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo,
+                                const T *val, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (use_vec_step(a)) {
+      int blocks, stride_items;
+      vec_grid(a, blocks, stride_items);
+      if (s == 0)
+        k_lanczos_step_vec<true><<<blocks, kVThreads, 0, st>>>(
+            a.n, a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,
+            a.part, stride_items);
+      else
+        k_lanczos_step_vec<false><<<blocks, kVThreads, 0, st>>>(
+            a.n, a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,
+            a.part, stride_items);
+      return cudaGetLastError();
+    }
+  }
+  const int nj = (a.m0 + 31) / 32;
+  switch (nj) {
+    case 1: launch_step_nj<T, 1>(a, s, V, Wp, Wo, val, st); break;
+    case 2: launch_step_nj<T, 2>(a, s, V, Wp, Wo, val, st); break;
+    case 3: launch_step_nj<T, 3>(a, s, V, Wp, Wo, val, st); break;
+    case 4: launch_step_nj<T, 4>(a, s, V, Wp, Wo, val, st); break;
+    case 5: launch_step_nj<T, 5>(a, s, V, Wp, Wo, val, st); break;
+    case 6: launch_step_nj<T, 6>(a, s, V, Wp, Wo, val, st); break;
+    case 7: launch_step_nj<T, 7>(a, s, V, Wp, Wo, val, st); break;
+    case 8: launch_step_nj<T, 8>(a, s, V, Wp, Wo, val, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -354,39 +708,60 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   const T *val = (const T *)a.val_t;
   const size_t pc = (size_t)a.nc * a.m0;
   const size_t g0 = nm > pc ? nm : pc;
+  IFEAST_PROF_BEGIN(a.prof, K_PREP);
   k_lz_prep<T><<<(unsigned)((g0 + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.nc, a.K, a.rhs, a.rnorm,
                                                              V, a.beta, a.ms);
-  const dim3 grid(a.tl.P, a.tl.tiles);
+  IFEAST_PROF_END(a.prof);
   const double brk2 = sizeof(T) == 4 ? 1e-6 : 1e-16;
+  int step_blocks = a.tl.P;
+  if (sizeof(T) == 4 && use_vec_step(a)) {
+    int stride_items;
+    vec_grid(a, step_blocks, stride_items);
+  }
   cudaError_t e = cudaGetLastError();
   int s = 0;
   for (; s < a.K && e == cudaSuccess; ++s) {
     const bool check = a.check_every > 0 && (s + 1) % a.check_every == 0 && s + 1 < a.K;
-    k_lanczos_step<T><<<grid, kThreads, 0, st>>>(a.n, a.m0, s, a.rowptr, a.colidx, val, V,
-                                                  W[(s + 1) & 1], W[s & 1], a.alpha, a.beta,
-                                                  a.ms.coldone, a.part, a.tl.rows);
-    if (check) e = cudaMemsetAsync(a.ms.active, 0, sizeof(int), st);
-    k_lanczos_givens<<<a.tl.tiles, kThreads, 0, st>>>(a.tl.P, a.m0, a.nc, a.K, s, a.part,
+    IFEAST_PROF_BEGIN(a.prof, K_LZ_STEP);
+    e = launch_lanczos_step<T>(a, s, V, W[(s + 1) & 1], W[s & 1], val, st);
+    IFEAST_PROF_END(a.prof);
+    if (check && e == cudaSuccess) e = cudaMemsetAsync(a.ms.active, 0, sizeof(int), st);
+    IFEAST_PROF_BEGIN(a.prof, K_LZ_GIVENS);
+    k_lanczos_givens<<<a.tl.tiles, kThreads, 0, st>>>(step_blocks, a.m0, a.nc, a.K, s, a.part,
                                                       a.alpha, a.beta, a.ms, brk2);
+    IFEAST_PROF_END(a.prof);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (check && e == cudaSuccess) {
       // stop early once no column is still running (one small read-back)
       e = cudaMemcpyAsync(a.active_host, a.ms.active, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess && a.prof && a.prof->collect()) e = cudaErrorUnknown;
       if (e == cudaSuccess && *a.active_host == 0) break;
     }
   }
   if (e != cudaSuccess) return e;
+  IFEAST_PROF_BEGIN(a.prof, K_LZ_SOLVE);
   k_lz_solve<<<(unsigned)((pc + 127) / 128), 128, 0, st>>>(a.m0, a.nc, a.K, a.ms, a.Yc);
+  IFEAST_PROF_END(a.prof);
   const size_t kc = (size_t)a.K * a.m0;
+  IFEAST_PROF_BEGIN(a.prof, K_LZ_COEF);
   k_lz_coef<<<(unsigned)((kc + 255) / 256), 256, 0, st>>>(a.m0, a.nc, a.K, a.ms, a.Yc, a.coef,
                                                            a.cx, a.Sj);
-  k_lz_quadrature<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, V, a.coef, a.cx,
-                                                                   a.Sj, a.X, a.Q);
+  IFEAST_PROF_END(a.prof);
+  IFEAST_PROF_BEGIN(a.prof, K_LZ_QUAD);
+  if (sizeof(T) == 4 && a.m0 % 4 == 0)
+    k_lz_quadrature4<<<(unsigned)((nm / 4 + 255) / 256), 256, 0, st>>>(
+        a.n, a.m0, (const float *)V, a.coef, a.cx, a.Sj, a.X, a.Q);
+  else
+    k_lz_quadrature<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, V, a.coef, a.cx,
+                                                                     a.Sj, a.X, a.Q);
+  IFEAST_PROF_END(a.prof);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t minres_init() { return cudaSuccess; }
 
 cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st) {
   if (a.fp32) return run_minres<float>(a, st);

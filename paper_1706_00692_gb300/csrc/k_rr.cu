@@ -8,6 +8,7 @@
 //   update_resid   X = Q X_Q, AX = AQ X_Q (AX never stored) and block partials
 //                  of ||AX_j - lam_j X_j||^2, ||AX_j||^2, ||X_j||^2
 //   reduce_resid   residuals, interval count, ||R_F||, next inner tolerance
+#include <algorithm>
 #include <cfloat>
 
 #include "internal.h"
@@ -17,6 +18,7 @@ namespace ifeast {
 namespace {
 
 constexpr int kGramRows = 32;  // rows of Q / AQ staged in shared memory at a time
+constexpr size_t kEigSmem = 200 * 1024;  // dynamic shared memory of the reduced eigensolver
 
 // AQ = A Q: warp per row, lane per column (32-column tiles).
 __global__ void __launch_bounds__(kThreads)
@@ -178,17 +180,21 @@ __device__ int cholesky_inplace(double *L, int m, int *flag) {
 // Generalised symmetric eigenproblem A_Q X = B_Q X Lambda in one CTA.
 __global__ void __launch_bounds__(512)
 k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ Bq,
-              double *__restrict__ L, double *__restrict__ Cg, double *__restrict__ U,
+              double *__restrict__ Lg, double *__restrict__ Cg, double *__restrict__ Ug,
               double *__restrict__ XQ, double *__restrict__ lam, DevStatus *__restrict__ status,
-              int use_smem) {
+              int smem_mats) {
+  // smem_mats = how many of (C, U, L) live in shared memory (in that order)
   extern __shared__ double smem[];
+  const size_t mm_ = (size_t)m * m;
+  double *Cm = smem_mats >= 1 ? smem : Cg;
+  double *U = smem_mats >= 2 ? smem + mm_ : Ug;
+  double *L = smem_mats >= 3 ? smem + 2 * mm_ : Lg;
   __shared__ double red[32];
   __shared__ int flag;
   __shared__ double rot_c[kMaxM0 / 2], rot_s[kMaxM0 / 2];
   __shared__ int rot_a[kMaxM0 / 2], rot_b[kMaxM0 / 2];
   __shared__ double evals[kMaxM0];
   __shared__ int rank[kMaxM0];
-  double *Cm = use_smem ? smem : Cg;
   const int tid = threadIdx.x, nth = blockDim.x;
   const size_t mm = (size_t)m * m;
 
@@ -493,7 +499,7 @@ cudaError_t rr_init() {
                                        2 * kGramRows * kMaxM0 * (int)sizeof(double));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              160 * 1024);
+                              (int)kEigSmem);
 }
 
 cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
@@ -504,8 +510,10 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
   {
     const int tiles = (m + 31) / 32;
     const int rows = (a.n + a.Pg - 1) / a.Pg;
+    IFEAST_PROF_BEGIN(a.prof, K_RR_SPMM);
     k_spmm_real<<<dim3((a.n + rows - 1) / rows, tiles), kThreads, 0, st>>>(
         a.n, m, a.rowptr, a.colidx, a.val, a.Q, a.AQ, rows);
+    IFEAST_PROF_END(a.prof);
   }
   // Gram partials
   {
@@ -514,17 +522,23 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
     const int gy = (ntiles + kThreads - 1) / kThreads;
     const int rows = (a.n + a.Pg - 1) / a.Pg;
     const size_t smem = 2 * (size_t)kGramRows * mp * sizeof(double);
+    IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM);
     k_gram<<<dim3((a.n + rows - 1) / rows, gy), kThreads, smem, st>>>(a.n, m, mp, a.Q, a.AQ,
                                                                      a.gram_part, rows);
+    IFEAST_PROF_END(a.prof);
     const int pg_used = (a.n + rows - 1) / rows;
+    IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM_REDUCE);
     k_reduce_gram<<<(m * m + 255) / 256, 256, 0, st>>>(pg_used, m, mp, a.gram_part, a.Aq, a.Bq);
+    IFEAST_PROF_END(a.prof);
   }
   // reduced eigenproblem
   {
-    const size_t need = (size_t)m * m * sizeof(double);
-    const int use_smem = need <= 160 * 1024;
-    k_reduced_eig<<<1, 512, use_smem ? need : 0, st>>>(m, a.Aq, a.Bq, a.L, a.Cm, a.U, a.XQ,
-                                                       a.lam, a.status, use_smem);
+    const size_t mat = (size_t)m * m * sizeof(double);
+    const int nmat = (int)std::min<size_t>(3, kEigSmem / mat);
+    IFEAST_PROF_BEGIN(a.prof, K_RR_EIG);
+    k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, a.Aq, a.Bq, a.L, a.Cm, a.U, a.XQ, a.lam,
+                                              a.status, nmat);
+    IFEAST_PROF_END(a.prof);
   }
   // X = Q X_Q and residual partials
   {
@@ -533,6 +547,7 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
     const size_t smem = 2 * 8 * (size_t)m * sizeof(double);
     const dim3 blk(32, 8);
     const int qm = (m + 31) / 32;
+    IFEAST_PROF_BEGIN(a.prof, K_RR_UPDATE);
     if (qm <= 1)
       k_update_resid<1><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
                                                      a.Rres, a.res_part, rows);
@@ -545,19 +560,49 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
     else
       k_update_resid<8><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
                                                      a.Rres, a.res_part, rows);
+    IFEAST_PROF_END(a.prof);
+    IFEAST_PROF_BEGIN(a.prof, K_RR_RESID);
     k_reduce_resid<<<1, 256, 0, st>>>(pr_used, m, a.res_part, a.lam, a.emin, a.emax, a.alpha,
                                       a.res, a.beta, a.rnorm, a.status);
+    IFEAST_PROF_END(a.prof);
   }
   return cudaGetLastError();
 }
 
 cudaError_t column_norms(int n, int m, const double *X, double *part, int Pr, double *beta,
-                         cudaStream_t st) {
+                         cudaStream_t st, Profiler *prof) {
   const int rows = (n + Pr - 1) / Pr;
   const int pr_used = (n + rows - 1) / rows;
+  IFEAST_PROF_BEGIN(prof, K_NORMS);
   k_colnorm_part<<<dim3(pr_used, (m + 31) / 32), kThreads, 0, st>>>(n, m, X, part, rows);
+  IFEAST_PROF_END(prof);
+  IFEAST_PROF_BEGIN(prof, K_NORMS_REDUCE);
   k_reduce_norms<<<(m + 127) / 128, 128, 0, st>>>(pr_used, m, part, beta);
+  IFEAST_PROF_END(prof);
   return cudaGetLastError();
+}
+
+void Profiler::begin(int k) {
+  if (used >= cap) return;  // pool full: the launch goes untimed
+  kid[used] = k;
+  cudaEventRecord(events[2 * used], stream);
+}
+
+void Profiler::end() {
+  if (used >= cap) return;
+  cudaEventRecord(events[2 * used + 1], stream);
+  ++used;
+}
+
+int Profiler::collect() {
+  for (int i = 0; i < used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, events[2 * i], events[2 * i + 1]) != cudaSuccess) return 1;
+    ms[kid[i]] += t;
+    count[kid[i]] += 1;
+  }
+  used = 0;
+  return 0;
 }
 
 }  // namespace ifeast

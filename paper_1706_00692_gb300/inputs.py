@@ -161,6 +161,11 @@ class Workload:
     alpha: float
     seed: int
     expected_count: int | None = None
+    inner: str = "gmres"
+    precision: str = "fp64"
+    # Krylov steps over all (node, column) pairs of one full solve, as measured
+    # on the GPU path; scales timed samples of the CPU oracle to a full solve
+    krylov_steps_full_solve: int | None = None
 
     def X0(self) -> np.ndarray:
         return initial_subspace(self.A.n, self.m0, self.seed)
@@ -191,3 +196,26 @@ def workload_lap3d_pot(N: int = 64, seed: int = 0, m0: int = 80, first: int = 10
     A = add_diagonal_fast(laplacian((N, N, N)), random_potential(N ** 3, seed + 1))
     return Workload(f"lap3d_{N}^3_pot_interior_m0_{m0}_gl{nc}", A, emin, emax, m0=m0, nc=nc,
                     rule="gl_half", inner_iters=inner_iters, alpha=alpha, seed=seed)
+
+
+# Interior window of the 64^3 Laplacian + U[0,1) potential (potential seed 1):
+# both endpoints sit in spectral gaps of at least 2.7e-4 (about 1/40 of the
+# window width) found by a converged run with a wider subspace; the window
+# holds 52 eigenvalues, the ~50 of the workload definition.
+LAP3D_64_WINDOW = (0.89869022, 0.91001238)
+
+
+def workload_lap3d_64_interior(seed: int = 0, precision: str = "fp32") -> Workload:
+    """3D 7-point Laplacian on 64^3 (n = 262,144) plus a U[0,1) diagonal
+    potential, interior window with 52 eigenvalues, m0 = 80, 8 trapezoid nodes
+    on the upper half circle, shared-basis MINRES inner solves (at most 1500
+    Lanczos steps, tolerance alpha = 1e-2 of ||R_F||)."""
+    N = 64
+    A = add_diagonal_fast(laplacian((N, N, N)), random_potential(N ** 3, seed + 1))
+    emin, emax = LAP3D_64_WINDOW
+    wl = Workload(f"lap3d_64^3_pot_interior52_m0_80_trap8_minres_{precision}", A, emin, emax,
+                  m0=80, nc=8, rule="trap_half", inner_iters=1500, alpha=1e-2, seed=seed,
+                  expected_count=52 if seed == 0 else None, krylov_steps_full_solve=8_370_778)
+    wl.inner = "minres"
+    wl.precision = precision
+    return wl

@@ -178,6 +178,21 @@ class Solver:
             raise IFEASTError(rc, "ifeast_spmm_shift")
         return W
 
+    # ------------------------------------------------------------------ timing
+    def set_profiling(self, on: bool = True):
+        rc = self.lib.ifeast_set_profiling(self.h, 1 if on else 0)
+        if rc:
+            raise IFEASTError(rc, "ifeast_set_profiling")
+
+    def kernel_times(self, reset: bool = False) -> dict:
+        """{kernel class: (launches, total ms)} measured with CUDA events."""
+        ms = np.zeros(32)
+        cnt = np.zeros(32, dtype=np.int64)
+        k = self.lib.ifeast_kernel_times(self.h, 32, ms.ctypes.data, cnt.ctypes.data,
+                                         1 if reset else 0)
+        return {self.lib.ifeast_kernel_name(i).decode(): (int(cnt[i]), float(ms[i]))
+                for i in range(k) if cnt[i] > 0}
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.ifeast_destroy(self.h)

@@ -108,3 +108,33 @@ def test_solve_interior_window_brute_force(torch, precision):
     st = S.stats()
     assert st["outer_iters"] <= 12
     S.close()
+
+
+def _arrow_matrix(n, seed):
+    """Random symmetric sparse matrix plus a dense first row and column: rows of
+    every length from 1 to n non-zeros (the long row is split into chunks by
+    the SpMM kernels)."""
+    B = inputs.random_sparse_symmetric(n, 4, seed).to_scipy().tolil()
+    g = np.random.default_rng(seed)
+    v = g.standard_normal(n) * 0.1
+    B[0, :] = v
+    B[:, 0] = v.reshape(-1, 1)
+    B[0, 0] = 3.0
+    B = B.tocsr()
+    B.sort_indices()
+    return inputs.CSR(n, B.indptr.astype(np.int32), B.indices.astype(np.int32), B.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("m0,precision,tol", [(8, "fp32", 2e-4), (8, "fp64", 1e-9),
+                                              (7, "fp32", 2e-4), (36, "fp32", 2e-4)])
+def test_filter_long_and_short_rows(torch, m0, precision, tol):
+    A = _arrow_matrix(517, 3)
+    assert np.diff(A.rowptr).max() > 64 and np.diff(A.rowptr).min() <= 4
+    nc, emin, emax = 3, 0.5, 1.5
+    X = inputs.initial_subspace(A.n, m0, 23)
+    S = _solver(A, emin, emax, m0, nc=nc, inner_iters=5, precision=precision)
+    Q, steps = S.apply_filter(torch.as_tensor(X, device="cuda"))
+    z, w = orc.contour_nodes("gl_half", nc, emin, emax)
+    Qr = orc._filtered_subspace_shared(A.to_scipy(), X, z, w, True, 5, 0.0, {"inner_steps": []})
+    assert np.abs(Q.cpu().numpy() - Qr).max() <= tol * np.abs(Qr).max()
+    S.close()
