@@ -44,7 +44,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp64",
-                                                                 "lap2d_50"])
+                                                                 "lap2d_50", "serve"])
+    p.add_argument("--requests", type=int, default=64, help="serving stream length")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -341,8 +342,70 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args):
+    """Serving stream: Poisson arrivals of eigen-requests (2D/3D Laplacians with a
+    potential, n log-uniform 1e3..2e5, m0 16..128), submitted at their arrival
+    times to one server (memory budget 160 GB, 8 running at once). Reports
+    converged eigenpairs/s over the makespan and p50/p99 request latency, and
+    the same stream served one request at a time for comparison."""
+    import torch
+    from paper_1706_00692_gb300 import Server, inputs
+    from paper_1706_00692_gb300.build import build
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    build()
+    reqs = inputs.serving_requests(args.requests, seed=1234, rate=4.0)
+    warm = inputs.serving_requests(3, seed=999, n_max=2e4)
+
+    def serve(max_active, timed_arrivals):
+        srv = Server(160 << 30, max_active=max_active, device=local)
+        for r in warm:  # load kernels, warm the allocator
+            srv.wait(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half"))
+        ids = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            if timed_arrivals:
+                dt = r.arrival - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            ids.append(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half"))
+        outs = [srv.wait(i) for i in ids]
+        span = time.perf_counter() - t0
+        srv.close()
+        lat = np.array([o[4]["submit_to_done_ms"] for o in outs])
+        pairs = sum(int((o[3] <= 1e-10).sum()) for o in outs if o[0] == 0)
+        failed = {}
+        for r, o in zip(reqs, outs):
+            if o[0] != 0:
+                failed[str(o[0])] = failed.get(str(o[0]), 0) + 1
+        return pairs, span, lat, failed
+
+    with ClockSampler(local) as clk:
+        pairs, span, lat, failed = serve(8, True)
+    pairs1, span1, lat1, failed1 = serve(1, False)
+    if rank == 0:
+        line = {"metric": "served eigenpairs/s (Poisson stream); p50/p99 latency",
+                "value": pairs * world / span, "unit": "eigenpairs/s", "n_gpus": world,
+                "steps": 1, "warmup": len(warm), "ms_per_step": span * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": f"serve_{args.requests}_poisson_rate4_n1e3-2e5_m0_16-128",
+                           "max_active": 8, "budget_gb": 160, "inner": "minres",
+                           "inner_precision": "fp32", "contour": "trap_half"},
+                "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                               "p99": float(np.percentile(lat, 99))},
+                "failed": failed, "pairs": pairs, "requests": len(reqs),
+                "one_at_a_time": {"value": pairs1 / span1, "makespan_s": span1,
+                                  "failed": failed1},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "serve" and args.impl == "ours":
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -9,7 +9,7 @@ from . import inputs  # noqa: F401  (seeded synthetic workloads; no solver arith
 
 
 def __getattr__(name):
-    if name in ("Solver", "IFEASTError", "contour_nodes"):
+    if name in ("Solver", "Server", "IFEASTError", "contour_nodes"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

@@ -49,6 +49,16 @@ class Stats(ct.Structure):
                 ("max_inner", ct.c_int), ("shifted_cholesky", ct.c_int), ("solve_ms", ct.c_double)]
 
 
+class ServerOpts(ct.Structure):
+    _fields_ = [("mem_budget_bytes", ct.c_size_t), ("max_active", ct.c_int), ("device", ct.c_int)]
+
+
+class RequestInfo(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("found", ct.c_int), ("outer_iters", ct.c_int),
+                ("RF", ct.c_double), ("submit_to_start_ms", ct.c_double),
+                ("submit_to_done_ms", ct.c_double), ("workspace_bytes", ct.c_size_t)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "ifeast_default_opts": (None, [ct.POINTER(Opts)]),
@@ -74,6 +84,13 @@ SIGNATURES = {
     "ifeast_set_profiling": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "ifeast_kernel_times": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "ifeast_kernel_name": (ct.c_char_p, [ct.c_int]),
+    "ifeast_server_create": (ct.c_int, [ct.POINTER(ServerOpts), ct.POINTER(ct.c_void_p)]),
+    "ifeast_server_submit": (ct.c_int, [ct.c_void_p, ct.POINTER(Csr), ct.POINTER(Contour), ct.c_int,
+                                        ct.POINTER(Opts), ct.c_void_p, ct.POINTER(ct.c_int64)]),
+    "ifeast_server_wait": (ct.c_int, [ct.c_void_p, ct.c_int64, ct.c_int, ct.POINTER(ct.c_int),
+                                      ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                      ct.POINTER(RequestInfo)]),
+    "ifeast_server_destroy": (None, [ct.c_void_p]),
 }
 
 _lib = None

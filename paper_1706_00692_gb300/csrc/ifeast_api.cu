@@ -49,6 +49,9 @@ struct ifeast_ctx {
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
   double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
   int *active_host = nullptr;  // pinned
+  int ell_w = 0;
+  int32_t *colE = nullptr;
+  float *valE = nullptr;
   Profiler prof;
   bool profiling = false;
   // results
@@ -73,7 +76,7 @@ struct Offsets {
   size_t rowptr, colidx, val, z, w, V, W, part, H1, H2, inv_h, CS, SN, R, G, Y, steps, done, X, Q,
       AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
   size_t val32, LV, LW0, LW1, lpart, lalpha, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
-      lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm;
+      lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
 };
 
 int device_sms() {
@@ -110,7 +113,12 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.done = L.take<int>(C);
   } else {  // shared Lanczos basis, tl tiles the n x m0 block
     const size_t es = fp32 ? sizeof(float) : sizeof(double);
-    if (fp32) o.val32 = L.take<float>(nnz > 0 ? nnz : 1);
+    if (fp32) {
+      o.val32 = L.take<float>(nnz > 0 ? nnz : 1);
+      // fixed-width copy of A for rows of at most 16 non-zeros
+      o.colE = L.take<int32_t>((size_t)n * 16);
+      o.valE = L.take<float>((size_t)n * 16);
+    }
     o.LV = L.take<char>((size_t)(K + 1) * n * m0 * es);
     o.LW0 = L.take<char>((size_t)n * m0 * es);
     o.LW1 = L.take<char>((size_t)n * m0 * es);
@@ -128,7 +136,7 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.lcoldone = L.take<int>(m0);
     o.lactive = L.take<int>(1);
     o.lSj = L.take<int>(m0);
-    o.lcoef = L.take<double>((size_t)K * m0);
+    o.lcoef = L.take<double>((size_t)K * m0 + ((size_t)K * m0 + 1) / 2);  // FP64 + FP32 copy
     o.lcx = L.take<double>(m0);
     o.Rres = L.take<double>((size_t)n * m0);
     o.rnorm = L.take<double>(m0);
@@ -360,6 +368,9 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.check_every = 16;
   a.active_host = h->active_host;
   a.P_async = 2 * h->num_sms;  // two resident blocks per SM
+  a.ell_w = h->ell_w;
+  a.colE = h->colE;
+  a.valE = h->valE;
   a.prof = h->profiling ? &h->prof : nullptr;
   MinresState &m = a.ms;
   m.z = h->z;
@@ -562,7 +573,11 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->res = (double *)(b + off.res);
   h->status = (DevStatus *)(b + off.status);
   if (h->minres) {
-    if (h->fp32) h->val32 = (float *)(b + off.val32);
+    if (h->fp32) {
+      h->val32 = (float *)(b + off.val32);
+      h->colE = (int32_t *)(b + off.colE);
+      h->valE = (float *)(b + off.valE);
+    }
     h->LV = b + off.LV;
     h->LW0 = b + off.LW0;
     h->LW1 = b + off.LW1;
@@ -597,6 +612,14 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   ok = ok && cudaMemcpyAsync(h->w, h->wh.data(), h->nc * sizeof(double2), cudaMemcpyHostToDevice,
                              h->stream) == cudaSuccess;
   if (h->fp32 && nnz > 0) ok = ok && convert_to_float(h->val, h->val32, nnz, h->stream) == cudaSuccess;
+  if (h->fp32 && h->minres && m0 % 4 == 0) {
+    int64_t maxlen = 0;
+    for (int64_t i = 0; i < n; ++i) maxlen = std::max<int64_t>(maxlen, A->rowptr[i + 1] - A->rowptr[i]);
+    h->ell_w = maxlen <= 8 ? 8 : (maxlen <= 16 ? 16 : 0);
+    if (h->ell_w)
+      ok = ok && build_ell((int)n, h->ell_w, h->rowptr, h->colidx, h->val32, h->colE, h->valE,
+                           h->stream) == cudaSuccess;
+  }
   ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();

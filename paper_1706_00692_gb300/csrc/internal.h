@@ -142,7 +142,7 @@ struct MinresArgs {
   double *part;             // P x 3 x m0
   double *alpha, *beta;     // [K][m0], [K+1][m0]
   double2 *Yc;              // [nc][K][m0]
-  double *coef, *cx;        // [K][m0], [m0]
+  double *coef, *cx;        // [K][m0] (+ an FP32 copy after it), [m0]
   int *Sj;                  // [m0]
   double *Q;
   RowTiling tl;
@@ -151,7 +151,12 @@ struct MinresArgs {
   int *active_host;         // pinned
   Profiler *prof;
   int P_async;              // max blocks of the FP32 (row, quad) step kernel
+  int ell_w;                // 8 or 16: fixed-width copy of A available (FP32), else 0
+  const int32_t *colE;      // n x ell_w indices (padded with the row's own index)
+  const float *valE;        // n x ell_w values (padded with zero)
 };
+cudaError_t build_ell(int n, int W, const int32_t *rowptr, const int32_t *colidx, const float *val,
+                      int32_t *colE, float *valE, cudaStream_t st);
 cudaError_t minres_init();  // once per device: opt-in shared-memory sizes
 cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st);
 cudaError_t convert_to_float(const double *a, float *b, size_t n, cudaStream_t st);

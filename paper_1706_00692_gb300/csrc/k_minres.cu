@@ -252,6 +252,173 @@ k_lanczos_step(int n, int m0, int s, const int32_t *__restrict__ rowptr,
   }
 }
 
+// Fixed-order reduction of the step's block partials (P blocks) for the 32
+// columns j0..j0+31, Lanczos coefficients and the Givens update of every
+// node's tridiagonal least-squares problem. Called by a whole block of
+// kThreads threads.
+__device__ void givens_tile(int j0, int P, int m0, int nc, int K, int s,
+                            const double *__restrict__ part, double *__restrict__ alpha,
+                            double *__restrict__ beta, const MinresState &st, double brk2) {
+  __shared__ double red[3][kWarps][32];
+  __shared__ double a_s[32], b_s1[32], b_s[32];
+  __shared__ int cdone[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // state of this thread's first (node, column) pair, loaded before the
+  // reduction so that its latency overlaps with it
+  const int t0p = threadIdx.x;
+  const int k0p = t0p / 32, j0p = j0 + (t0p % 32);
+  const bool pre = k0p < nc && j0p < m0;
+  const int p0 = k0p * m0 + j0p;
+  double2 pre_rot[4];
+  double2 pre_g = make_double2(0.0, 0.0);
+  int pre_done = 1;
+  double pre_tol = 0.0;
+  if (pre) {
+    pre_done = st.done[p0];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pre_rot[u] = st.rot[(size_t)p0 * 4 + u];
+    pre_g = st.g[(size_t)p0 * (K + 1) + s];
+    pre_tol = st.tol[p0];
+  }
+  {
+    // warp w sums blocks w, w + 8, ...: eight independent accumulator sets so
+    // that eight rounds of loads are in flight, combined in a fixed order
+    const int j = j0 + lane;
+    double t0[8], t1[8], t2[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t0[u] = t1[u] = t2[u] = 0.0;
+    if (j < m0)
+      for (int b = warp; b < P; b += 8 * kWarps) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int bb = b + u * kWarps;
+          if (bb < P) {
+            // L2 reads: the partials may have been written by other SMs in this launch
+            t0[u] += __ldcg(part + ((size_t)bb * 3 + 0) * m0 + j);
+            t1[u] += __ldcg(part + ((size_t)bb * 3 + 1) * m0 + j);
+            t2[u] += __ldcg(part + ((size_t)bb * 3 + 2) * m0 + j);
+          }
+        }
+      }
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      s0 += t0[u];
+      s1 += t1[u];
+      s2 += t2[u];
+    }
+    red[0][warp][lane] = s0;
+    red[1][warp][lane] = s1;
+    red[2][warp][lane] = s2;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int j = j0 + lane;
+    double vv = 0.0, vw = 0.0, ww = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      vv += red[0][w][lane];
+      vw += red[1][w][lane];
+      ww += red[2][w][lane];
+    }
+    int cd = 1;
+    if (j < m0) {
+      cd = st.coldone[j];
+      if (!cd) {
+        const double a = vv > 0.0 ? vw / vv : 0.0;
+        const double b2 = ww - (vv > 0.0 ? vw * vw / vv : 0.0);
+        const double b = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
+        alpha[(size_t)s * m0 + j] = a;
+        beta[(size_t)(s + 1) * m0 + j] = b;
+        a_s[lane] = a;
+        b_s1[lane] = b;
+        b_s[lane] = beta[(size_t)s * m0 + j];
+      }
+    }
+    cdone[lane] = cd;
+  }
+  __syncthreads();
+  // Givens update for (node k, column j)
+  for (int t = threadIdx.x; t < nc * 32; t += blockDim.x) {
+    const int k = t / 32, jj = t % 32, j = j0 + jj;
+    if (j >= m0 || cdone[jj]) continue;
+    const int p = k * m0 + j;
+    const bool first = t == t0p;
+    if (first ? pre_done : st.done[p]) continue;
+    const double a = a_s[jj], b1 = b_s1[jj], b0 = b_s[jj];
+    // column s of (z I - Tbar): rows s-2 (fill), s-1, s, s+1
+    double2 e2 = make_double2(0.0, 0.0);
+    double2 e1 = make_double2(-b0, 0.0);
+    double2 e0 = make_double2(st.z[k].x - a, st.z[k].y);
+    double2 *rot = st.rot + (size_t)p * 4;  // [cs(s-2), sn(s-2), cs(s-1), sn(s-1)] by parity
+    double2 rr[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rr[u] = first ? pre_rot[u] : rot[u];
+    if (s >= 2) {
+      const double2 cs = rr[((s - 2) & 1) * 2], sn = rr[((s - 2) & 1) * 2 + 1];
+      // rows (s-2, s-1): [conj cs, conj sn; -sn, cs] applied to (0, e1)
+      const double2 t0 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
+      const double2 t1 = cmul(cs, e1);
+      e2 = t0;
+      e1 = t1;
+    }
+    if (s >= 1) {
+      const double2 cs = rr[((s - 1) & 1) * 2], sn = rr[((s - 1) & 1) * 2 + 1];
+      const double2 x = e1, y = e0;
+      e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
+                        cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
+      const double2 sx = cmul(sn, x), cy = cmul(cs, y);
+      e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
+    }
+    const double rho = hypot(sqrt(cabs2(e0)), b1);
+    double2 *R = st.R + ((size_t)p * K + s) * 3;
+    double2 *g = st.g + (size_t)p * (K + 1);
+    if (!(rho > 0.0)) {
+      st.done[p] = 1;
+      continue;
+    }
+    // rotation annihilating the subdiagonal entry -beta_{s+1} below e0
+    const double2 cs = make_double2(e0.x / rho, e0.y / rho);
+    const double2 sn = make_double2(-b1 / rho, 0.0);
+    R[0] = make_double2(rho, 0.0);
+    R[1] = e1;
+    R[2] = e2;
+    rot[(s & 1) * 2] = cs;
+    rot[(s & 1) * 2 + 1] = sn;
+    const double2 gs = first ? pre_g : g[s];
+    const double2 sg = cmul(sn, gs);
+    const double2 gn = make_double2(-sg.x, -sg.y);
+    g[s + 1] = gn;
+    g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
+    st.steps[p] = s + 1;
+    const double res = sqrt(cabs2(gn));
+    const double tol = first ? pre_tol : st.tol[p];
+    if (b1 == 0.0 || (tol > 0.0 && res <= tol)) st.done[p] = 1;
+  }
+  __syncthreads();
+  // column j finished when every node is done (or the basis broke down)
+  if (threadIdx.x < 32) {
+    const int j = j0 + threadIdx.x;
+    if (j < m0 && !cdone[threadIdx.x]) {
+      int all = 1;  // a broken-down basis (beta_{s+1} = 0) finishes the column
+      if (b_s1[threadIdx.x] != 0.0)
+        for (int k = 0; k < nc; ++k) all &= st.done[k * m0 + j];
+      if (all)
+        st.coldone[j] = 1;
+      else
+        atomicAdd(st.active, 1);
+    }
+  }
+  __syncthreads();  // shared arrays are reused by the next tile
+}
+
+// Grid: one block per 32-column tile.
+__global__ void __launch_bounds__(kThreads)
+k_lanczos_givens(int P, int m0, int nc, int K, int s, const double *__restrict__ part,
+                 double *__restrict__ alpha, double *__restrict__ beta, const MinresState st,
+                 double brk2) {
+  givens_tile(blockIdx.x * 32, P, m0, nc, K, s, part, alpha, beta, st, brk2);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 Lanczos step for m0 % 4 == 0: one thread per (row, four-column quad).
 // Threads walk the rows grid-stride, so at any moment the whole grid works on
@@ -386,121 +553,179 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
   }
 }
 
-// Fixed-order reduction of the step's partials, Lanczos coefficients and the
-// Givens update of every node's tridiagonal least-squares problem. Grid: one
-// block per 32-column tile.
-__global__ void __launch_bounds__(kThreads)
-k_lanczos_givens(int P, int m0, int nc, int K, int s, const double *__restrict__ part,
-                 double *__restrict__ alpha, double *__restrict__ beta, const MinresState st,
-                 double brk2) {
-  __shared__ double red[3][kWarps][32];
-  __shared__ double a_s[32], b_s1[32], b_s[32];
-  __shared__ int cdone[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j0 = blockIdx.x * 32;
-  {
-    const int j = j0 + lane;
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-    if (j < m0)
-      for (int b = warp; b < P; b += kWarps) {
-        t0 += part[((size_t)b * 3 + 0) * m0 + j];
-        t1 += part[((size_t)b * 3 + 1) * m0 + j];
-        t2 += part[((size_t)b * 3 + 2) * m0 + j];
+// ---------------------------------------------------------------------------
+// FP32 Lanczos step on a fixed-width (ELL) copy of A: every row holds exactly
+// W slots (W = 8 or 16, padded with the row's own index and a zero value), so
+// a row's indices are one or two 16-byte loads that do not wait on rowptr,
+// and the next row's indices are fetched while the current row's gathers are
+// in flight. The row's own w_{s-1}[r], v_{s-1}[r] come from the slot whose
+// index is r (the diagonal or a padding slot); rows with W non-zeros and no
+// diagonal load them directly. The Lanczos coefficients of the block's
+// columns sit in shared memory. Same recurrence as k_lanczos_step.
+// ---------------------------------------------------------------------------
+template <bool FIRST, int W>
+__global__ void __launch_bounds__(kVThreads, 2)
+k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
+                   const float *__restrict__ valE, float *__restrict__ V,
+                   const float *__restrict__ Wprev, float *__restrict__ Wout,
+                   const double *__restrict__ alpha, const double *__restrict__ beta,
+                   const int *__restrict__ coldone, double *__restrict__ part, int stride_items) {
+  __shared__ float coefs[3][1024];  // alpha_{s-1}, 1/beta_s, beta_s per column
+  __shared__ int cdone[1024];
+  for (int j = threadIdx.x; j < m0; j += kVThreads) {
+    const int cd = coldone[j];
+    cdone[j] = cd;
+    float a = 0.f, ib = 1.f, b = 0.f;
+    if (!FIRST && !cd) {
+      a = (float)alpha[(size_t)(s - 1) * m0 + j];
+      b = (float)beta[(size_t)s * m0 + j];
+      ib = (float)(1.0 / beta[(size_t)s * m0 + j]);
+    }
+    coefs[0][j] = a;
+    coefs[1][j] = ib;
+    coefs[2][j] = b;
+  }
+  __syncthreads();
+  const int MQ = m0 >> 2;
+  const size_t vs = (size_t)n * m0;
+  float *__restrict__ Vs = V + (size_t)s * vs;
+  const float *__restrict__ G1 = FIRST ? Vs : Wprev;
+  const float *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
+  const int gt = blockIdx.x * kVThreads + threadIdx.x;
+  const bool thr = gt < stride_items;
+  const int q = thr ? gt % MQ : 0;
+  const int rstep = stride_items / MQ;
+  bool act[4];
+  bool qact = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    act[i] = thr && cdone[4 * q + i] == 0;
+    qact = qact || act[i];
+  }
+  const bool all4 = act[0] && act[1] && act[2] && act[3];
+  float vv[4] = {0.f, 0.f, 0.f, 0.f}, vw[4] = {0.f, 0.f, 0.f, 0.f}, ww[4] = {0.f, 0.f, 0.f, 0.f};
+  int r = gt / MQ;
+  if (qact && r < n) {
+    int cn[W];
+#pragma unroll
+    for (int u = 0; u < W; u += 4) {
+      const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)r * W + u);
+      cn[u] = c4.x;
+      cn[u + 1] = c4.y;
+      cn[u + 2] = c4.z;
+      cn[u + 3] = c4.w;
+    }
+    for (; r < n; r += rstep) {
+      int c[W];
+#pragma unroll
+      for (int u = 0; u < W; ++u) c[u] = cn[u];
+      float a[W];
+#pragma unroll
+      for (int u = 0; u < W; u += 4) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(valE + (size_t)r * W + u);
+        a[u] = a4.x;
+        a[u + 1] = a4.y;
+        a[u + 2] = a4.z;
+        a[u + 3] = a4.w;
       }
-    red[0][warp][lane] = t0;
-    red[1][warp][lane] = t1;
-    red[2][warp][lane] = t2;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const int j = j0 + lane;
-    double vv = 0.0, vw = 0.0, ww = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      vv += red[0][w][lane];
-      vw += red[1][w][lane];
-      ww += red[2][w][lane];
-    }
-    int cd = 1;
-    if (j < m0) {
-      cd = st.coldone[j];
-      if (!cd) {
-        const double a = vv > 0.0 ? vw / vv : 0.0;
-        const double b2 = ww - (vv > 0.0 ? vw * vw / vv : 0.0);
-        const double b = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
-        alpha[(size_t)s * m0 + j] = a;
-        beta[(size_t)(s + 1) * m0 + j] = b;
-        a_s[lane] = a;
-        b_s1[lane] = b;
-        b_s[lane] = beta[(size_t)s * m0 + j];
+      float4 g1[W], g2[W];
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const size_t co = (size_t)c[u] * m0 + 4 * q;
+        g1[u] = *reinterpret_cast<const float4 *>(G1 + co);
+        if (!FIRST) g2[u] = *reinterpret_cast<const float4 *>(G2 + co);
+      }
+      const int rn = r + rstep;  // next row's indices, in flight with the gathers
+      if (rn < n) {
+#pragma unroll
+        for (int u = 0; u < W; u += 4) {
+          const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)rn * W + u);
+          cn[u] = c4.x;
+          cn[u + 1] = c4.y;
+          cn[u + 2] = c4.z;
+          cn[u + 3] = c4.w;
+        }
+      }
+      float4 acc1 = make_float4(0.f, 0.f, 0.f, 0.f), acc2 = acc1, o1 = acc1, o2 = acc1;
+      bool own = false;
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        acc1 = f4fma(a[u], g1[u], acc1);
+        if (!FIRST) acc2 = f4fma(a[u], g2[u], acc2);
+        if (c[u] == r) {
+          o1 = g1[u];
+          if (!FIRST) o2 = g2[u];
+          own = true;
+        }
+      }
+      const size_t off = (size_t)r * m0 + 4 * q;
+      if (!own) {
+        o1 = *reinterpret_cast<const float4 *>(G1 + off);
+        if (!FIRST) o2 = *reinterpret_cast<const float4 *>(G2 + off);
+      }
+      const float o1a[4] = {o1.x, o1.y, o1.z, o1.w}, o2a[4] = {o2.x, o2.y, o2.z, o2.w};
+      const float a1a[4] = {acc1.x, acc1.y, acc1.z, acc1.w}, a2a[4] = {acc2.x, acc2.y, acc2.z, acc2.w};
+      float v[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (FIRST) {
+          v[i] = o1a[i];
+          w[i] = a1a[i];
+        } else {
+          const int j = 4 * q + i;
+          const float ap = coefs[0][j], ib = coefs[1][j], bs = coefs[2][j];
+          v[i] = (o1a[i] - ap * o2a[i]) * ib;
+          w[i] = (a1a[i] - ap * a2a[i]) * ib - bs * o2a[i];
+        }
+        if (act[i]) {
+          vv[i] = fmaf(v[i], v[i], vv[i]);
+          vw[i] = fmaf(v[i], w[i], vw[i]);
+          ww[i] = fmaf(w[i], w[i], ww[i]);
+        }
+      }
+      if (all4) {
+        if (!FIRST) *reinterpret_cast<float4 *>(Vs + off) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(Wout + off) = make_float4(w[0], w[1], w[2], w[3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (act[i]) {
+            if (!FIRST) Vs[off + i] = v[i];
+            Wout[off + i] = w[i];
+          }
       }
     }
-    cdone[lane] = cd;
+  }
+  __shared__ float red[kVThreads][13];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    red[threadIdx.x][3 * i + 0] = vv[i];
+    red[threadIdx.x][3 * i + 1] = vw[i];
+    red[threadIdx.x][3 * i + 2] = ww[i];
   }
   __syncthreads();
-  // Givens update for (node k, column j)
-  for (int t = threadIdx.x; t < nc * 32; t += blockDim.x) {
-    const int k = t / 32, jj = t % 32, j = j0 + jj;
-    if (j >= m0 || cdone[jj]) continue;
-    const int p = k * m0 + j;
-    if (st.done[p]) continue;
-    const double a = a_s[jj], b1 = b_s1[jj], b0 = b_s[jj];
-    // column s of (z I - Tbar): rows s-2 (fill), s-1, s, s+1
-    double2 e2 = make_double2(0.0, 0.0);
-    double2 e1 = make_double2(-b0, 0.0);
-    double2 e0 = make_double2(st.z[k].x - a, st.z[k].y);
-    double2 *rot = st.rot + (size_t)p * 4;  // [cs(s-2), sn(s-2), cs(s-1), sn(s-1)] by parity
-    if (s >= 2) {
-      const double2 cs = rot[((s - 2) & 1) * 2], sn = rot[((s - 2) & 1) * 2 + 1];
-      // rows (s-2, s-1): [conj cs, conj sn; -sn, cs] applied to (0, e1)
-      const double2 t0 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
-      const double2 t1 = cmul(cs, e1);
-      e2 = t0;
-      e1 = t1;
-    }
-    if (s >= 1) {
-      const double2 cs = rot[((s - 1) & 1) * 2], sn = rot[((s - 1) & 1) * 2 + 1];
-      const double2 x = e1, y = e0;
-      e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
-                        cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
-      const double2 sx = cmul(sn, x), cy = cmul(cs, y);
-      e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
-    }
-    const double rho = hypot(sqrt(cabs2(e0)), b1);
-    double2 *R = st.R + ((size_t)p * K + s) * 3;
-    double2 *g = st.g + (size_t)p * (K + 1);
-    if (!(rho > 0.0)) {
-      st.done[p] = 1;
-      continue;
-    }
-    // rotation annihilating the subdiagonal entry -beta_{s+1} below e0
-    const double2 cs = make_double2(e0.x / rho, e0.y / rho);
-    const double2 sn = make_double2(-b1 / rho, 0.0);
-    R[0] = make_double2(rho, 0.0);
-    R[1] = e1;
-    R[2] = e2;
-    rot[(s & 1) * 2] = cs;
-    rot[(s & 1) * 2 + 1] = sn;
-    const double2 gs = g[s];
-    const double2 sg = cmul(sn, gs);
-    g[s + 1] = make_double2(-sg.x, -sg.y);
-    g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
-    st.steps[p] = s + 1;
-    const double res = sqrt(cabs2(g[s + 1]));
-    if (b1 == 0.0 || (st.tol[p] > 0.0 && res <= st.tol[p])) st.done[p] = 1;
+  const int base_q = (blockIdx.x * kVThreads) % MQ;
+  for (int t = threadIdx.x; t < 3 * m0; t += kVThreads) {
+    const int k = t / m0, j = t % m0;
+    const int qj = j >> 2, ij = j & 3;
+    double acc = 0.0;
+    for (int l = (qj - base_q + MQ) % MQ; l < kVThreads; l += MQ)
+      if (blockIdx.x * kVThreads + l < stride_items) acc += (double)red[l][3 * ij + k];
+    part[((size_t)blockIdx.x * 3 + k) * m0 + j] = acc;
   }
-  __syncthreads();
-  // column j finished when every node is done (or the basis broke down)
-  if (threadIdx.x < 32) {
-    const int j = j0 + threadIdx.x;
-    if (j < m0 && !cdone[threadIdx.x]) {
-      int all = 1;  // a broken-down basis (beta_{s+1} = 0) finishes the column
-      if (b_s1[threadIdx.x] != 0.0)
-        for (int k = 0; k < nc; ++k) all &= st.done[k * m0 + j];
-      if (all)
-        st.coldone[j] = 1;
-      else
-        atomicAdd(st.active, 1);
-    }
+}
+
+// Fixed-width copy of the CSR matrix (FP32 values): W slots per row, padded
+// with the row's own index and zero. Built on the device from the CSR arrays.
+__global__ void k_build_ell(int n, int W, const int32_t *__restrict__ rowptr,
+                            const int32_t *__restrict__ colidx, const float *__restrict__ val,
+                            int32_t *__restrict__ colE, float *__restrict__ valE) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int pb = rowptr[r], len = rowptr[r + 1] - pb;
+  for (int u = 0; u < W; ++u) {
+    colE[(size_t)r * W + u] = u < len ? colidx[pb + u] : r;
+    valE[(size_t)r * W + u] = u < len ? val[pb + u] : 0.f;
   }
 }
 
@@ -516,24 +741,37 @@ __global__ void k_lz_solve(int m0, int nc, int K, const MinresState st, double2 
   const double2 *g = st.g + (size_t)p * (K + 1);
   double2 wt = st.w[k];
   if (st.correction) wt = cdiv(wt, make_double2(st.z[k].x - st.lam[j], st.z[k].y));
-  double2 y1 = make_double2(0.0, 0.0), y2 = make_double2(0.0, 0.0);  // y_{l+1}, y_{l+2}
   for (int l = K - 1; l >= m; --l) Yc[((size_t)k * K + l) * m0 + j] = make_double2(0.0, 0.0);
-  for (int l = m - 1; l >= 0; --l) {
-    double2 t = g[l];
-    if (l + 1 < m) {
-      const double2 q = cmul(R[(size_t)(l + 1) * 3 + 1], y1);
-      t.x -= q.x;
-      t.y -= q.y;
+  double2 y1 = make_double2(0.0, 0.0), y2 = make_double2(0.0, 0.0);  // y_{l+1}, y_{l+2}
+  // chunks of 8 rows, bottom up; the chunk's g and band entries are loaded
+  // before the dependent recurrence runs over them
+  constexpr int CH = 8;
+  for (int hi = m - 1; hi >= 0; hi -= CH) {
+    double2 gg[CH], r0[CH], r1[CH], r2[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int l = hi - u;
+      if (l >= 0) {
+        gg[u] = g[l];
+        r0[u] = R[(size_t)l * 3];
+        r1[u] = (l + 1 < m) ? R[(size_t)(l + 1) * 3 + 1] : make_double2(0.0, 0.0);
+        r2[u] = (l + 2 < m) ? R[(size_t)(l + 2) * 3 + 2] : make_double2(0.0, 0.0);
+      }
     }
-    if (l + 2 < m) {
-      const double2 q = cmul(R[(size_t)(l + 2) * 3 + 2], y2);
-      t.x -= q.x;
-      t.y -= q.y;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int l = hi - u;
+      if (l >= 0) {
+        double2 t = gg[u];
+        const double2 q1 = cmul(r1[u], y1), q2 = cmul(r2[u], y2);
+        t.x -= q1.x + q2.x;
+        t.y -= q1.y + q2.y;
+        const double2 y = cdiv(t, r0[u]);
+        Yc[((size_t)k * K + l) * m0 + j] = cmul(wt, y);
+        y2 = y1;
+        y1 = y;
+      }
     }
-    const double2 y = cdiv(t, R[(size_t)l * 3]);
-    Yc[((size_t)k * K + l) * m0 + j] = cmul(wt, y);
-    y2 = y1;
-    y1 = y;
   }
   atomicMax(&st.status->max_steps, m);
   atomicAdd((unsigned long long *)&st.status->total_steps, (unsigned long long)m);
@@ -550,6 +788,8 @@ __global__ void k_lz_coef(int m0, int nc, int K, const MinresState st,
     double t = 0.0;
     for (int k = 0; k < nc; ++k) t += Yc[((size_t)k * K + l) * m0 + j].x;
     coef[idx] = t;
+    // FP32 copy (after the K x m0 doubles) for the FP32 quadrature
+    reinterpret_cast<float *>(coef + (size_t)K * m0)[idx] = (float)t;
   }
   if (idx < (size_t)m0) {
     const int j = (int)idx;
@@ -590,7 +830,7 @@ __global__ void k_lz_quadrature(int n, int m0, const T *__restrict__ V, const do
 // flight. A column only takes the basis vectors its own solves built
 // (l < Sj[j]); later ones were not written for it and are never multiplied.
 __global__ void __launch_bounds__(256)
-k_lz_quadrature4(int n, int m0, const float *__restrict__ V, const double *__restrict__ coef,
+k_lz_quadrature4(int n, int m0, int K, const float *__restrict__ V, const double *__restrict__ coef,
                  const double *__restrict__ cx, const int *__restrict__ Sj,
                  const double *__restrict__ X, double *__restrict__ Q) {
   const size_t i4 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -601,29 +841,35 @@ k_lz_quadrature4(int n, int m0, const float *__restrict__ V, const double *__res
   const int S = max(max(s0, s1), max(s2, s3));
   const size_t vq = (size_t)n * m0 / 4;  // basis stride in float4
   const float4 *__restrict__ V4 = reinterpret_cast<const float4 *>(V) + i4;
+  // FP32 coefficients (written by k_lz_coef after the FP64 ones), float4 per quad
+  const float4 *__restrict__ C4 =
+      reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(coef + (size_t)K * m0) + j0);
+  const int cq = m0 / 4;  // float4 stride of one coefficient row
   float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
   int l = 0;
   for (; l + 8 <= S; l += 8) {
-    float4 v[8];
+    float4 v[8], c[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = V4[(size_t)(l + u) * vq];
+    for (int u = 0; u < 8; ++u) {
+      v[u] = V4[(size_t)(l + u) * vq];
+      c[u] = C4[(size_t)(l + u) * cq];
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int ll = l + u;
-      const double *c = coef + (size_t)ll * m0 + j0;
-      ax = ll < s0 ? fmaf((float)c[0], v[u].x, ax) : ax;
-      ay = ll < s1 ? fmaf((float)c[1], v[u].y, ay) : ay;
-      az = ll < s2 ? fmaf((float)c[2], v[u].z, az) : az;
-      aw = ll < s3 ? fmaf((float)c[3], v[u].w, aw) : aw;
+      ax = ll < s0 ? fmaf(c[u].x, v[u].x, ax) : ax;
+      ay = ll < s1 ? fmaf(c[u].y, v[u].y, ay) : ay;
+      az = ll < s2 ? fmaf(c[u].z, v[u].z, az) : az;
+      aw = ll < s3 ? fmaf(c[u].w, v[u].w, aw) : aw;
     }
   }
   for (; l < S; ++l) {
     const float4 v = V4[(size_t)l * vq];
-    const double *c = coef + (size_t)l * m0 + j0;
-    ax = l < s0 ? fmaf((float)c[0], v.x, ax) : ax;
-    ay = l < s1 ? fmaf((float)c[1], v.y, ay) : ay;
-    az = l < s2 ? fmaf((float)c[2], v.z, az) : az;
-    aw = l < s3 ? fmaf((float)c[3], v.w, aw) : aw;
+    const float4 c = C4[(size_t)l * cq];
+    ax = l < s0 ? fmaf(c.x, v.x, ax) : ax;
+    ay = l < s1 ? fmaf(c.y, v.y, ay) : ay;
+    az = l < s2 ? fmaf(c.z, v.z, az) : az;
+    aw = l < s3 ? fmaf(c.w, v.w, aw) : aw;
   }
   const size_t e = i4 * 4;
   Q[e + 0] = cx[j0 + 0] * X[e + 0] + (double)ax;
@@ -652,6 +898,14 @@ void launch_step_nj(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo, const 
 
 bool use_vec_step(const MinresArgs &a) { return a.fp32 && a.m0 % 4 == 0 && a.m0 <= 1024; }
 
+bool use_ell_step(const MinresArgs &a) { return use_vec_step(a) && (a.ell_w == 8 || a.ell_w == 16); }
+
+// Lanczos breakdown threshold on beta^2 / ||w||^2 for the storage precision
+template <typename T>
+double brk2_of() {
+  return sizeof(T) == 4 ? 1e-6 : 1e-16;
+}
+
 // Blocks of k_lanczos_step_vec and the number of (row, quad) items the grid
 // covers per sweep (a multiple of m0 / 4).
 void vec_grid(const MinresArgs &a, int &blocks, int &stride_items) {
@@ -671,6 +925,27 @@ template <typename T>
 cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo,
                                 const T *val, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
+    if (use_ell_step(a)) {
+      int blocks, stride_items;
+      vec_grid(a, blocks, stride_items);
+#define IFEAST_ELL_LAUNCH(F, WW)                                                              \
+  k_lanczos_step_ell<F, WW><<<blocks, kVThreads, 0, st>>>(                                     \
+      a.n, a.m0, s, a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone, a.part,        \
+      stride_items)
+      if (a.ell_w == 8) {
+        if (s == 0)
+          IFEAST_ELL_LAUNCH(true, 8);
+        else
+          IFEAST_ELL_LAUNCH(false, 8);
+      } else {
+        if (s == 0)
+          IFEAST_ELL_LAUNCH(true, 16);
+        else
+          IFEAST_ELL_LAUNCH(false, 16);
+      }
+#undef IFEAST_ELL_LAUNCH
+      return cudaGetLastError();
+    }
     if (use_vec_step(a)) {
       int blocks, stride_items;
       vec_grid(a, blocks, stride_items);
@@ -712,7 +987,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   k_lz_prep<T><<<(unsigned)((g0 + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.nc, a.K, a.rhs, a.rnorm,
                                                              V, a.beta, a.ms);
   IFEAST_PROF_END(a.prof);
-  const double brk2 = sizeof(T) == 4 ? 1e-6 : 1e-16;
+  const double brk2 = brk2_of<T>();
   int step_blocks = a.tl.P;
   if (sizeof(T) == 4 && use_vec_step(a)) {
     int stride_items;
@@ -751,7 +1026,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   IFEAST_PROF_BEGIN(a.prof, K_LZ_QUAD);
   if (sizeof(T) == 4 && a.m0 % 4 == 0)
     k_lz_quadrature4<<<(unsigned)((nm / 4 + 255) / 256), 256, 0, st>>>(
-        a.n, a.m0, (const float *)V, a.coef, a.cx, a.Sj, a.X, a.Q);
+        a.n, a.m0, a.K, (const float *)V, a.coef, a.cx, a.Sj, a.X, a.Q);
   else
     k_lz_quadrature<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, V, a.coef, a.cx,
                                                                      a.Sj, a.X, a.Q);
@@ -766,6 +1041,12 @@ cudaError_t minres_init() { return cudaSuccess; }
 cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st) {
   if (a.fp32) return run_minres<float>(a, st);
   return run_minres<double>(a, st);
+}
+
+cudaError_t build_ell(int n, int W, const int32_t *rowptr, const int32_t *colidx, const float *val,
+                      int32_t *colE, float *valE, cudaStream_t st) {
+  k_build_ell<<<(n + 255) / 256, 256, 0, st>>>(n, W, rowptr, colidx, val, colE, valE);
+  return cudaGetLastError();
 }
 
 cudaError_t convert_to_float(const double *a, float *b, size_t n, cudaStream_t st) {

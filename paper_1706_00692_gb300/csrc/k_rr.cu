@@ -267,7 +267,7 @@ k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ B
     }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
-    if (!(off > 1e-32 * tot)) break;
+    if (!(off > 1e-28 * tot)) break;  // off-diagonal norm below 1e-14 of the matrix norm
     for (int round = 0; round < mp - 1; ++round) {
       for (int p = tid; p < npairs; p += nth) {
         const int pa = p, pb = mp - 1 - p;

@@ -204,3 +204,71 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous serving of many solves on one GPU (include/ifeast_serve.h).
+
+    Requests are admitted in arrival order as their device workspace fits in
+    ``mem_budget_bytes``; up to ``max_active`` run at once, each on its own
+    stream and worker thread inside the library."""
+
+    def __init__(self, mem_budget_bytes: int, max_active: int = 8, device: int = 0):
+        self.lib = _lib.load()
+        o = _lib.ServerOpts(int(mem_budget_bytes), int(max_active), int(device))
+        h = ct.c_void_p()
+        rc = self.lib.ifeast_server_create(ct.byref(o), ct.byref(h))
+        if rc:
+            raise IFEASTError(rc, "ifeast_server_create")
+        self.h = h
+        self._meta = {}
+
+    def submit(self, A: CSR, emin: float, emax: float, m0: int, X0: np.ndarray, *, nc: int = 8,
+               rule: str = "gl_half", inner: str = "minres", inner_iters: int = 300,
+               alpha: float = 3e-2, max_outer: int = 100, tol: float = 1e-10,
+               precision: str = "fp32") -> int:
+        c = _lib.Contour(_lib.RULES[rule], nc, emin, emax)
+        o = _lib.Opts()
+        self.lib.ifeast_default_opts(ct.byref(o))
+        o.inner_solver = _lib.INNERS[inner]
+        o.inner_max_iters = inner_iters
+        o.alpha = alpha
+        o.max_outer = max_outer
+        o.tol = tol
+        o.precision = _lib.PRECISIONS[precision]
+        rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
+        va = np.ascontiguousarray(A.val, dtype=np.float64)
+        x = np.ascontiguousarray(X0, dtype=np.float64)
+        assert x.shape == (A.n, m0)
+        csr = _lib.Csr(A.n, A.nnz, rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+        rid = ct.c_int64()
+        rc = self.lib.ifeast_server_submit(self.h, ct.byref(csr), ct.byref(c), m0, ct.byref(o),
+                                           x.ctypes.data, ct.byref(rid))
+        if rc:
+            raise IFEASTError(rc, "ifeast_server_submit")
+        self._meta[rid.value] = (A.n, m0)
+        return rid.value
+
+    def wait(self, rid: int):
+        """(status, lam, X, res, info dict) of request rid (blocks until done)."""
+        n, m0 = self._meta.pop(rid)
+        lam, X, res = np.zeros(m0), np.zeros((n, m0)), np.zeros(m0)
+        m = ct.c_int()
+        info = _lib.RequestInfo()
+        rc = self.lib.ifeast_server_wait(self.h, rid, m0, ct.byref(m), lam.ctypes.data,
+                                         X.ctypes.data, res.ctypes.data, ct.byref(info))
+        k = min(m.value, m0)
+        d = {f: getattr(info, f) for f, _ in _lib.RequestInfo._fields_}
+        return rc, lam[:k], X[:, :k], res[:k], d
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ifeast_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
