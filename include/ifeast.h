@@ -205,6 +205,30 @@ int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, do
 int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0,
                       const double *z);
 
+/* Rayleigh-Ritz without any device allocation, for callers that cannot call
+ * cudaMalloc (code inside a fixed memory pool, a runtime that forbids device
+ * allocation, or a process that reserved all device memory up front). The
+ * paper has no counterpart: it is a packaging of ifeast_rayleigh_ritz.
+ * Same outputs (X = Q X_Q, lam ascending, resid) for the matrix given as
+ * caller-owned DEVICE CSR arrays (rowptr int32[n+1], colidx int32[nnz],
+ * val float64[nnz]; not validated: the caller passes a well-formed matrix)
+ * and device Q, X (n x m0 row-major), lam[m0], resid[m0].
+ *   - No handle and no workspace: intermediates live in one file-scope
+ *     device array of about 4.5 MiB that every GPU loading the library keeps
+ *     until the process exits. m0 must be <= 64 (larger: INVALID_ARG).
+ *   - The first call on a device looks up that array's device address (and
+ *     sets the eigensolver's shared-memory limit); make the first call before
+ *     any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU race, so the
+ *     caller serialises them. Each call overwrites every scratch entry it
+ *     reads, so results never depend on an earlier call.
+ *   - Runs on stream (cudaStream_t as void*) and returns when it finished;
+ *     BREAKDOWN if B_Q = Q^T Q cannot be factored. */
+int ifeast_rayleigh_ritz_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr,
+                                 const int32_t *colidx, const double *val, int m0,
+                                 const double *Q, double *X, double *lam, double *resid,
+                                 void *stream);
+
 /* ---------------------------------------------------------------------------
  * Kernel timing. When on, every kernel launch of the handle is bracketed by
  * CUDA events on the handle's stream (a few microseconds of overhead per

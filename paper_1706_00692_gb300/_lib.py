@@ -91,6 +91,9 @@ SIGNATURES = {
                                       ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                       ct.POINTER(RequestInfo)]),
     "ifeast_server_destroy": (None, [ct.c_void_p]),
+    "ifeast_rayleigh_ritz_noalloc": (ct.c_int, [ct.c_int64, ct.c_int64, ct.c_void_p, ct.c_void_p,
+                                                ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                                ct.c_void_p, ct.c_void_p, ct.c_void_p]),
 }
 
 _lib = None

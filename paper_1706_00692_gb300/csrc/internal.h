@@ -191,5 +191,9 @@ cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
 cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st);
 cudaError_t column_norms(int n, int m0, const double *X, double *part, int Pr, double *beta,
                          cudaStream_t st, Profiler *prof);
+// The reduced generalised eigensolver of rayleigh_ritz on caller buffers.
+cudaError_t reduced_eig_launch(int m, const double *Aq, const double *Bq, double *L, double *Cm,
+                               double *U, double *XQ, double *lam, DevStatus *status,
+                               cudaStream_t st);
 
 }  // namespace ifeast

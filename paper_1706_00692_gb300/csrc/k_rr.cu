@@ -569,6 +569,16 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t reduced_eig_launch(int m, const double *Aq, const double *Bq, double *L, double *Cm,
+                               double *U, double *XQ, double *lam, DevStatus *status,
+                               cudaStream_t st) {
+  if (m < 1 || m > kMaxM0) return cudaErrorInvalidValue;
+  const size_t mat = (size_t)m * m * sizeof(double);
+  const int nmat = (int)std::min<size_t>(3, kEigSmem / mat);
+  k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, Aq, Bq, L, Cm, U, XQ, lam, status, nmat);
+  return cudaGetLastError();
+}
+
 cudaError_t column_norms(int n, int m, const double *X, double *part, int Pr, double *beta,
                          cudaStream_t st, Profiler *prof) {
   const int rows = (n + Pr - 1) / Pr;
