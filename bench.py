@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp64",
                                                                  "lap2d_50", "serve"])
     p.add_argument("--requests", type=int, default=64, help="serving stream length")
+    p.add_argument("--rate", type=float, default=8.0, help="serving arrivals per second")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -71,6 +72,13 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+# DRAM bytes per launch of k_lanczos_step_ell<false, 8> on the 64^3 workload
+# (m0 = 80, FP32), dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture (profiles/k_lanczos_step_ell_lap3d64.md). Re-measure when that kernel
+# changes; None when unknown for the workload.
+ELL_STEP_TRAFFIC_LAP3D64 = 315.7e6
 
 
 def step_bytes(wl, elem):
@@ -308,7 +316,10 @@ def run_ours(args):
         achieved = nbytes / (ms / launches * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": "k_lanczos_step", "achieved": achieved,
                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_source": f"{peak_kind} copy bandwidth", "traffic": None,
+                    "peak_source": f"{peak_kind} copy bandwidth",
+                    "traffic": (ELL_STEP_TRAFFIC_LAP3D64
+                                if wl.name.startswith("lap3d_64") and wl.precision == "fp32"
+                                else None),
                     "bytes_per_launch": nbytes, "launches": launches,
                     "us_per_launch": 1e3 * ms / launches}
     gpu_launches = int(sum(c for c, _ in ktimes.values()))
@@ -316,7 +327,8 @@ def run_ours(args):
         st = stats[-1]
         line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if wl.precision == "fp32" else "f64",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "n": wl.A.n, "nnz": wl.A.nnz, "m0": wl.m0,
                            "nc": wl.nc, "contour": wl.rule, "inner": wl.inner,
@@ -354,7 +366,7 @@ def run_serve(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     build()
-    reqs = inputs.serving_requests(args.requests, seed=1234, rate=4.0)
+    reqs = inputs.serving_requests(args.requests, seed=1234, rate=args.rate)
     warm = inputs.serving_requests(3, seed=999, n_max=2e4)
 
     def serve(max_active, timed_arrivals):
@@ -387,9 +399,9 @@ def run_serve(args):
         line = {"metric": "served eigenpairs/s (Poisson stream); p50/p99 latency",
                 "value": pairs * world / span, "unit": "eigenpairs/s", "n_gpus": world,
                 "steps": 1, "warmup": len(warm), "ms_per_step": span * 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"serve_{args.requests}_poisson_rate4_n1e3-2e5_m0_16-128",
+                "config": {"workload": f"serve_{args.requests}_poisson_rate{args.rate:g}_n1e3-2e5_m0_16-128",
                            "max_active": 8, "budget_gb": 160, "inner": "minres",
                            "inner_precision": "fp32", "contour": "trap_half"},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
