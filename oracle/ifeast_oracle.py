@@ -19,7 +19,7 @@ Map to the paper:
                                         modified Gram-Schmidt Arnoldi, Givens)
   gmres_shared_basis ................. Section 3, Eqs. (yz)-(contint_krylov):
                                         the Krylov basis does not depend on z
-  rayleigh_ritz ...................... Algorithm 1/2 step 3
+  rayleigh_ritz ...................... Algorithm 1/2 step 3 (B_Q = Q^T B Q for A x = lam B x)
   eigen_residuals .................... Algorithm 1/2 step 4
   convergence_bound .................. Eq. (upperbound), Eq. (deltadef)
 """
@@ -218,12 +218,12 @@ def cholesky_shifted(Bq):
         return np.linalg.cholesky(Bq + shift * np.eye(m)), True
 
 
-def rayleigh_ritz(Q, AQ):
-    """Solve A_Q X_Q = B_Q X_Q Lambda with A_Q = Q^H A Q, B_Q = Q^H Q through
-    B_Q = L L^H, C = L^{-1} A_Q L^{-H}, C = U Lambda U^H, X_Q = L^{-H} U.
-    Returns (lam ascending, X_Q) with X_Q^H B_Q X_Q = I."""
+def rayleigh_ritz(Q, AQ, BQ=None):
+    """Solve A_Q X_Q = B_Q X_Q Lambda with A_Q = Q^H A Q, B_Q = Q^H B Q (B = I
+    when BQ is None) through B_Q = L L^H, C = L^{-1} A_Q L^{-H}, C = U Lambda
+    U^H, X_Q = L^{-H} U. Returns (lam ascending, X_Q) with X_Q^H B_Q X_Q = I."""
     Aq = Q.conj().T @ AQ
-    Bq = Q.conj().T @ Q
+    Bq = Q.conj().T @ (Q if BQ is None else BQ)
     Aq = 0.5 * (Aq + Aq.conj().T)
     Bq = 0.5 * (Bq + Bq.conj().T)
     L, _ = cholesky_shifted(Bq)
@@ -235,9 +235,10 @@ def rayleigh_ritz(Q, AQ):
     return lam, XQ
 
 
-def eigen_residuals(AX, X, lam):
-    """Relative eigenpair residuals ||A x_j - lam_j x_j|| / ||A x_j||."""
-    num = np.linalg.norm(AX - X * lam[None, :], axis=0)
+def eigen_residuals(AX, X, lam, BX=None):
+    """Relative eigenpair residuals ||A x_j - lam_j B x_j|| / ||A x_j|| (B = I
+    when BX is None)."""
+    num = np.linalg.norm(AX - (X if BX is None else BX) * lam[None, :], axis=0)
     den = np.linalg.norm(AX, axis=0)
     return num / np.where(den > 0, den, 1.0)
 
@@ -250,21 +251,32 @@ def in_interval(lam, emin, emax):
 # FEAST (Algorithm 1) and IFEAST (Algorithm 2)
 # ---------------------------------------------------------------------------
 
-def _filtered_subspace_exact(A_dense, X, z, w, half):
+def _filtered_subspace_exact(A_dense, X, z, w, half, B_dense=None):
+    """Sum_k w_k (z_k B - A)^{-1} B X by dense LU (Alg. 1 steps 1-2; the
+    generalized systems of Eq. generalized_linsys when B is given)."""
     n = X.shape[0]
+    Bd = np.eye(n) if B_dense is None else B_dense
+    rhs = (Bd @ X).astype(np.complex128)
     Q = np.zeros(X.shape, np.complex128)
     for zk, wk in zip(z, w):
-        lu = sla.lu_factor(zk * np.eye(n) - A_dense)
-        Q += wk * sla.lu_solve(lu, X.astype(np.complex128))
+        lu = sla.lu_factor(zk * Bd - A_dense)
+        Q += wk * sla.lu_solve(lu, rhs)
     return Q.real if half else Q
 
 
-def _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats):
+def _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats, B=None):
+    """Per (node, column) GMRES on (z_k B - A) y = B x_j (Alg. 2 step 1;
+    Eq. generalized_linsys when B is given)."""
     n, m0 = X.shape
+    rhs = X if B is None else B @ X
     Q = np.zeros(X.shape, np.complex128)
     for zk, wk in zip(z, w):
+        if B is None:
+            op = lambda v, zk=zk: shifted_apply(A, zk, v)
+        else:
+            op = lambda v, zk=zk: zk * (B @ v) - A @ v
         for j in range(m0):
-            out = gmres(lambda v: shifted_apply(A, zk, v), X[:, j], k, tol_rel)
+            out = gmres(op, rhs[:, j], k, tol_rel)
             stats["inner_steps"].append(out["steps"])
             Q[:, j] += wk * out["y"]
     return Q.real if half else Q
@@ -282,9 +294,10 @@ def _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats):
 
 
 def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0,
-           tol=1e-10, max_outer=100, callback=None):
+           tol=1e-10, max_outer=100, callback=None, B=None):
     """Algorithm 2 (and, with inner="exact", Algorithm 1) for a real symmetric
-    standard problem A x = lambda x.
+    problem A x = lambda x, or A x = lambda B x with B symmetric positive
+    definite (the generalized systems (z_k B - A) Y_k = B X of Section 2.2).
 
     inner: "exact" dense LU per node (Alg. 1 step 1),
            "gmres" per-node complex GMRES (Alg. 2 step 1),
@@ -299,28 +312,36 @@ def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0
     Returns dict(lam, X, res, inside, iters, history, converged).
     """
     A = A.tocsr() if sp.issparse(A) else A
+    if B is not None:
+        B = B.tocsr() if sp.issparse(B) else B
+        if inner == "shared":
+            raise ValueError("the shift-independent basis needs B = I")
     X = np.asarray(X0, dtype=np.float64).copy()
     RF = 1.0
     history = []
     A_dense = None
+    B_dense = None
     for it in range(1, max_outer + 1):
         stats = {"inner_steps": []}
         tol_rel = alpha * RF if alpha > 0 else 0.0
         if inner == "exact":
             if A_dense is None:
                 A_dense = A.toarray() if sp.issparse(A) else np.asarray(A)
-            Q = _filtered_subspace_exact(A_dense, X, z, w, half)
+                if B is not None:
+                    B_dense = B.toarray() if sp.issparse(B) else np.asarray(B)
+            Q = _filtered_subspace_exact(A_dense, X, z, w, half, B_dense)
         elif inner == "gmres":
-            Q = _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats)
+            Q = _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats, B)
         elif inner == "shared":
             Q = _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats)
         else:
             raise ValueError(inner)
         AQ = A @ Q
-        lam, XQ = rayleigh_ritz(Q, AQ)
+        BQ = None if B is None else B @ Q
+        lam, XQ = rayleigh_ritz(Q, AQ, BQ)
         X = Q @ XQ
         AX = AQ @ XQ
-        res = eigen_residuals(AX, X, lam)
+        res = eigen_residuals(AX, X, lam, None if B is None else BQ @ XQ)
         inside = in_interval(lam, emin, emax)
         RF = float(res[inside].max()) if inside.any() else 1.0
         history.append(dict(RF=RF, count=int(inside.sum()),
@@ -335,20 +356,27 @@ def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0
                 converged=False)
 
 
-def feast(A, X0, emin, emax, z, w, *, half=True, tol=1e-10, max_outer=100):
+def feast(A, X0, emin, emax, z, w, *, half=True, tol=1e-10, max_outer=100, B=None):
     """Algorithm 1: FEAST with direct (dense LU) shifted solves."""
-    return ifeast(A, X0, emin, emax, z, w, half=half, inner="exact", tol=tol, max_outer=max_outer)
+    return ifeast(A, X0, emin, emax, z, w, half=half, inner="exact", tol=tol, max_outer=max_outer,
+                  B=B)
 
 
 # ---------------------------------------------------------------------------
 # One filtering step from the spectral definition (Eq. rhoh), for pins
 # ---------------------------------------------------------------------------
 
-def filter_step_spectral(A_dense, X, z, w, half=True):
-    """rho_hat(A) X = U rho_hat(Lambda) U^H X with A = U Lambda U^H (Eq. rhoh)."""
-    lam, U = np.linalg.eigh(A_dense)
+def filter_step_spectral(A_dense, X, z, w, half=True, B_dense=None):
+    """rho_hat X = U rho_hat(Lambda) U^H B X with A U = B U Lambda, U^H B U = I
+    (Eq. rhoh; B = I for the standard problem)."""
+    if B_dense is None:
+        lam, U = np.linalg.eigh(A_dense)
+        BX = X
+    else:
+        lam, U = sla.eigh(A_dense, B_dense)
+        BX = B_dense @ X
     r = filter_rho(lam, z, w, half)
-    return U @ (r[:, None] * (U.conj().T @ X))
+    return U @ (r[:, None] * (U.conj().T @ BX))
 
 
 def convergence_bound_delta(lam_all, z, w, half=True):

@@ -130,6 +130,60 @@ def random_sparse_symmetric(n: int, nnz_per_row: int, seed: int) -> CSR:
     return _csr_from_coo(n, (uk // n).astype(np.int64), (uk % n).astype(np.int64), vals)
 
 
+def _kron_csr(mats):
+    import scipy.sparse as sp
+    out = mats[0]
+    for m in mats[1:]:
+        out = sp.kron(out, m, format="csr")
+    return out
+
+
+def fem_q1(grid: tuple[int, ...]) -> tuple[CSR, CSR]:
+    """Stiffness K and mass M of multilinear (Q1) finite elements for -Laplace
+    on the unit cube with Dirichlet boundary, N interior nodes per dimension
+    (h = 1/(N+1)): K = sum_d M1 x .. x K1 (slot d) x .. x M1, M = M1 x .. x M1
+    with K1 = (1/h) tridiag(-1, 2, -1), M1 = (h/6) tridiag(1, 4, 1). 9-point in
+    2D, 27-point in 3D; M is symmetric positive definite. Both share K's
+    sparsity pattern (M's entries are stored on it)."""
+    import scipy.sparse as sp
+    K1s, M1s = [], []
+    for N in grid:
+        h = 1.0 / (N + 1)
+        e = np.ones(N)
+        K1s.append(sp.diags([-e[:-1], 2 * e, -e[:-1]], [-1, 0, 1], format="csr") / h)
+        M1s.append(sp.diags([e[:-1], 4 * e, e[:-1]], [-1, 0, 1], format="csr") * (h / 6.0))
+    d = len(grid)
+    K = None
+    for a in range(d):
+        term = _kron_csr([K1s[b] if b == a else M1s[b] for b in range(d)])
+        K = term if K is None else K + term
+    M = _kron_csr(M1s)
+    pattern = (abs(K) + abs(M)).tocsr()
+    pattern.sort_indices()
+    n = pattern.shape[0]
+
+    def on_pattern(X):
+        X = X.tocsr()
+        out = np.zeros(pattern.nnz)
+        rows = np.repeat(np.arange(n), np.diff(pattern.indptr))
+        out[:] = np.asarray(X[rows, pattern.indices]).ravel()
+        return CSR(n, pattern.indptr.astype(np.int32), pattern.indices.astype(np.int32), out)
+
+    return on_pattern(K), on_pattern(M)
+
+
+def fem_q1_eigs(grid: tuple[int, ...]) -> np.ndarray:
+    """Eigenvalues of K x = lambda M x for fem_q1(grid), ascending: sums over the
+    dimensions of (6/h^2)(1 - cos t)/(2 + cos t), t = p pi/(N+1), p = 1..N."""
+    ev = np.zeros(1)
+    for N in grid:
+        h = 1.0 / (N + 1)
+        t = np.arange(1, N + 1) * math.pi / (N + 1)
+        mu = (6.0 / h ** 2) * (1 - np.cos(t)) / (2 + np.cos(t))
+        ev = (ev[:, None] + mu[None, :]).ravel()
+    return np.sort(ev)
+
+
 # ---------------------------------------------------------------------------
 # Closed-form spectra of the stencils (used to place interval endpoints in
 # spectral gaps and as test pins).

@@ -290,3 +290,62 @@ def test_residual_form_identity_exact_solves():
         lhs = np.linalg.solve(M, x)
         rhs = (x + np.linalg.solve(M, Ad @ x - lam * x)) / (z - lam)
         assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(lhs).max()
+
+
+# ---------------------------------------------------------------- generalized problem A x = lam B x
+
+@pytest.mark.parametrize("grid", [(9,), (7, 6), (4, 5, 3)])
+def test_fem_generator_closed_form(grid):
+    """Q1 stiffness/mass pencil: eigenvalues sum_d (6/h^2)(1 - cos t)/(2 + cos t)."""
+    K, M = inputs.fem_q1(grid)
+    Kd, Md = K.to_scipy().toarray(), M.to_scipy().toarray()
+    assert np.allclose(Kd, Kd.T) and np.allclose(Md, Md.T)
+    assert np.linalg.eigvalsh(Md).min() > 0
+    ev = sla.eigh(Kd, Md, eigvals_only=True)
+    ref = inputs.fem_q1_eigs(grid)
+    assert np.abs(ev - ref).max() <= 1e-10 * ref.max()
+    assert np.array_equal(K.rowptr, M.rowptr) and np.array_equal(K.colidx, M.colidx)
+
+
+def _fem_problem():
+    K, M = inputs.fem_q1((10, 9))
+    ev = inputs.fem_q1_eigs((10, 9))
+    return K, M, ev, 0.0, 0.5 * (ev[5] + ev[6])
+
+
+def test_generalized_exact_filter_matches_spectral_definition():
+    K, M, ev, emin, emax = _fem_problem()
+    Kd, Md = K.to_scipy().toarray(), M.to_scipy().toarray()
+    z, w = orc.contour_nodes(orc.GL_HALF, 8, emin, emax)
+    X = inputs.initial_subspace(K.n, 9, 4)
+    Q_lu = orc._filtered_subspace_exact(Kd, X, z, w, True, Md)
+    Q_sp = orc.filter_step_spectral(Kd, X, z, w, True, Md)
+    assert np.abs(Q_lu - Q_sp).max() < 1e-10 * np.abs(Q_sp).max()
+
+
+def test_generalized_feast_matches_brute_force():
+    K, M, ev, emin, emax = _fem_problem()
+    z, w = orc.contour_nodes(orc.GL_HALF, 8, emin, emax)
+    out = orc.feast(K.to_scipy(), inputs.initial_subspace(K.n, 10, 1), emin, emax, z, w,
+                    B=M.to_scipy())
+    assert out["converged"]
+    lam = out["lam"][out["inside"]]
+    assert lam.size == 6
+    assert np.abs(lam - ev[:6]).max() <= 1e-11 * ev[5]
+    X = out["X"][:, out["inside"]]
+    Md = M.to_scipy().toarray()
+    assert np.abs(X.T @ Md @ X - np.eye(6)).max() < 1e-9  # B-orthonormal Ritz vectors
+
+
+def test_generalized_ifeast_exact_inner_reproduces_feast():
+    K, M, ev, emin, emax = _fem_problem()
+    z, w = orc.contour_nodes(orc.GL_HALF, 6, emin, emax)
+    X0 = inputs.initial_subspace(K.n, 9, 2)
+    h1, h2 = [], []
+    orc.ifeast(K.to_scipy(), X0, emin, emax, z, w, inner="exact", max_outer=3, tol=0.0,
+               B=M.to_scipy(), callback=lambda it, lam, X, res, ins: h1.append(lam.copy()))
+    orc.ifeast(K.to_scipy(), X0, emin, emax, z, w, inner="gmres", k=K.n, max_outer=3, tol=0.0,
+               B=M.to_scipy(), callback=lambda it, lam, X, res, ins: h2.append(lam.copy()))
+    for a, b in zip(h1, h2):
+        ins = (a > emin) & (a < emax)
+        assert np.abs(a[ins] - b[ins]).max() < 1e-9 * np.abs(a).max()
