@@ -130,16 +130,29 @@ void ifeast_default_opts(ifeast_opts *o);
  * lower half, so the filter is rho(lambda) = Re sum_k w_k / (z_k - lambda). */
 int ifeast_contour_nodes(const ifeast_contour *c, double *zw);
 
-/* Device bytes a handle needs for (n, nnz, m0, contour, opts). */
+/* Device bytes a handle needs for (n, nnz, m0, contour, opts), B = I. */
 int ifeast_workspace_bytes(int64_t n, int64_t nnz, int m0, const ifeast_contour *c,
                            const ifeast_opts *o, size_t *bytes);
+
+/* Same for the generalized problem A x = lambda B x with nnz_b non-zeros in
+ * B (nnz_b < 0: B = I). B != I needs IFEAST_INNER_GMRES (else UNSUPPORTED). */
+int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, int m0,
+                                       const ifeast_contour *c, const ifeast_opts *o,
+                                       size_t *bytes);
 
 typedef struct ifeast_ctx *ifeast_t;
 
 /* Validates A (square, rowptr[0] = 0, non-decreasing rowptr, rowptr[n] = nnz,
  * colidx in range), computes the contour on the host, lays out the workspace
  * and copies A into it.
- *   B          must be NULL (standard problem B = I); otherwise UNSUPPORTED.
+ *   B          NULL: standard problem (B = I). Otherwise the symmetric positive
+ *              definite B of A x = lambda B x (host CSR, same n, any pattern;
+ *              definiteness is not checked): the shifted systems become
+ *              (z_k B - A) Y_k = B X (Section 2.2), B_Q = Q^T B Q, the Ritz
+ *              vectors are B-orthonormal and the residual is
+ *              ||A x - lambda B x|| / ||A x||. Needs IFEAST_INNER_GMRES (the
+ *              Krylov basis of z B - A depends on z) and the GMRES stop test
+ *              is taken relative to ||B x_j||.
  *   workspace  device buffer of ws_bytes >= ifeast_workspace_bytes(...) that
  *              the caller keeps alive until ifeast_destroy; NULL makes the
  *              library cudaMalloc (and later cudaFree) its own.
@@ -184,20 +197,22 @@ void ifeast_destroy(ifeast_t h);
  * stream is synchronised). They are the same kernels ifeast_solve launches.
  * ------------------------------------------------------------------------- */
 
-/* Alg. 2 steps 1-2: Q = Re sum_k w_k Y_k with (z_k I - A) Y_k ~= X solved by the
- * configured inner solver, using tolerance alpha * RF (RF >= 0 given here).
+/* Alg. 2 steps 1-2: Q = Re sum_k w_k Y_k with (z_k B - A) Y_k ~= B X (B = I for
+ * a standard handle) solved by the configured inner solver, using tolerance
+ * alpha * RF (RF >= 0 given here).
  * X, Q: n x m0 float64 device. steps (optional, device int32[nc*m0], column
  * c = k*m0 + j) receives the Krylov steps taken by each (node, column). */
 int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32_t *steps);
 
 /* Alg. 2 steps 3-4 on a given Q (n x m0 float64 device): Rayleigh-Ritz with
- * B_Q = Q^T Q, A_Q = Q^T A Q, then X = Q X_Q (n x m0 device, B-orthonormal
+ * B_Q = Q^T B Q, A_Q = Q^T A Q, then X = Q X_Q (n x m0 device, B-orthonormal
  * Ritz vectors), lam[m0] ascending, resid[m0] relative residuals (device).
  * Returns BREAKDOWN if B_Q cannot be factored. */
 int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, double *resid);
 
 /* One sparse product with a per-column complex shift (the operator of Alg. 2
- * step 1): W[:, c] = z[c / m0] V[:, c] - A V[:, c] for c < ncols, where V and W
+ * step 1): W[:, c] = z[c / m0] B V[:, c] - A V[:, c] for c < ncols (B = I for
+ * a standard handle), where V and W
  * are n x ncols complex float64 blocks (row-major, real and imaginary parts
  * interleaved: element (i, c) at [2*(i*ncols + c)]), z holds nc = ncols / m0
  * complex values interleaved (device). Uses the handle's A. ncols must be a

@@ -65,6 +65,9 @@ SIGNATURES = {
     "ifeast_contour_nodes": (ct.c_int, [ct.POINTER(Contour), ct.c_void_p]),
     "ifeast_workspace_bytes": (ct.c_int, [ct.c_int64, ct.c_int64, ct.c_int, ct.POINTER(Contour),
                                           ct.POINTER(Opts), ct.POINTER(ct.c_size_t)]),
+    "ifeast_workspace_bytes_generalized": (ct.c_int, [ct.c_int64, ct.c_int64, ct.c_int64, ct.c_int,
+                                                      ct.POINTER(Contour), ct.POINTER(Opts),
+                                                      ct.POINTER(ct.c_size_t)]),
     "ifeast_create": (ct.c_int, [ct.POINTER(Csr), ct.c_void_p, ct.POINTER(Contour), ct.c_int,
                                  ct.POINTER(Opts), ct.c_void_p, ct.c_size_t, ct.c_void_p,
                                  ct.POINTER(ct.c_void_p)]),

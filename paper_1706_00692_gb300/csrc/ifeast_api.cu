@@ -30,6 +30,10 @@ struct ifeast_ctx {
   // device buffers (carved from ws)
   int32_t *rowptr = nullptr, *colidx = nullptr;
   double *val = nullptr;
+  // B of A x = lambda B x (generalized problem; null: B = I)
+  int64_t nnzB = -1;
+  int32_t *rowptrB = nullptr, *colidxB = nullptr;
+  double *valB = nullptr, *BQ = nullptr, *BX = nullptr;
   double2 *z = nullptr, *w = nullptr;
   double2 *V = nullptr, *W = nullptr, *part = nullptr, *H1 = nullptr, *H2 = nullptr;
   double *inv_h = nullptr;
@@ -77,6 +81,7 @@ struct Offsets {
       AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
   size_t val32, LV, LW0, LW1, lpart, lalpha, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
       lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
+  size_t rowptrB, colidxB, valB, BQ, BX;
 };
 
 int device_sms() {
@@ -87,7 +92,7 @@ int device_sms() {
 }
 
 Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr,
-             bool minres, bool fp32, int sms_for_plan) {
+             bool minres, bool fp32, int sms_for_plan, int64_t nnzB) {
   Layout L;
   Offsets o{};
   const size_t C = (size_t)nc * m0;
@@ -156,6 +161,13 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
   o.res_part = L.take<double>((size_t)Pr * 3 * m0);
   o.res = L.take<double>(m0);
   o.status = L.take<DevStatus>(1);
+  if (nnzB >= 0) {  // generalized problem
+    o.rowptrB = L.take<int32_t>(n + 1);
+    o.colidxB = L.take<int32_t>(nnzB > 0 ? nnzB : 1);
+    o.valB = L.take<double>(nnzB > 0 ? nnzB : 1);
+    o.BQ = L.take<double>((size_t)n * m0);
+    o.BX = L.take<double>((size_t)n * m0);
+  }
   o.total = (L.off + 255) / 256 * 256;
   return o;
 }
@@ -301,6 +313,9 @@ GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q) {
   a.status = h->status;
   a.tl = h->tl;
   a.prof = h->profiling ? &h->prof : nullptr;
+  a.rowptrB = h->rowptrB;
+  a.colidxB = h->colidxB;
+  a.valB = h->valB;
   return a;
 }
 
@@ -334,7 +349,32 @@ RRArgs rr_args(ifeast_ctx *h, const double *Q, double *X) {
   a.Rres = h->minres ? h->Rres : nullptr;
   a.rnorm = h->minres ? h->rnorm : nullptr;
   a.prof = h->profiling ? &h->prof : nullptr;
+  a.rowptrB = h->rowptrB;
+  a.colidxB = h->colidxB;
+  a.valB = h->valB;
+  a.BQ = h->BQ;
+  a.BX = h->BX;
   return a;
+}
+
+// Right-hand side block of the shifted systems: X (B = I) or B X written to
+// h->BX, with its column norms in h->beta.
+int prepare_rhs(ifeast_ctx *h, const double *X, const double **rhs) {
+  Profiler *pf = h->profiling ? &h->prof : nullptr;
+  if (!h->rowptrB) {
+    if (column_norms((int)h->n, h->m0, X, h->res_part, h->Pr, h->beta, h->stream, pf) !=
+        cudaSuccess)
+      return IFEAST_ERR_CUDA;
+    *rhs = X;
+    return IFEAST_OK;
+  }
+  if (spmm_block((int)h->n, h->m0, h->rowptrB, h->colidxB, h->valB, X, h->BX, h->Pg, h->stream) !=
+          cudaSuccess ||
+      column_norms((int)h->n, h->m0, h->BX, h->res_part, h->Pr, h->beta, h->stream, pf) !=
+          cudaSuccess)
+    return IFEAST_ERR_CUDA;
+  *rhs = h->BX;
+  return IFEAST_OK;
 }
 
 // Shared-basis inner solve. correction = 0: right-hand sides X (norms in
@@ -457,7 +497,15 @@ int ifeast_contour_nodes(const ifeast_contour *c, double *zw) {
 
 int ifeast_workspace_bytes(int64_t n, int64_t nnz, int m0, const ifeast_contour *c,
                            const ifeast_opts *o, size_t *bytes) {
+  return ifeast_workspace_bytes_generalized(n, nnz, -1, m0, c, o, bytes);
+}
+
+int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, int m0,
+                                       const ifeast_contour *c, const ifeast_opts *o,
+                                       size_t *bytes) {
   if (!bytes || n < 1 || nnz < 0 || m0 < 1 || m0 > kMaxM0 || m0 > n) return IFEAST_ERR_INVALID_ARG;
+  if (nnz_b > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
+  if (nnz_b >= 0 && o && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (n > (int64_t)INT32_MAX - 1 || nnz > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
   int rc = validate_contour(c);
   if (rc) return rc;
@@ -470,7 +518,7 @@ int ifeast_workspace_bytes(int64_t n, int64_t nnz, int m0, const ifeast_contour 
   const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
   const int Pr = Pg;
   *bytes = plan(n, nnz, m0, c->nc, o->inner_max_iters, tl, Pg, Pr, minres,
-                o->precision == IFEAST_FP32, sms).total;
+                o->precision == IFEAST_FP32, sms, nnz_b < 0 ? -1 : nnz_b).total;
   return IFEAST_OK;
 }
 
@@ -479,20 +527,25 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
                   ifeast_t *out) {
   if (!out) return IFEAST_ERR_INVALID_ARG;
   *out = nullptr;
-  if (B) return IFEAST_ERR_UNSUPPORTED;
   if (!A || !A->rowptr || (A->nnz > 0 && (!A->colidx || !A->val))) return IFEAST_ERR_INVALID_ARG;
   const int64_t n = A->n, nnz = A->nnz;
   if (n < 1 || nnz < 0) return IFEAST_ERR_INVALID_ARG;
+  if (B && (B->n != n || !B->rowptr || B->nnz < 0 || (B->nnz > 0 && (!B->colidx || !B->val))))
+    return IFEAST_ERR_INVALID_ARG;
+  const int64_t nnzB = B ? B->nnz : -1;
   size_t need = 0;
-  int rc = ifeast_workspace_bytes(n, nnz, m0, c, o, &need);
+  int rc = ifeast_workspace_bytes_generalized(n, nnz, nnzB, m0, c, o, &need);
   if (rc) return rc;
   // CSR structure checks on the host
-  if (A->rowptr[0] != 0 || A->rowptr[n] != nnz) return IFEAST_ERR_INVALID_ARG;
-  for (int64_t i = 0; i < n; ++i)
-    if (A->rowptr[i + 1] < A->rowptr[i]) return IFEAST_ERR_INVALID_ARG;
-  for (int64_t p = 0; p < nnz; ++p)
-    if (A->colidx[p] < 0 || A->colidx[p] >= n || !std::isfinite(A->val[p]))
-      return IFEAST_ERR_INVALID_ARG;
+  for (const ifeast_csr *M : {A, B}) {
+    if (!M) continue;
+    if (M->rowptr[0] != 0 || M->rowptr[n] != M->nnz) return IFEAST_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i)
+      if (M->rowptr[i + 1] < M->rowptr[i]) return IFEAST_ERR_INVALID_ARG;
+    for (int64_t p = 0; p < M->nnz; ++p)
+      if (M->colidx[p] < 0 || M->colidx[p] >= n || !std::isfinite(M->val[p]))
+        return IFEAST_ERR_INVALID_ARG;
+  }
   if (workspace && ws_bytes < need) return IFEAST_ERR_OOM;
   rc = ensure_device_init();
   if (rc) return rc;
@@ -517,7 +570,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->Pr = h->Pg;
   contour_host(c, h->zh, h->wh);
   const Offsets off =
-      plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, h->fp32, h->num_sms);
+      plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, h->fp32, h->num_sms, nnzB);
   if (workspace) {
     h->ws = (char *)workspace;
     h->ws_bytes = ws_bytes;
@@ -572,6 +625,14 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->res_part = (double *)(b + off.res_part);
   h->res = (double *)(b + off.res);
   h->status = (DevStatus *)(b + off.status);
+  if (B) {
+    h->nnzB = nnzB;
+    h->rowptrB = (int32_t *)(b + off.rowptrB);
+    h->colidxB = (int32_t *)(b + off.colidxB);
+    h->valB = (double *)(b + off.valB);
+    h->BQ = (double *)(b + off.BQ);
+    h->BX = (double *)(b + off.BX);
+  }
   if (h->minres) {
     if (h->fp32) {
       h->val32 = (float *)(b + off.val32);
@@ -606,6 +667,16 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
                                h->stream) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(h->val, A->val, nnz * sizeof(double), cudaMemcpyHostToDevice,
                                h->stream) == cudaSuccess;
+  }
+  if (B) {
+    ok = ok && cudaMemcpyAsync(h->rowptrB, B->rowptr, (n + 1) * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+    if (nnzB > 0) {
+      ok = ok && cudaMemcpyAsync(h->colidxB, B->colidx, nnzB * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+      ok = ok && cudaMemcpyAsync(h->valB, B->val, nnzB * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream) == cudaSuccess;
+    }
   }
   ok = ok && cudaMemcpyAsync(h->z, h->zh.data(), h->nc * sizeof(double2), cudaMemcpyHostToDevice,
                              h->stream) == cudaSuccess;
@@ -652,9 +723,10 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
   const size_t xbytes = (size_t)h->n * h->m0 * sizeof(double);
   CK(cudaMemcpyAsync(h->X, X0, xbytes,
                      x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-  CK(column_norms((int)h->n, h->m0, h->X, h->res_part, h->Pr, h->beta, h->stream,
-                  h->profiling ? &h->prof : nullptr));
-  int rc = set_tolerance(h, 1.0);
+  const double *rhs = nullptr;
+  int rc = prepare_rhs(h, h->X, &rhs);
+  if (rc) return rc;
+  rc = set_tolerance(h, 1.0);
   if (rc) return rc;
   int result = IFEAST_ERR_NOT_CONVERGED;
   for (int it = 1; it <= h->opts.max_outer; ++it) {
@@ -662,8 +734,8 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
     if (rc) return rc;
     if (h->minres)
       CK(minres_filter(minres_args(h, h->X, h->Q, it > 1 ? 1 : 0), h->stream));
-    else
-      CK(gmres_filter(gmres_args(h, h->X, h->Q), h->stream));
+    else  // right-hand sides X, or B X (norms in beta) from the previous Rayleigh-Ritz
+      CK(gmres_filter(gmres_args(h, h->rowptrB ? h->BX : h->X, h->Q), h->stream));
     CK(rayleigh_ritz(rr_args(h, h->Q, h->X), h->stream));
     CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                        h->stream));
@@ -755,14 +827,15 @@ int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *
 
 int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32_t *steps) {
   if (!h || !X || !Q || !(RF >= 0.0)) return IFEAST_ERR_INVALID_ARG;
-  CK(column_norms((int)h->n, h->m0, X, h->res_part, h->Pr, h->beta, h->stream,
-                  h->profiling ? &h->prof : nullptr));
-  int rc = set_tolerance(h, RF);
+  const double *rhs = nullptr;
+  int rc = prepare_rhs(h, X, &rhs);
+  if (rc) return rc;
+  rc = set_tolerance(h, RF);
   if (rc) return rc;
   if (h->minres)
     CK(minres_filter(minres_args(h, X, Q, 0), h->stream));
   else
-    CK(gmres_filter(gmres_args(h, X, Q), h->stream));
+    CK(gmres_filter(gmres_args(h, rhs, Q), h->stream));
   if (steps)
     CK(cudaMemcpyAsync(steps, h->minres ? h->lsteps : h->steps, h->C * sizeof(int),
                        cudaMemcpyDeviceToDevice, h->stream));
@@ -792,7 +865,8 @@ int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0,
     return IFEAST_ERR_INVALID_ARG;
   const RowTiling tl = make_tiling(h->n, ncols, h->num_sms);
   CK(spmm_shift_only((int)h->n, h->rowptr, h->colidx, h->val, (const double2 *)V, (double2 *)W,
-                     ncols, m0, (const double2 *)z, tl, h->stream));
+                     ncols, m0, (const double2 *)z, tl, h->stream, h->rowptrB, h->colidxB,
+                     h->valB));
   CK(cudaStreamSynchronize(h->stream));
   return IFEAST_OK;
 }

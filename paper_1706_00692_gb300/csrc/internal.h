@@ -109,11 +109,14 @@ struct GmresArgs {
   DevStatus *status;        // tol_rel read from here, step counts written here
   RowTiling tl;
   Profiler *prof;
+  const int32_t *rowptrB, *colidxB;  // B of A x = lambda B x (null: B = I)
+  const double *valB;
 };
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st);
 cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
                             const double *val, const double2 *V, double2 *W, int ncols,
-                            int m0, const double2 *z, RowTiling tl, cudaStream_t st);
+                            int m0, const double2 *z, RowTiling tl, cudaStream_t st,
+                            const int32_t *rowptrB, const int32_t *colidxB, const double *valB);
 
 // ---- inner solve on one shared Lanczos basis per column (FP32 or FP64) ----
 struct MinresState {
@@ -183,6 +186,10 @@ struct RRArgs {
   double *beta;             // m0 norms of the new X columns
   double *Rres;             // n x m0 A X - X Lambda of the new X (nullptr: not stored)
   double *rnorm;            // m0 ||A x_j - lambda_j x_j|| (nullptr: not stored)
+  const int32_t *rowptrB, *colidxB;  // B of A x = lambda B x (null: B = I)
+  const double *valB;
+  double *BQ;               // n x m0 B Q (generalized only)
+  double *BX;               // n x m0 B X of the new X (generalized only); beta = ||B x_j||
   double emin, emax, alpha;
   DevStatus *status;
   Profiler *prof;
@@ -191,6 +198,9 @@ cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
 cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st);
 cudaError_t column_norms(int n, int m0, const double *X, double *part, int Pr, double *beta,
                          cudaStream_t st, Profiler *prof);
+// Y = A X for an n x m0 real block (one row-tiled sparse product).
+cudaError_t spmm_block(int n, int m0, const int32_t *rowptr, const int32_t *colidx,
+                       const double *val, const double *X, double *Y, int P, cudaStream_t st);
 // The reduced generalised eigensolver of rayleigh_ritz on caller buffers.
 cudaError_t reduced_eig_launch(int m, const double *Aq, const double *Bq, double *L, double *Cm,
                                double *U, double *XQ, double *lam, DevStatus *status,

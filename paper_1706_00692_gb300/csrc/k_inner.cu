@@ -65,15 +65,17 @@ __device__ __forceinline__ void block_store_partials(const double2 (&acc)[LMAX],
   }
 }
 
-// W = z_{node(c)} V_s - A V_s on every active column; with DOTS also the
-// block partials of <V_l, W>, l = 0..s.
+// W = z_{node(c)} B V_s - A V_s on every active column (B = I when rowptrB is
+// null); with DOTS also the block partials of <V_l, W>, l = 0..s.
 template <int LMAX, bool DOTS>
 __global__ void __launch_bounds__(kThreads)
 k_spmm_shift_dot(int n, int C, int m0, const int32_t *__restrict__ rowptr,
                  const int32_t *__restrict__ colidx, const double *__restrict__ val,
                  const double2 *__restrict__ V, size_t vstride, int s,
                  const double2 *__restrict__ z, const int *__restrict__ done,
-                 double2 *__restrict__ W, double2 *__restrict__ part, int rows, int K2) {
+                 double2 *__restrict__ W, double2 *__restrict__ part, int rows, int K2,
+                 const int32_t *__restrict__ rowptrB, const int32_t *__restrict__ colidxB,
+                 const double *__restrict__ valB) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * 32 + lane;
   const bool active = c < C && (done == nullptr || done[c] == 0);
@@ -87,7 +89,21 @@ k_spmm_shift_dot(int n, int C, int m0, const int32_t *__restrict__ rowptr,
   if (active) {
     for (int r = r0 + warp; r < r1; r += kWarps) {
       const size_t rc = (size_t)r * C + c;
-      double2 w = cmul(zc, Vs[rc]);
+      double2 bv;
+      if (rowptrB == nullptr) {
+        bv = Vs[rc];
+      } else {
+        bv = make_double2(0.0, 0.0);
+        const int qb = rowptrB[r], qe = rowptrB[r + 1];
+#pragma unroll 4
+        for (int q = qb; q < qe; ++q) {
+          const double b = valB[q];
+          const double2 v = Vs[(size_t)colidxB[q] * C + c];
+          bv.x = fma(b, v.x, bv.x);
+          bv.y = fma(b, v.y, bv.y);
+        }
+      }
+      double2 w = cmul(zc, bv);
       const int jb = rowptr[r], je = rowptr[r + 1];
 #pragma unroll 4
       for (int j = jb; j < je; ++j) {
@@ -349,7 +365,7 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
   IFEAST_PROF_BEGIN(a.prof, K_GM_SPMM);
   k_spmm_shift_dot<LMAX, true><<<grid, kThreads, 0, st>>>(
       a.n, a.C, a.m0, a.rowptr, a.colidx, a.val, a.V, vstride, s, a.z, a.done, a.W, a.part,
-      a.tl.rows, K2);
+      a.tl.rows, K2, a.rowptrB, a.colidxB, a.valB);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 1, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H1);
@@ -421,10 +437,11 @@ cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
 
 cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
                             const double *val, const double2 *V, double2 *W, int ncols, int m0,
-                            const double2 *z, RowTiling tl, cudaStream_t st) {
+                            const double2 *z, RowTiling tl, cudaStream_t st,
+                            const int32_t *rowptrB, const int32_t *colidxB, const double *valB) {
   k_spmm_shift_dot<1, false><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
       n, ncols, m0, rowptr, colidx, val, V, (size_t)n * ncols, 0, z, nullptr, W, nullptr, tl.rows,
-      0);
+      0, rowptrB, colidxB, valB);
   return cudaGetLastError();
 }
 

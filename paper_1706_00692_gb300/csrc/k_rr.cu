@@ -42,12 +42,14 @@ k_spmm_real(int n, int m, const int32_t *__restrict__ rowptr, const int32_t *__r
 // Partials of Q^T AQ and Q^T Q over this block's rows. Thread t of block
 // (bx, by) owns the 4x4 output tile number by*256 + t of the upper triangle
 // of tiles (m0 padded to mp = multiple of 4).
+// With BQ (generalized problem) the second matrix is Q^T (B Q) instead of Q^T Q.
 __global__ void __launch_bounds__(kThreads)
 k_gram(int n, int m, int mp, const double *__restrict__ Q, const double *__restrict__ AQ,
-       double *__restrict__ part, int rows) {
+       const double *__restrict__ BQ, double *__restrict__ part, int rows) {
   extern __shared__ double sm[];
   double *Qs = sm;                       // kGramRows x mp
   double *As = sm + kGramRows * mp;      // kGramRows x mp
+  double *Bs = BQ ? sm + 2 * kGramRows * mp : Qs;  // kGramRows x mp
   const int nt = mp / 4;
   const int ntiles = nt * (nt + 1) / 2;
   const int tile = blockIdx.y * kThreads + threadIdx.x;
@@ -76,17 +78,19 @@ k_gram(int n, int m, int mp, const double *__restrict__ Q, const double *__restr
       const bool in = rr < nr && jj < m;
       Qs[e] = in ? Q[(size_t)(rb + rr) * m + jj] : 0.0;
       As[e] = in ? AQ[(size_t)(rb + rr) * m + jj] : 0.0;
+      if (BQ) Bs[e] = in ? BQ[(size_t)(rb + rr) * m + jj] : 0.0;
     }
     __syncthreads();
     if (own) {
       for (int rr = 0; rr < nr; ++rr) {
         const double *qr = Qs + rr * mp;
         const double *ar = As + rr * mp;
+        const double *br = Bs + rr * mp;
         double qi[4], qj[4], aj[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           qi[p] = qr[4 * ti + p];
-          qj[p] = qr[4 * tj + p];
+          qj[p] = br[4 * tj + p];
           aj[p] = ar[4 * tj + p];
         }
 #pragma unroll
@@ -123,15 +127,21 @@ __global__ void k_reduce_gram(int Pg, int m, int mp, const double *__restrict__ 
   const int i = idx / m, j = idx % m;
   if (i > j) return;
   const bool same_tile = (i / 4) == (j / 4);
-  double sa = 0.0, sb = 0.0, sa2 = 0.0;
+  double sa = 0.0, sb = 0.0, sa2 = 0.0, sb2 = 0.0;
   for (int b = 0; b < Pg; ++b) {
     const double *pa = part + (size_t)b * 2 * mp * mp;
     const double *pb = pa + (size_t)mp * mp;
     sa += pa[(size_t)i * mp + j];
     sb += pb[(size_t)i * mp + j];
-    if (same_tile) sa2 += pa[(size_t)j * mp + i];
+    if (same_tile) {
+      sa2 += pa[(size_t)j * mp + i];
+      sb2 += pb[(size_t)j * mp + i];
+    }
   }
-  if (same_tile) sa = 0.5 * (sa + sa2);
+  if (same_tile) {
+    sa = 0.5 * (sa + sa2);
+    sb = 0.5 * (sb + sb2);
+  }
   Aq[(size_t)i * m + j] = sa;
   Aq[(size_t)j * m + i] = sa;
   Bq[(size_t)i * m + j] = sb;
@@ -352,11 +362,12 @@ __global__ void __launch_bounds__(256)
 k_update_resid(int n, int m, const double *__restrict__ Q, const double *__restrict__ AQ,
                const double *__restrict__ XQ, const double *__restrict__ lam,
                double *__restrict__ X, double *__restrict__ Rres, double *__restrict__ part,
-               int rows) {
+               int rows, const double *__restrict__ BQ, double *__restrict__ BX) {
   extern __shared__ double sm[];
   const int RB = 8;
   double *Qs = sm;            // RB x m
   double *As = sm + RB * m;   // RB x m
+  double *Bs = sm + 2 * RB * m;  // RB x m (generalized only)
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
   double e2[QMAX], a2[QMAX], x2[QMAX];
@@ -370,27 +381,32 @@ k_update_resid(int n, int m, const double *__restrict__ Q, const double *__restr
       const int rr = e / m, jj = e % m;
       Qs[e] = rr < nr ? Q[(size_t)(rb + rr) * m + jj] : 0.0;
       As[e] = rr < nr ? AQ[(size_t)(rb + rr) * m + jj] : 0.0;
+      if (BQ) Bs[e] = rr < nr ? BQ[(size_t)(rb + rr) * m + jj] : 0.0;
     }
     __syncthreads();
     if (ty < nr) {
       const double *qr = Qs + ty * m;
       const double *ar = As + ty * m;
+      const double *br = Bs + ty * m;
 #pragma unroll
       for (int q = 0; q < QMAX; ++q) {
         const int j = tx + 32 * q;
         if (j < m) {
-          double x = 0.0, ax = 0.0;
+          double x = 0.0, ax = 0.0, bx = 0.0;
           for (int i = 0; i < m; ++i) {
             const double xq = XQ[(size_t)i * m + j];
             x = fma(qr[i], xq, x);
             ax = fma(ar[i], xq, ax);
+            if (BQ) bx = fma(br[i], xq, bx);
           }
           X[(size_t)(rb + ty) * m + j] = x;
-          const double d = ax - lam[j] * x;
+          if (!BQ) bx = x;
+          else BX[(size_t)(rb + ty) * m + j] = bx;
+          const double d = ax - lam[j] * bx;
           if (Rres) Rres[(size_t)(rb + ty) * m + j] = d;
           e2[q] = fma(d, d, e2[q]);
           a2[q] = fma(ax, ax, a2[q]);
-          x2[q] = fma(x, x, x2[q]);
+          x2[q] = fma(bx, bx, x2[q]);  // ||B x_j||^2: norm of the next right-hand side
         }
       }
     }
@@ -496,7 +512,7 @@ __global__ void k_reduce_resid(int Pr, int m, const double *__restrict__ part,
 
 cudaError_t rr_init() {
   cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       2 * kGramRows * kMaxM0 * (int)sizeof(double));
+                                       3 * kGramRows * kMaxM0 * (int)sizeof(double));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kEigSmem);
@@ -514,6 +530,12 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
     k_spmm_real<<<dim3((a.n + rows - 1) / rows, tiles), kThreads, 0, st>>>(
         a.n, m, a.rowptr, a.colidx, a.val, a.Q, a.AQ, rows);
     IFEAST_PROF_END(a.prof);
+    if (a.rowptrB) {
+      IFEAST_PROF_BEGIN(a.prof, K_RR_SPMM);
+      k_spmm_real<<<dim3((a.n + rows - 1) / rows, tiles), kThreads, 0, st>>>(
+          a.n, m, a.rowptrB, a.colidxB, a.valB, a.Q, a.BQ, rows);
+      IFEAST_PROF_END(a.prof);
+    }
   }
   // Gram partials
   {
@@ -521,10 +543,10 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
     const int ntiles = nt * (nt + 1) / 2;
     const int gy = (ntiles + kThreads - 1) / kThreads;
     const int rows = (a.n + a.Pg - 1) / a.Pg;
-    const size_t smem = 2 * (size_t)kGramRows * mp * sizeof(double);
+    const size_t smem = (a.rowptrB ? 3 : 2) * (size_t)kGramRows * mp * sizeof(double);
     IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM);
-    k_gram<<<dim3((a.n + rows - 1) / rows, gy), kThreads, smem, st>>>(a.n, m, mp, a.Q, a.AQ,
-                                                                     a.gram_part, rows);
+    k_gram<<<dim3((a.n + rows - 1) / rows, gy), kThreads, smem, st>>>(
+        a.n, m, mp, a.Q, a.AQ, a.rowptrB ? a.BQ : nullptr, a.gram_part, rows);
     IFEAST_PROF_END(a.prof);
     const int pg_used = (a.n + rows - 1) / rows;
     IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM_REDUCE);
@@ -544,22 +566,23 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
   {
     const int rows = (a.n + a.Pr - 1) / a.Pr;
     const int pr_used = (a.n + rows - 1) / rows;
-    const size_t smem = 2 * 8 * (size_t)m * sizeof(double);
+    const size_t smem = (a.rowptrB ? 3 : 2) * 8 * (size_t)m * sizeof(double);
+    const double *BQ = a.rowptrB ? a.BQ : nullptr;
     const dim3 blk(32, 8);
     const int qm = (m + 31) / 32;
     IFEAST_PROF_BEGIN(a.prof, K_RR_UPDATE);
     if (qm <= 1)
       k_update_resid<1><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.Rres, a.res_part, rows);
+                                                     a.Rres, a.res_part, rows, BQ, a.BX);
     else if (qm <= 2)
       k_update_resid<2><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.Rres, a.res_part, rows);
+                                                     a.Rres, a.res_part, rows, BQ, a.BX);
     else if (qm <= 4)
       k_update_resid<4><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.Rres, a.res_part, rows);
+                                                     a.Rres, a.res_part, rows, BQ, a.BX);
     else
       k_update_resid<8><<<pr_used, blk, smem, st>>>(a.n, m, a.Q, a.AQ, a.XQ, a.lam, a.X,
-                                                     a.Rres, a.res_part, rows);
+                                                     a.Rres, a.res_part, rows, BQ, a.BX);
     IFEAST_PROF_END(a.prof);
     IFEAST_PROF_BEGIN(a.prof, K_RR_RESID);
     k_reduce_resid<<<1, 256, 0, st>>>(pr_used, m, a.res_part, a.lam, a.emin, a.emax, a.alpha,
@@ -589,6 +612,14 @@ cudaError_t column_norms(int n, int m, const double *X, double *part, int Pr, do
   IFEAST_PROF_BEGIN(prof, K_NORMS_REDUCE);
   k_reduce_norms<<<(m + 127) / 128, 128, 0, st>>>(pr_used, m, part, beta);
   IFEAST_PROF_END(prof);
+  return cudaGetLastError();
+}
+
+cudaError_t spmm_block(int n, int m, const int32_t *rowptr, const int32_t *colidx,
+                       const double *val, const double *X, double *Y, int P, cudaStream_t st) {
+  const int rows = (n + P - 1) / P;
+  k_spmm_real<<<dim3((n + rows - 1) / rows, (m + 31) / 32), kThreads, 0, st>>>(n, m, rowptr, colidx,
+                                                                             val, X, Y, rows);
   return cudaGetLastError();
 }
 

@@ -41,13 +41,14 @@ def contour_nodes(rule: str, nc: int, emin: float, emax: float):
 
 
 class Solver:
-    """One IFEAST problem (A, interval, m0, contour, options) bound to a handle."""
+    """One IFEAST problem (A, optional SPD B, interval, m0, contour, options)
+    bound to a handle."""
 
     def __init__(self, A: CSR, emin: float, emax: float, m0: int, *, nc: int = 8,
                  rule: str = "gl_half", inner: str = "gmres", inner_iters: int = 10,
                  alpha: float = 0.0, max_outer: int = 100, tol: float = 1e-10,
                  precision: str = "fp64", device: str | int = "cuda",
-                 torch_workspace: bool = True, verbose: bool = False):
+                 torch_workspace: bool = True, verbose: bool = False, B: CSR | None = None):
         torch = _torch()
         self.lib = _lib.load()
         self.torch = torch
@@ -65,10 +66,11 @@ class Solver:
         self.opts.precision = _lib.PRECISIONS[precision]
         self.opts.verbose = 1 if verbose else 0
         nbytes = ct.c_size_t(0)
-        rc = self.lib.ifeast_workspace_bytes(self.n, A.nnz, self.m0, ct.byref(self.contour),
-                                             ct.byref(self.opts), ct.byref(nbytes))
+        rc = self.lib.ifeast_workspace_bytes_generalized(
+            self.n, A.nnz, -1 if B is None else B.nnz, self.m0, ct.byref(self.contour),
+            ct.byref(self.opts), ct.byref(nbytes))
         if rc:
-            raise IFEASTError(rc, "ifeast_workspace_bytes")
+            raise IFEASTError(rc, "ifeast_workspace_bytes_generalized")
         self.workspace_bytes = int(nbytes.value)
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.current_stream(self.device)
@@ -82,8 +84,14 @@ class Solver:
             self._val = np.ascontiguousarray(A.val, dtype=np.float64)
             csr = _lib.Csr(self.n, A.nnz, self._rowptr.ctypes.data, self._colidx.ctypes.data,
                            self._val.ctypes.data)
+            bref = None
+            if B is not None:
+                self._B = (np.ascontiguousarray(B.rowptr, dtype=np.int32),
+                           np.ascontiguousarray(B.colidx, dtype=np.int32),
+                           np.ascontiguousarray(B.val, dtype=np.float64))
+                bref = ct.byref(_lib.Csr(int(B.n), B.nnz, *(a.ctypes.data for a in self._B)))
             h = ct.c_void_p()
-            rc = self.lib.ifeast_create(ct.byref(csr), None, ct.byref(self.contour), self.m0,
+            rc = self.lib.ifeast_create(ct.byref(csr), bref, ct.byref(self.contour), self.m0,
                                         ct.byref(self.opts), ws_ptr, ws_len,
                                         ct.c_void_p(self.stream.cuda_stream), ct.byref(h))
             if rc:
@@ -165,7 +173,8 @@ class Solver:
         return X, lam, res
 
     def spmm_shift(self, V, z):
-        """W[:, c] = z[c // m0] V[:, c] - A V[:, c] for a CUDA complex128 (n, C) V."""
+        """W[:, c] = z[c // m0] B V[:, c] - A V[:, c] (B = I unless given) for a CUDA
+        complex128 (n, C) V."""
         torch = self.torch
         V = V.contiguous()
         assert V.dtype == torch.complex128 and V.shape[0] == self.n

@@ -123,7 +123,35 @@ def test_create_rejects_bad_options(lib):
         _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, contour=_lib.Contour(0, 4, 1.0, 0.5))[0] == _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, contour=_lib.Contour(2, 4, 0.0, 0.5))[0] == _lib.IFEAST_ERR_UNSUPPORTED
-    assert _create(lib, A, B=ct.c_void_p(1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+
+
+def _csr_ref(M, keep):
+    arrs = (np.ascontiguousarray(M.rowptr, np.int32), np.ascontiguousarray(M.colidx, np.int32),
+            np.ascontiguousarray(M.val, np.float64))
+    keep.append(arrs)
+    return ct.byref(_lib.Csr(M.n, M.nnz, *(a.ctypes.data for a in arrs)))
+
+
+def test_create_checks_B(lib):
+    K, M = inputs.fem_q1((5, 4))
+    keep = []
+    # B of another size, malformed B, and B with the shared-basis inner solver
+    # (its Krylov basis is only z-independent for B = I) are refused on the host.
+    assert _create(lib, K, B=_csr_ref(inputs.laplacian((4, 4)), keep))[0] == \
+        _lib.IFEAST_ERR_INVALID_ARG
+    bad = inputs.CSR(M.n, M.rowptr.copy(), M.colidx.copy(), M.val.copy())
+    bad.colidx[0] = -1
+    assert _create(lib, K, B=_csr_ref(bad, keep))[0] == _lib.IFEAST_ERR_INVALID_ARG
+    assert _create(lib, K, B=_csr_ref(M, keep), opts=_opts(lib, inner_solver=1))[0] == \
+        _lib.IFEAST_ERR_UNSUPPORTED
+    c = _lib.Contour(0, 8, 0.0, 1.0)
+    b0, b1 = ct.c_size_t(), ct.c_size_t()
+    assert lib.ifeast_workspace_bytes(K.n, K.nnz, 4, ct.byref(c), ct.byref(_opts(lib)),
+                                      ct.byref(b0)) == 0
+    assert lib.ifeast_workspace_bytes_generalized(K.n, K.nnz, M.nnz, 4, ct.byref(c),
+                                                  ct.byref(_opts(lib)), ct.byref(b1)) == 0
+    # B's CSR plus the n x m0 blocks B Q and B X
+    assert b1.value - b0.value >= 4 * (K.n + 1) + 12 * M.nnz + 2 * 8 * K.n * 4
 
 
 def test_strerror_and_null_handles(lib):
