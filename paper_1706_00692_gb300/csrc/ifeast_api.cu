@@ -51,6 +51,7 @@ struct ifeast_ctx {
   double *lpart = nullptr, *lalpha = nullptr, *lbeta = nullptr, *ltol = nullptr;
   double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
+  int *lticket = nullptr;
   double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
   int *active_host = nullptr;  // pinned
   int ell_w = 0;
@@ -80,7 +81,7 @@ struct Offsets {
   size_t rowptr, colidx, val, z, w, V, W, part, H1, H2, inv_h, CS, SN, R, G, Y, steps, done, X, Q,
       AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
   size_t val32, LV, LW0, LW1, lpart, lalpha, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
-      lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
+      lcoldone, lactive, lticket, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
   size_t rowptrB, colidxB, valB, BQ, BX;
 };
 
@@ -140,6 +141,7 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.ldone = L.take<int>(C);
     o.lcoldone = L.take<int>(m0);
     o.lactive = L.take<int>(1);
+    o.lticket = L.take<int>((m0 + 31) / 32);
     o.lSj = L.take<int>(m0);
     o.lcoef = L.take<double>((size_t)K * m0 + ((size_t)K * m0 + 1) / 2);  // FP64 + FP32 copy
     o.lcx = L.take<double>(m0);
@@ -426,6 +428,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   m.done = h->ldone;
   m.coldone = h->lcoldone;
   m.active = h->lactive;
+  m.ticket = h->lticket;
   m.status = h->status;
   return a;
 }
@@ -654,6 +657,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->ldone = (int *)(b + off.ldone);
     h->lcoldone = (int *)(b + off.lcoldone);
     h->lactive = (int *)(b + off.lactive);
+    h->lticket = (int *)(b + off.lticket);
     h->lSj = (int *)(b + off.lSj);
     h->lcoef = (double *)(b + off.lcoef);
     h->lcx = (double *)(b + off.lcx);
@@ -684,8 +688,14 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
                              h->stream) == cudaSuccess;
   if (h->fp32 && nnz > 0) ok = ok && convert_to_float(h->val, h->val32, nnz, h->stream) == cudaSuccess;
   if (h->fp32 && h->minres && m0 % 4 == 0) {
+    // ELL slots a row needs: its entries, plus slot 0 for a missing diagonal
     int64_t maxlen = 0;
-    for (int64_t i = 0; i < n; ++i) maxlen = std::max<int64_t>(maxlen, A->rowptr[i + 1] - A->rowptr[i]);
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t len = A->rowptr[i + 1] - A->rowptr[i];
+      bool diag = false;
+      for (int64_t p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) diag = diag || A->colidx[p] == i;
+      maxlen = std::max<int64_t>(maxlen, len + (diag ? 0 : 1));
+    }
     h->ell_w = maxlen <= 8 ? 8 : (maxlen <= 16 ? 16 : 0);
     if (h->ell_w)
       ok = ok && build_ell((int)n, h->ell_w, h->rowptr, h->colidx, h->val32, h->colE, h->valE,

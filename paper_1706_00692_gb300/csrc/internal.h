@@ -131,6 +131,7 @@ struct MinresState {
   int *steps, *done;        // [nc*m0]
   int *coldone;             // [m0]
   int *active;              // [1] columns still running at the last checked step
+  int *ticket;              // [ceil(m0/32)] blocks of a column tile done with a step
   DevStatus *status;
 };
 struct MinresArgs {

@@ -74,6 +74,7 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
     st.coldone[idx] = rnorm[idx] > 0.0 ? 0 : 1;
     beta[idx] = 0.0;  // beta_0
   }
+  if (idx < (size_t)(m0 + 31) / 32) st.ticket[idx] = 0;
   if (idx == 0) st.active[0] = 0;
 }
 
@@ -420,6 +421,171 @@ k_lanczos_givens(int P, int m0, int nc, int K, int s, const double *__restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Coefficient and Givens step after an FP32 Lanczos step (k_lanczos_step_vec,
+// k_lanczos_step_ell), whose blocks leave FP32 partials part[b][3][m0].
+// One block per (32-column tile, node k), so the FP64 Givens arithmetic of the
+// nc x m0 pairs is spread over tiles x nc blocks instead of one block per tile.
+//  1. every block of a tile sums the P partials of its 32 columns: warp w takes
+//     the rows b = w (mod 8) with compensated (Kahan) FP32 sums, then the eight
+//     warp sums are added in FP64 in warp order. The order is the same in
+//     every block, so all nodes see bit-identical alpha_s and beta_{s+1};
+//     node 0's block stores them.
+//  2. warp 0 advances the QR of the tridiagonal (z_k I - Tbar_s) for its 32
+//     pairs (same rotations as givens_tile; the rotation is formed from
+//     rsqrt of rho^2, and the stop test compares |g_{s+1}|^2 with tol^2).
+//  3. the last block of the tile to finish (atomic ticket after a memory
+//     fence) marks the tile's columns whose pairs are all done and counts the
+//     columns still running.
+// ---------------------------------------------------------------------------
+constexpr int kGfThreads = 256;
+
+__global__ void __launch_bounds__(kGfThreads)
+k_lanczos_givens_f(int P, int m0, int nc, int K, int s, const float *__restrict__ part,
+                   double *__restrict__ alpha, double *__restrict__ beta, const MinresState st,
+                   double brk2) {
+  constexpr int NW = kGfThreads / 32;
+  __shared__ double red[3][NW][32];
+  __shared__ double b1_s[32];
+  __shared__ int cd_s[32];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = blockIdx.x, k = blockIdx.y;
+  const int j = tile * 32 + lane;
+  const int p = k * m0 + j;
+  // warp 0: the pair's state, in flight during the reduction
+  int cd = 1, pdone = 1;
+  double2 rr[4];
+  double2 gs = make_double2(0.0, 0.0);
+  double tol = 0.0, b0 = 0.0;
+  if (warp == 0 && j < m0) {
+    cd = st.coldone[j];
+    if (!cd) {
+      pdone = st.done[p];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rr[u] = st.rot[(size_t)p * 4 + u];
+      gs = st.g[(size_t)p * (K + 1) + s];
+      tol = st.tol[p];
+      b0 = beta[(size_t)s * m0 + j];
+    }
+  }
+  {
+    float sm[3] = {0.f, 0.f, 0.f}, cp[3] = {0.f, 0.f, 0.f};
+    if (j < m0) {
+      constexpr int U = 8;  // rows in flight per warp
+      for (int b0r = warp; b0r < P; b0r += U * NW) {
+        float x[U][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int b = b0r + u * NW;
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            x[u][q] = b < P ? __ldcg(part + ((size_t)b * 3 + q) * m0 + j) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float y = x[u][q] - cp[q];
+            const float t = sm[q] + y;
+            cp[q] = (t - sm[q]) - y;
+            sm[q] = t;
+          }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) red[q][warp][lane] = (double)sm[q] - (double)cp[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double vv = 0.0, vw = 0.0, ww = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      vv += red[0][w][lane];
+      vw += red[1][w][lane];
+      ww += red[2][w][lane];
+    }
+    double b1 = 0.0;
+    if (j < m0 && !cd) {
+      const double a = vv > 0.0 ? vw / vv : 0.0;
+      const double b2 = ww - a * vw;
+      b1 = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
+      if (k == 0) {
+        alpha[(size_t)s * m0 + j] = a;
+        beta[(size_t)(s + 1) * m0 + j] = b1;
+      }
+      if (!pdone) {
+        // column s of (z I - Tbar): rows s-2 (fill), s-1, s, s+1
+        double2 e2 = make_double2(0.0, 0.0);
+        double2 e1 = make_double2(-b0, 0.0);
+        double2 e0 = make_double2(st.z[k].x - a, st.z[k].y);
+        // rotation of step s - 2 sits in slots (s & 1) * 2, that of step s - 1 in the other
+        const bool odd = s & 1;
+        if (s >= 2) {
+          const double2 cs = odd ? rr[2] : rr[0], sn = odd ? rr[3] : rr[1];
+          e2 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
+          e1 = cmul(cs, e1);
+        }
+        if (s >= 1) {
+          const double2 cs = odd ? rr[0] : rr[2], sn = odd ? rr[1] : rr[3];
+          const double2 x = e1, y = e0;
+          e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
+                            cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
+          const double2 sx = cmul(sn, x), cy = cmul(cs, y);
+          e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
+        }
+        const double rho2 = cabs2(e0) + b1 * b1;
+        if (!(rho2 > 0.0)) {
+          st.done[p] = 1;
+        } else {
+          const double inv = rsqrt(rho2);
+          const double rho = rho2 * inv;
+          // rotation annihilating the subdiagonal entry -beta_{s+1} below e0
+          const double2 cs = make_double2(e0.x * inv, e0.y * inv);
+          const double2 sn = make_double2(-b1 * inv, 0.0);
+          double2 *R = st.R + ((size_t)p * K + s) * 3;
+          R[0] = make_double2(rho, 0.0);
+          R[1] = e1;
+          R[2] = e2;
+          double2 *rot = st.rot + (size_t)p * 4;
+          rot[(s & 1) * 2] = cs;
+          rot[(s & 1) * 2 + 1] = sn;
+          const double2 gn = make_double2(-sn.x * gs.x, -sn.x * gs.y);  // sn is real
+          double2 *g = st.g + (size_t)p * (K + 1);
+          g[s + 1] = gn;
+          g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
+          st.steps[p] = s + 1;
+          if (b1 == 0.0 || (tol > 0.0 && cabs2(gn) <= tol * tol)) st.done[p] = 1;
+        }
+      }
+    }
+    b1_s[lane] = b1;
+    cd_s[lane] = cd;
+  }
+  // ticket: the tile's last block sees every node's done flags
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int t = atomicAdd(st.ticket + tile, 1);
+    is_last = t == nc - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (warp == 0) {
+    if (j < m0 && !cd_s[lane]) {
+      int all = 1;  // a broken-down basis (beta_{s+1} = 0) finishes the column
+      if (b1_s[lane] != 0.0)
+        for (int kk = 0; kk < nc; ++kk) all &= __ldcg(st.done + kk * m0 + j);
+      if (all)
+        st.coldone[j] = 1;
+      else
+        atomicAdd(st.active, 1);
+    }
+    if (lane == 0) st.ticket[tile] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP32 Lanczos step for m0 % 4 == 0: one thread per (row, four-column quad).
 // Threads walk the rows grid-stride, so at any moment the whole grid works on
 // one window of consecutive rows and the neighbour rows a stencil-like matrix
@@ -435,6 +601,33 @@ __device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
   return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
 }
 
+// Block partials of the FP32 step kernels: thread t holds the sums of
+// columns 4 q(t) .. 4 q(t) + 3; part[block][0..2][j] = the block's <v,v>,
+// <v,w>, <w,w> of column j, added in FP32 in thread order (fixed order).
+__device__ __forceinline__ void store_partials_f(const float (&vv)[4], const float (&vw)[4],
+                                                 const float (&ww)[4], int m0, int stride_items,
+                                                 float *__restrict__ part) {
+  __shared__ float red[kVThreads][13];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    red[threadIdx.x][3 * i + 0] = vv[i];
+    red[threadIdx.x][3 * i + 1] = vw[i];
+    red[threadIdx.x][3 * i + 2] = ww[i];
+  }
+  __syncthreads();
+  const int MQ = m0 >> 2;
+  const int base_q = (blockIdx.x * kVThreads) % MQ;
+  for (int t = threadIdx.x; t < 3 * m0; t += kVThreads) {
+    const int k = t / m0, j = t % m0;
+    const int qj = j >> 2, ij = j & 3;
+    // threads of this block with q == qj: local index l with (base_q + l) % MQ == qj
+    float acc = 0.f;
+    for (int l = (qj - base_q + MQ) % MQ; l < kVThreads; l += MQ)
+      if (blockIdx.x * kVThreads + l < stride_items) acc += red[l][3 * ij + k];
+    part[((size_t)blockIdx.x * 3 + k) * m0 + j] = acc;
+  }
+}
+
 template <bool FIRST>
 __global__ void __launch_bounds__(kVThreads, 2)
 k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
@@ -442,7 +635,7 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
                    float *__restrict__ V, const float *__restrict__ Wprev,
                    float *__restrict__ Wout, const double *__restrict__ alpha,
                    const double *__restrict__ beta, const int *__restrict__ coldone,
-                   double *__restrict__ part, int stride_items) {
+                   float *__restrict__ part, int stride_items) {
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
   float *__restrict__ Vs = V + (size_t)s * vs;
@@ -531,37 +724,19 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
       }
     }
   }
-  // block partials per column: thread t holds columns 4 q(t) .. 4 q(t) + 3;
-  // summed over the block's threads in thread order (fixed order)
-  __shared__ float red[kVThreads][13];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    red[threadIdx.x][3 * i + 0] = vv[i];
-    red[threadIdx.x][3 * i + 1] = vw[i];
-    red[threadIdx.x][3 * i + 2] = ww[i];
-  }
-  __syncthreads();
-  const int base_q = (blockIdx.x * kVThreads) % MQ;
-  for (int t = threadIdx.x; t < 3 * m0; t += kVThreads) {
-    const int k = t / m0, j = t % m0;
-    const int qj = j >> 2, ij = j & 3;
-    // threads of this block with q == qj: local index l with (base_q + l) % MQ == qj
-    double acc = 0.0;
-    for (int l = (qj - base_q + MQ) % MQ; l < kVThreads; l += MQ)
-      if (blockIdx.x * kVThreads + l < stride_items) acc += (double)red[l][3 * ij + k];
-    part[((size_t)blockIdx.x * 3 + k) * m0 + j] = acc;
-  }
+  store_partials_f(vv, vw, ww, m0, stride_items, part);
 }
 
 // ---------------------------------------------------------------------------
-// FP32 Lanczos step on a fixed-width (ELL) copy of A: every row holds exactly
-// W slots (W = 8 or 16, padded with the row's own index and a zero value), so
-// a row's indices are one or two 16-byte loads that do not wait on rowptr,
-// and the next row's indices are fetched while the current row's gathers are
-// in flight. The row's own w_{s-1}[r], v_{s-1}[r] come from the slot whose
-// index is r (the diagonal or a padding slot); rows with W non-zeros and no
-// diagonal load them directly. The Lanczos coefficients of the block's
-// columns sit in shared memory. Same recurrence as k_lanczos_step.
+// FP32 Lanczos step on a fixed-width (ELL) copy of A (k_build_ell): every row
+// holds exactly W slots (W = 8 or 16), slot 0 is the diagonal entry (its value
+// is 0 when A has none there), and unused slots repeat the row's own index
+// with a zero value. So a row's indices are one or two 16-byte loads that do
+// not wait on rowptr, the next row's indices are fetched while the current
+// row's gathers are in flight, the row's own w_{s-1}[r], v_{s-1}[r] are the
+// gathers of slot 0, and padding slots (index r past slot 0) are skipped.
+// Element offsets are 32-bit (n * m0 < 2^31). Same recurrence as
+// k_lanczos_step.
 // ---------------------------------------------------------------------------
 template <bool FIRST, int W>
 __global__ void __launch_bounds__(kVThreads, 2)
@@ -569,23 +744,7 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
                    const float *__restrict__ valE, float *__restrict__ V,
                    const float *__restrict__ Wprev, float *__restrict__ Wout,
                    const double *__restrict__ alpha, const double *__restrict__ beta,
-                   const int *__restrict__ coldone, double *__restrict__ part, int stride_items) {
-  __shared__ float coefs[3][1024];  // alpha_{s-1}, 1/beta_s, beta_s per column
-  __shared__ int cdone[1024];
-  for (int j = threadIdx.x; j < m0; j += kVThreads) {
-    const int cd = coldone[j];
-    cdone[j] = cd;
-    float a = 0.f, ib = 1.f, b = 0.f;
-    if (!FIRST && !cd) {
-      a = (float)alpha[(size_t)(s - 1) * m0 + j];
-      b = (float)beta[(size_t)s * m0 + j];
-      ib = (float)(1.0 / beta[(size_t)s * m0 + j]);
-    }
-    coefs[0][j] = a;
-    coefs[1][j] = ib;
-    coefs[2][j] = b;
-  }
-  __syncthreads();
+                   const int *__restrict__ coldone, float *__restrict__ part, int stride_items) {
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
   float *__restrict__ Vs = V + (size_t)s * vs;
@@ -594,13 +753,21 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
   const int gt = blockIdx.x * kVThreads + threadIdx.x;
   const bool thr = gt < stride_items;
   const int q = thr ? gt % MQ : 0;
+  const int q4 = 4 * q;
   const int rstep = stride_items / MQ;
   bool act[4];
   bool qact = false;
+  float ap[4] = {0.f, 0.f, 0.f, 0.f}, ib[4] = {1.f, 1.f, 1.f, 1.f}, bs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    act[i] = thr && cdone[4 * q + i] == 0;
+    const int j = q4 + i;
+    act[i] = thr && coldone[j] == 0;
     qact = qact || act[i];
+    if (!FIRST && act[i]) {
+      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
+      bs[i] = (float)beta[(size_t)s * m0 + j];
+      ib[i] = (float)(1.0 / beta[(size_t)s * m0 + j]);
+    }
   }
   const bool all4 = act[0] && act[1] && act[2] && act[3];
   float vv[4] = {0.f, 0.f, 0.f, 0.f}, vw[4] = {0.f, 0.f, 0.f, 0.f}, ww[4] = {0.f, 0.f, 0.f, 0.f};
@@ -628,12 +795,14 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
         a[u + 2] = a4.z;
         a[u + 3] = a4.w;
       }
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       float4 g1[W], g2[W];
 #pragma unroll
       for (int u = 0; u < W; ++u) {
-        const size_t co = (size_t)c[u] * m0 + 4 * q;
-        g1[u] = *reinterpret_cast<const float4 *>(G1 + co);
-        if (!FIRST) g2[u] = *reinterpret_cast<const float4 *>(G2 + co);
+        const int co = c[u] * m0 + q4;
+        const bool ld = u == 0 || c[u] != r;
+        g1[u] = ld ? *reinterpret_cast<const float4 *>(G1 + co) : z4;
+        if (!FIRST) g2[u] = ld ? *reinterpret_cast<const float4 *>(G2 + co) : z4;
       }
       const int rn = r + rstep;  // next row's indices, in flight with the gathers
       if (rn < n) {
@@ -646,23 +815,14 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
           cn[u + 3] = c4.w;
         }
       }
-      float4 acc1 = make_float4(0.f, 0.f, 0.f, 0.f), acc2 = acc1, o1 = acc1, o2 = acc1;
-      bool own = false;
+      float4 acc1 = z4, acc2 = z4;
 #pragma unroll
       for (int u = 0; u < W; ++u) {
         acc1 = f4fma(a[u], g1[u], acc1);
         if (!FIRST) acc2 = f4fma(a[u], g2[u], acc2);
-        if (c[u] == r) {
-          o1 = g1[u];
-          if (!FIRST) o2 = g2[u];
-          own = true;
-        }
       }
-      const size_t off = (size_t)r * m0 + 4 * q;
-      if (!own) {
-        o1 = *reinterpret_cast<const float4 *>(G1 + off);
-        if (!FIRST) o2 = *reinterpret_cast<const float4 *>(G2 + off);
-      }
+      const float4 o1 = g1[0], o2 = FIRST ? z4 : g2[0];
+      const int off = r * m0 + q4;
       const float o1a[4] = {o1.x, o1.y, o1.z, o1.w}, o2a[4] = {o2.x, o2.y, o2.z, o2.w};
       const float a1a[4] = {acc1.x, acc1.y, acc1.z, acc1.w}, a2a[4] = {acc2.x, acc2.y, acc2.z, acc2.w};
       float v[4], w[4];
@@ -672,10 +832,8 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
           v[i] = o1a[i];
           w[i] = a1a[i];
         } else {
-          const int j = 4 * q + i;
-          const float ap = coefs[0][j], ib = coefs[1][j], bs = coefs[2][j];
-          v[i] = (o1a[i] - ap * o2a[i]) * ib;
-          w[i] = (a1a[i] - ap * a2a[i]) * ib - bs * o2a[i];
+          v[i] = (o1a[i] - ap[i] * o2a[i]) * ib[i];
+          w[i] = (a1a[i] - ap[i] * a2a[i]) * ib[i] - bs[i] * o2a[i];
         }
         if (act[i]) {
           vv[i] = fmaf(v[i], v[i], vv[i]);
@@ -696,36 +854,37 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
       }
     }
   }
-  __shared__ float red[kVThreads][13];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    red[threadIdx.x][3 * i + 0] = vv[i];
-    red[threadIdx.x][3 * i + 1] = vw[i];
-    red[threadIdx.x][3 * i + 2] = ww[i];
-  }
-  __syncthreads();
-  const int base_q = (blockIdx.x * kVThreads) % MQ;
-  for (int t = threadIdx.x; t < 3 * m0; t += kVThreads) {
-    const int k = t / m0, j = t % m0;
-    const int qj = j >> 2, ij = j & 3;
-    double acc = 0.0;
-    for (int l = (qj - base_q + MQ) % MQ; l < kVThreads; l += MQ)
-      if (blockIdx.x * kVThreads + l < stride_items) acc += (double)red[l][3 * ij + k];
-    part[((size_t)blockIdx.x * 3 + k) * m0 + j] = acc;
-  }
+  store_partials_f(vv, vw, ww, m0, stride_items, part);
 }
 
-// Fixed-width copy of the CSR matrix (FP32 values): W slots per row, padded
-// with the row's own index and zero. Built on the device from the CSR arrays.
+// Fixed-width copy of the CSR matrix (FP32 values) for k_lanczos_step_ell:
+// slot 0 holds the diagonal entry (value 0 if the row has none), then the
+// row's other entries in CSR order, then padding (index r, value 0). W must
+// be at least the row length plus one when the row has no diagonal entry.
 __global__ void k_build_ell(int n, int W, const int32_t *__restrict__ rowptr,
                             const int32_t *__restrict__ colidx, const float *__restrict__ val,
                             int32_t *__restrict__ colE, float *__restrict__ valE) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  const int pb = rowptr[r], len = rowptr[r + 1] - pb;
-  for (int u = 0; u < W; ++u) {
-    colE[(size_t)r * W + u] = u < len ? colidx[pb + u] : r;
-    valE[(size_t)r * W + u] = u < len ? val[pb + u] : 0.f;
+  const int pb = rowptr[r], pe = rowptr[r + 1];
+  int32_t *ce = colE + (size_t)r * W;
+  float *ve = valE + (size_t)r * W;
+  float d = 0.f;
+  int u = 1;
+  for (int p = pb; p < pe; ++p) {
+    if (colidx[p] == r) {
+      d = val[p];
+    } else if (u < W) {
+      ce[u] = colidx[p];
+      ve[u] = val[p];
+      ++u;
+    }
+  }
+  ce[0] = r;
+  ve[0] = d;
+  for (; u < W; ++u) {
+    ce[u] = r;
+    ve[u] = 0.f;
   }
 }
 
@@ -898,7 +1057,9 @@ void launch_step_nj(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo, const 
 
 bool use_vec_step(const MinresArgs &a) { return a.fp32 && a.m0 % 4 == 0 && a.m0 <= 1024; }
 
-bool use_ell_step(const MinresArgs &a) { return use_vec_step(a) && (a.ell_w == 8 || a.ell_w == 16); }
+bool use_ell_step(const MinresArgs &a) {
+  return use_vec_step(a) && (a.ell_w == 8 || a.ell_w == 16) && (long long)a.n * a.m0 < (1LL << 31);
+}
 
 // Lanczos breakdown threshold on beta^2 / ||w||^2 for the storage precision
 template <typename T>
@@ -930,8 +1091,8 @@ cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T
       vec_grid(a, blocks, stride_items);
 #define IFEAST_ELL_LAUNCH(F, WW)                                                              \
   k_lanczos_step_ell<F, WW><<<blocks, kVThreads, 0, st>>>(                                     \
-      a.n, a.m0, s, a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone, a.part,        \
-      stride_items)
+      a.n, a.m0, s, a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,                \
+      reinterpret_cast<float *>(a.part), stride_items)
       if (a.ell_w == 8) {
         if (s == 0)
           IFEAST_ELL_LAUNCH(true, 8);
@@ -952,11 +1113,11 @@ cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T
       if (s == 0)
         k_lanczos_step_vec<true><<<blocks, kVThreads, 0, st>>>(
             a.n, a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,
-            a.part, stride_items);
+            reinterpret_cast<float *>(a.part), stride_items);
       else
         k_lanczos_step_vec<false><<<blocks, kVThreads, 0, st>>>(
             a.n, a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,
-            a.part, stride_items);
+            reinterpret_cast<float *>(a.part), stride_items);
       return cudaGetLastError();
     }
   }
@@ -989,7 +1150,9 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   IFEAST_PROF_END(a.prof);
   const double brk2 = brk2_of<T>();
   int step_blocks = a.tl.P;
-  if (sizeof(T) == 4 && use_vec_step(a)) {
+  // the FP32 vec / ELL step kernels leave FP32 partials for k_lanczos_givens_f
+  const bool f32_partials = sizeof(T) == 4 && use_vec_step(a);
+  if (f32_partials) {
     int stride_items;
     vec_grid(a, step_blocks, stride_items);
   }
@@ -1002,8 +1165,13 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
     IFEAST_PROF_END(a.prof);
     if (check && e == cudaSuccess) e = cudaMemsetAsync(a.ms.active, 0, sizeof(int), st);
     IFEAST_PROF_BEGIN(a.prof, K_LZ_GIVENS);
-    k_lanczos_givens<<<a.tl.tiles, kThreads, 0, st>>>(step_blocks, a.m0, a.nc, a.K, s, a.part,
-                                                      a.alpha, a.beta, a.ms, brk2);
+    if (f32_partials)
+      k_lanczos_givens_f<<<dim3(a.tl.tiles, a.nc), kGfThreads, 0, st>>>(
+          step_blocks, a.m0, a.nc, a.K, s, reinterpret_cast<const float *>(a.part), a.alpha,
+          a.beta, a.ms, brk2);
+    else
+      k_lanczos_givens<<<a.tl.tiles, kThreads, 0, st>>>(step_blocks, a.m0, a.nc, a.K, s, a.part,
+                                                        a.alpha, a.beta, a.ms, brk2);
     IFEAST_PROF_END(a.prof);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (check && e == cudaSuccess) {

@@ -138,3 +138,53 @@ def test_filter_long_and_short_rows(torch, m0, precision, tol):
     Qr = orc._filtered_subspace_shared(A.to_scipy(), X, z, w, True, 5, 0.0, {"inner_steps": []})
     assert np.abs(Q.cpu().numpy() - Qr).max() <= tol * np.abs(Qr).max()
     S.close()
+
+
+def _ell_case(kind):
+    """Matrices for the fixed-width FP32 step kernel (m0 % 4 == 0, rows of at
+    most 16 slots): rows without a stored diagonal entry (slot 0 then holds a
+    zero), rows filling all 8 slots, and 9-point rows (16 slots)."""
+    import scipy.sparse as sp
+    if kind == "no_diag":
+        B = inputs.random_sparse_symmetric(1001, 1, 7).to_scipy().tolil()
+        for i in range(0, 1001, 3):
+            B[i, i] = 0.0
+        B = B.tocsr()
+        B.eliminate_zeros()
+    elif kind == "full8":
+        L = inputs.add_diagonal(inputs.laplacian((13, 11, 7)), inputs.random_potential(1001, 5))
+        n = L.n
+        i = np.arange(n // 2)
+        far = sp.coo_matrix((np.full(i.size, 0.3), (i, n - 1 - i)), shape=(n, n))
+        B = (L.to_scipy() + far + far.T).tocsr()
+    else:
+        B = inputs.fem_q1((23, 19))[0].to_scipy()
+    B.sort_indices()
+    return inputs.CSR(B.shape[0], B.indptr.astype(np.int32), B.indices.astype(np.int32),
+                      B.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("kind", ["no_diag", "full8", "fem9"])
+@pytest.mark.parametrize("m0", [12, 40])
+def test_filter_fixed_width_rows(torch, kind, m0):
+    A = _ell_case(kind)
+    lens = np.diff(A.rowptr)
+    if kind == "no_diag":
+        diag = np.array([(A.colidx[A.rowptr[r]:A.rowptr[r + 1]] == r).any() for r in range(A.n)])
+        assert (~diag).any() and (lens + ~diag).max() <= 8
+    elif kind == "full8":
+        assert lens.max() == 8
+    else:
+        assert 8 < lens.max() <= 16
+    nc = 4
+    Sd = A.to_scipy()
+    ev = np.linalg.eigvalsh(Sd.toarray())
+    emin, emax = 0.5 * (ev[10] + ev[11]), 0.5 * (ev[30] + ev[31])
+    X = inputs.initial_subspace(A.n, m0, 24)
+    S = _solver(A, emin, emax, m0, nc=nc, inner_iters=6, precision="fp32")
+    Q, steps = S.apply_filter(torch.as_tensor(X, device="cuda"))
+    z, w = orc.contour_nodes("gl_half", nc, emin, emax)
+    Qr = orc._filtered_subspace_shared(Sd, X, z, w, True, 6, 0.0, {"inner_steps": []})
+    assert np.abs(Q.cpu().numpy() - Qr).max() <= 2e-4 * np.abs(Qr).max()
+    assert (steps.cpu().numpy() == 6).all()
+    S.close()
