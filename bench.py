@@ -43,8 +43,9 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp64",
-                                                                 "lap2d_50", "serve"])
+    p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp16",
+                                                                 "lap3d_64_fp64", "lap2d_50",
+                                                                 "serve"])
     p.add_argument("--requests", type=int, default=64, help="serving stream length")
     p.add_argument("--rate", type=float, default=8.0, help="serving arrivals per second")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -59,6 +60,8 @@ def make_workload(name):
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp32")
     if name == "lap3d_64_fp64":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp64")
+    if name == "lap3d_64_fp16":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp16")
     raise ValueError(name)
 
 
@@ -83,10 +86,12 @@ ELL_STEP_TRAFFIC_LAP3D64 = 315.7e6
 
 def step_bytes(wl, elem):
     """Algorithmic bytes of one Lanczos step launch (s > 0): read w_{s-1} and
-    v_{s-1} (the gathered rows counted once), write v_s and w_s, read the CSR
-    structure and values once."""
+    v_{s-1} (the gathered rows counted once), write v_s and w_s (elem bytes per
+    stored entry), read the CSR structure and values once (FP32 values unless
+    the inner arithmetic is FP64)."""
     n, m0, nnz = wl.A.n, wl.m0, wl.A.nnz
-    return 4 * n * m0 * elem + 4 * (n + 1) + nnz * (4 + elem)
+    val_elem = 8 if wl.precision == "fp64" else 4
+    return 4 * n * m0 * elem + 4 * (n + 1) + nnz * (4 + val_elem)
 
 
 class ClockSampler:
@@ -310,7 +315,7 @@ def run_ours(args):
     top = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
     roofline = None
     if top is not None and top[0] == "lanczos_step":
-        elem = 4 if wl.precision == "fp32" else 8
+        elem = {"fp16": 2, "fp32": 4}.get(wl.precision, 8)
         launches, ms = top[1]
         nbytes = step_bytes(wl, elem)
         achieved = nbytes / (ms / launches * 1e-3) / 1e9
@@ -328,11 +333,13 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if wl.precision == "fp32" else "f64",
+                "dtype": "f64" if wl.precision == "fp64" else "f32",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "n": wl.A.n, "nnz": wl.A.nnz, "m0": wl.m0,
                            "nc": wl.nc, "contour": wl.rule, "inner": wl.inner,
-                           "inner_precision": wl.precision, "inner_iters": wl.inner_iters,
+                           "inner_precision": wl.precision,
+                           "inner_storage": {"fp16": "f16", "fp32": "f32"}.get(wl.precision, "f64"),
+                           "inner_iters": wl.inner_iters,
                            "alpha": wl.alpha, "l2": "flushed between steps (256 MB write)",
                            "outer_iters": st["outer_iters"], "pairs": pairs,
                            "krylov_steps_total": st["total_matvecs"],

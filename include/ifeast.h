@@ -77,10 +77,15 @@ typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } 
 typedef enum { IFEAST_INNER_GMRES = 0, IFEAST_INNER_MINRES = 1 } ifeast_inner;
 
 /* Arithmetic of the inner solve (Krylov vectors, sparse products and their
- * inner products; FP32 is accepted with IFEAST_INNER_MINRES only). The
- * quadrature weights, least-squares updates, reduced eigenproblem,
+ * inner products; FP32 and FP16 are accepted with IFEAST_INNER_MINRES only).
+ *   FP64: FP64 vectors and arithmetic.
+ *   FP32: FP32 vectors and arithmetic.
+ *   FP16: FP16 storage of the Lanczos vectors (half the bytes of FP32),
+ *         FP32 arithmetic; needs m0 % 4 == 0. The work vectors are stored
+ *         scaled by 1/||A||_inf to stay in FP16 range.
+ * The quadrature weights, least-squares updates, reduced eigenproblem,
  * Rayleigh-Ritz products and residual check are FP64 in every mode. */
-typedef enum { IFEAST_FP64 = 0, IFEAST_FP32 = 1 } ifeast_precision;
+typedef enum { IFEAST_FP64 = 0, IFEAST_FP32 = 1, IFEAST_FP16 = 2 } ifeast_precision;
 
 typedef struct {
   int64_t n;

@@ -21,9 +21,9 @@ IFEAST_ERR_UNSUPPORTED = 10
 
 GL_HALF, TRAP_HALF, TRAP_FULL = 0, 1, 2
 INNER_GMRES, INNER_MINRES = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, FP16 = 0, 1, 2
 INNERS = {"gmres": INNER_GMRES, "minres": INNER_MINRES}
-PRECISIONS = {"fp64": FP64, "fp32": FP32}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16}
 
 RULES = {"gl_half": GL_HALF, "trap_half": TRAP_HALF, "trap_full": TRAP_FULL}
 

@@ -1,6 +1,6 @@
 """Run one IFEAST solve of a named synthetic workload and report the result.
 
-    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp64|lap2d_50]
+    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_fp64|lap2d_50]
                                          [--max-outer M] [--inner-iters K] [--verbose]
 
 Prints one JSON line: status, eigenpairs found, largest residual, outer
@@ -24,6 +24,8 @@ def workload(name: str):
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp32")
     if name == "lap3d_64_fp64":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp64")
+    if name == "lap3d_64_fp16":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp16")
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -45,13 +45,13 @@ struct ifeast_ctx {
   DevStatus *status = nullptr;
   DevStatus *status_host = nullptr;  // pinned
   // shared-basis (MINRES) mode
-  bool minres = false, fp32 = false;
+  bool minres = false, fp32 = false, half = false;  // fp32: FP32 arithmetic (FP32 or FP16 storage)
+  float wscale = 1.f;
   float *val32 = nullptr;
   void *LV = nullptr, *LW0 = nullptr, *LW1 = nullptr;
   double *lpart = nullptr, *lalpha = nullptr, *lbeta = nullptr, *ltol = nullptr;
   double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
-  int *lticket = nullptr;
   double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
   int *active_host = nullptr;  // pinned
   int ell_w = 0;
@@ -81,7 +81,7 @@ struct Offsets {
   size_t rowptr, colidx, val, z, w, V, W, part, H1, H2, inv_h, CS, SN, R, G, Y, steps, done, X, Q,
       AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
   size_t val32, LV, LW0, LW1, lpart, lalpha, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
-      lcoldone, lactive, lticket, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
+      lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
   size_t rowptrB, colidxB, valB, BQ, BX;
 };
 
@@ -93,7 +93,7 @@ int device_sms() {
 }
 
 Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr,
-             bool minres, bool fp32, int sms_for_plan, int64_t nnzB) {
+             bool minres, int prec, int sms_for_plan, int64_t nnzB) {
   Layout L;
   Offsets o{};
   const size_t C = (size_t)nc * m0;
@@ -118,7 +118,8 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.steps = L.take<int>(C);
     o.done = L.take<int>(C);
   } else {  // shared Lanczos basis, tl tiles the n x m0 block
-    const size_t es = fp32 ? sizeof(float) : sizeof(double);
+    const bool fp32 = prec != IFEAST_FP64;
+    const size_t es = prec == IFEAST_FP16 ? 2 : (fp32 ? sizeof(float) : sizeof(double));
     if (fp32) {
       o.val32 = L.take<float>(nnz > 0 ? nnz : 1);
       // fixed-width copy of A for rows of at most 16 non-zeros
@@ -138,10 +139,9 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.lrot = L.take<double2>(C * 4);
     o.lYc = L.take<double2>(C * K);
     o.lsteps = L.take<int>(C);
-    o.ldone = L.take<int>(C);
+    o.ldone = L.take<int>(2 * C);  // pair done flags, two parity buffers
     o.lcoldone = L.take<int>(m0);
     o.lactive = L.take<int>(1);
-    o.lticket = L.take<int>((m0 + 31) / 32);
     o.lSj = L.take<int>(m0);
     o.lcoef = L.take<double>((size_t)K * m0 + ((size_t)K * m0 + 1) / 2);  // FP64 + FP32 copy
     o.lcx = L.take<double>(m0);
@@ -190,7 +190,8 @@ int validate_opts(const ifeast_opts *o) {
     if (o->precision != IFEAST_FP64) return IFEAST_ERR_UNSUPPORTED;
     if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxInner) return IFEAST_ERR_INVALID_ARG;
   } else if (o->inner_solver == IFEAST_INNER_MINRES) {
-    if (o->precision != IFEAST_FP64 && o->precision != IFEAST_FP32) return IFEAST_ERR_UNSUPPORTED;
+    if (o->precision != IFEAST_FP64 && o->precision != IFEAST_FP32 && o->precision != IFEAST_FP16)
+      return IFEAST_ERR_UNSUPPORTED;
     if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxLanczos) return IFEAST_ERR_INVALID_ARG;
   } else {
     return IFEAST_ERR_UNSUPPORTED;
@@ -389,6 +390,8 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.nc = h->nc;
   a.K = h->K;
   a.fp32 = h->fp32 ? 1 : 0;
+  a.half = h->half ? 1 : 0;
+  a.wscale = h->wscale;
   a.rowptr = h->rowptr;
   a.colidx = h->colidx;
   a.val_t = h->fp32 ? (const void *)h->val32 : (const void *)h->val;
@@ -428,7 +431,6 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   m.done = h->ldone;
   m.coldone = h->lcoldone;
   m.active = h->lactive;
-  m.ticket = h->lticket;
   m.status = h->status;
   return a;
 }
@@ -509,6 +511,8 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   if (!bytes || n < 1 || nnz < 0 || m0 < 1 || m0 > kMaxM0 || m0 > n) return IFEAST_ERR_INVALID_ARG;
   if (nnz_b > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
   if (nnz_b >= 0 && o && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
+  // FP16 storage runs on the four-column kernels only
+  if (o && o->precision == IFEAST_FP16 && m0 % 4 != 0) return IFEAST_ERR_UNSUPPORTED;
   if (n > (int64_t)INT32_MAX - 1 || nnz > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
   int rc = validate_contour(c);
   if (rc) return rc;
@@ -521,7 +525,7 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
   const int Pr = Pg;
   *bytes = plan(n, nnz, m0, c->nc, o->inner_max_iters, tl, Pg, Pr, minres,
-                o->precision == IFEAST_FP32, sms, nnz_b < 0 ? -1 : nnz_b).total;
+                o->precision, sms, nnz_b < 0 ? -1 : nnz_b).total;
   return IFEAST_OK;
 }
 
@@ -566,14 +570,15 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->stream = (cudaStream_t)stream;
   h->num_sms = device_sms();
   h->minres = o->inner_solver == IFEAST_INNER_MINRES;
-  h->fp32 = o->precision == IFEAST_FP32;
+  h->fp32 = o->precision == IFEAST_FP32 || o->precision == IFEAST_FP16;
+  h->half = o->precision == IFEAST_FP16;
   h->tl = make_tiling(n, h->minres ? 32 : h->C, h->num_sms);
   if (h->minres) h->tl.tiles = (m0 + 31) / 32;
   h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
   h->Pr = h->Pg;
   contour_host(c, h->zh, h->wh);
   const Offsets off =
-      plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, h->fp32, h->num_sms, nnzB);
+      plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, o->precision, h->num_sms, nnzB);
   if (workspace) {
     h->ws = (char *)workspace;
     h->ws_bytes = ws_bytes;
@@ -657,7 +662,6 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->ldone = (int *)(b + off.ldone);
     h->lcoldone = (int *)(b + off.lcoldone);
     h->lactive = (int *)(b + off.lactive);
-    h->lticket = (int *)(b + off.lticket);
     h->lSj = (int *)(b + off.lSj);
     h->lcoef = (double *)(b + off.lcoef);
     h->lcx = (double *)(b + off.lcx);
@@ -688,6 +692,16 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
                              h->stream) == cudaSuccess;
   if (h->fp32 && nnz > 0) ok = ok && convert_to_float(h->val, h->val32, nnz, h->stream) == cudaSuccess;
   if (h->fp32 && h->minres && m0 % 4 == 0) {
+    // FP16 storage keeps w_s / ||A||_inf (|w_s| <= ||A||_inf ||v_s||_inf + |beta_s| ...)
+    if (h->half) {
+      double mx = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        double rs = 0.0;
+        for (int64_t p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) rs += std::fabs(A->val[p]);
+        mx = std::max(mx, rs);
+      }
+      h->wscale = mx > 0.0 ? (float)mx : 1.f;
+    }
     // ELL slots a row needs: its entries, plus slot 0 for a missing diagonal
     int64_t maxlen = 0;
     for (int64_t i = 0; i < n; ++i) {

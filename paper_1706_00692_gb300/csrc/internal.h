@@ -128,15 +128,17 @@ struct MinresState {
   double2 *R;               // [nc*m0][K][3] band of the triangular factor
   double2 *rot;             // [nc*m0][4] last two Givens rotations
   double *tol;              // [nc*m0] bound on |g_{s+1}|
-  int *steps, *done;        // [nc*m0]
+  int *steps;               // [nc*m0]
+  int *done;                // [nc*m0] (FP32 step kernels: two buffers, by step parity)
   int *coldone;             // [m0]
   int *active;              // [1] columns still running at the last checked step
-  int *ticket;              // [ceil(m0/32)] blocks of a column tile done with a step
   DevStatus *status;
 };
 struct MinresArgs {
   int n, m0, nc, K;
-  int fp32;
+  int fp32;                 // FP32 arithmetic in the Krylov kernels
+  int half;                 // FP16 storage of the Krylov vectors (with fp32)
+  float wscale;             // FP16: w_s is stored as w_s / wscale (||A||_inf); else 1
   const int32_t *rowptr, *colidx;
   const void *val_t;        // float or double values of A
   const double *rhs;        // n x m0 right-hand sides (X or A X - X Lambda)

@@ -21,7 +21,11 @@
 // <v,w>^2/<v,v> (the squared norm of w_s - alpha_s v_s, using the actual
 // <v,v> so that rounding in earlier normalisations does not feed back), and
 // advances every node's Givens QR.
+#include <cuda_fp16.h>
+
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -38,6 +42,20 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Programmatic dependent launch between the kernels of the Lanczos loop: a
+// kernel waits for the previous kernel of the stream (and its memory) before
+// it touches anything that kernel or an earlier one wrote, and only then lets
+// the next kernel launch, so the next kernel's launch and prologue overlap
+// with its tail. Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // v_0 = b / ||b|| with b = X (plain right-hand side of Alg. 2 step 1) or b =
 // Rres = A X - X Lambda (residual form); per-column tolerances; Givens state
 // reset.
@@ -49,7 +67,11 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
   if (idx < (size_t)n * m0) {
     const int j = (int)(idx % m0);
     const double b = rnorm[j];
-    V0[idx] = (T)(b > 0.0 ? rhs[idx] / b : 0.0);
+    const double x = b > 0.0 ? rhs[idx] / b : 0.0;
+    if constexpr (std::is_same_v<T, __half>)
+      V0[idx] = __float2half_rn((float)x);
+    else
+      V0[idx] = (T)x;
   }
   if (idx < (size_t)nc * m0) {
     const int p = (int)idx;  // p = k * m0 + j
@@ -74,7 +96,6 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
     st.coldone[idx] = rnorm[idx] > 0.0 ? 0 : 1;
     beta[idx] = 0.0;  // beta_0
   }
-  if (idx < (size_t)(m0 + 31) / 32) st.ticket[idx] = 0;
   if (idx == 0) st.active[0] = 0;
 }
 
@@ -425,53 +446,60 @@ k_lanczos_givens(int P, int m0, int nc, int K, int s, const double *__restrict__
 // k_lanczos_step_ell), whose blocks leave FP32 partials part[b][3][m0].
 // One block per (32-column tile, node k), so the FP64 Givens arithmetic of the
 // nc x m0 pairs is spread over tiles x nc blocks instead of one block per tile.
+// The pairs' done flags are double-buffered by step parity: step s reads
+// done[s & 1] and writes done[(s + 1) & 1], and a column is finished when all
+// of its pairs are done, so no block reads a flag another block of the same
+// launch writes.
 //  1. every block of a tile sums the P partials of its 32 columns: warp w takes
-//     the rows b = w (mod 8) with compensated (Kahan) FP32 sums, then the eight
-//     warp sums are added in FP64 in warp order. The order is the same in
-//     every block, so all nodes see bit-identical alpha_s and beta_{s+1};
-//     node 0's block stores them.
+//     the rows b = w (mod NW) with compensated (Kahan) FP32 sums, then warp 0
+//     adds the warp sums (and compensations) in warp order, again
+//     compensated. The order is the same in every block, so all nodes see
+//     bit-identical alpha_s and beta_{s+1}; node 0's block stores them.
 //  2. warp 0 advances the QR of the tridiagonal (z_k I - Tbar_s) for its 32
 //     pairs (same rotations as givens_tile; the rotation is formed from
-//     rsqrt of rho^2, and the stop test compares |g_{s+1}|^2 with tol^2).
-//  3. the last block of the tile to finish (atomic ticket after a memory
-//     fence) marks the tile's columns whose pairs are all done and counts the
-//     columns still running.
+//     rsqrt of rho^2, and the stop test compares |g_{s+1}|^2 with tol^2),
+//     writes the pairs' new done flags and raises *active for a pair that
+//     still runs.
+// Launched with programmatic dependent launch after the step kernel: the
+// pair state is loaded before waiting for the step kernel to finish.
 // ---------------------------------------------------------------------------
-constexpr int kGfThreads = 256;
+constexpr int kGfThreads = 512;
 
 __global__ void __launch_bounds__(kGfThreads)
 k_lanczos_givens_f(int P, int m0, int nc, int K, int s, const float *__restrict__ part,
                    double *__restrict__ alpha, double *__restrict__ beta, const MinresState st,
                    double brk2) {
   constexpr int NW = kGfThreads / 32;
-  __shared__ double red[3][NW][32];
-  __shared__ double b1_s[32];
-  __shared__ int cd_s[32];
-  __shared__ int is_last;
+  __shared__ float red[3][2][NW][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tile = blockIdx.x, k = blockIdx.y;
   const int j = tile * 32 + lane;
   const int p = k * m0 + j;
-  // warp 0: the pair's state, in flight during the reduction
+  const size_t C = (size_t)nc * m0;
+  const int *__restrict__ done_r = st.done + (size_t)(s & 1) * C;
+  int *__restrict__ done_w = st.done + (size_t)((s + 1) & 1) * C;
+  // warp 0: the pair's state and the column's flags, in flight during the reduction
   int cd = 1, pdone = 1;
   double2 rr[4];
   double2 gs = make_double2(0.0, 0.0);
   double tol = 0.0, b0 = 0.0;
   if (warp == 0 && j < m0) {
-    cd = st.coldone[j];
-    if (!cd) {
-      pdone = st.done[p];
+    pdone = done_r[p];
+    for (int kk = 0; kk < nc; ++kk) cd &= done_r[(size_t)kk * m0 + j];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) rr[u] = st.rot[(size_t)p * 4 + u];
-      gs = st.g[(size_t)p * (K + 1) + s];
-      tol = st.tol[p];
-      b0 = beta[(size_t)s * m0 + j];
-    }
+    for (int u = 0; u < 4; ++u) rr[u] = st.rot[(size_t)p * 4 + u];
+    gs = st.g[(size_t)p * (K + 1) + s];
+    tol = st.tol[p];
+    b0 = beta[(size_t)s * m0 + j];
   }
+  // the state above was written by the previous Givens step, which finished
+  // before the step kernel passed its wait; the partials need the step kernel
+  pdl_wait();
+  pdl_launch_next();
   {
     float sm[3] = {0.f, 0.f, 0.f}, cp[3] = {0.f, 0.f, 0.f};
     if (j < m0) {
-      constexpr int U = 8;  // rows in flight per warp
+      constexpr int U = 10;  // rows in flight per warp
       for (int b0r = warp; b0r < P; b0r += U * NW) {
         float x[U][3];
 #pragma unroll
@@ -493,96 +521,85 @@ k_lanczos_givens_f(int P, int m0, int nc, int K, int s, const float *__restrict_
       }
     }
 #pragma unroll
-    for (int q = 0; q < 3; ++q) red[q][warp][lane] = (double)sm[q] - (double)cp[q];
+    for (int q = 0; q < 3; ++q) {
+      red[q][0][warp][lane] = sm[q];
+      red[q][1][warp][lane] = cp[q];
+    }
   }
   __syncthreads();
-  if (warp == 0) {
-    double vv = 0.0, vw = 0.0, ww = 0.0;
+  if (warp != 0 || j >= m0) return;
+  // warp sums and their compensations, combined in FP32 with the same
+  // compensated sum, then one conversion to FP64 (FP64 instructions are the
+  // slow part of this kernel)
+  double tot[3];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      vv += red[0][w][lane];
-      vw += red[1][w][lane];
-      ww += red[2][w][lane];
+  for (int q = 0; q < 3; ++q) {
+    float S = 0.f, Cc = 0.f;
+#pragma unroll
+    for (int w = 0; w < 2 * NW; ++w) {
+      const float x = w < NW ? red[q][0][w][lane] : -red[q][1][w - NW][lane];
+      const float y = x - Cc;
+      const float t = S + y;
+      Cc = (t - S) - y;
+      S = t;
     }
-    double b1 = 0.0;
-    if (j < m0 && !cd) {
-      const double a = vv > 0.0 ? vw / vv : 0.0;
-      const double b2 = ww - a * vw;
-      b1 = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
-      if (k == 0) {
-        alpha[(size_t)s * m0 + j] = a;
-        beta[(size_t)(s + 1) * m0 + j] = b1;
+    tot[q] = (double)S - (double)Cc;
+  }
+  const double vv = tot[0], vw = tot[1], ww = tot[2];
+  int nd = 1;  // the pair's done flag after this step
+  if (!cd) {
+    const double a = vv > 0.0 ? vw / vv : 0.0;
+    const double b2 = ww - a * vw;
+    const double b1 = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
+    if (k == 0) {
+      alpha[(size_t)s * m0 + j] = a;
+      beta[(size_t)(s + 1) * m0 + j] = b1;
+    }
+    if (!pdone) {
+      // column s of (z I - Tbar): rows s-2 (fill), s-1, s, s+1
+      double2 e2 = make_double2(0.0, 0.0);
+      double2 e1 = make_double2(-b0, 0.0);
+      double2 e0 = make_double2(st.z[k].x - a, st.z[k].y);
+      // rotation of step s - 2 sits in slots (s & 1) * 2, that of step s - 1 in the other
+      const bool odd = s & 1;
+      if (s >= 2) {
+        const double2 cs = odd ? rr[2] : rr[0], sn = odd ? rr[3] : rr[1];
+        e2 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
+        e1 = cmul(cs, e1);
       }
-      if (!pdone) {
-        // column s of (z I - Tbar): rows s-2 (fill), s-1, s, s+1
-        double2 e2 = make_double2(0.0, 0.0);
-        double2 e1 = make_double2(-b0, 0.0);
-        double2 e0 = make_double2(st.z[k].x - a, st.z[k].y);
-        // rotation of step s - 2 sits in slots (s & 1) * 2, that of step s - 1 in the other
-        const bool odd = s & 1;
-        if (s >= 2) {
-          const double2 cs = odd ? rr[2] : rr[0], sn = odd ? rr[3] : rr[1];
-          e2 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
-          e1 = cmul(cs, e1);
-        }
-        if (s >= 1) {
-          const double2 cs = odd ? rr[0] : rr[2], sn = odd ? rr[1] : rr[3];
-          const double2 x = e1, y = e0;
-          e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
-                            cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
-          const double2 sx = cmul(sn, x), cy = cmul(cs, y);
-          e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
-        }
-        const double rho2 = cabs2(e0) + b1 * b1;
-        if (!(rho2 > 0.0)) {
-          st.done[p] = 1;
-        } else {
-          const double inv = rsqrt(rho2);
-          const double rho = rho2 * inv;
-          // rotation annihilating the subdiagonal entry -beta_{s+1} below e0
-          const double2 cs = make_double2(e0.x * inv, e0.y * inv);
-          const double2 sn = make_double2(-b1 * inv, 0.0);
-          double2 *R = st.R + ((size_t)p * K + s) * 3;
-          R[0] = make_double2(rho, 0.0);
-          R[1] = e1;
-          R[2] = e2;
-          double2 *rot = st.rot + (size_t)p * 4;
-          rot[(s & 1) * 2] = cs;
-          rot[(s & 1) * 2 + 1] = sn;
-          const double2 gn = make_double2(-sn.x * gs.x, -sn.x * gs.y);  // sn is real
-          double2 *g = st.g + (size_t)p * (K + 1);
-          g[s + 1] = gn;
-          g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
-          st.steps[p] = s + 1;
-          if (b1 == 0.0 || (tol > 0.0 && cabs2(gn) <= tol * tol)) st.done[p] = 1;
-        }
+      if (s >= 1) {
+        const double2 cs = odd ? rr[0] : rr[2], sn = odd ? rr[1] : rr[3];
+        const double2 x = e1, y = e0;
+        e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
+                          cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
+        const double2 sx = cmul(sn, x), cy = cmul(cs, y);
+        e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
+      }
+      const double rho2 = cabs2(e0) + b1 * b1;
+      if (rho2 > 0.0) {
+        const double inv = rsqrt(rho2);
+        const double rho = rho2 * inv;
+        // rotation annihilating the subdiagonal entry -beta_{s+1} below e0
+        const double2 cs = make_double2(e0.x * inv, e0.y * inv);
+        const double2 sn = make_double2(-b1 * inv, 0.0);
+        double2 *R = st.R + ((size_t)p * K + s) * 3;
+        R[0] = make_double2(rho, 0.0);
+        R[1] = e1;
+        R[2] = e2;
+        double2 *rot = st.rot + (size_t)p * 4;
+        rot[(s & 1) * 2] = cs;
+        rot[(s & 1) * 2 + 1] = sn;
+        const double2 gn = make_double2(-sn.x * gs.x, -sn.x * gs.y);  // sn is real
+        double2 *g = st.g + (size_t)p * (K + 1);
+        g[s + 1] = gn;
+        g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
+        st.steps[p] = s + 1;
+        nd = (b1 == 0.0 || (tol > 0.0 && cabs2(gn) <= tol * tol)) ? 1 : 0;
       }
     }
-    b1_s[lane] = b1;
-    cd_s[lane] = cd;
   }
-  // ticket: the tile's last block sees every node's done flags
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int t = atomicAdd(st.ticket + tile, 1);
-    is_last = t == nc - 1;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  if (warp == 0) {
-    if (j < m0 && !cd_s[lane]) {
-      int all = 1;  // a broken-down basis (beta_{s+1} = 0) finishes the column
-      if (b1_s[lane] != 0.0)
-        for (int kk = 0; kk < nc; ++kk) all &= __ldcg(st.done + kk * m0 + j);
-      if (all)
-        st.coldone[j] = 1;
-      else
-        atomicAdd(st.active, 1);
-    }
-    if (lane == 0) st.ticket[tile] = 0;
-  }
+  done_w[p] = nd;
+  if (!nd) *st.active = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -599,6 +616,110 @@ constexpr int kVThreads = 256;
 
 __device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
   return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+// Storage of the inner Krylov vectors of the FP32-arithmetic kernels: FP32, or
+// FP16 (rounded to nearest; arithmetic stays FP32). Four consecutive columns
+// of a row are one 16-byte (FP32) or 8-byte (FP16) access. In FP16 the work
+// vectors w_s are stored divided by a scale of A (so that they stay in FP16
+// range); rnd() gives the value a number has after a round trip through the
+// storage type, so that the Lanczos dots are those of the stored vectors.
+template <typename S>
+struct Store4;
+template <>
+struct Store4<float> {
+  static constexpr bool kHalf = false;
+  using Raw = float4;  // four stored values as loaded
+  __device__ static Raw load_raw(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+  __device__ static float4 cvt(Raw r) { return r; }
+  __device__ static float4 load(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+  __device__ static void store(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+  __device__ static void store1(float *p, float x) { *p = x; }
+  __device__ static float rnd(float x) { return x; }
+};
+template <>
+struct Store4<__half> {
+  static constexpr bool kHalf = true;
+  using Raw = uint2;
+  __device__ static Raw load_raw(const __half *p) { return *reinterpret_cast<const uint2 *>(p); }
+  __device__ static float4 cvt(Raw u) {
+    __half2 h0, h1;
+    memcpy(&h0, &u.x, 4);
+    memcpy(&h1, &u.y, 4);
+    const float2 a = __half22float2(h0), b = __half22float2(h1);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  __device__ static float4 load(const __half *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    __half2 h0, h1;
+    memcpy(&h0, &u.x, 4);
+    memcpy(&h1, &u.y, 4);
+    const float2 a = __half22float2(h0), b = __half22float2(h1);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  __device__ static void store(__half *p, float4 v) {
+    const __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
+    uint2 u;
+    memcpy(&u.x, &h0, 4);
+    memcpy(&u.y, &h1, 4);
+    *reinterpret_cast<uint2 *>(p) = u;
+  }
+  __device__ static void store1(__half *p, float x) { *p = __float2half_rn(x); }
+  __device__ static float rnd(float x) { return __half2float(__float2half_rn(x)); }
+};
+
+// Row epilogue of the FP32-arithmetic step kernels. From the row's own
+// gathered values o1 (w_{s-1}, or v_0 at s = 0) and o2 (v_{s-1}) and the row
+// products acc1 = (A G1)[r], acc2 = (A v_{s-1})[r]: v_s = (w_{s-1} -
+// alpha_{s-1} v_{s-1}) / beta_s, w_s = A v_s - beta_s v_{s-1} by linearity;
+// both are rounded to the storage type, their dots accumulated and stored.
+template <typename S, bool FIRST>
+__device__ __forceinline__ void finish_row(float4 o1, float4 o2, float4 acc1, float4 acc2,
+                                           const float (&ap)[4], const float (&ib)[4],
+                                           const float (&bs)[4], const bool (&act)[4], bool all4,
+                                           float wsc, S *__restrict__ Vs, S *__restrict__ Wout,
+                                           size_t off, float (&vv)[4], float (&vw)[4],
+                                           float (&ww)[4]) {
+  using St = Store4<S>;
+  if (St::kHalf && !FIRST) {  // w_{s-1} is stored divided by wsc
+    o1 = make_float4(o1.x * wsc, o1.y * wsc, o1.z * wsc, o1.w * wsc);
+    acc1 = make_float4(acc1.x * wsc, acc1.y * wsc, acc1.z * wsc, acc1.w * wsc);
+  }
+  const float o1a[4] = {o1.x, o1.y, o1.z, o1.w}, o2a[4] = {o2.x, o2.y, o2.z, o2.w};
+  const float a1a[4] = {acc1.x, acc1.y, acc1.z, acc1.w}, a2a[4] = {acc2.x, acc2.y, acc2.z, acc2.w};
+  float v[4], w[4], wst[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (FIRST) {
+      v[i] = o1a[i];
+      w[i] = a1a[i];
+    } else {
+      v[i] = (o1a[i] - ap[i] * o2a[i]) * ib[i];
+      w[i] = (a1a[i] - ap[i] * a2a[i]) * ib[i] - bs[i] * o2a[i];
+    }
+    wst[i] = w[i];
+    if constexpr (St::kHalf) {
+      v[i] = St::rnd(v[i]);
+      wst[i] = St::rnd(w[i] / wsc);
+      w[i] = wst[i] * wsc;
+    }
+    if (act[i]) {
+      vv[i] = fmaf(v[i], v[i], vv[i]);
+      vw[i] = fmaf(v[i], w[i], vw[i]);
+      ww[i] = fmaf(w[i], w[i], ww[i]);
+    }
+  }
+  if (all4) {
+    if (!FIRST) St::store(Vs + off, make_float4(v[0], v[1], v[2], v[3]));
+    St::store(Wout + off, make_float4(wst[0], wst[1], wst[2], wst[3]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (act[i]) {
+        if (!FIRST) St::store1(Vs + off + i, v[i]);
+        St::store1(Wout + off + i, wst[i]);
+      }
+  }
 }
 
 // Block partials of the FP32 step kernels: thread t holds the sums of
@@ -628,36 +749,57 @@ __device__ __forceinline__ void store_partials_f(const float (&vv)[4], const flo
   }
 }
 
-template <bool FIRST>
+// Column mask of an FP32 step kernel: column j still runs while some node's
+// pair (k, j) is not done (flags left by the previous Givens step).
+__device__ __forceinline__ void load_column_mask(int m0, int nc, const int *__restrict__ done_r,
+                                                 int *cdone) {
+  for (int j = threadIdx.x; j < m0; j += kVThreads) cdone[j] = 1;
+  __syncthreads();
+  for (int t = threadIdx.x; t < nc * m0; t += kVThreads)
+    if (done_r[t] == 0) cdone[t % m0] = 0;  // every writer stores the same value
+  __syncthreads();
+}
+
+template <typename S, bool FIRST>
 __global__ void __launch_bounds__(kVThreads, 2)
 k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
                    const int32_t *__restrict__ colidx, const float *__restrict__ val,
-                   float *__restrict__ V, const float *__restrict__ Wprev,
-                   float *__restrict__ Wout, const double *__restrict__ alpha,
-                   const double *__restrict__ beta, const int *__restrict__ coldone,
-                   float *__restrict__ part, int stride_items) {
+                   S *__restrict__ V, const S *__restrict__ Wprev, S *__restrict__ Wout,
+                   const double *__restrict__ alpha, const double *__restrict__ beta,
+                   const int *__restrict__ done_r, int nc, float *__restrict__ part,
+                   int stride_items, float wsc, int *__restrict__ active_reset) {
+  using St = Store4<S>;
+  pdl_wait();
+  pdl_launch_next();
+  if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
-  float *__restrict__ Vs = V + (size_t)s * vs;
-  const float *__restrict__ G1 = FIRST ? Vs : Wprev;
-  const float *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
+  S *__restrict__ Vs = V + (size_t)s * vs;
+  const S *__restrict__ G1 = FIRST ? Vs : Wprev;
+  const S *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
   const int gt = blockIdx.x * kVThreads + threadIdx.x;
   const bool thr = gt < stride_items;
   const int q = thr ? gt % MQ : 0;
   const int rstep = stride_items / MQ;
+  float ap[4] = {0.f, 0.f, 0.f, 0.f}, ib[4] = {1.f, 1.f, 1.f, 1.f}, bs[4] = {0.f, 0.f, 0.f, 0.f};
+  if (!FIRST && thr) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = 4 * q + i;
+      const double bj = beta[(size_t)s * m0 + j];
+      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
+      bs[i] = (float)bj;
+      ib[i] = bj != 0.0 ? (float)(1.0 / bj) : 0.f;
+    }
+  }
+  __shared__ int cdone[1024];
+  load_column_mask(m0, nc, done_r, cdone);
   bool act[4];
   bool qact = false;
-  float ap[4] = {0.f, 0.f, 0.f, 0.f}, ib[4] = {1.f, 1.f, 1.f, 1.f}, bs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = 4 * q + i;
-    act[i] = thr && coldone[j] == 0;
+    act[i] = thr && cdone[4 * q + i] == 0;
     qact = qact || act[i];
-    if (!FIRST && act[i]) {
-      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
-      bs[i] = (float)beta[(size_t)s * m0 + j];
-      ib[i] = (float)(1.0 / beta[(size_t)s * m0 + j]);
-    }
   }
   const bool all4 = act[0] && act[1] && act[2] && act[3];
   float vv[4] = {0.f, 0.f, 0.f, 0.f}, vw[4] = {0.f, 0.f, 0.f, 0.f}, ww[4] = {0.f, 0.f, 0.f, 0.f};
@@ -665,9 +807,9 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
     for (int r = gt / MQ; r < n; r += rstep) {
       const size_t off = (size_t)r * m0 + 4 * q;
       const int pb = rowptr[r], pe = rowptr[r + 1];
-      const float4 o1 = *reinterpret_cast<const float4 *>(G1 + off);
+      const float4 o1 = St::load(G1 + off);
       float4 o2 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!FIRST) o2 = *reinterpret_cast<const float4 *>(G2 + off);
+      if (!FIRST) o2 = St::load(G2 + off);
       float4 acc1 = make_float4(0.f, 0.f, 0.f, 0.f), acc2 = acc1;
       for (int p0 = pb; p0 < pe; p0 += kVG) {
         int c[kVG];
@@ -683,9 +825,8 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
         for (int u = 0; u < kVG; ++u) {
           const bool in = p0 + u < pe;
           const size_t co = (size_t)c[u] * m0 + 4 * q;
-          g1[u] = in ? *reinterpret_cast<const float4 *>(G1 + co) : make_float4(0.f, 0.f, 0.f, 0.f);
-          if (!FIRST)
-            g2[u] = in ? *reinterpret_cast<const float4 *>(G2 + co) : make_float4(0.f, 0.f, 0.f, 0.f);
+          g1[u] = in ? St::load(G1 + co) : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (!FIRST) g2[u] = in ? St::load(G2 + co) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < kVG; ++u) {
@@ -693,35 +834,8 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
           if (!FIRST) acc2 = f4fma(a[u], g2[u], acc2);
         }
       }
-      const float o1a[4] = {o1.x, o1.y, o1.z, o1.w}, o2a[4] = {o2.x, o2.y, o2.z, o2.w};
-      const float a1a[4] = {acc1.x, acc1.y, acc1.z, acc1.w}, a2a[4] = {acc2.x, acc2.y, acc2.z, acc2.w};
-      float v[4], w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (FIRST) {
-          v[i] = o1a[i];
-          w[i] = a1a[i];
-        } else {
-          v[i] = (o1a[i] - ap[i] * o2a[i]) * ib[i];
-          w[i] = (a1a[i] - ap[i] * a2a[i]) * ib[i] - bs[i] * o2a[i];
-        }
-        if (act[i]) {
-          vv[i] = fmaf(v[i], v[i], vv[i]);
-          vw[i] = fmaf(v[i], w[i], vw[i]);
-          ww[i] = fmaf(w[i], w[i], ww[i]);
-        }
-      }
-      if (all4) {
-        if (!FIRST) *reinterpret_cast<float4 *>(Vs + off) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4 *>(Wout + off) = make_float4(w[0], w[1], w[2], w[3]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (act[i]) {
-            if (!FIRST) Vs[off + i] = v[i];
-            Wout[off + i] = w[i];
-          }
-      }
+      finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout, off, vv, vw,
+                           ww);
     }
   }
   store_partials_f(vv, vw, ww, m0, stride_items, part);
@@ -738,36 +852,47 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
 // Element offsets are 32-bit (n * m0 < 2^31). Same recurrence as
 // k_lanczos_step.
 // ---------------------------------------------------------------------------
-template <bool FIRST, int W>
+template <typename S, bool FIRST, int W, bool PF>
 __global__ void __launch_bounds__(kVThreads, 2)
 k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
-                   const float *__restrict__ valE, float *__restrict__ V,
-                   const float *__restrict__ Wprev, float *__restrict__ Wout,
+                   const float *__restrict__ valE, S *__restrict__ V,
+                   const S *__restrict__ Wprev, S *__restrict__ Wout,
                    const double *__restrict__ alpha, const double *__restrict__ beta,
-                   const int *__restrict__ coldone, float *__restrict__ part, int stride_items) {
+                   const int *__restrict__ done_r, int nc, float *__restrict__ part,
+                   int stride_items, float wsc, int *__restrict__ active_reset) {
+  using St = Store4<S>;
+  pdl_wait();
+  pdl_launch_next();
+  if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
-  float *__restrict__ Vs = V + (size_t)s * vs;
-  const float *__restrict__ G1 = FIRST ? Vs : Wprev;
-  const float *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
+  S *__restrict__ Vs = V + (size_t)s * vs;
+  const S *__restrict__ G1 = FIRST ? Vs : Wprev;
+  const S *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
   const int gt = blockIdx.x * kVThreads + threadIdx.x;
   const bool thr = gt < stride_items;
   const int q = thr ? gt % MQ : 0;
   const int q4 = 4 * q;
   const int rstep = stride_items / MQ;
+  float ap[4] = {0.f, 0.f, 0.f, 0.f}, ib[4] = {1.f, 1.f, 1.f, 1.f}, bs[4] = {0.f, 0.f, 0.f, 0.f};
+  if (!FIRST && thr) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = q4 + i;
+      const double bj = beta[(size_t)s * m0 + j];
+      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
+      bs[i] = (float)bj;
+      ib[i] = bj != 0.0 ? (float)(1.0 / bj) : 0.f;
+    }
+  }
+  __shared__ int cdone[1024];
+  load_column_mask(m0, nc, done_r, cdone);
   bool act[4];
   bool qact = false;
-  float ap[4] = {0.f, 0.f, 0.f, 0.f}, ib[4] = {1.f, 1.f, 1.f, 1.f}, bs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int j = q4 + i;
-    act[i] = thr && coldone[j] == 0;
+    act[i] = thr && cdone[q4 + i] == 0;
     qact = qact || act[i];
-    if (!FIRST && act[i]) {
-      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
-      bs[i] = (float)beta[(size_t)s * m0 + j];
-      ib[i] = (float)(1.0 / beta[(size_t)s * m0 + j]);
-    }
   }
   const bool all4 = act[0] && act[1] && act[2] && act[3];
   float vv[4] = {0.f, 0.f, 0.f, 0.f}, vw[4] = {0.f, 0.f, 0.f, 0.f}, ww[4] = {0.f, 0.f, 0.f, 0.f};
@@ -796,13 +921,26 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
         a[u + 3] = a4.w;
       }
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 g1[W], g2[W];
+      typename St::Raw g1[W], g2[W];  // converted where they are multiplied
+      const typename St::Raw zr = {};
 #pragma unroll
       for (int u = 0; u < W; ++u) {
         const int co = c[u] * m0 + q4;
         const bool ld = u == 0 || c[u] != r;
-        g1[u] = ld ? *reinterpret_cast<const float4 *>(G1 + co) : z4;
-        if (!FIRST) g2[u] = ld ? *reinterpret_cast<const float4 *>(G2 + co) : z4;
+        g1[u] = ld ? St::load_raw(G1 + co) : zr;
+        if (!FIRST) g2[u] = ld ? St::load_raw(G2 + co) : zr;
+      }
+      // In a forward sweep the largest column of a row is usually the first
+      // touch of that row of G1 / G2 (an HBM miss). The same column one sweep
+      // later is the next row's first touch: prefetch it into L2 now, so that
+      // the next iteration's gathers hit L2.
+      if (PF) {
+        int cmax = c[0];
+#pragma unroll
+        for (int u = 1; u < W; ++u) cmax = max(cmax, c[u]);
+        const int pr = min(cmax + rstep, n - 1);
+        prefetch_l2(G1 + pr * m0 + q4);
+        if (!FIRST) prefetch_l2(G2 + pr * m0 + q4);
       }
       const int rn = r + rstep;  // next row's indices, in flight with the gathers
       if (rn < n) {
@@ -818,40 +956,12 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
       float4 acc1 = z4, acc2 = z4;
 #pragma unroll
       for (int u = 0; u < W; ++u) {
-        acc1 = f4fma(a[u], g1[u], acc1);
-        if (!FIRST) acc2 = f4fma(a[u], g2[u], acc2);
+        acc1 = f4fma(a[u], St::cvt(g1[u]), acc1);
+        if (!FIRST) acc2 = f4fma(a[u], St::cvt(g2[u]), acc2);
       }
-      const float4 o1 = g1[0], o2 = FIRST ? z4 : g2[0];
-      const int off = r * m0 + q4;
-      const float o1a[4] = {o1.x, o1.y, o1.z, o1.w}, o2a[4] = {o2.x, o2.y, o2.z, o2.w};
-      const float a1a[4] = {acc1.x, acc1.y, acc1.z, acc1.w}, a2a[4] = {acc2.x, acc2.y, acc2.z, acc2.w};
-      float v[4], w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (FIRST) {
-          v[i] = o1a[i];
-          w[i] = a1a[i];
-        } else {
-          v[i] = (o1a[i] - ap[i] * o2a[i]) * ib[i];
-          w[i] = (a1a[i] - ap[i] * a2a[i]) * ib[i] - bs[i] * o2a[i];
-        }
-        if (act[i]) {
-          vv[i] = fmaf(v[i], v[i], vv[i]);
-          vw[i] = fmaf(v[i], w[i], vw[i]);
-          ww[i] = fmaf(w[i], w[i], ww[i]);
-        }
-      }
-      if (all4) {
-        if (!FIRST) *reinterpret_cast<float4 *>(Vs + off) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4 *>(Wout + off) = make_float4(w[0], w[1], w[2], w[3]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (act[i]) {
-            if (!FIRST) Vs[off + i] = v[i];
-            Wout[off + i] = w[i];
-          }
-      }
+      const float4 o1 = St::cvt(g1[0]), o2 = FIRST ? z4 : St::cvt(g2[0]);
+      finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout,
+                           (size_t)(r * m0 + q4), vv, vw, ww);
     }
   }
   store_partials_f(vv, vw, ww, m0, stride_items, part);
@@ -985,11 +1095,12 @@ __global__ void k_lz_quadrature(int n, int m0, const T *__restrict__ V, const do
   Q[idx] = cx[j] * X[idx] + (double)acc;
 }
 
-// FP32 basis, m0 % 4 == 0: four columns per thread, eight basis vectors in
+// FP32 or FP16 basis, m0 % 4 == 0: four columns per thread, eight basis vectors in
 // flight. A column only takes the basis vectors its own solves built
 // (l < Sj[j]); later ones were not written for it and are never multiplied.
+template <typename ST>
 __global__ void __launch_bounds__(256)
-k_lz_quadrature4(int n, int m0, int K, const float *__restrict__ V, const double *__restrict__ coef,
+k_lz_quadrature4(int n, int m0, int K, const ST *__restrict__ V, const double *__restrict__ coef,
                  const double *__restrict__ cx, const int *__restrict__ Sj,
                  const double *__restrict__ X, double *__restrict__ Q) {
   const size_t i4 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -998,8 +1109,8 @@ k_lz_quadrature4(int n, int m0, int K, const float *__restrict__ V, const double
   const int j0 = (int)((i4 * 4) % m0);
   const int s0 = Sj[j0], s1 = Sj[j0 + 1], s2 = Sj[j0 + 2], s3 = Sj[j0 + 3];
   const int S = max(max(s0, s1), max(s2, s3));
-  const size_t vq = (size_t)n * m0 / 4;  // basis stride in float4
-  const float4 *__restrict__ V4 = reinterpret_cast<const float4 *>(V) + i4;
+  const size_t vs = (size_t)n * m0;  // basis stride in elements
+  const ST *__restrict__ V4 = V + i4 * 4;
   // FP32 coefficients (written by k_lz_coef after the FP64 ones), float4 per quad
   const float4 *__restrict__ C4 =
       reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(coef + (size_t)K * m0) + j0);
@@ -1010,7 +1121,7 @@ k_lz_quadrature4(int n, int m0, int K, const float *__restrict__ V, const double
     float4 v[8], c[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      v[u] = V4[(size_t)(l + u) * vq];
+      v[u] = Store4<ST>::load(V4 + (size_t)(l + u) * vs);
       c[u] = C4[(size_t)(l + u) * cq];
     }
 #pragma unroll
@@ -1023,7 +1134,7 @@ k_lz_quadrature4(int n, int m0, int K, const float *__restrict__ V, const double
     }
   }
   for (; l < S; ++l) {
-    const float4 v = V4[(size_t)l * vq];
+    const float4 v = Store4<ST>::load(V4 + (size_t)l * vs);
     const float4 c = C4[(size_t)l * cq];
     ax = l < s0 ? fmaf(c.x, v.x, ax) : ax;
     ay = l < s1 ? fmaf(c.y, v.y, ay) : ay;
@@ -1061,11 +1172,33 @@ bool use_ell_step(const MinresArgs &a) {
   return use_vec_step(a) && (a.ell_w == 8 || a.ell_w == 16) && (long long)a.n * a.m0 < (1LL << 31);
 }
 
+// Launch with programmatic stream serialization (see pdl_wait)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Lanczos breakdown threshold on beta^2 / ||w||^2 for the storage precision
 template <typename T>
 double brk2_of() {
+  if constexpr (std::is_same_v<T, __half>) return 1e-4;
   return sizeof(T) == 4 ? 1e-6 : 1e-16;
 }
+
+// Values of A in the kernels that store the basis as T
+template <typename T>
+using ValOf = std::conditional_t<std::is_same_v<T, double>, double, float>;
 
 // Blocks of k_lanczos_step_vec and the number of (row, quad) items the grid
 // covers per sweep (a multiple of m0 / 4).
@@ -1084,64 +1217,62 @@ void vec_grid(const MinresArgs &a, int &blocks, int &stride_items) {
 
 template <typename T>
 cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo,
-                                const T *val, cudaStream_t st) {
-  if constexpr (sizeof(T) == 4) {
+                                const ValOf<T> *val, int *active_reset, cudaStream_t st) {
+  if constexpr (sizeof(T) <= 4) {
+    // pair done flags of the previous Givens step (double-buffered by parity)
+    const int *done_r = a.ms.done + (size_t)(s & 1) * a.nc * a.m0;
+    float *part = reinterpret_cast<float *>(a.part);
     if (use_ell_step(a)) {
       int blocks, stride_items;
       vec_grid(a, blocks, stride_items);
+// the 16-slot kernel has no registers left for the prefetch
 #define IFEAST_ELL_LAUNCH(F, WW)                                                              \
-  k_lanczos_step_ell<F, WW><<<blocks, kVThreads, 0, st>>>(                                     \
-      a.n, a.m0, s, a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,                \
-      reinterpret_cast<float *>(a.part), stride_items)
-      if (a.ell_w == 8) {
-        if (s == 0)
-          IFEAST_ELL_LAUNCH(true, 8);
-        else
-          IFEAST_ELL_LAUNCH(false, 8);
-      } else {
-        if (s == 0)
-          IFEAST_ELL_LAUNCH(true, 16);
-        else
-          IFEAST_ELL_LAUNCH(false, 16);
-      }
+  launch_pdl(k_lanczos_step_ell<T, F, WW, WW == 8>, dim3(blocks), dim3(kVThreads), st, a.n,     \
+             a.m0, s, a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc, part,          \
+             stride_items, a.wscale, active_reset)
+      if (a.ell_w == 8)
+        return s == 0 ? IFEAST_ELL_LAUNCH(true, 8) : IFEAST_ELL_LAUNCH(false, 8);
+      return s == 0 ? IFEAST_ELL_LAUNCH(true, 16) : IFEAST_ELL_LAUNCH(false, 16);
 #undef IFEAST_ELL_LAUNCH
-      return cudaGetLastError();
     }
     if (use_vec_step(a)) {
       int blocks, stride_items;
       vec_grid(a, blocks, stride_items);
       if (s == 0)
-        k_lanczos_step_vec<true><<<blocks, kVThreads, 0, st>>>(
-            a.n, a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,
-            reinterpret_cast<float *>(a.part), stride_items);
-      else
-        k_lanczos_step_vec<false><<<blocks, kVThreads, 0, st>>>(
-            a.n, a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, a.ms.coldone,
-            reinterpret_cast<float *>(a.part), stride_items);
-      return cudaGetLastError();
+        return launch_pdl(k_lanczos_step_vec<T, true>, dim3(blocks), dim3(kVThreads), st, a.n,
+                          a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, done_r,
+                          a.nc, part, stride_items, a.wscale, active_reset);
+      return launch_pdl(k_lanczos_step_vec<T, false>, dim3(blocks), dim3(kVThreads), st, a.n, a.m0,
+                        s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc,
+                        part, stride_items, a.wscale, active_reset);
     }
   }
-  const int nj = (a.m0 + 31) / 32;
-  switch (nj) {
-    case 1: launch_step_nj<T, 1>(a, s, V, Wp, Wo, val, st); break;
-    case 2: launch_step_nj<T, 2>(a, s, V, Wp, Wo, val, st); break;
-    case 3: launch_step_nj<T, 3>(a, s, V, Wp, Wo, val, st); break;
-    case 4: launch_step_nj<T, 4>(a, s, V, Wp, Wo, val, st); break;
-    case 5: launch_step_nj<T, 5>(a, s, V, Wp, Wo, val, st); break;
-    case 6: launch_step_nj<T, 6>(a, s, V, Wp, Wo, val, st); break;
-    case 7: launch_step_nj<T, 7>(a, s, V, Wp, Wo, val, st); break;
-    case 8: launch_step_nj<T, 8>(a, s, V, Wp, Wo, val, st); break;
-    default: return cudaErrorInvalidValue;
+  if constexpr (std::is_same_v<T, __half>) {
+    return cudaErrorInvalidValue;  // FP16 storage needs m0 % 4 == 0 (checked at create)
+  } else {
+    const int nj = (a.m0 + 31) / 32;
+    switch (nj) {
+      case 1: launch_step_nj<T, 1>(a, s, V, Wp, Wo, val, st); break;
+      case 2: launch_step_nj<T, 2>(a, s, V, Wp, Wo, val, st); break;
+      case 3: launch_step_nj<T, 3>(a, s, V, Wp, Wo, val, st); break;
+      case 4: launch_step_nj<T, 4>(a, s, V, Wp, Wo, val, st); break;
+      case 5: launch_step_nj<T, 5>(a, s, V, Wp, Wo, val, st); break;
+      case 6: launch_step_nj<T, 6>(a, s, V, Wp, Wo, val, st); break;
+      case 7: launch_step_nj<T, 7>(a, s, V, Wp, Wo, val, st); break;
+      case 8: launch_step_nj<T, 8>(a, s, V, Wp, Wo, val, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
 }
 
+// T: storage of the Krylov vectors (double, float or __half)
 template <typename T>
 cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   const size_t nm = (size_t)a.n * a.m0;
   T *V = (T *)a.V;
   T *W[2] = {(T *)a.W0, (T *)a.W1};
-  const T *val = (const T *)a.val_t;
+  const ValOf<T> *val = (const ValOf<T> *)a.val_t;
   const size_t pc = (size_t)a.nc * a.m0;
   const size_t g0 = nm > pc ? nm : pc;
   IFEAST_PROF_BEGIN(a.prof, K_PREP);
@@ -1150,8 +1281,8 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   IFEAST_PROF_END(a.prof);
   const double brk2 = brk2_of<T>();
   int step_blocks = a.tl.P;
-  // the FP32 vec / ELL step kernels leave FP32 partials for k_lanczos_givens_f
-  const bool f32_partials = sizeof(T) == 4 && use_vec_step(a);
+  // the FP32-arithmetic vec / ELL step kernels leave FP32 partials for k_lanczos_givens_f
+  const bool f32_partials = sizeof(T) <= 4 && use_vec_step(a);
   if (f32_partials) {
     int stride_items;
     vec_grid(a, step_blocks, stride_items);
@@ -1161,17 +1292,23 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   for (; s < a.K && e == cudaSuccess; ++s) {
     const bool check = a.check_every > 0 && (s + 1) % a.check_every == 0 && s + 1 < a.K;
     IFEAST_PROF_BEGIN(a.prof, K_LZ_STEP);
-    e = launch_lanczos_step<T>(a, s, V, W[(s + 1) & 1], W[s & 1], val, st);
+    // on a checked step the FP32 step kernels clear *active themselves (no
+    // memset between the step and Givens kernels breaks their launch overlap)
+    e = launch_lanczos_step<T>(a, s, V, W[(s + 1) & 1], W[s & 1], val,
+                               (check && f32_partials) ? a.ms.active : nullptr, st);
     IFEAST_PROF_END(a.prof);
-    if (check && e == cudaSuccess) e = cudaMemsetAsync(a.ms.active, 0, sizeof(int), st);
+    if (check && !f32_partials && e == cudaSuccess)
+      e = cudaMemsetAsync(a.ms.active, 0, sizeof(int), st);
     IFEAST_PROF_BEGIN(a.prof, K_LZ_GIVENS);
-    if (f32_partials)
-      k_lanczos_givens_f<<<dim3(a.tl.tiles, a.nc), kGfThreads, 0, st>>>(
-          step_blocks, a.m0, a.nc, a.K, s, reinterpret_cast<const float *>(a.part), a.alpha,
-          a.beta, a.ms, brk2);
-    else
-      k_lanczos_givens<<<a.tl.tiles, kThreads, 0, st>>>(step_blocks, a.m0, a.nc, a.K, s, a.part,
-                                                        a.alpha, a.beta, a.ms, brk2);
+    if (e == cudaSuccess) {
+      if (f32_partials)
+        e = launch_pdl(k_lanczos_givens_f, dim3(a.tl.tiles, a.nc), dim3(kGfThreads), st,
+                       step_blocks, a.m0, a.nc, a.K, s, reinterpret_cast<const float *>(a.part),
+                       a.alpha, a.beta, a.ms, brk2);
+      else
+        k_lanczos_givens<<<a.tl.tiles, kThreads, 0, st>>>(step_blocks, a.m0, a.nc, a.K, s,
+                                                          a.part, a.alpha, a.beta, a.ms, brk2);
+    }
     IFEAST_PROF_END(a.prof);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (check && e == cudaSuccess) {
@@ -1192,12 +1329,16 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
                                                            a.cx, a.Sj);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_LZ_QUAD);
-  if (sizeof(T) == 4 && a.m0 % 4 == 0)
-    k_lz_quadrature4<<<(unsigned)((nm / 4 + 255) / 256), 256, 0, st>>>(
-        a.n, a.m0, a.K, (const float *)V, a.coef, a.cx, a.Sj, a.X, a.Q);
-  else
-    k_lz_quadrature<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, V, a.coef, a.cx,
-                                                                     a.Sj, a.X, a.Q);
+  if constexpr (sizeof(T) <= 4) {
+    if (a.m0 % 4 == 0)
+      k_lz_quadrature4<T><<<(unsigned)((nm / 4 + 255) / 256), 256, 0, st>>>(
+          a.n, a.m0, a.K, V, a.coef, a.cx, a.Sj, a.X, a.Q);
+  }
+  if constexpr (!std::is_same_v<T, __half>) {
+    if (sizeof(T) == 8 || a.m0 % 4 != 0)
+      k_lz_quadrature<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, V, a.coef, a.cx,
+                                                                       a.Sj, a.X, a.Q);
+  }
   IFEAST_PROF_END(a.prof);
   return cudaGetLastError();
 }
@@ -1207,6 +1348,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
 cudaError_t minres_init() { return cudaSuccess; }
 
 cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st) {
+  if (a.half) return run_minres<__half>(a, st);
   if (a.fp32) return run_minres<float>(a, st);
   return run_minres<double>(a, st);
 }

@@ -119,6 +119,11 @@ def test_create_rejects_bad_options(lib):
     assert _create(lib, A, opts=_opts(lib, max_outer=0))[0] == _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, opts=_opts(lib, inner_solver=9))[0] == _lib.IFEAST_ERR_UNSUPPORTED
     assert _create(lib, A, opts=_opts(lib, precision=1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, opts=_opts(lib, precision=2))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    # FP16 storage needs the four-column kernels (m0 % 4 == 0)
+    assert _create(lib, A, m0=7, opts=_opts(lib, inner_solver=1, inner_max_iters=8,
+                                            precision=2))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, opts=_opts(lib, precision=3))[0] == _lib.IFEAST_ERR_UNSUPPORTED
     assert _create(lib, A, opts=_opts(lib, inner_solver=1, inner_max_iters=5000))[0] == \
         _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, contour=_lib.Contour(0, 4, 1.0, 0.5))[0] == _lib.IFEAST_ERR_INVALID_ARG
