@@ -77,11 +77,11 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per launch of k_lanczos_step_ell<false, 8> on the 64^3 workload
+# DRAM bytes per launch of k_lanczos_step_ell<float, false, 8> on the 64^3 workload
 # (m0 = 80, FP32), dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture (profiles/k_lanczos_step_ell_lap3d64.md). Re-measure when that kernel
 # changes; None when unknown for the workload.
-ELL_STEP_TRAFFIC_LAP3D64 = 315.7e6
+ELL_STEP_TRAFFIC_LAP3D64 = 314.7e6
 
 
 def step_bytes(wl, elem):
@@ -291,6 +291,11 @@ def run_ours(args):
     lam, X, res = S.eigenpairs()
     pairs = int((res <= 1e-10).sum())
     value = pairs * args.steps * world / (total_ms / 1e3)
+    # the end-to-end solver below holds a workspace of its own (the FP64 basis
+    # alone is ~250 GB at this size): release this one first
+    S.close()
+    del flush
+    torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: create (A host->device),
     # solve (X0 host->device), eigenpairs (device->host), destroy

@@ -42,10 +42,6 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // Programmatic dependent launch between the kernels of the Lanczos loop: a
 // kernel waits for the previous kernel of the stream (and its memory) before
 // it touches anything that kernel or an earlier one wrote, and only then lets
@@ -852,7 +848,7 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
 // Element offsets are 32-bit (n * m0 < 2^31). Same recurrence as
 // k_lanczos_step.
 // ---------------------------------------------------------------------------
-template <typename S, bool FIRST, int W, bool PF>
+template <typename S, bool FIRST, int W>
 __global__ void __launch_bounds__(kVThreads, 2)
 k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
                    const float *__restrict__ valE, S *__restrict__ V,
@@ -929,18 +925,6 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
         const bool ld = u == 0 || c[u] != r;
         g1[u] = ld ? St::load_raw(G1 + co) : zr;
         if (!FIRST) g2[u] = ld ? St::load_raw(G2 + co) : zr;
-      }
-      // In a forward sweep the largest column of a row is usually the first
-      // touch of that row of G1 / G2 (an HBM miss). The same column one sweep
-      // later is the next row's first touch: prefetch it into L2 now, so that
-      // the next iteration's gathers hit L2.
-      if (PF) {
-        int cmax = c[0];
-#pragma unroll
-        for (int u = 1; u < W; ++u) cmax = max(cmax, c[u]);
-        const int pr = min(cmax + rstep, n - 1);
-        prefetch_l2(G1 + pr * m0 + q4);
-        if (!FIRST) prefetch_l2(G2 + pr * m0 + q4);
       }
       const int rn = r + rstep;  // next row's indices, in flight with the gathers
       if (rn < n) {
@@ -1225,11 +1209,10 @@ cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T
     if (use_ell_step(a)) {
       int blocks, stride_items;
       vec_grid(a, blocks, stride_items);
-// the 16-slot kernel has no registers left for the prefetch
 #define IFEAST_ELL_LAUNCH(F, WW)                                                              \
-  launch_pdl(k_lanczos_step_ell<T, F, WW, WW == 8>, dim3(blocks), dim3(kVThreads), st, a.n,     \
-             a.m0, s, a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc, part,          \
-             stride_items, a.wscale, active_reset)
+  launch_pdl(k_lanczos_step_ell<T, F, WW>, dim3(blocks), dim3(kVThreads), st, a.n, a.m0, s,     \
+             a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc, part, stride_items,     \
+             a.wscale, active_reset)
       if (a.ell_w == 8)
         return s == 0 ? IFEAST_ELL_LAUNCH(true, 8) : IFEAST_ELL_LAUNCH(false, 8);
       return s == 0 ? IFEAST_ELL_LAUNCH(true, 16) : IFEAST_ELL_LAUNCH(false, 16);
