@@ -22,6 +22,8 @@ Map to the paper:
   rayleigh_ritz ...................... Algorithm 1/2 step 3 (B_Q = Q^T B Q for A x = lam B x)
   eigen_residuals .................... Algorithm 1/2 step 4
   convergence_bound .................. Eq. (upperbound), Eq. (deltadef)
+  ifeast_nonsym / rayleigh_ritz_nonsym  non-Hermitian extension (stated without
+                                        steps in the paper; readings in the docstring)
 """
 from __future__ import annotations
 
@@ -360,6 +362,97 @@ def feast(A, X0, emin, emax, z, w, *, half=True, tol=1e-10, max_outer=100, B=Non
     """Algorithm 1: FEAST with direct (dense LU) shifted solves."""
     return ifeast(A, X0, emin, emax, z, w, half=half, inner="exact", tol=tol, max_outer=max_outer,
                   B=B)
+
+
+# ---------------------------------------------------------------------------
+# Non-Hermitian extension (the paper states that the method extends to
+# non-Hermitian problems without giving the steps; readings below)
+# ---------------------------------------------------------------------------
+
+def rayleigh_ritz_nonsym(Q, AQ):
+    """Galerkin projection onto span(Q) for a real non-symmetric A:
+    B_Q = Q^T Q = L L^T, Xb = Q L^{-T} (orthonormal columns), C = Xb^T A Xb =
+    L^{-1} Q^T A Q L^{-T}, C U = U diag(theta) with complex theta and unit
+    columns u_j. The Ritz vectors are Xb u_j (unit norm). Returns (theta, U,
+    Linv_T) with Linv_T = L^{-T}."""
+    Bq = Q.T @ Q
+    Bq = 0.5 * (Bq + Bq.T)
+    L, _ = cholesky_shifted(Bq)
+    Linv_T = sla.solve_triangular(L.T, np.eye(L.shape[0]), lower=False)
+    C = Linv_T.T @ (Q.T @ AQ) @ Linv_T
+    theta, U = sla.eig(C)
+    U = U / np.linalg.norm(U, axis=0)[None, :]
+    return theta, U, Linv_T
+
+
+def in_circle(theta, c, r):
+    return np.abs(theta - c) < r
+
+
+def ifeast_nonsym(A, X0, c, r, z, w, *, half=True, inner="gmres", k=10, alpha=0.0,
+                  tol=1e-10, max_outer=100):
+    """IFEAST (Algorithm 2; Algorithm 1 with inner="exact") for a real
+    non-symmetric A, eigenvalues inside the circle |lambda - c| < r.
+
+    Readings taken (the paper gives no steps for this case):
+    * contour: the circle itself; for real A and a real block X the solutions
+      at conjugate nodes are conjugate, so a half-contour rule with the Re-sum
+      (half=True) equals the full-circle sum with twice the nodes;
+    * the subspace carried between iterations is the real orthonormal basis
+      X = Q L^{-T} of span(Q) (B_Q = Q^T Q = L L^T), not the complex Ritz
+      vectors; the span, and hence the iteration, is the same;
+    * Rayleigh-Ritz is the Galerkin projection C = X^T A X with a general
+      eigensolver; residuals ||A x_j - theta_j x_j|| / ||A x_j|| of the unit
+      Ritz vectors x_j = X u_j; ||R_F|| is their maximum over theta_j inside
+      the circle;
+    * inner stop ||x_j - (z_k I - A) y|| <= alpha ||R_F|| ||x_j|| (||x_j|| = 1).
+
+    Returns dict(theta, V (Ritz vectors, n x m0 complex), res, inside, iters,
+    history, converged)."""
+    A = A.tocsr() if sp.issparse(A) else A
+    X = np.asarray(X0, dtype=np.float64).copy()
+    RF = 1.0
+    history = []
+    A_dense = None
+    for it in range(1, max_outer + 1):
+        stats = {"inner_steps": []}
+        tol_rel = alpha * RF if alpha > 0 else 0.0
+        if inner == "exact":
+            if A_dense is None:
+                A_dense = A.toarray() if sp.issparse(A) else np.asarray(A)
+            Q = _filtered_subspace_exact(A_dense, X, z, w, half)
+        elif inner == "gmres":
+            Q = _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats)
+        else:
+            raise ValueError(inner)
+        # a full-circle rule pairs conjugate nodes: for real A and X the sum is real
+        Q = np.asarray(Q.real, dtype=np.float64)
+        AQ = A @ Q
+        theta, U, Linv_T = rayleigh_ritz_nonsym(Q, AQ)
+        X = Q @ Linv_T
+        AX = AQ @ Linv_T
+        V = X @ U
+        res = eigen_residuals(AX @ U, V, theta)
+        inside = in_circle(theta, c, r)
+        RF = float(res[inside].max()) if inside.any() else 1.0
+        history.append(dict(RF=RF, count=int(inside.sum()),
+                            max_inner=max(stats["inner_steps"], default=0)))
+        if inside.any() and RF <= tol:
+            return dict(theta=theta, V=V, res=res, inside=inside, iters=it, history=history,
+                        converged=True)
+    return dict(theta=theta, V=V, res=res, inside=inside, iters=max_outer, history=history,
+                converged=False)
+
+
+def filter_step_spectral_nonsym(A_dense, X, z, w, half=True):
+    """sum_k w_k (z_k I - A)^{-1} X = V rho(Lambda) V^{-1} X for a diagonalisable
+    A = V Lambda V^{-1}, rho(lambda) = sum_k w_k / (z_k - lambda) (Eq. rhoh with
+    the eigenvector basis in place of an orthonormal one); real part for a
+    half rule."""
+    lam, V = np.linalg.eig(A_dense)
+    rho = np.sum(w[None, :] / (z[None, :] - lam[:, None]), axis=1)
+    Y = V @ (rho[:, None] * np.linalg.solve(V, X.astype(np.complex128)))
+    return Y.real if half else Y
 
 
 # ---------------------------------------------------------------------------

@@ -172,6 +172,38 @@ def fem_q1(grid: tuple[int, ...]) -> tuple[CSR, CSR]:
     return on_pattern(K), on_pattern(M)
 
 
+def upwind_convection_diffusion(grid: tuple[int, int], Pe: float) -> CSR:
+    """-Laplace u + Pe du/dx on (0,1)^2 with Dirichlet boundary, N_x x N_y
+    interior nodes (h_d = 1/(N_d+1)), second differences in both directions
+    and a first-order upwind difference for du/dx: the x-line stencil is
+    (-1/h^2 - Pe/h, 2/h^2 + Pe/h, -1/h^2) (sub-, main, super-diagonal). Real,
+    non-symmetric; row index i + N_x j."""
+    import scipy.sparse as sp
+    Nx, Ny = grid
+    hx, hy = 1.0 / (Nx + 1), 1.0 / (Ny + 1)
+    ex, ey = np.ones(Nx), np.ones(Ny)
+    Tx = sp.diags([(-1.0 / hx ** 2 - Pe / hx) * ex[:-1], (2.0 / hx ** 2 + Pe / hx) * ex,
+                   (-1.0 / hx ** 2) * ex[:-1]], [-1, 0, 1], format="csr")
+    Ty = sp.diags([(-1.0 / hy ** 2) * ey[:-1], (2.0 / hy ** 2) * ey, (-1.0 / hy ** 2) * ey[:-1]],
+                  [-1, 0, 1], format="csr")
+    M = (sp.kron(sp.identity(Ny), Tx) + sp.kron(Ty, sp.identity(Nx))).tocsr()
+    M.sort_indices()
+    return CSR(M.shape[0], M.indptr.astype(np.int32), M.indices.astype(np.int32),
+               M.data.astype(np.float64))
+
+
+def upwind_convection_diffusion_eigs(grid: tuple[int, int], Pe: float) -> np.ndarray:
+    """Eigenvalues of upwind_convection_diffusion(grid, Pe), ascending (real):
+    a tridiagonal Toeplitz (a, b, c) with a c > 0 has b + 2 sqrt(ac) cos(p pi/(N+1)),
+    and the 2D operator is the Kronecker sum of the two 1D ones."""
+    Nx, Ny = grid
+    hx, hy = 1.0 / (Nx + 1), 1.0 / (Ny + 1)
+    a, b, c = -1.0 / hx ** 2 - Pe / hx, 2.0 / hx ** 2 + Pe / hx, -1.0 / hx ** 2
+    lx = b - 2.0 * math.sqrt(a * c) * np.cos(np.arange(1, Nx + 1) * math.pi / (Nx + 1))
+    ly = (2.0 / hy ** 2) * (1.0 - np.cos(np.arange(1, Ny + 1) * math.pi / (Ny + 1)))
+    return np.sort((lx[:, None] + ly[None, :]).ravel())
+
+
 def fem_q1_eigs(grid: tuple[int, ...]) -> np.ndarray:
     """Eigenvalues of K x = lambda M x for fem_q1(grid), ascending: sums over the
     dimensions of (6/h^2)(1 - cos t)/(2 + cos t), t = p pi/(N+1), p = 1..N."""
