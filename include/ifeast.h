@@ -54,10 +54,12 @@ typedef enum {
 /* Quadrature rules on the circle centred at c = (emin+emax)/2 with radius
  * r = (emax-emin)/2 (Eq. contour_int_quad; half-contour symmetry of Sec. 4.1):
  *   GL_HALF   nc Gauss-Legendre nodes on the upper half circle, filter taken
- *             as 2 Re of the upper-half sum (real symmetric A only)
+ *             as 2 Re of the upper-half sum
  *   TRAP_HALF nc trapezoid nodes theta_j = pi (j-1/2)/nc on the upper half
  *   TRAP_FULL nc trapezoid nodes theta_j = 2 pi (j-1/2)/nc on the full circle
- *             (needs complex Q; reserved for the non-Hermitian extension)   */
+ *             (nc even). A is real and X real, so the solutions at conjugate
+ *             nodes are conjugate: the library runs the equal TRAP_HALF sum
+ *             over the nc/2 upper nodes.                                     */
 typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } ifeast_rule;
 
 /* Inner solver for Alg. 2 step 1.
@@ -112,6 +114,13 @@ typedef struct {
   double tol;           /* stop when ||R_F|| <= tol (default 1e-10)              */
   int precision;        /* ifeast_precision                                      */
   int verbose;          /* 1: one line per outer iteration on stderr             */
+  int nonsymmetric;     /* 1: A is real non-symmetric (non-Hermitian extension,
+                           stated without steps in the paper): Galerkin
+                           Rayleigh-Ritz on span(Q) with a general reduced
+                           eigensolver, complex Ritz values, a value counts when
+                           it lies inside the circle |lambda - c| < r of the
+                           contour, eigenpairs through ifeast_eigenpairs_complex.
+                           Needs IFEAST_INNER_GMRES, B = NULL, m0 <= 64.       */
 } ifeast_opts;
 
 typedef struct {
@@ -180,6 +189,15 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device);
  * row i at evecs[i*cap + j]), resid[m] relative residuals. Any output pointer
  * may be NULL. *m_found gets the number inside (may exceed cap; then only the
  * first cap are copied). out_on_device != 0: outputs are device pointers. */
+/* Non-symmetric handles (opts.nonsymmetric = 1): the Ritz pairs inside the
+ * circle |lambda - c| < r, ordered by real then imaginary part. evals: 2*cap
+ * doubles (re, im); evecs: n x cap complex (re, im interleaved, row-major,
+ * unit 2-norm); resid: cap relative residuals ||A x - lambda x|| / ||A x||.
+ * Host or device outputs as ifeast_eigenpairs; any may be NULL.
+ * ifeast_eigenpairs returns UNSUPPORTED for such handles. */
+int ifeast_eigenpairs_complex(ifeast_t h, int cap, int *m_found, double *evals, double *evecs,
+                              double *resid, int out_on_device);
+
 int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *evecs,
                       double *resid, int out_on_device);
 
@@ -214,6 +232,15 @@ int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32
  * Ritz vectors), lam[m0] ascending, resid[m0] relative residuals (device).
  * Returns BREAKDOWN if B_Q cannot be factored. */
 int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, double *resid);
+
+/* Non-symmetric handles: Galerkin Rayleigh-Ritz on a given Q (n x m0 device):
+ * X (n x m0 device) receives the orthonormal basis Q L^{-T} of span(Q)
+ * (B_Q = Q^T Q = L L^T), theta (2*m0 doubles, device) the unordered Ritz values
+ * (re, im) of C = L^{-1} Q^T A Q L^{-T}, resid (m0, device) the relative
+ * residuals of the unit Ritz vectors X u_j. BREAKDOWN if B_Q cannot be
+ * factored or the reduced QR iteration does not converge. */
+int ifeast_rayleigh_ritz_nonsym(ifeast_t h, const double *Q, double *X, double *theta,
+                                double *resid);
 
 /* One sparse product with a per-column complex shift (the operator of Alg. 2
  * step 1): W[:, c] = z[c / m0] B V[:, c] - A V[:, c] for c < ncols (B = I for

@@ -40,7 +40,7 @@ class Contour(ct.Structure):
 class Opts(ct.Structure):
     _fields_ = [("inner_solver", ct.c_int), ("inner_max_iters", ct.c_int), ("alpha", ct.c_double),
                 ("max_outer", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
-                ("verbose", ct.c_int)]
+                ("verbose", ct.c_int), ("nonsymmetric", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -75,6 +75,10 @@ SIGNATURES = {
     "ifeast_eigenpairs": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.c_void_p,
                                      ct.c_void_p, ct.c_void_p, ct.c_int]),
     "ifeast_ritz_all": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "ifeast_eigenpairs_complex": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int),
+                                             ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "ifeast_rayleigh_ritz_nonsym": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                               ct.c_void_p, ct.c_void_p]),
     "ifeast_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(Stats)]),
     "ifeast_strerror": (ct.c_char_p, [ct.c_int]),
     "ifeast_destroy": (None, [ct.c_void_p]),

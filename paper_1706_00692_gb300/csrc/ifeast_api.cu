@@ -34,6 +34,11 @@ struct ifeast_ctx {
   int64_t nnzB = -1;
   int32_t *rowptrB = nullptr, *colidxB = nullptr;
   double *valB = nullptr, *BQ = nullptr, *BX = nullptr;
+  // non-symmetric extension
+  bool nonsym = false;
+  double *LinvT = nullptr;
+  double2 *theta = nullptr, *Uc = nullptr;
+  int *ridx = nullptr;
   double2 *z = nullptr, *w = nullptr;
   double2 *V = nullptr, *W = nullptr, *part = nullptr, *H1 = nullptr, *H2 = nullptr;
   double *inv_h = nullptr;
@@ -83,6 +88,7 @@ struct Offsets {
   size_t val32, LV, LW0, LW1, lpart, lalpha, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
       lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
   size_t rowptrB, colidxB, valB, BQ, BX;
+  size_t LinvT, theta, Uc, ridx;
 };
 
 int device_sms() {
@@ -93,7 +99,7 @@ int device_sms() {
 }
 
 Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr,
-             bool minres, int prec, int sms_for_plan, int64_t nnzB) {
+             bool minres, int prec, int sms_for_plan, int64_t nnzB, bool nonsym) {
   Layout L;
   Offsets o{};
   const size_t C = (size_t)nc * m0;
@@ -163,6 +169,12 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
   o.res_part = L.take<double>((size_t)Pr * 3 * m0);
   o.res = L.take<double>(m0);
   o.status = L.take<DevStatus>(1);
+  if (nonsym) {  // non-symmetric extension
+    o.LinvT = L.take<double>((size_t)m0 * m0);
+    o.theta = L.take<double2>(m0);
+    o.Uc = L.take<double2>((size_t)m0 * m0);
+    o.ridx = L.take<int>(m0);
+  }
   if (nnzB >= 0) {  // generalized problem
     o.rowptrB = L.take<int32_t>(n + 1);
     o.colidxB = L.take<int32_t>(nnzB > 0 ? nnzB : 1);
@@ -176,12 +188,26 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
 
 int validate_contour(const ifeast_contour *c) {
   if (!c) return IFEAST_ERR_INVALID_ARG;
-  if (c->nc < 1 || c->nc > kMaxNodes) return IFEAST_ERR_INVALID_ARG;
   if (!(c->emin < c->emax) || !std::isfinite(c->emin) || !std::isfinite(c->emax))
     return IFEAST_ERR_INVALID_ARG;
-  if (c->rule == IFEAST_TRAP_FULL) return IFEAST_ERR_UNSUPPORTED;
+  if (c->rule == IFEAST_TRAP_FULL) {
+    if (c->nc < 2 || c->nc % 2 != 0 || c->nc / 2 > kMaxNodes) return IFEAST_ERR_INVALID_ARG;
+    return IFEAST_OK;
+  }
+  if (c->nc < 1 || c->nc > kMaxNodes) return IFEAST_ERR_INVALID_ARG;
   if (c->rule != IFEAST_GL_HALF && c->rule != IFEAST_TRAP_HALF) return IFEAST_ERR_INVALID_ARG;
   return IFEAST_OK;
+}
+
+// The rule the solver runs: a full-circle trapezoid rule on a real problem
+// (real A, real X) equals the half rule on its upper nodes with the Re-sum.
+ifeast_contour effective_contour(const ifeast_contour &c) {
+  ifeast_contour e = c;
+  if (c.rule == IFEAST_TRAP_FULL) {
+    e.rule = IFEAST_TRAP_HALF;
+    e.nc = c.nc / 2;
+  }
+  return e;
 }
 
 int validate_opts(const ifeast_opts *o) {
@@ -198,6 +224,8 @@ int validate_opts(const ifeast_opts *o) {
   }
   if (o->max_outer < 1 || !(o->tol >= 0.0) || !std::isfinite(o->alpha))
     return IFEAST_ERR_INVALID_ARG;
+  if (o->nonsymmetric != 0 && o->nonsymmetric != 1) return IFEAST_ERR_INVALID_ARG;
+  if (o->nonsymmetric && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   return IFEAST_OK;
 }
 
@@ -360,6 +388,14 @@ RRArgs rr_args(ifeast_ctx *h, const double *Q, double *X) {
   return a;
 }
 
+NonsymArgs ns_args(ifeast_ctx *h) {
+  NonsymArgs a;
+  a.LinvT = h->LinvT;
+  a.theta = h->theta;
+  a.Uc = h->Uc;
+  return a;
+}
+
 // Right-hand side block of the shifted systems: X (B = I) or B X written to
 // h->BX, with its column norms in h->beta.
 int prepare_rhs(ifeast_ctx *h, const double *X, const double **rhs) {
@@ -465,6 +501,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->tol = 1e-10;
   o->precision = IFEAST_FP64;
   o->verbose = 0;
+  o->nonsymmetric = 0;
 }
 
 const char *ifeast_strerror(int code) {
@@ -511,6 +548,8 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   if (!bytes || n < 1 || nnz < 0 || m0 < 1 || m0 > kMaxM0 || m0 > n) return IFEAST_ERR_INVALID_ARG;
   if (nnz_b > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
   if (nnz_b >= 0 && o && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
+  // the non-symmetric extension: standard problem, m0 within the reduced solver's limit
+  if (o && o->nonsymmetric == 1 && (nnz_b >= 0 || m0 > kNonsymMaxM0)) return IFEAST_ERR_UNSUPPORTED;
   // FP16 storage runs on the four-column kernels only
   if (o && o->precision == IFEAST_FP16 && m0 % 4 != 0) return IFEAST_ERR_UNSUPPORTED;
   if (n > (int64_t)INT32_MAX - 1 || nnz > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
@@ -518,14 +557,15 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   if (rc) return rc;
   rc = validate_opts(o);
   if (rc) return rc;
+  const int nc = effective_contour(*c).nc;
   const int sms = device_sms();
   const bool minres = o->inner_solver == IFEAST_INNER_MINRES;
-  RowTiling tl = make_tiling(n, minres ? 32 : c->nc * m0, sms);
+  RowTiling tl = make_tiling(n, minres ? 32 : nc * m0, sms);
   if (minres) tl.tiles = (m0 + 31) / 32;  // row blocks cover every column
   const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
   const int Pr = Pg;
-  *bytes = plan(n, nnz, m0, c->nc, o->inner_max_iters, tl, Pg, Pr, minres,
-                o->precision, sms, nnz_b < 0 ? -1 : nnz_b).total;
+  *bytes = plan(n, nnz, m0, nc, o->inner_max_iters, tl, Pg, Pr, minres, o->precision, sms,
+                nnz_b < 0 ? -1 : nnz_b, o->nonsymmetric == 1).total;
   return IFEAST_OK;
 }
 
@@ -562,11 +602,13 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->n = n;
   h->nnz = nnz;
   h->m0 = m0;
-  h->nc = c->nc;
-  h->C = c->nc * m0;
+  const ifeast_contour ce = effective_contour(*c);
+  h->nc = ce.nc;
+  h->C = ce.nc * m0;
   h->K = o->inner_max_iters;
   h->opts = *o;
-  h->contour = *c;
+  h->contour = ce;
+  h->nonsym = o->nonsymmetric == 1;
   h->stream = (cudaStream_t)stream;
   h->num_sms = device_sms();
   h->minres = o->inner_solver == IFEAST_INNER_MINRES;
@@ -576,9 +618,9 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   if (h->minres) h->tl.tiles = (m0 + 31) / 32;
   h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
   h->Pr = h->Pg;
-  contour_host(c, h->zh, h->wh);
-  const Offsets off =
-      plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, o->precision, h->num_sms, nnzB);
+  contour_host(&ce, h->zh, h->wh);
+  const Offsets off = plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, o->precision,
+                           h->num_sms, nnzB, h->nonsym);
   if (workspace) {
     h->ws = (char *)workspace;
     h->ws_bytes = ws_bytes;
@@ -633,6 +675,12 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->res_part = (double *)(b + off.res_part);
   h->res = (double *)(b + off.res);
   h->status = (DevStatus *)(b + off.status);
+  if (h->nonsym) {
+    h->LinvT = (double *)(b + off.LinvT);
+    h->theta = (double2 *)(b + off.theta);
+    h->Uc = (double2 *)(b + off.Uc);
+    h->ridx = (int *)(b + off.ridx);
+  }
   if (B) {
     h->nnzB = nnzB;
     h->rowptrB = (int32_t *)(b + off.rowptrB);
@@ -760,7 +808,10 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
       CK(minres_filter(minres_args(h, h->X, h->Q, it > 1 ? 1 : 0), h->stream));
     else  // right-hand sides X, or B X (norms in beta) from the previous Rayleigh-Ritz
       CK(gmres_filter(gmres_args(h, h->rowptrB ? h->BX : h->X, h->Q), h->stream));
-    CK(rayleigh_ritz(rr_args(h, h->Q, h->X), h->stream));
+    if (h->nonsym)
+      CK(rayleigh_ritz_nonsym(rr_args(h, h->Q, h->X), ns_args(h), h->stream));
+    else
+      CK(rayleigh_ritz(rr_args(h, h->Q, h->X), h->stream));
     CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -814,8 +865,90 @@ int ifeast_ritz_all(ifeast_t h, double *lam, double *resid, int out_on_device) {
   return IFEAST_OK;
 }
 
+int ifeast_eigenpairs_complex(ifeast_t h, int cap, int *m_found, double *evals, double *evecs,
+                              double *resid, int out_on_device) {
+  if (!h || cap < 0) return IFEAST_ERR_INVALID_ARG;
+  if (!h->nonsym) return IFEAST_ERR_UNSUPPORTED;
+  if (!h->solved) return IFEAST_ERR_STATE;
+  const int m0 = h->m0;
+  std::vector<double2> th(m0);
+  std::vector<double> res(m0);
+  CK(cudaMemcpyAsync(th.data(), h->theta, m0 * sizeof(double2), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(res.data(), h->res, m0 * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double cc = 0.5 * (h->contour.emin + h->contour.emax);
+  const double rr = 0.5 * (h->contour.emax - h->contour.emin);
+  std::vector<int> idx;
+  for (int j = 0; j < m0; ++j)
+    if (std::hypot(th[j].x - cc, th[j].y) < rr) idx.push_back(j);
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    return th[a].x < th[b].x || (th[a].x == th[b].x && (th[a].y < th[b].y || (th[a].y == th[b].y && a < b)));
+  });
+  const int m = (int)idx.size();
+  if (m_found) *m_found = m;
+  const int cnt = std::min(m, cap);
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  std::vector<double> ev(2 * (size_t)cnt), rs(cnt);
+  for (int q = 0; q < cnt; ++q) {
+    ev[2 * q] = th[idx[q]].x;
+    ev[2 * q + 1] = th[idx[q]].y;
+    rs[q] = res[idx[q]];
+  }
+  if (evals && cnt) CK(cudaMemcpy(evals, ev.data(), 2 * cnt * sizeof(double), kind));
+  if (resid && cnt) CK(cudaMemcpy(resid, rs.data(), cnt * sizeof(double), kind));
+  if (evecs && cnt) {
+    CK(cudaMemcpyAsync(h->ridx, idx.data(), cnt * sizeof(int), cudaMemcpyHostToDevice,
+                       h->stream));
+    // the Ritz vectors go to the Q buffer (n x m0 doubles holds n x cnt complex
+    // only when 2 cnt <= m0), else to a temporary allocation
+    const size_t need = (size_t)h->n * cap * sizeof(double2);
+    double2 *out = nullptr;
+    bool own = false;
+    if (out_on_device) {
+      out = reinterpret_cast<double2 *>(evecs);
+    } else if (need <= (size_t)h->n * m0 * sizeof(double)) {
+      out = reinterpret_cast<double2 *>(h->Q);
+    } else {
+      if (cudaMallocAsync(reinterpret_cast<void **>(&out), need, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return IFEAST_ERR_OOM;
+      }
+      own = true;
+    }
+    CK(ritz_vectors_nonsym((int)h->n, m0, h->X, h->Uc, h->ridx, cnt, cap, out, h->stream));
+    if (!out_on_device)
+      CK(cudaMemcpyAsync(evecs, out, need, cudaMemcpyDeviceToHost, h->stream));
+    if (own) CK(cudaFreeAsync(out, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return IFEAST_OK;
+}
+
+int ifeast_rayleigh_ritz_nonsym(ifeast_t h, const double *Q, double *X, double *theta,
+                                double *resid) {
+  if (!h || !Q || !X) return IFEAST_ERR_INVALID_ARG;
+  if (!h->nonsym) return IFEAST_ERR_UNSUPPORTED;
+  int rc = set_tolerance(h, 1.0);
+  if (rc) return rc;
+  CK(rayleigh_ritz_nonsym(rr_args(h, Q, X), ns_args(h), h->stream));
+  CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                     h->stream));
+  if (theta)
+    CK(cudaMemcpyAsync(theta, h->theta, h->m0 * sizeof(double2), cudaMemcpyDeviceToDevice,
+                       h->stream));
+  if (resid)
+    CK(cudaMemcpyAsync(resid, h->res, h->m0 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->profiling && h->prof.collect()) return IFEAST_ERR_CUDA;
+  if (h->status_host->breakdown) return IFEAST_ERR_BREAKDOWN;
+  return IFEAST_OK;
+}
+
 int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *evecs,
                       double *resid, int out_on_device) {
+  if (h && h->nonsym) return IFEAST_ERR_UNSUPPORTED;
   if (!h || cap < 0) return IFEAST_ERR_INVALID_ARG;
   if (!h->solved) return IFEAST_ERR_STATE;
   std::vector<double> lam(h->m0), res(h->m0);

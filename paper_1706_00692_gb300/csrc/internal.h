@@ -197,6 +197,16 @@ struct RRArgs {
   DevStatus *status;
   Profiler *prof;
 };
+// Non-Hermitian extension (real non-symmetric A, m0 <= 64)
+struct NonsymArgs {
+  double *LinvT;            // m0 x m0: the carried basis is X = Q L^{-T}
+  double2 *theta;           // [m0] Ritz values (unordered)
+  double2 *Uc;              // m0 x m0 unit eigenvectors of C = L^{-1} Q^T A Q L^{-T}
+};
+cudaError_t rayleigh_ritz_nonsym(const RRArgs &a, const NonsymArgs &ns, cudaStream_t st);
+cudaError_t ritz_vectors_nonsym(int n, int m, const double *X, const double2 *Uc, const int *idx,
+                                int cnt, int cap, double2 *out, cudaStream_t st);
+constexpr int kNonsymMaxM0 = 64;
 cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
 cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st);
 cudaError_t column_norms(int n, int m0, const double *X, double *part, int Pr, double *beta,

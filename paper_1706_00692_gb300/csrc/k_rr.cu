@@ -41,21 +41,24 @@ k_spmm_real(int n, int m, const int32_t *__restrict__ rowptr, const int32_t *__r
 
 // Partials of Q^T AQ and Q^T Q over this block's rows. Thread t of block
 // (bx, by) owns the 4x4 output tile number by*256 + t of the upper triangle
-// of tiles (m0 padded to mp = multiple of 4).
+// of tiles (m0 padded to mp = multiple of 4), or of all tiles when full != 0.
 // With BQ (generalized problem) the second matrix is Q^T (B Q) instead of Q^T Q.
 __global__ void __launch_bounds__(kThreads)
 k_gram(int n, int m, int mp, const double *__restrict__ Q, const double *__restrict__ AQ,
-       const double *__restrict__ BQ, double *__restrict__ part, int rows) {
+       const double *__restrict__ BQ, double *__restrict__ part, int rows, int full) {
   extern __shared__ double sm[];
   double *Qs = sm;                       // kGramRows x mp
   double *As = sm + kGramRows * mp;      // kGramRows x mp
   double *Bs = BQ ? sm + 2 * kGramRows * mp : Qs;  // kGramRows x mp
   const int nt = mp / 4;
-  const int ntiles = nt * (nt + 1) / 2;
+  const int ntiles = full ? nt * nt : nt * (nt + 1) / 2;
   const int tile = blockIdx.y * kThreads + threadIdx.x;
   int ti = 0, tj = 0;
   const bool own = tile < ntiles;
-  if (own) {  // tile -> (ti, tj), ti <= tj, row-major over the upper triangle
+  if (own && full) {  // every tile (non-symmetric A_Q)
+    ti = tile / nt;
+    tj = tile % nt;
+  } else if (own) {  // tile -> (ti, tj), ti <= tj, row-major over the upper triangle
     int t = tile, r = 0;
     while (t >= nt - r) {
       t -= nt - r;
@@ -508,11 +511,473 @@ __global__ void k_reduce_resid(int Pr, int m, const double *__restrict__ part,
   }
 }
 
+
+// ===========================================================================
+// Non-Hermitian extension (real non-symmetric A): Galerkin Rayleigh-Ritz on
+// span(Q). B_Q = Q^T Q = L L^T, the carried basis is X = Q L^{-T} (orthonormal
+// columns), C = L^{-1} (Q^T A Q) L^{-T} is a general real matrix whose
+// eigenpairs (theta_j, u_j) give the Ritz pairs (theta_j, X u_j).
+// ===========================================================================
+
+// Full sums of the gram partials: A_Q as computed (no symmetrisation), B_Q
+// symmetrised.
+__global__ void k_reduce_gram_full(int Pg, int m, int mp, const double *__restrict__ part,
+                                   double *__restrict__ Aq, double *__restrict__ Bq) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  const int i = idx / m, j = idx % m;
+  double sa = 0.0, sb = 0.0, sb2 = 0.0;
+  for (int b = 0; b < Pg; ++b) {
+    const double *pa = part + (size_t)b * 2 * mp * mp;
+    const double *pb = pa + (size_t)mp * mp;
+    sa += pa[(size_t)i * mp + j];
+    sb += pb[(size_t)i * mp + j];
+    sb2 += pb[(size_t)j * mp + i];
+  }
+  Aq[(size_t)i * m + j] = sa;
+  Bq[(size_t)i * m + j] = 0.5 * (sb + sb2);
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+// principal square root
+__device__ double2 zsqrt(double2 z) {
+  const double r = zabs(z);
+  if (r == 0.0) return make_double2(0.0, 0.0);
+  const double t = sqrt(0.5 * (r + fabs(z.x)));
+  if (z.x >= 0.0) return make_double2(t, z.y / (2.0 * t));
+  return make_double2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+
+constexpr int kNsMaxM0 = 64;  // largest m0 of the non-symmetric reduced solver
+constexpr size_t kNsEigSmem = 6 * (size_t)kNsMaxM0 * kNsMaxM0 * sizeof(double);
+
+// One CTA. Steps: Cholesky of B_Q (one shifted retry), L^{-1}, C = L^{-1}
+// A_Q L^{-T}; Householder reduction of C to upper Hessenberg form (H = Z^T
+// C Z); complex single-shift QR iteration (Wilkinson shifts, deflation on
+// negligible subdiagonals, rotations applied to the whole matrix and to Z) to
+// the Schur form T = W^H C W; eigenvectors of T by back substitution; u_j =
+// W y_j normalised. Outputs L^{-T}, theta, U. status->breakdown = 1: B_Q not
+// factorable; 2: the QR iteration did not converge in 30 m steps.
+__global__ void __launch_bounds__(256)
+k_reduced_eig_nonsym(int m, const double *__restrict__ Aq, const double *__restrict__ Bq,
+                     double *__restrict__ LinvT, double2 *__restrict__ theta,
+                     double2 *__restrict__ Uc, DevStatus *__restrict__ status) {
+  extern __shared__ __align__(16) double smem[];
+  const size_t mm = (size_t)m * m;
+  double *L = smem;                                 // region 0: Cholesky factor, then Zr
+  double *Li = smem + mm;                           // region 1: L^{-1}
+  double *Y = smem + 2 * mm;                        // region 2: L^{-1} A_Q, then H
+  double *Cr = smem + 4 * mm;                       // region 3: C (real), then Z
+  double2 *H = reinterpret_cast<double2 *>(smem + 2 * mm);
+  double2 *Z = reinterpret_cast<double2 *>(smem + 4 * mm);
+  double2 *Yv = reinterpret_cast<double2 *>(smem);  // regions 0-1: eigenvectors of T
+  double *Zr = L;
+  __shared__ double red[32];
+  __shared__ int flag, sh_l;
+  __shared__ double hv[kNsMaxM0];
+  __shared__ double sh_vv, sh_norm;
+  __shared__ double gc[kNsMaxM0];
+  __shared__ double2 gs[kNsMaxM0];
+  __shared__ double2 sh_mu;
+  const int tid = threadIdx.x, nth = blockDim.x;
+
+  // ---- Cholesky of B_Q, with one shifted retry --------------------------
+  double fro2 = 0.0;
+  for (size_t e = tid; e < mm; e += nth) fro2 += Bq[e] * Bq[e];
+  fro2 = block_sum(fro2, red);
+  int shifted = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const double shift =
+        attempt ? 11.0 * ((double)m * m + (double)m * (m + 1)) * DBL_EPSILON * sqrt(fro2) : 0.0;
+    for (size_t e = tid; e < mm; e += nth) {
+      const int i = (int)(e / m), k = (int)(e % m);
+      L[e] = (k <= i) ? Bq[e] + (i == k ? shift : 0.0) : 0.0;
+    }
+    if (tid == 0) flag = 0;
+    __syncthreads();
+    if (cholesky_inplace(L, m, &flag) == 0) break;
+    __syncthreads();
+    if (attempt == 1) {
+      if (tid == 0) status->breakdown = 1;
+      return;
+    }
+    shifted = 1;
+  }
+  if (tid == 0) {
+    status->breakdown = 0;
+    status->shifted = shifted;
+  }
+  __syncthreads();
+  // ---- L^{-1} (thread per column), L^{-T} out, C = L^{-1} A_Q L^{-T} -----
+  for (int j = tid; j < m; j += nth)
+    for (int i = 0; i < m; ++i) {
+      double t = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) t -= L[(size_t)i * m + k] * Li[(size_t)k * m + j];
+      Li[(size_t)i * m + j] = i < j ? 0.0 : t / L[(size_t)i * m + i];
+    }
+  __syncthreads();
+  for (size_t e = tid; e < mm; e += nth) {
+    const int i = (int)(e / m), j = (int)(e % m);
+    LinvT[e] = Li[(size_t)j * m + i];
+    double t = 0.0;
+    for (int k = 0; k <= i; ++k) t += Li[(size_t)i * m + k] * Aq[(size_t)k * m + j];
+    Y[e] = t;
+  }
+  __syncthreads();
+  for (size_t e = tid; e < mm; e += nth) {
+    const int i = (int)(e / m), j = (int)(e % m);
+    double t = 0.0;
+    for (int k = 0; k <= j; ++k) t += Y[(size_t)i * m + k] * Li[(size_t)j * m + k];
+    Cr[e] = t;
+    Zr[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // ---- Householder reduction to upper Hessenberg form ---------------------
+  for (int k = 0; k + 2 < m; ++k) {
+    if (tid == 0) {
+      double nx = 0.0;
+      for (int i = k + 1; i < m; ++i) nx += Cr[(size_t)i * m + k] * Cr[(size_t)i * m + k];
+      nx = sqrt(nx);
+      const double x0 = Cr[(size_t)(k + 1) * m + k];
+      double vv = 0.0;
+      if (nx > 0.0) {
+        const double al = x0 >= 0.0 ? -nx : nx;
+        for (int i = k + 1; i < m; ++i) hv[i] = Cr[(size_t)i * m + k];
+        hv[k + 1] = x0 - al;
+        for (int i = k + 1; i < m; ++i) vv += hv[i] * hv[i];
+      }
+      sh_vv = vv;
+    }
+    __syncthreads();
+    const double vv = sh_vv;
+    if (vv > 0.0) {
+      // C <- (I - 2 v v^T / vv) C on rows k+1.., columns k..
+      for (int j = k + tid; j < m; j += nth) {
+        double t = 0.0;
+        for (int i = k + 1; i < m; ++i) t += hv[i] * Cr[(size_t)i * m + j];
+        const double f = 2.0 * t / vv;
+        for (int i = k + 1; i < m; ++i) Cr[(size_t)i * m + j] -= f * hv[i];
+      }
+      __syncthreads();
+      // C <- C (I - 2 v v^T / vv), Z <- Z (I - 2 v v^T / vv) on columns k+1..
+      for (int r = tid; r < 2 * m; r += nth) {
+        double *row = r < m ? Cr + (size_t)r * m : Zr + (size_t)(r - m) * m;
+        double t = 0.0;
+        for (int j = k + 1; j < m; ++j) t += row[j] * hv[j];
+        const double f = 2.0 * t / vv;
+        for (int j = k + 1; j < m; ++j) row[j] -= f * hv[j];
+      }
+      __syncthreads();
+      for (int i = k + 2 + tid; i < m; i += nth) Cr[(size_t)i * m + k] = 0.0;
+      __syncthreads();
+    }
+  }
+  // ---- complex copies: H = C (region 2), Z = Zr (region 3, after C is read) ----
+  for (size_t e = tid; e < mm; e += nth) H[e] = make_double2(Cr[e], 0.0);
+  __syncthreads();
+  double hn = 0.0;
+  for (size_t e = tid; e < mm; e += nth) hn += fabs(H[e].x);
+  hn = block_sum(hn, red);
+  for (size_t e = tid; e < mm; e += nth) Z[e] = make_double2(Zr[e], 0.0);
+  if (tid == 0) sh_norm = hn > 0.0 ? hn : 1.0;
+  __syncthreads();
+  // ---- complex single-shift QR iteration --------------------------------
+  int hi = m - 1, its = 0, total = 0;
+  bool failed = false;
+  while (hi > 0) {
+    if (tid == 0) {
+      int l = hi;
+      while (l > 0) {
+        double sc = zabs(H[(size_t)(l - 1) * m + l - 1]) + zabs(H[(size_t)l * m + l]);
+        if (sc == 0.0) sc = sh_norm;
+        if (zabs(H[(size_t)l * m + l - 1]) <= DBL_EPSILON * sc) {
+          H[(size_t)l * m + l - 1] = make_double2(0.0, 0.0);
+          break;
+        }
+        --l;
+      }
+      sh_l = l;
+      if (l < hi) {  // shift for the active block [l, hi]
+        const double2 a = H[(size_t)(hi - 1) * m + hi - 1], b = H[(size_t)(hi - 1) * m + hi];
+        const double2 c = H[(size_t)hi * m + hi - 1], d = H[(size_t)hi * m + hi];
+        double2 mu;
+        if (its == 10 || its == 20) {  // exceptional shift
+          mu = zadd(d, make_double2(zabs(c) + (hi >= 2 ? zabs(H[(size_t)(hi - 1) * m + hi - 2]) : 0.0), 0.0));
+        } else {  // Wilkinson: eigenvalue of the trailing 2 x 2 closer to d
+          const double2 hd = zscale(zsub(a, d), 0.5);
+          const double2 disc = zsqrt(zadd(zmul(hd, hd), zmul(b, c)));
+          const double2 mid = zscale(zadd(a, d), 0.5);
+          const double2 e1 = zadd(mid, disc), e2 = zsub(mid, disc);
+          mu = zabs(zsub(e1, d)) <= zabs(zsub(e2, d)) ? e1 : e2;
+        }
+        sh_mu = mu;
+      }
+    }
+    __syncthreads();
+    const int l = sh_l;
+    if (l == hi) {
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (++total > 30 * m) {
+      failed = true;
+      break;
+    }
+    ++its;
+    const double2 mu = sh_mu;
+    for (int i = l + tid; i <= hi; i += nth) H[(size_t)i * m + i] = zsub(H[(size_t)i * m + i], mu);
+    __syncthreads();
+    // H - mu I = G^H R: rotations from the left, each on two full rows
+    for (int k = l; k < hi; ++k) {
+      if (tid == 0) {
+        const double2 a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
+        const double na = zabs(a), nb = zabs(b);
+        const double r = hypot(na, nb);
+        if (r == 0.0) {
+          gc[k] = 1.0;
+          gs[k] = make_double2(0.0, 0.0);
+        } else if (na == 0.0) {
+          gc[k] = 0.0;
+          gs[k] = zscale(zconj(b), 1.0 / nb);
+        } else {
+          gc[k] = na / r;
+          gs[k] = zscale(zmul(zscale(a, 1.0 / na), zconj(b)), 1.0 / r);
+        }
+      }
+      __syncthreads();
+      const double c = gc[k];
+      const double2 sn = gs[k];
+      for (int j = k + tid; j < m; j += nth) {
+        const double2 x = H[(size_t)k * m + j], y = H[(size_t)(k + 1) * m + j];
+        H[(size_t)k * m + j] = zadd(zscale(x, c), zmul(sn, y));
+        H[(size_t)(k + 1) * m + j] = zsub(zscale(y, c), zmul(zconj(sn), x));
+      }
+      __syncthreads();
+    }
+    // R G (rotations from the right) + mu I; Z <- Z G
+    for (int k = l; k < hi; ++k) {
+      const double c = gc[k];
+      const double2 sn = gs[k];
+      const int rmax = min(k + 1, hi);
+      for (int i = tid; i <= rmax + m; i += nth) {
+        double2 *row = i <= rmax ? H + (size_t)i * m : Z + (size_t)(i - rmax - 1) * m;
+        if (i > rmax && i - rmax - 1 >= m) continue;
+        const double2 x = row[k], y = row[k + 1];
+        row[k] = zadd(zscale(x, c), zmul(y, zconj(sn)));
+        row[k + 1] = zsub(zscale(y, c), zmul(x, sn));
+      }
+      __syncthreads();
+    }
+    for (int i = l + tid; i <= hi; i += nth) H[(size_t)i * m + i] = zadd(H[(size_t)i * m + i], mu);
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) status->breakdown = 2;
+    return;
+  }
+  // ---- eigenvectors of the triangular T = H (thread per eigenvalue) -------
+  for (int k = tid; k < m; k += nth) {
+    const double2 tk = H[(size_t)k * m + k];
+    const double small = DBL_EPSILON * sh_norm;
+    for (int j = m - 1; j > k; --j) Yv[(size_t)j * m + k] = make_double2(0.0, 0.0);
+    Yv[(size_t)k * m + k] = make_double2(1.0, 0.0);
+    for (int j = k - 1; j >= 0; --j) {
+      double2 sacc = make_double2(0.0, 0.0);
+      for (int q = j + 1; q <= k; ++q) sacc = zadd(sacc, zmul(H[(size_t)j * m + q], Yv[(size_t)q * m + k]));
+      double2 d = zsub(H[(size_t)j * m + j], tk);
+      if (zabs(d) < small) d = make_double2(small, 0.0);
+      Yv[(size_t)j * m + k] = zscale(zdiv(sacc, d), -1.0);
+    }
+    theta[k] = tk;
+  }
+  __syncthreads();
+  // ---- u_k = W y_k (W = Z), normalised; written to Uc ----------------------
+  for (size_t e = tid; e < mm; e += nth) {
+    const int i = (int)(e / m), k = (int)(e % m);
+    double2 t = make_double2(0.0, 0.0);
+    for (int q = 0; q <= k; ++q) t = zadd(t, zmul(Z[(size_t)i * m + q], Yv[(size_t)q * m + k]));
+    Uc[e] = t;
+  }
+  __threadfence_block();
+  __syncthreads();
+  for (int k = tid; k < m; k += nth) {
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double2 u = Uc[(size_t)i * m + k];
+      nrm += u.x * u.x + u.y * u.y;
+    }
+    nrm = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
+    for (int i = 0; i < m; ++i) Uc[(size_t)i * m + k] = zscale(Uc[(size_t)i * m + k], nrm);
+  }
+}
+
+// X = Q L^{-T}, AX = AQ L^{-T} on this block's rows (X written); partials per
+// column j of |AX u_j - theta_j X u_j|^2, |AX u_j|^2 and the new X's column
+// norm^2. blockDim = (32, 8): x over columns (j = tx, tx + 32), y over rows.
+__global__ void __launch_bounds__(256)
+k_update_nonsym(int n, int m, const double *__restrict__ Q, const double *__restrict__ AQ,
+                const double *__restrict__ LinvT, const double2 *__restrict__ Uc,
+                const double2 *__restrict__ theta, double *__restrict__ X,
+                double *__restrict__ part, int rows) {
+  extern __shared__ __align__(16) double sm[];
+  const int RB = 8;
+  // the complex tile first: 16-byte aligned for every m
+  double2 *Us = reinterpret_cast<double2 *>(sm);           // m x m
+  double *Ls = sm + 2 * (size_t)m * m;                     // m x m
+  double *Qs = sm + 3 * (size_t)m * m;                     // RB x m
+  double *As = Qs + RB * m;                                // RB x m
+  double *Xs = As + RB * m;                                // RB x m (new X rows)
+  double *AXs = Xs + RB * m;                               // RB x m
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  for (size_t e = tid; e < (size_t)m * m; e += 256) {
+    Ls[e] = LinvT[e];
+    Us[e] = Uc[e];
+  }
+  double e2[2] = {0.0, 0.0}, a2[2] = {0.0, 0.0}, x2[2] = {0.0, 0.0};
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(n, r0 + rows);
+  for (int rb = r0; rb < r1; rb += RB) {
+    const int nr = min(RB, r1 - rb);
+    __syncthreads();
+    for (int e = tid; e < RB * m; e += 256) {
+      const int rr = e / m, jj = e % m;
+      Qs[e] = rr < nr ? Q[(size_t)(rb + rr) * m + jj] : 0.0;
+      As[e] = rr < nr ? AQ[(size_t)(rb + rr) * m + jj] : 0.0;
+    }
+    __syncthreads();
+    for (int q = 0; q < 2; ++q) {
+      const int j = tx + 32 * q;
+      if (ty < nr && j < m) {
+        double x = 0.0, ax = 0.0;
+        for (int i = 0; i <= j; ++i) {  // L^{-T} is upper triangular
+          const double l = Ls[(size_t)i * m + j];
+          x = fma(Qs[ty * m + i], l, x);
+          ax = fma(As[ty * m + i], l, ax);
+        }
+        Xs[ty * m + j] = x;
+        AXs[ty * m + j] = ax;
+        X[(size_t)(rb + ty) * m + j] = x;
+        x2[q] = fma(x, x, x2[q]);
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < 2; ++q) {
+      const int j = tx + 32 * q;
+      if (ty < nr && j < m) {
+        double2 xu = make_double2(0.0, 0.0), axu = make_double2(0.0, 0.0);
+        for (int i = 0; i < m; ++i) {
+          const double2 u = Us[(size_t)i * m + j];
+          xu = zadd(xu, zscale(u, Xs[ty * m + i]));
+          axu = zadd(axu, zscale(u, AXs[ty * m + i]));
+        }
+        const double2 d = zsub(axu, zmul(theta[j], xu));
+        e2[q] += d.x * d.x + d.y * d.y;
+        a2[q] += axu.x * axu.x + axu.y * axu.y;
+      }
+    }
+  }
+  __syncthreads();
+  __shared__ double red[8][32];
+  for (int q = 0; q < 2; ++q)
+    for (int which = 0; which < 3; ++which) {
+      red[ty][tx] = which == 0 ? e2[q] : (which == 1 ? a2[q] : x2[q]);
+      __syncthreads();
+      if (ty == 0) {
+        double t = 0.0;
+        for (int y = 0; y < 8; ++y) t += red[y][tx];
+        const int j = tx + 32 * q;
+        if (j < m) part[((size_t)blockIdx.x * 3 + which) * m + j] = t;
+      }
+      __syncthreads();
+    }
+}
+
+// Residuals, count of Ritz values inside the circle |theta - c| < r, ||R_F||,
+// the next tolerance, the new basis' column norms; lam = Re theta (one block).
+__global__ void k_reduce_resid_nonsym(int Pr, int m, const double *__restrict__ part,
+                                      const double2 *__restrict__ theta, double cc, double rr,
+                                      double alpha, double *__restrict__ res,
+                                      double *__restrict__ beta, double *__restrict__ lam,
+                                      DevStatus *__restrict__ status) {
+  __shared__ double smax[256];
+  __shared__ int scnt[256], snan[256];
+  double mx = 0.0;
+  int cnt = 0, bad = 0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double e = 0.0, a = 0.0, x = 0.0;
+    for (int b = 0; b < Pr; ++b) {
+      e += part[((size_t)b * 3 + 0) * m + j];
+      a += part[((size_t)b * 3 + 1) * m + j];
+      x += part[((size_t)b * 3 + 2) * m + j];
+    }
+    const double r = sqrt(e) / (a > 0.0 ? sqrt(a) : 1.0);
+    res[j] = r;
+    beta[j] = sqrt(x);
+    const double2 t = theta[j];
+    lam[j] = t.x;
+    if (!isfinite(r) || !isfinite(t.x) || !isfinite(t.y)) bad = 1;
+    if (hypot(t.x - cc, t.y) < rr) {
+      ++cnt;
+      mx = fmax(mx, r);
+    }
+  }
+  smax[threadIdx.x] = mx;
+  scnt[threadIdx.x] = cnt;
+  snan[threadIdx.x] = bad;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double M = 0.0;
+    int N = 0, B = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      M = fmax(M, smax[t]);
+      N += scnt[t];
+      B |= snan[t];
+    }
+    const double RF = N > 0 ? M : 1.0;
+    status->RF = RF;
+    status->count = N;
+    status->nonfinite = B;
+    status->tol_rel = alpha > 0.0 ? alpha * RF : 0.0;
+  }
+}
+
+// Ritz vectors x_q = X u_{idx[q]} (n x cap complex, row-major, cap columns)
+__global__ void k_ritz_vectors_nonsym(int n, int m, const double *__restrict__ X,
+                                      const double2 *__restrict__ Uc, const int *__restrict__ idx,
+                                      int cnt, int cap, double2 *__restrict__ out) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * cnt) return;
+  const int i = (int)(e / cnt), q = (int)(e % cnt);
+  const int j = idx[q];
+  double2 t = make_double2(0.0, 0.0);
+  for (int l = 0; l < m; ++l) t = zadd(t, zscale(Uc[(size_t)l * m + j], X[(size_t)i * m + l]));
+  out[(size_t)i * cap + q] = t;
+}
+
 }  // namespace
 
 cudaError_t rr_init() {
   cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        3 * kGramRows * kMaxM0 * (int)sizeof(double));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_reduced_eig_nonsym, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kNsEigSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_update_nonsym, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((3 * kNsMaxM0 * kNsMaxM0 + 4 * 8 * kNsMaxM0) * sizeof(double)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kEigSmem);
@@ -546,7 +1011,7 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
     const size_t smem = (a.rowptrB ? 3 : 2) * (size_t)kGramRows * mp * sizeof(double);
     IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM);
     k_gram<<<dim3((a.n + rows - 1) / rows, gy), kThreads, smem, st>>>(
-        a.n, m, mp, a.Q, a.AQ, a.rowptrB ? a.BQ : nullptr, a.gram_part, rows);
+        a.n, m, mp, a.Q, a.AQ, a.rowptrB ? a.BQ : nullptr, a.gram_part, rows, 0);
     IFEAST_PROF_END(a.prof);
     const int pg_used = (a.n + rows - 1) / rows;
     IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM_REDUCE);
@@ -644,6 +1109,67 @@ int Profiler::collect() {
   }
   used = 0;
   return 0;
+}
+
+}  // namespace ifeast
+
+namespace ifeast {
+
+cudaError_t rayleigh_ritz_nonsym(const RRArgs &a, const NonsymArgs &ns, cudaStream_t st) {
+  const int m = a.m0;
+  if (m < 1 || m > kNsMaxM0) return cudaErrorInvalidValue;
+  const int mp = (m + 3) / 4 * 4;
+  {
+    const int tiles = (m + 31) / 32;
+    const int rows = (a.n + a.Pg - 1) / a.Pg;
+    IFEAST_PROF_BEGIN(a.prof, K_RR_SPMM);
+    k_spmm_real<<<dim3((a.n + rows - 1) / rows, tiles), kThreads, 0, st>>>(
+        a.n, m, a.rowptr, a.colidx, a.val, a.Q, a.AQ, rows);
+    IFEAST_PROF_END(a.prof);
+  }
+  {
+    const int nt = mp / 4;
+    const int gy = (nt * nt + kThreads - 1) / kThreads;
+    const int rows = (a.n + a.Pg - 1) / a.Pg;
+    const size_t smem = 2 * (size_t)kGramRows * mp * sizeof(double);
+    IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM);
+    k_gram<<<dim3((a.n + rows - 1) / rows, gy), kThreads, smem, st>>>(a.n, m, mp, a.Q, a.AQ,
+                                                                      nullptr, a.gram_part, rows, 1);
+    IFEAST_PROF_END(a.prof);
+    const int pg_used = (a.n + rows - 1) / rows;
+    IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM_REDUCE);
+    k_reduce_gram_full<<<(m * m + 255) / 256, 256, 0, st>>>(pg_used, m, mp, a.gram_part, a.Aq,
+                                                            a.Bq);
+    IFEAST_PROF_END(a.prof);
+  }
+  IFEAST_PROF_BEGIN(a.prof, K_RR_EIG);
+  k_reduced_eig_nonsym<<<1, 256, 6 * (size_t)m * m * sizeof(double), st>>>(
+      m, a.Aq, a.Bq, ns.LinvT, ns.theta, ns.Uc, a.status);
+  IFEAST_PROF_END(a.prof);
+  {
+    const int rows = (a.n + a.Pr - 1) / a.Pr;
+    const int pr_used = (a.n + rows - 1) / rows;
+    const size_t smem = (3 * (size_t)m * m + 4 * 8 * (size_t)m) * sizeof(double);
+    IFEAST_PROF_BEGIN(a.prof, K_RR_UPDATE);
+    k_update_nonsym<<<pr_used, dim3(32, 8), smem, st>>>(a.n, m, a.Q, a.AQ, ns.LinvT, ns.Uc,
+                                                        ns.theta, a.X, a.res_part, rows);
+    IFEAST_PROF_END(a.prof);
+    IFEAST_PROF_BEGIN(a.prof, K_RR_RESID);
+    k_reduce_resid_nonsym<<<1, 256, 0, st>>>(pr_used, m, a.res_part, ns.theta,
+                                             0.5 * (a.emin + a.emax), 0.5 * (a.emax - a.emin),
+                                             a.alpha, a.res, a.beta, a.lam, a.status);
+    IFEAST_PROF_END(a.prof);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t ritz_vectors_nonsym(int n, int m, const double *X, const double2 *Uc, const int *idx,
+                                int cnt, int cap, double2 *out, cudaStream_t st) {
+  if (cnt <= 0) return cudaSuccess;
+  const size_t tot = (size_t)n * cnt;
+  k_ritz_vectors_nonsym<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, m, X, Uc, idx, cnt, cap,
+                                                                       out);
+  return cudaGetLastError();
 }
 
 }  // namespace ifeast

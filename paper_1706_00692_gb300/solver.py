@@ -48,7 +48,8 @@ class Solver:
                  rule: str = "gl_half", inner: str = "gmres", inner_iters: int = 10,
                  alpha: float = 0.0, max_outer: int = 100, tol: float = 1e-10,
                  precision: str = "fp64", device: str | int = "cuda",
-                 torch_workspace: bool = True, verbose: bool = False, B: CSR | None = None):
+                 torch_workspace: bool = True, verbose: bool = False, B: CSR | None = None,
+                 nonsymmetric: bool = False):
         torch = _torch()
         self.lib = _lib.load()
         self.torch = torch
@@ -65,6 +66,7 @@ class Solver:
         self.opts.inner_solver = _lib.INNERS[inner]
         self.opts.precision = _lib.PRECISIONS[precision]
         self.opts.verbose = 1 if verbose else 0
+        self.opts.nonsymmetric = 1 if nonsymmetric else 0
         nbytes = ct.c_size_t(0)
         rc = self.lib.ifeast_workspace_bytes_generalized(
             self.n, A.nnz, -1 if B is None else B.nnz, self.m0, ct.byref(self.contour),
@@ -131,6 +133,38 @@ class Solver:
         if rc:
             raise IFEASTError(rc, "ifeast_eigenpairs")
         return lam, X, res
+
+    def eigenpairs_complex(self):
+        """Non-symmetric handles: (lam complex, X complex (n, m), res) for the
+        Ritz pairs inside the contour's circle, ordered by real, then imaginary
+        part."""
+        m = ct.c_int(0)
+        rc = self.lib.ifeast_eigenpairs_complex(self.h, 0, ct.byref(m), None, None, None, 0)
+        if rc:
+            raise IFEASTError(rc, "ifeast_eigenpairs_complex")
+        cnt = m.value
+        lam = np.zeros(cnt, np.complex128)
+        X = np.zeros((self.n, cnt), np.complex128)
+        res = np.zeros(cnt)
+        ptrs = (lam.ctypes.data, X.ctypes.data, res.ctypes.data) if cnt else (None, None, None)
+        rc = self.lib.ifeast_eigenpairs_complex(self.h, cnt, ct.byref(m), *ptrs, 0)
+        if rc:
+            raise IFEASTError(rc, "ifeast_eigenpairs_complex")
+        return lam, X, res
+
+    def rayleigh_ritz_nonsym(self, Q):
+        """Galerkin Rayleigh-Ritz on a CUDA float64 (n, m0) tensor: returns
+        (X orthonormal basis, theta complex (m0,) unordered, res)."""
+        torch = self.torch
+        Q = Q.contiguous()
+        X = torch.empty_like(Q)
+        theta = torch.empty(self.m0, dtype=torch.complex128, device=self.device)
+        res = torch.empty(self.m0, dtype=torch.float64, device=self.device)
+        rc = self.lib.ifeast_rayleigh_ritz_nonsym(self.h, Q.data_ptr(), X.data_ptr(),
+                                                  theta.data_ptr(), res.data_ptr())
+        if rc:
+            raise IFEASTError(rc, "ifeast_rayleigh_ritz_nonsym")
+        return X, theta, res
 
     def ritz_all(self):
         lam, res = np.zeros(self.m0), np.zeros(self.m0)

@@ -72,7 +72,7 @@ def _opts(lib, **kw):
 def test_default_opts(lib):
     o = _opts(lib)
     assert (o.inner_solver, o.inner_max_iters, o.alpha, o.max_outer, o.tol, o.precision,
-            o.verbose) == (0, 10, 0.0, 100, 1e-10, 0, 0)
+            o.verbose, o.nonsymmetric) == (0, 10, 0.0, 100, 1e-10, 0, 0, 0)
 
 
 def test_workspace_bytes_grows_with_basis(lib):
@@ -127,7 +127,14 @@ def test_create_rejects_bad_options(lib):
     assert _create(lib, A, opts=_opts(lib, inner_solver=1, inner_max_iters=5000))[0] == \
         _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, contour=_lib.Contour(0, 4, 1.0, 0.5))[0] == _lib.IFEAST_ERR_INVALID_ARG
-    assert _create(lib, A, contour=_lib.Contour(2, 4, 0.0, 0.5))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    # a full-circle rule needs an even node count (it runs as the half rule on nc/2)
+    assert _create(lib, A, contour=_lib.Contour(2, 5, 0.0, 0.5))[0] == _lib.IFEAST_ERR_INVALID_ARG
+    # the non-symmetric extension: GMRES inner solves, m0 <= 64, flag 0 or 1
+    assert _create(lib, A, opts=_opts(lib, nonsymmetric=1, inner_solver=1,
+                                      inner_max_iters=8))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    big = inputs.laplacian((10, 10))
+    assert _create(lib, big, m0=65, opts=_opts(lib, nonsymmetric=1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, opts=_opts(lib, nonsymmetric=2))[0] == _lib.IFEAST_ERR_INVALID_ARG
 
 
 def _csr_ref(M, keep):
