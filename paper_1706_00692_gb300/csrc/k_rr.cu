@@ -190,6 +190,102 @@ __device__ int cholesky_inplace(double *L, int m, int *flag) {
   return 0;
 }
 
+// Cyclic Jacobi on the symmetric m x m matrix Cm (leading dimension ld) with
+// rotations accumulated into U (same ld), both of type T, round-robin pairing
+// so that m/2 disjoint rotations are applied at once; warp w updates the two
+// rows (or columns) of pairs w, w + nwarps, ... with its lanes along them. An
+// odd ld keeps the column passes free of shared-memory bank conflicts. Stops
+// when the off-diagonal part's squared Frobenius norm is at most stop times
+// the whole matrix's, when a sweep finds no pair worth rotating at the working
+// precision, or after max_sweeps sweeps.
+template <typename T>
+__device__ void jacobi_rr(T *Cm, T *U, int m, int ld, int max_sweeps, double stop, double *red,
+                          double *rot_c, double *rot_s, int *rot_a, int *rot_b) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+  const int mp = m + (m & 1);
+  const int npairs = mp / 2;
+  __shared__ int any_rot;  // a sweep that rotates nothing ends the iteration
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = warp; i < m; i += nwarps)
+      for (int k = lane; k < m; k += 32) {
+        const double v = (double)Cm[(size_t)i * ld + k] * (double)Cm[(size_t)i * ld + k];
+        tot += v;
+        if (i != k) off += v;
+      }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (!(off > stop * tot)) break;
+    if (tid == 0) any_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < mp - 1; ++round) {
+      for (int p = tid; p < npairs; p += nth) {
+        const int pa = p, pb = mp - 1 - p;
+        int a = pa == 0 ? 0 : 1 + (pa - 1 + round) % (mp - 1);
+        int b = pb == 0 ? 0 : 1 + (pb - 1 + round) % (mp - 1);
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+        }
+        // the rotation is formed in the sweep's own precision T (FP64
+        // division and square root cost ~1,100 cycles per round on this GPU)
+        T c = 1, s = 0;
+        if (b < m) {
+          const T apq = Cm[(size_t)a * ld + b];
+          const T app = Cm[(size_t)a * ld + a], aqq = Cm[(size_t)b * ld + b];
+          // below this the rotation changes nothing at the working precision
+          const T tiny = sizeof(T) == 4 ? (T)1e-30 : (T)1e-300;
+          const T rel = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
+          if (fabs(apq) > tiny && fabs(apq) > rel * sqrt(fabs(app * aqq))) {
+            const T tau = (aqq - app) / (2 * apq);
+            const T big = sizeof(T) == 4 ? (T)1e18 : (T)1e150;
+            const T t = (tau >= 0 ? (T)1 : (T)-1) /
+                        (fabs(tau) + (fabs(tau) < big ? sqrt(1 + tau * tau) : fabs(tau)));
+            c = 1 / sqrt(1 + t * t);
+            s = t * c;
+            any_rot = 1;  // every writer stores the same value
+          }
+        }
+        rot_a[p] = a;
+        rot_b[p] = b < m ? b : a;
+        rot_c[p] = (double)c;
+        rot_s[p] = (b < m) ? (double)s : 0.0;
+      }
+      __syncthreads();
+      // rows: C <- J^T C
+      for (int p = warp; p < npairs; p += nwarps) {
+        const int a = rot_a[p], b = rot_b[p];
+        if (a == b || rot_s[p] == 0.0) continue;
+        const T c = (T)rot_c[p], s = (T)rot_s[p];
+        for (int k = lane; k < m; k += 32) {
+          const T x = Cm[(size_t)a * ld + k], y = Cm[(size_t)b * ld + k];
+          Cm[(size_t)a * ld + k] = c * x - s * y;
+          Cm[(size_t)b * ld + k] = s * x + c * y;
+        }
+      }
+      __syncthreads();
+      // columns: C <- C J, U <- U J
+      for (int p = warp; p < npairs; p += nwarps) {
+        const int a = rot_a[p], b = rot_b[p];
+        if (a == b || rot_s[p] == 0.0) continue;
+        const T c = (T)rot_c[p], s = (T)rot_s[p];
+        for (int k = lane; k < m; k += 32) {
+          const T x = Cm[(size_t)k * ld + a], y = Cm[(size_t)k * ld + b];
+          Cm[(size_t)k * ld + a] = c * x - s * y;
+          Cm[(size_t)k * ld + b] = s * x + c * y;
+          const T u = U[(size_t)k * ld + a], v = U[(size_t)k * ld + b];
+          U[(size_t)k * ld + a] = c * u - s * v;
+          U[(size_t)k * ld + b] = s * u + c * v;
+        }
+      }
+      __syncthreads();
+    }
+    if (!any_rot) break;
+  }
+}
+
 // Generalised symmetric eigenproblem A_Q X = B_Q X Lambda in one CTA.
 __global__ void __launch_bounds__(512)
 k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ Bq,
@@ -198,7 +294,9 @@ k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ B
               int smem_mats) {
   // smem_mats = how many of (C, U, L) live in shared memory (in that order)
   extern __shared__ double smem[];
-  const size_t mm_ = (size_t)m * m;
+  // each matrix in shared memory takes m x (m | 1) doubles (room for the odd
+  // leading dimension of the mixed-precision path)
+  const size_t mm_ = (size_t)m * (m | 1);
   double *Cm = smem_mats >= 1 ? smem : Cg;
   double *U = smem_mats >= 2 ? smem + mm_ : Ug;
   double *L = smem_mats >= 3 ? smem + 2 * mm_ : Lg;
@@ -268,74 +366,118 @@ k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ B
   for (size_t e = tid; e < mm; e += nth) U[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
   __syncthreads();
 
-  // ---- cyclic Jacobi, round-robin pairing (parallel rotations) -----------
-  const int mp = m + (m & 1);
-  const int npairs = mp / 2;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (size_t e = tid; e < mm; e += nth) {
-      const double v = Cm[e] * Cm[e];
-      tot += v;
-      if ((e / m) != (e % m)) off += v;
-    }
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
-    if (!(off > 1e-28 * tot)) break;  // off-diagonal norm below 1e-14 of the matrix norm
-    for (int round = 0; round < mp - 1; ++round) {
-      for (int p = tid; p < npairs; p += nth) {
-        const int pa = p, pb = mp - 1 - p;
-        int a = pa == 0 ? 0 : 1 + (pa - 1 + round) % (mp - 1);
-        int b = pb == 0 ? 0 : 1 + (pb - 1 + round) % (mp - 1);
-        if (a > b) {
-          const int t = a;
-          a = b;
-          b = t;
-        }
-        double c = 1.0, s = 0.0;
-        if (b < m) {
-          const double apq = Cm[(size_t)a * m + b];
-          const double app = Cm[(size_t)a * m + a], aqq = Cm[(size_t)b * m + b];
-          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) /
-                             (fabs(tau) + (fabs(tau) < 1e150 ? sqrt(1.0 + tau * tau) : fabs(tau)));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        rot_a[p] = a;
-        rot_b[p] = b < m ? b : a;
-        rot_c[p] = c;
-        rot_s[p] = (b < m) ? s : 0.0;
-      }
+  if (smem_mats >= 3) {
+    // ---- mixed precision: FP32 sweeps, FP64 re-orthonormalisation and finish
+    // Dense work matrices use an odd leading dimension (bank-conflict-free
+    // column access); the launch gives each of C, U, L m x ld doubles.
+    const int ld = m | 1;
+    const size_t ml = (size_t)m * ld;
+    // C, computed above with leading dimension m, moved to ld through U's buffer
+    if (ld != m) {
+      for (size_t e = tid; e < mm; e += nth) U[e] = Cm[e];
       __syncthreads();
-      // rows: C <- J^T C
-      for (int e = tid; e < npairs * m; e += nth) {
-        const int p = e / m, k = e % m;
-        const int a = rot_a[p], b = rot_b[p];
-        if (a == b || rot_s[p] == 0.0) continue;
-        const double c = rot_c[p], s = rot_s[p];
-        const double x = Cm[(size_t)a * m + k], y = Cm[(size_t)b * m + k];
-        Cm[(size_t)a * m + k] = c * x - s * y;
-        Cm[(size_t)b * m + k] = s * x + c * y;
-      }
-      __syncthreads();
-      // columns: C <- C J, U <- U J
-      for (int e = tid; e < npairs * m; e += nth) {
-        const int p = e / m, k = e % m;
-        const int a = rot_a[p], b = rot_b[p];
-        if (a == b || rot_s[p] == 0.0) continue;
-        const double c = rot_c[p], s = rot_s[p];
-        const double x = Cm[(size_t)k * m + a], y = Cm[(size_t)k * m + b];
-        Cm[(size_t)k * m + a] = c * x - s * y;
-        Cm[(size_t)k * m + b] = s * x + c * y;
-        const double u = U[(size_t)k * m + a], v = U[(size_t)k * m + b];
-        U[(size_t)k * m + a] = c * u - s * v;
-        U[(size_t)k * m + b] = s * u + c * v;
-      }
+      for (int i = tid / 32; i < m; i += nth / 32)
+        for (int k = tid & 31; k < m; k += 32) Cm[(size_t)i * ld + k] = U[(size_t)i * m + k];
       __syncthreads();
     }
+    // FP32 Jacobi (64x the FP64 rate on this GPU) on Cf = (float) C, with its
+    // rotations in Uf; both live in U's buffer.
+    float *Cf = reinterpret_cast<float *>(U);
+    float *Uf = Cf + ml;
+    for (int i = tid / 32; i < m; i += nth / 32)
+      for (int k = tid & 31; k < m; k += 32) {
+        Cf[(size_t)i * ld + k] = (float)Cm[(size_t)i * ld + k];
+        Uf[(size_t)i * ld + k] = i == k ? 1.f : 0.f;
+      }
+    __syncthreads();
+    // stop near the FP32 rounding floor (off-diagonal norm ~1e-5 of the
+    // matrix); the FP64 sweeps below finish the job
+    jacobi_rr<float>(Cf, Uf, m, ld, 16, 1e-10, red, rot_c, rot_s, rot_a, rot_b);
+    // U0 = Uf in FP64 (in L's buffer; L is kept in global memory), then
+    // CholQR in FP64: G = U0^T U0 = R^T R, U0 <- U0 R^{-1}, orthonormal to
+    // FP64 rounding
+    double *U0 = L;
+    for (size_t e = tid; e < mm; e += nth) Lg[e] = L[e];
+    __syncthreads();
+    for (int i = tid / 32; i < m; i += nth / 32)
+      for (int k = tid & 31; k < m; k += 32) U0[(size_t)i * ld + k] = (double)Uf[(size_t)i * ld + k];
+    __syncthreads();
+    double *G = U;  // Cf / Uf are consumed; G is m x m compact
+    for (int i = tid / 32; i < m; i += nth / 32)
+      for (int k = tid & 31; k < m; k += 32) {
+        double t = 0.0;
+        if (k <= i)
+          for (int r = 0; r < m; ++r) t += U0[(size_t)r * ld + i] * U0[(size_t)r * ld + k];
+        G[(size_t)i * m + k] = t;
+      }
+    if (tid == 0) flag = 0;
+    __syncthreads();
+    cholesky_inplace(G, m, &flag);  // U0 is orthonormal to FP32 rounding: G is SPD
+    __syncthreads();
+    // each row x of U0 solves x_new R = x with R = G^T (upper): forward substitution
+    for (int r = tid; r < m; r += nth) {
+      double *x = U0 + (size_t)r * ld;
+      for (int k = 0; k < m; ++k) {
+        double t = x[k];
+        for (int i = 0; i < k; ++i) t -= x[i] * G[(size_t)k * m + i];
+        x[k] = t / G[(size_t)k * m + k];
+      }
+    }
+    __syncthreads();
+    // C' = U0^T C U0 (T = C U0 in U's buffer, C' over C)
+    double *Tm = U;
+    for (int i = tid / 32; i < m; i += nth / 32)
+      for (int k = tid & 31; k < m; k += 32) {
+        double t = 0.0;
+        for (int r = 0; r < m; ++r) t += Cm[(size_t)i * ld + r] * U0[(size_t)r * ld + k];
+        Tm[(size_t)i * ld + k] = t;
+      }
+    __syncthreads();
+    for (int i = tid / 32; i < m; i += nth / 32)
+      for (int k = tid & 31; k < m; k += 32) {
+        if (k < i) continue;
+        double t = 0.0;
+        for (int r = 0; r < m; ++r) t += U0[(size_t)r * ld + i] * Tm[(size_t)r * ld + k];
+        Cm[(size_t)i * ld + k] = t;
+        Cm[(size_t)k * ld + i] = t;
+      }
+    __syncthreads();
+    for (int i = tid / 32; i < m; i += nth / 32)
+      for (int k = tid & 31; k < m; k += 32) U[(size_t)i * ld + k] = i == k ? 1.0 : 0.0;
+    __syncthreads();
+    // FP64 sweeps on the nearly diagonal C' (quadratic convergence: one or two)
+    jacobi_rr<double>(Cm, U, m, ld, 60, 1e-28, red, rot_c, rot_s, rot_a, rot_b);
+    for (int i = tid; i < m; i += nth) evals[i] = Cm[(size_t)i * ld + i];
+    __syncthreads();
+    // eigenvectors of C: U0 V (into C's buffer)
+    for (int i = tid / 32; i < m; i += nth / 32)
+      for (int k = tid & 31; k < m; k += 32) {
+        double t = 0.0;
+        for (int r = 0; r < m; ++r) t += U0[(size_t)i * ld + r] * U[(size_t)r * ld + k];
+        Cm[(size_t)i * ld + k] = t;
+      }
+    __syncthreads();
+    for (int i = tid; i < m; i += nth) {
+      int r = 0;
+      const double v = evals[i];
+      for (int k = 0; k < m; ++k) r += (evals[k] < v) || (evals[k] == v && k < i);
+      rank[i] = r;
+    }
+    __syncthreads();
+    // X_Q = L^-T (U0 V) with L from global memory, ascending order
+    for (int col = tid; col < m; col += nth) {
+      const int dst = rank[col];
+      for (int i = m - 1; i >= 0; --i) {
+        double t = Cm[(size_t)i * ld + col];
+        for (int k = i + 1; k < m; ++k) t -= Lg[(size_t)k * m + i] * XQ[(size_t)k * m + dst];
+        XQ[(size_t)i * m + dst] = t / Lg[(size_t)i * m + i];
+      }
+      lam[dst] = evals[col];
+    }
+    return;
   }
+  // ---- FP64 cyclic Jacobi (large m: matrices in global memory) --------------
+  jacobi_rr<double>(Cm, U, m, m, 60, 1e-28, red, rot_c, rot_s, rot_a, rot_b);
   for (int i = tid; i < m; i += nth) evals[i] = Cm[(size_t)i * m + i];
   __syncthreads();
   // ---- X_Q = L^-T U (back substitution per column), ascending order -------
@@ -1020,7 +1162,7 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
   }
   // reduced eigenproblem
   {
-    const size_t mat = (size_t)m * m * sizeof(double);
+    const size_t mat = (size_t)m * (m | 1) * sizeof(double);
     const int nmat = (int)std::min<size_t>(3, kEigSmem / mat);
     IFEAST_PROF_BEGIN(a.prof, K_RR_EIG);
     k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, a.Aq, a.Bq, a.L, a.Cm, a.U, a.XQ, a.lam,
@@ -1061,7 +1203,7 @@ cudaError_t reduced_eig_launch(int m, const double *Aq, const double *Bq, double
                                double *U, double *XQ, double *lam, DevStatus *status,
                                cudaStream_t st) {
   if (m < 1 || m > kMaxM0) return cudaErrorInvalidValue;
-  const size_t mat = (size_t)m * m * sizeof(double);
+  const size_t mat = (size_t)m * (m | 1) * sizeof(double);
   const int nmat = (int)std::min<size_t>(3, kEigSmem / mat);
   k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, Aq, Bq, L, Cm, U, XQ, lam, status, nmat);
   return cudaGetLastError();
