@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp16",
+                                                                 "lap3d_64_twopass",
                                                                  "lap3d_64_fp64", "lap2d_50",
                                                                  "serve"])
     p.add_argument("--requests", type=int, default=64, help="serving stream length")
@@ -62,6 +63,8 @@ def make_workload(name):
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp64")
     if name == "lap3d_64_fp16":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp16")
+    if name == "lap3d_64_twopass":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp32", two_pass=True)
     raise ValueError(name)
 
 
@@ -250,7 +253,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     X0 = torch.as_tensor(wl.X0(), device=dev)
     skw = dict(nc=wl.nc, rule=wl.rule, inner=wl.inner, inner_iters=wl.inner_iters,
-               alpha=wl.alpha, precision=wl.precision, device=dev)
+               alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass, device=dev)
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, **skw)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2

@@ -121,6 +121,14 @@ typedef struct {
                            it lies inside the circle |lambda - c| < r of the
                            contour, eigenpairs through ifeast_eigenpairs_complex.
                            Needs IFEAST_INNER_GMRES, B = NULL, m0 <= 64.       */
+  int minres_two_pass;  /* 1 (IFEAST_INNER_MINRES with FP32 or FP16, m0 % 4 == 0):
+                           keep three Lanczos vectors instead of the whole basis.
+                           A first pass runs the Lanczos and Givens steps; a
+                           second pass rebuilds v_0 .. v_{S-1} from the stored
+                           alpha, beta with the same arithmetic and accumulates
+                           the quadrature on the fly, so Q is bit-identical to
+                           the stored-basis mode. Workspace O(n m0) instead of
+                           O(inner_max_iters n m0); about twice the inner time. */
 } ifeast_opts;
 
 typedef struct {

@@ -1,6 +1,6 @@
 """Run one IFEAST solve of a named synthetic workload and report the result.
 
-    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_fp64|lap2d_50]
+    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_twopass|lap3d_64_fp64|lap2d_50]
                                          [--max-outer M] [--inner-iters K] [--verbose]
 
 Prints one JSON line: status, eigenpairs found, largest residual, outer
@@ -26,6 +26,8 @@ def workload(name: str):
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp64")
     if name == "lap3d_64_fp16":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp16")
+    if name == "lap3d_64_twopass":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="fp32", two_pass=True)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -40,7 +42,8 @@ def main(argv=None) -> int:
     wl = workload(a.workload)
     k = a.inner_iters or wl.inner_iters
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
-               inner_iters=k, alpha=wl.alpha, precision=wl.precision, max_outer=a.max_outer,
+               inner_iters=k, alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass,
+               max_outer=a.max_outer,
                verbose=a.verbose)
     X0 = torch.as_tensor(wl.X0(), device="cuda")
     torch.cuda.synchronize()

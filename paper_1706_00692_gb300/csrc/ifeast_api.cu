@@ -54,6 +54,8 @@ struct ifeast_ctx {
   float wscale = 1.f;
   float *val32 = nullptr;
   void *LV = nullptr, *LW0 = nullptr, *LW1 = nullptr;
+  bool two_pass = false;
+  float *Qf = nullptr;
   double *lpart = nullptr, *lalpha = nullptr, *lbeta = nullptr, *ltol = nullptr;
   double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
@@ -89,6 +91,7 @@ struct Offsets {
       lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
   size_t rowptrB, colidxB, valB, BQ, BX;
   size_t LinvT, theta, Uc, ridx;
+  size_t Qf;
 };
 
 int device_sms() {
@@ -99,7 +102,8 @@ int device_sms() {
 }
 
 Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr,
-             bool minres, int prec, int sms_for_plan, int64_t nnzB, bool nonsym) {
+             bool minres, int prec, int sms_for_plan, int64_t nnzB, bool nonsym,
+             bool two_pass) {
   Layout L;
   Offsets o{};
   const size_t C = (size_t)nc * m0;
@@ -132,7 +136,9 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
       o.colE = L.take<int32_t>((size_t)n * 16);
       o.valE = L.take<float>((size_t)n * 16);
     }
-    o.LV = L.take<char>((size_t)(K + 1) * n * m0 * es);
+    // stored basis (K + 1 vectors), or three slots and an FP32 accumulator
+    o.LV = L.take<char>((size_t)(two_pass ? 3 : K + 1) * n * m0 * es);
+    if (two_pass) o.Qf = L.take<float>((size_t)n * m0);
     o.LW0 = L.take<char>((size_t)n * m0 * es);
     o.LW1 = L.take<char>((size_t)n * m0 * es);
     // partials of the step kernels: tl.P blocks (generic) or up to 2 per SM (FP32)
@@ -226,6 +232,10 @@ int validate_opts(const ifeast_opts *o) {
     return IFEAST_ERR_INVALID_ARG;
   if (o->nonsymmetric != 0 && o->nonsymmetric != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->nonsymmetric && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
+  if (o->minres_two_pass != 0 && o->minres_two_pass != 1) return IFEAST_ERR_INVALID_ARG;
+  if (o->minres_two_pass &&
+      (o->inner_solver != IFEAST_INNER_MINRES || o->precision == IFEAST_FP64))
+    return IFEAST_ERR_UNSUPPORTED;
   return IFEAST_OK;
 }
 
@@ -449,6 +459,8 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.check_every = 16;
   a.active_host = h->active_host;
   a.P_async = 2 * h->num_sms;  // two resident blocks per SM
+  a.two_pass = h->two_pass ? 1 : 0;
+  a.Qf = h->Qf;
   a.ell_w = h->ell_w;
   a.colE = h->colE;
   a.valE = h->valE;
@@ -502,6 +514,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->precision = IFEAST_FP64;
   o->verbose = 0;
   o->nonsymmetric = 0;
+  o->minres_two_pass = 0;
 }
 
 const char *ifeast_strerror(int code) {
@@ -550,8 +563,9 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   if (nnz_b >= 0 && o && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   // the non-symmetric extension: standard problem, m0 within the reduced solver's limit
   if (o && o->nonsymmetric == 1 && (nnz_b >= 0 || m0 > kNonsymMaxM0)) return IFEAST_ERR_UNSUPPORTED;
-  // FP16 storage runs on the four-column kernels only
-  if (o && o->precision == IFEAST_FP16 && m0 % 4 != 0) return IFEAST_ERR_UNSUPPORTED;
+  // FP16 storage and the two-pass mode run on the four-column kernels only
+  if (o && (o->precision == IFEAST_FP16 || o->minres_two_pass == 1) && m0 % 4 != 0)
+    return IFEAST_ERR_UNSUPPORTED;
   if (n > (int64_t)INT32_MAX - 1 || nnz > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
   int rc = validate_contour(c);
   if (rc) return rc;
@@ -565,7 +579,7 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
   const int Pr = Pg;
   *bytes = plan(n, nnz, m0, nc, o->inner_max_iters, tl, Pg, Pr, minres, o->precision, sms,
-                nnz_b < 0 ? -1 : nnz_b, o->nonsymmetric == 1).total;
+                nnz_b < 0 ? -1 : nnz_b, o->nonsymmetric == 1, o->minres_two_pass == 1).total;
   return IFEAST_OK;
 }
 
@@ -619,8 +633,9 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
   h->Pr = h->Pg;
   contour_host(&ce, h->zh, h->wh);
+  h->two_pass = o->minres_two_pass == 1;
   const Offsets off = plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, o->precision,
-                           h->num_sms, nnzB, h->nonsym);
+                           h->num_sms, nnzB, h->nonsym, h->two_pass);
   if (workspace) {
     h->ws = (char *)workspace;
     h->ws_bytes = ws_bytes;
@@ -696,6 +711,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
       h->valE = (float *)(b + off.valE);
     }
     h->LV = b + off.LV;
+    if (h->two_pass) h->Qf = (float *)(b + off.Qf);
     h->LW0 = b + off.LW0;
     h->LW1 = b + off.LW1;
     h->lpart = (double *)(b + off.lpart);

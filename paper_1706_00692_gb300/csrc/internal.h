@@ -134,6 +134,15 @@ struct MinresState {
   int *active;              // [1] columns still running at the last checked step
   DevStatus *status;
 };
+// Second pass of the two-pass (memory-bounded) shared-basis mode: the basis
+// is rebuilt from the stored alpha, beta and Q accumulates coef_s v_s.
+struct Pass2 {
+  float *Qacc;              // n x m0 FP32 accumulator (null: not the second pass)
+  const float *cf;          // FP32 coefficients [K][m0]
+  const int *Sj;            // second pass: column j takes the steps s < Sj[j]
+  int vring;                // 0: basis slot s; 3: slot s % 3 (two-pass mode)
+};
+
 struct MinresArgs {
   int n, m0, nc, K;
   int fp32;                 // FP32 arithmetic in the Krylov kernels
@@ -160,6 +169,8 @@ struct MinresArgs {
   int ell_w;                // 8 or 16: fixed-width copy of A available (FP32), else 0
   const int32_t *colE;      // n x ell_w indices (padded with the row's own index)
   const float *valE;        // n x ell_w values (padded with zero)
+  int two_pass;             // 1: three basis slots and a second pass (FP32 kernels only)
+  float *Qf;                // n x m0 FP32 accumulator of the second pass
 };
 cudaError_t build_ell(int n, int W, const int32_t *rowptr, const int32_t *colidx, const float *val,
                       int32_t *colE, float *valE, cudaStream_t st);

@@ -95,6 +95,21 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
   if (idx == 0) st.active[0] = 0;
 }
 
+// v_0 = b / ||b|| again (second pass of the two-pass mode; the same
+// arithmetic as k_lz_prep, which also resets the least-squares state).
+template <typename T>
+__global__ void k_lz_v0(int n, int m0, const double *__restrict__ rhs,
+                        const double *__restrict__ rnorm, T *__restrict__ V0) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * m0) return;
+  const double b = rnorm[idx % m0];
+  const double x = b > 0.0 ? rhs[idx] / b : 0.0;
+  if constexpr (std::is_same_v<T, __half>)
+    V0[idx] = __float2half_rn((float)x);
+  else
+    V0[idx] = (T)x;
+}
+
 // One Lanczos step s on every column still running.
 //
 // A warp owns a contiguous segment of rows; lane l handles the columns
@@ -675,7 +690,7 @@ __device__ __forceinline__ void finish_row(float4 o1, float4 o2, float4 acc1, fl
                                            const float (&bs)[4], const bool (&act)[4], bool all4,
                                            float wsc, S *__restrict__ Vs, S *__restrict__ Wout,
                                            size_t off, float (&vv)[4], float (&vw)[4],
-                                           float (&ww)[4]) {
+                                           float (&ww)[4], float (&vout)[4]) {
   using St = Store4<S>;
   if (St::kHalf && !FIRST) {  // w_{s-1} is stored divided by wsc
     o1 = make_float4(o1.x * wsc, o1.y * wsc, o1.z * wsc, o1.w * wsc);
@@ -705,6 +720,8 @@ __device__ __forceinline__ void finish_row(float4 o1, float4 o2, float4 acc1, fl
       ww[i] = fmaf(w[i], w[i], ww[i]);
     }
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) vout[i] = v[i];
   if (all4) {
     if (!FIRST) St::store(Vs + off, make_float4(v[0], v[1], v[2], v[3]));
     St::store(Wout + off, make_float4(wst[0], wst[1], wst[2], wst[3]));
@@ -746,14 +763,40 @@ __device__ __forceinline__ void store_partials_f(const float (&vv)[4], const flo
 }
 
 // Column mask of an FP32 step kernel: column j still runs while some node's
-// pair (k, j) is not done (flags left by the previous Givens step).
+// pair (k, j) is not done (flags left by the previous Givens step); in the
+// second pass of the two-pass mode, while s < Sj[j] (the steps its solves took).
 __device__ __forceinline__ void load_column_mask(int m0, int nc, const int *__restrict__ done_r,
-                                                 int *cdone) {
+                                                 int *cdone, const int *__restrict__ Sj, int s) {
+  if (Sj != nullptr) {
+    for (int j = threadIdx.x; j < m0; j += kVThreads) cdone[j] = s < Sj[j] ? 0 : 1;
+    __syncthreads();
+    return;
+  }
   for (int j = threadIdx.x; j < m0; j += kVThreads) cdone[j] = 1;
   __syncthreads();
   for (int t = threadIdx.x; t < nc * m0; t += kVThreads)
     if (done_r[t] == 0) cdone[t % m0] = 0;  // every writer stores the same value
   __syncthreads();
+}
+
+// Q accumulation of the second pass: Qacc[r][j] += cf[s][j] v_s[r][j] in FP32
+// fused multiply-adds, in step order (the same sums as k_lz_quadrature4).
+__device__ __forceinline__ void accumulate_q(const Pass2 &p2, int m0, int s, size_t off, int q4,
+                                             const float (&v)[4], const bool (&act)[4],
+                                             bool all4) {
+  const float *c = p2.cf + (size_t)s * m0 + q4;
+  if (all4) {
+    float4 qv = *reinterpret_cast<const float4 *>(p2.Qacc + off);
+    qv.x = fmaf(c[0], v[0], qv.x);
+    qv.y = fmaf(c[1], v[1], qv.y);
+    qv.z = fmaf(c[2], v[2], qv.z);
+    qv.w = fmaf(c[3], v[3], qv.w);
+    *reinterpret_cast<float4 *>(p2.Qacc + off) = qv;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (act[i]) p2.Qacc[off + i] = fmaf(c[i], v[i], p2.Qacc[off + i]);
+  }
 }
 
 template <typename S, bool FIRST>
@@ -763,16 +806,19 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
                    S *__restrict__ V, const S *__restrict__ Wprev, S *__restrict__ Wout,
                    const double *__restrict__ alpha, const double *__restrict__ beta,
                    const int *__restrict__ done_r, int nc, float *__restrict__ part,
-                   int stride_items, float wsc, int *__restrict__ active_reset) {
+                   int stride_items, float wsc, int *__restrict__ active_reset,
+                   const Pass2 p2) {
   using St = Store4<S>;
   pdl_wait();
   pdl_launch_next();
   if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
-  S *__restrict__ Vs = V + (size_t)s * vs;
+  // basis slot of step s: the stored basis, or a ring of three in the two-pass mode
+  S *__restrict__ Vs = V + (size_t)(p2.vring ? s % p2.vring : s) * vs;
   const S *__restrict__ G1 = FIRST ? Vs : Wprev;
-  const S *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
+  const S *__restrict__ G2 =
+      FIRST ? Vs : V + (size_t)(p2.vring ? (s - 1) % p2.vring : s - 1) * vs;
   const int gt = blockIdx.x * kVThreads + threadIdx.x;
   const bool thr = gt < stride_items;
   const int q = thr ? gt % MQ : 0;
@@ -789,7 +835,7 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
     }
   }
   __shared__ int cdone[1024];
-  load_column_mask(m0, nc, done_r, cdone);
+  load_column_mask(m0, nc, done_r, cdone, p2.Sj, s);
   bool act[4];
   bool qact = false;
 #pragma unroll
@@ -830,8 +876,10 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
           if (!FIRST) acc2 = f4fma(a[u], g2[u], acc2);
         }
       }
+      float vo[4];
       finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout, off, vv, vw,
-                           ww);
+                           ww, vo);
+      if (p2.Qacc != nullptr) accumulate_q(p2, m0, s, off, 4 * q, vo, act, all4);
     }
   }
   store_partials_f(vv, vw, ww, m0, stride_items, part);
@@ -855,16 +903,19 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
                    const S *__restrict__ Wprev, S *__restrict__ Wout,
                    const double *__restrict__ alpha, const double *__restrict__ beta,
                    const int *__restrict__ done_r, int nc, float *__restrict__ part,
-                   int stride_items, float wsc, int *__restrict__ active_reset) {
+                   int stride_items, float wsc, int *__restrict__ active_reset,
+                   const Pass2 p2) {
   using St = Store4<S>;
   pdl_wait();
   pdl_launch_next();
   if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
-  S *__restrict__ Vs = V + (size_t)s * vs;
+  // basis slot of step s: the stored basis, or a ring of three in the two-pass mode
+  S *__restrict__ Vs = V + (size_t)(p2.vring ? s % p2.vring : s) * vs;
   const S *__restrict__ G1 = FIRST ? Vs : Wprev;
-  const S *__restrict__ G2 = FIRST ? Vs : V + (size_t)(s - 1) * vs;
+  const S *__restrict__ G2 =
+      FIRST ? Vs : V + (size_t)(p2.vring ? (s - 1) % p2.vring : s - 1) * vs;
   const int gt = blockIdx.x * kVThreads + threadIdx.x;
   const bool thr = gt < stride_items;
   const int q = thr ? gt % MQ : 0;
@@ -882,7 +933,7 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
     }
   }
   __shared__ int cdone[1024];
-  load_column_mask(m0, nc, done_r, cdone);
+  load_column_mask(m0, nc, done_r, cdone, p2.Sj, s);
   bool act[4];
   bool qact = false;
 #pragma unroll
@@ -944,8 +995,10 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
         if (!FIRST) acc2 = f4fma(a[u], St::cvt(g2[u]), acc2);
       }
       const float4 o1 = St::cvt(g1[0]), o2 = FIRST ? z4 : St::cvt(g2[0]);
+      float vo[4];
       finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout,
-                           (size_t)(r * m0 + q4), vv, vw, ww);
+                           (size_t)(r * m0 + q4), vv, vw, ww, vo);
+      if (p2.Qacc != nullptr) accumulate_q(p2, m0, s, (size_t)(r * m0 + q4), q4, vo, act, all4);
     }
   }
   store_partials_f(vv, vw, ww, m0, stride_items, part);
@@ -1132,6 +1185,15 @@ k_lz_quadrature4(int n, int m0, int K, const ST *__restrict__ V, const double *_
   Q[e + 3] = cx[j0 + 3] * X[e + 3] + (double)aw;
 }
 
+// Q = cx X + Qacc (second pass of the two-pass mode; the quadrature's last step)
+__global__ void k_lz_combine(int n, int m0, const float *__restrict__ Qacc,
+                             const double *__restrict__ cx, const double *__restrict__ X,
+                             double *__restrict__ Q) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * m0) return;
+  Q[e] = cx[e % m0] * X[e] + (double)Qacc[e];
+}
+
 __global__ void k_to_float(size_t n, const double *__restrict__ a, float *__restrict__ b) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -1201,7 +1263,8 @@ void vec_grid(const MinresArgs &a, int &blocks, int &stride_items) {
 
 template <typename T>
 cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo,
-                                const ValOf<T> *val, int *active_reset, cudaStream_t st) {
+                                const ValOf<T> *val, int *active_reset, const Pass2 &p2,
+                                cudaStream_t st) {
   if constexpr (sizeof(T) <= 4) {
     // pair done flags of the previous Givens step (double-buffered by parity)
     const int *done_r = a.ms.done + (size_t)(s & 1) * a.nc * a.m0;
@@ -1212,7 +1275,7 @@ cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T
 #define IFEAST_ELL_LAUNCH(F, WW)                                                              \
   launch_pdl(k_lanczos_step_ell<T, F, WW>, dim3(blocks), dim3(kVThreads), st, a.n, a.m0, s,     \
              a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc, part, stride_items,     \
-             a.wscale, active_reset)
+             a.wscale, active_reset, p2)
       if (a.ell_w == 8)
         return s == 0 ? IFEAST_ELL_LAUNCH(true, 8) : IFEAST_ELL_LAUNCH(false, 8);
       return s == 0 ? IFEAST_ELL_LAUNCH(true, 16) : IFEAST_ELL_LAUNCH(false, 16);
@@ -1224,10 +1287,10 @@ cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T
       if (s == 0)
         return launch_pdl(k_lanczos_step_vec<T, true>, dim3(blocks), dim3(kVThreads), st, a.n,
                           a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, done_r,
-                          a.nc, part, stride_items, a.wscale, active_reset);
+                          a.nc, part, stride_items, a.wscale, active_reset, p2);
       return launch_pdl(k_lanczos_step_vec<T, false>, dim3(blocks), dim3(kVThreads), st, a.n, a.m0,
                         s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc,
-                        part, stride_items, a.wscale, active_reset);
+                        part, stride_items, a.wscale, active_reset, p2);
     }
   }
   if constexpr (std::is_same_v<T, __half>) {
@@ -1270,6 +1333,8 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
     int stride_items;
     vec_grid(a, step_blocks, stride_items);
   }
+  // first pass: stored basis, or (two-pass mode) a ring of three basis slots
+  const Pass2 pass1 = {nullptr, nullptr, nullptr, a.two_pass ? 3 : 0};
   cudaError_t e = cudaGetLastError();
   int s = 0;
   for (; s < a.K && e == cudaSuccess; ++s) {
@@ -1278,7 +1343,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
     // on a checked step the FP32 step kernels clear *active themselves (no
     // memset between the step and Givens kernels breaks their launch overlap)
     e = launch_lanczos_step<T>(a, s, V, W[(s + 1) & 1], W[s & 1], val,
-                               (check && f32_partials) ? a.ms.active : nullptr, st);
+                               (check && f32_partials) ? a.ms.active : nullptr, pass1, st);
     IFEAST_PROF_END(a.prof);
     if (check && !f32_partials && e == cudaSuccess)
       e = cudaMemsetAsync(a.ms.active, 0, sizeof(int), st);
@@ -1311,6 +1376,34 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   k_lz_coef<<<(unsigned)((kc + 255) / 256), 256, 0, st>>>(a.m0, a.nc, a.K, a.ms, a.Yc, a.coef,
                                                            a.cx, a.Sj);
   IFEAST_PROF_END(a.prof);
+  if constexpr (sizeof(T) <= 4) {
+    if (a.two_pass) {
+      // second pass: rebuild v_0 .. v_{S-1} from the stored alpha, beta (same
+      // arithmetic as the first pass) and accumulate Q; the solves' steps bound
+      // the pass (max over the (node, column) pairs)
+      e = cudaMemcpyAsync(a.active_host, &a.ms.status->max_steps, sizeof(int),
+                          cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return e;
+      const int S = *a.active_host;
+      if (cudaMemsetAsync(a.Qf, 0, nm * sizeof(float), st) != cudaSuccess) return cudaGetLastError();
+      IFEAST_PROF_BEGIN(a.prof, K_PREP);
+      k_lz_v0<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.rhs, a.rnorm, V);
+      IFEAST_PROF_END(a.prof);
+      const Pass2 pass2 = {a.Qf, reinterpret_cast<const float *>(a.coef + (size_t)a.K * a.m0),
+                           a.Sj, 3};
+      for (int s2 = 0; s2 < S && e == cudaSuccess; ++s2) {
+        IFEAST_PROF_BEGIN(a.prof, K_LZ_STEP);
+        e = launch_lanczos_step<T>(a, s2, V, W[(s2 + 1) & 1], W[s2 & 1], val, nullptr, pass2, st);
+        IFEAST_PROF_END(a.prof);
+      }
+      if (e != cudaSuccess) return e;
+      IFEAST_PROF_BEGIN(a.prof, K_LZ_QUAD);
+      k_lz_combine<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.Qf, a.cx, a.X, a.Q);
+      IFEAST_PROF_END(a.prof);
+      return cudaGetLastError();
+    }
+  }
   IFEAST_PROF_BEGIN(a.prof, K_LZ_QUAD);
   if constexpr (sizeof(T) <= 4) {
     if (a.m0 % 4 == 0)

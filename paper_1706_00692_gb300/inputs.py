@@ -249,6 +249,7 @@ class Workload:
     expected_count: int | None = None
     inner: str = "gmres"
     precision: str = "fp64"
+    two_pass: bool = False  # shared-basis solver without the stored basis
     # Krylov steps over all (node, column) pairs of one full solve, as measured
     # on the GPU path; scales timed samples of the CPU oracle to a full solve
     krylov_steps_full_solve: int | None = None
@@ -294,7 +295,7 @@ LAP3D_64_WINDOW = (0.89754658, 0.91001238)
 
 
 def workload_lap3d_64_interior(seed: int = 0, precision: str = "fp32", alpha: float = 3e-2,
-                               inner_iters: int = 1500) -> Workload:
+                               inner_iters: int = 1500, two_pass: bool = False) -> Workload:
     """3D 7-point Laplacian on 64^3 (n = 262,144) plus a U[0,1) diagonal
     potential, interior window with 56 eigenvalues, m0 = 80, 8 trapezoid nodes
     on the upper half circle, shared-basis MINRES inner solves (at most 1500
@@ -307,6 +308,9 @@ def workload_lap3d_64_interior(seed: int = 0, precision: str = "fp32", alpha: fl
                   expected_count=56 if seed == 0 else None, krylov_steps_full_solve=5_377_530)
     wl.inner = "minres"
     wl.precision = precision
+    wl.two_pass = two_pass
+    if two_pass:
+        wl.name += "_twopass"
     return wl
 
 

@@ -135,6 +135,14 @@ def test_create_rejects_bad_options(lib):
     big = inputs.laplacian((10, 10))
     assert _create(lib, big, m0=65, opts=_opts(lib, nonsymmetric=1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
     assert _create(lib, A, opts=_opts(lib, nonsymmetric=2))[0] == _lib.IFEAST_ERR_INVALID_ARG
+    # the two-pass mode: shared-basis solver with FP32 or FP16 vectors, m0 % 4 == 0
+    assert _create(lib, A, opts=_opts(lib, minres_two_pass=1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, opts=_opts(lib, minres_two_pass=1, inner_solver=1, inner_max_iters=8))[0] \
+        == _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, m0=6, opts=_opts(lib, minres_two_pass=1, inner_solver=1,
+                                            inner_max_iters=8, precision=1))[0] == \
+        _lib.IFEAST_ERR_UNSUPPORTED
+    assert _create(lib, A, opts=_opts(lib, minres_two_pass=2))[0] == _lib.IFEAST_ERR_INVALID_ARG
 
 
 def _csr_ref(M, keep):
@@ -182,3 +190,15 @@ def test_product_path_has_no_oracle_import():
                 text = open(os.path.join(dp, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", text, re.M), os.path.join(dp, f)
                 assert "ifeast_oracle" not in text, os.path.join(dp, f)
+
+
+def test_two_pass_workspace_drops_the_basis(lib):
+    c = _lib.Contour(1, 8, 0.0, 1.0)
+    n, nnz, m0, K = 100000, 700000, 80, 1000
+    b1, b2 = ct.c_size_t(), ct.c_size_t()
+    o1 = _opts(lib, inner_solver=1, inner_max_iters=K, precision=1)
+    o2 = _opts(lib, inner_solver=1, inner_max_iters=K, precision=1, minres_two_pass=1)
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c), ct.byref(o1), ct.byref(b1)) == 0
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c), ct.byref(o2), ct.byref(b2)) == 0
+    # K + 1 FP32 basis vectors become three slots plus one FP32 accumulator
+    assert b1.value - b2.value >= (K + 1 - 4) * n * m0 * 4

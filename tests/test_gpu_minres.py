@@ -210,3 +210,50 @@ def test_filter_fp16_storage_matches_oracle(torch, k):
     assert err <= FP16_TOL, err
     assert (steps.cpu().numpy() == k).all()
     S.close()
+
+
+@pytest.mark.parametrize("case,precision,m0,alpha", [
+    ("lap2d", "fp32", 20, 0.0),       # fixed-width rows, fixed step count
+    ("ragged", "fp32", 12, 0.5),      # tolerance mode: columns stop at different steps
+    ("arrow", "fp32", 8, 0.0),        # CSR kernel (rows longer than 16)
+    ("ragged", "fp16", 8, 0.5),       # FP16 storage
+])
+def test_two_pass_filter_is_bit_identical(torch, case, precision, m0, alpha):
+    if case == "lap2d":
+        A = inputs.workload_lap2d_50().A
+        emin, emax = 0.0, 0.07
+    elif case == "ragged":
+        A = inputs.add_diagonal(inputs.laplacian((13, 11, 7)), inputs.random_potential(1001, 5))
+        emin, emax = 0.9, 1.4
+    else:
+        A = _arrow_matrix(517, 3)
+        emin, emax = 0.5, 1.5
+    X = torch.as_tensor(inputs.initial_subspace(A.n, m0, 31), device="cuda")
+    out = []
+    for two_pass in (False, True):
+        S = _solver(A, emin, emax, m0, nc=5, inner_iters=60, alpha=alpha, precision=precision,
+                    two_pass=two_pass)
+        Q, steps = S.apply_filter(X, RF=0.2)
+        out.append((Q.cpu().numpy(), steps.cpu().numpy()))
+        S.close()
+    assert np.array_equal(out[0][1], out[1][1])
+    if alpha > 0:
+        assert out[0][1].min() < out[0][1].max()  # the columns stopped at different steps
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_two_pass_solve_is_bit_identical(torch):
+    A, ev, emin, emax, i0, cnt = _interior_problem()
+    m0 = 48
+    res = []
+    for two_pass in (False, True):
+        S = _solver(A, emin, emax, m0, nc=8, inner_iters=400, alpha=1e-3, precision="fp32",
+                    max_outer=30, two_pass=two_pass)
+        assert S.solve(inputs.initial_subspace(A.n, m0, 1)) == 0
+        lam, X, r = S.eigenpairs()
+        res.append((lam, X, S.stats()["outer_iters"]))
+        S.close()
+    assert res[0][2] == res[1][2]
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    assert np.abs(res[1][0] - ev[i0:i0 + cnt]).max() / np.abs(ev).max() <= 1e-10
