@@ -49,6 +49,7 @@ def parse():
                                                                  "serve"])
     p.add_argument("--requests", type=int, default=64, help="serving stream length")
     p.add_argument("--rate", type=float, default=8.0, help="serving arrivals per second")
+    p.add_argument("--n-max", type=float, default=1e6, help="largest serving request size")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -371,17 +372,22 @@ def run_ours(args):
 
 def run_serve(args):
     """Serving stream: Poisson arrivals of eigen-requests (2D/3D Laplacians with a
-    potential, n log-uniform 1e3..2e5, m0 16..128), submitted at their arrival
-    times to one server (memory budget 160 GB, 8 running at once). Reports
-    converged eigenpairs/s over the makespan and p50/p99 request latency, and
-    the same stream served one request at a time for comparison."""
+    potential, n log-uniform 1e3..n_max, m0 16..128), submitted at their arrival
+    times to one server (memory budget 160 GB, 8 running at once). A request
+    whose stored Lanczos basis would exceed 8 GB runs in the two-pass mode
+    (three basis vectors). Reports converged eigenpairs/s over the makespan and
+    p50/p99 request latency, and the same stream served one request at a time
+    for comparison."""
     import torch
     from paper_1706_00692_gb300 import Server, inputs
     from paper_1706_00692_gb300.build import build
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     build()
-    reqs = inputs.serving_requests(args.requests, seed=1234, rate=args.rate)
+    reqs = inputs.serving_requests(args.requests, seed=1234, rate=args.rate, n_max=args.n_max)
+    K = 300
+    # FP32 basis of K + 1 vectors over 8 GB: keep three vectors and rebuild in a second pass
+    two_pass = [(K + 1) * r.A.n * r.m0 * 4 > (8 << 30) for r in reqs]
     warm = inputs.serving_requests(3, seed=999, n_max=2e4)
 
     def serve(max_active, timed_arrivals):
@@ -390,12 +396,13 @@ def run_serve(args):
             srv.wait(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half"))
         ids = []
         t0 = time.perf_counter()
-        for r in reqs:
+        for r, tp in zip(reqs, two_pass):
             if timed_arrivals:
                 dt = r.arrival - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
-            ids.append(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half"))
+            ids.append(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half",
+                                  inner_iters=K, two_pass=tp))
         outs = [srv.wait(i) for i in ids]
         span = time.perf_counter() - t0
         srv.close()
@@ -416,9 +423,12 @@ def run_serve(args):
                 "steps": 1, "warmup": len(warm), "ms_per_step": span * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"serve_{args.requests}_poisson_rate{args.rate:g}_n1e3-2e5_m0_16-128",
+                "config": {"workload": f"serve_{args.requests}_poisson_rate{args.rate:g}"
+                                       f"_n1e3-{args.n_max:.0e}_m0_16-128",
                            "max_active": 8, "budget_gb": 160, "inner": "minres",
-                           "inner_precision": "fp32", "contour": "trap_half"},
+                           "inner_precision": "fp32", "contour": "trap_half",
+                           "two_pass_requests": int(sum(two_pass)),
+                           "n_max_seen": int(max(r.A.n for r in reqs))},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                "p99": float(np.percentile(lat, 99))},
                 "failed": failed, "pairs": pairs, "requests": len(reqs),

@@ -270,7 +270,7 @@ class Server:
     def submit(self, A: CSR, emin: float, emax: float, m0: int, X0: np.ndarray, *, nc: int = 8,
                rule: str = "gl_half", inner: str = "minres", inner_iters: int = 300,
                alpha: float = 3e-2, max_outer: int = 100, tol: float = 1e-10,
-               precision: str = "fp32") -> int:
+               precision: str = "fp32", two_pass: bool = False) -> int:
         c = _lib.Contour(_lib.RULES[rule], nc, emin, emax)
         o = _lib.Opts()
         self.lib.ifeast_default_opts(ct.byref(o))
@@ -280,6 +280,7 @@ class Server:
         o.max_outer = max_outer
         o.tol = tol
         o.precision = _lib.PRECISIONS[precision]
+        o.minres_two_pass = 1 if two_pass else 0
         rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
         ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
         va = np.ascontiguousarray(A.val, dtype=np.float64)
