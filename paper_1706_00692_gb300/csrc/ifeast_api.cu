@@ -60,7 +60,8 @@ struct ifeast_ctx {
   double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
   double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
-  int *active_host = nullptr;  // pinned
+  int *active_host = nullptr;  // pinned, kCheckLag + 1 slots
+  cudaEvent_t check_events[kCheckLag + 1] = {};
   int ell_w = 0;
   int32_t *colE = nullptr;
   float *valE = nullptr;
@@ -458,6 +459,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.tl = h->tl;
   a.check_every = 16;
   a.active_host = h->active_host;
+  a.check_events = h->check_events;
   a.P_async = 2 * h->num_sms;  // two resident blocks per SM
   a.two_pass = h->two_pass ? 1 : 0;
   a.Qf = h->Qf;
@@ -649,12 +651,19 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->ws_bytes = off.total;
   }
   if (cudaMallocHost(&h->status_host, sizeof(DevStatus)) != cudaSuccess ||
-      cudaMallocHost(&h->active_host, sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&h->active_host, (kCheckLag + 1) * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->owns_ws) cudaFree(h->ws);
     delete h;
     return IFEAST_ERR_OOM;
+  }
+  for (cudaEvent_t &ev : h->check_events) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      ifeast_destroy(h);
+      return IFEAST_ERR_CUDA;
+    }
   }
   char *b = h->ws;
   h->rowptr = (int32_t *)(b + off.rowptr);
@@ -795,6 +804,8 @@ void ifeast_destroy(ifeast_t h) {
   if (h->owns_ws && h->ws) cudaFree(h->ws);
   if (h->status_host) cudaFreeHost(h->status_host);
   if (h->active_host) cudaFreeHost(h->active_host);
+  for (cudaEvent_t ev : h->check_events)
+    if (ev) cudaEventDestroy(ev);
   if (h->prof.events) {
     for (int i = 0; i < 2 * h->prof.cap; ++i) cudaEventDestroy(h->prof.events[i]);
     delete[] h->prof.events;

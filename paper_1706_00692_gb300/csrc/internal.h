@@ -52,6 +52,7 @@ struct Profiler {
   void begin(int k);
   void end();
   int collect();                  // after a stream synchronisation
+  int collect_ready();            // the leading pairs that have completed
 };
 #define IFEAST_PROF_BEGIN(p, k) \
   do {                          \
@@ -143,6 +144,10 @@ struct Pass2 {
   int vring;                // 0: basis slot s; 3: slot s % 3 (two-pass mode)
 };
 
+// Early exit of the Lanczos loop: the flag of checkpoint c is read after
+// checkpoint c + kCheckLag has been enqueued, so the stream never drains.
+constexpr int kCheckLag = 2;
+
 struct MinresArgs {
   int n, m0, nc, K;
   int fp32;                 // FP32 arithmetic in the Krylov kernels
@@ -163,7 +168,8 @@ struct MinresArgs {
   RowTiling tl;
   MinresState ms;
   int check_every;          // steps between early-exit checks (0: never)
-  int *active_host;         // pinned
+  int *active_host;         // pinned, kCheckLag + 1 slots
+  cudaEvent_t *check_events;  // kCheckLag + 1 events
   Profiler *prof;
   int P_async;              // max blocks of the FP32 (row, quad) step kernel
   int ell_w;                // 8 or 16: fixed-width copy of A available (FP32), else 0

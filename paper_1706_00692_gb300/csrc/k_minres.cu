@@ -1336,7 +1336,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   // first pass: stored basis, or (two-pass mode) a ring of three basis slots
   const Pass2 pass1 = {nullptr, nullptr, nullptr, a.two_pass ? 3 : 0};
   cudaError_t e = cudaGetLastError();
-  int s = 0;
+  int s = 0, ck = 0;  // ck: checkpoints enqueued
   for (; s < a.K && e == cudaSuccess; ++s) {
     const bool check = a.check_every > 0 && (s + 1) % a.check_every == 0 && s + 1 < a.K;
     IFEAST_PROF_BEGIN(a.prof, K_LZ_STEP);
@@ -1360,11 +1360,21 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
     IFEAST_PROF_END(a.prof);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (check && e == cudaSuccess) {
-      // stop early once no column is still running (one small read-back)
-      e = cudaMemcpyAsync(a.active_host, a.ms.active, sizeof(int), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e == cudaSuccess && a.prof && a.prof->collect()) e = cudaErrorUnknown;
-      if (e == cudaSuccess && *a.active_host == 0) break;
+      // stop early once no column is still running: this checkpoint's flag is
+      // copied and marked by an event; the host waits on the checkpoint
+      // kCheckLag earlier, so kCheckLag * check_every steps stay queued (steps
+      // after every column is done do no work and change no state)
+      const int slot = ck % (kCheckLag + 1);
+      e = cudaMemcpyAsync(a.active_host + slot, a.ms.active, sizeof(int), cudaMemcpyDeviceToHost,
+                          st);
+      if (e == cudaSuccess) e = cudaEventRecord(a.check_events[slot], st);
+      ++ck;
+      if (e == cudaSuccess && ck > kCheckLag) {
+        const int old = (ck - 1 - kCheckLag) % (kCheckLag + 1);
+        e = cudaEventSynchronize(a.check_events[old]);
+        if (e == cudaSuccess && a.prof && a.prof->collect_ready()) e = cudaErrorUnknown;
+        if (e == cudaSuccess && a.active_host[old] == 0) break;
+      }
     }
   }
   if (e != cudaSuccess) return e;

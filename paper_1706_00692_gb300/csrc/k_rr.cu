@@ -1242,6 +1242,26 @@ void Profiler::end() {
   ++used;
 }
 
+int Profiler::collect_ready() {
+  int done = 0;
+  while (done < used && cudaEventQuery(events[2 * done + 1]) == cudaSuccess) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, events[2 * done], events[2 * done + 1]) != cudaSuccess) return 1;
+    ms[kid[done]] += t;
+    count[kid[done]] += 1;
+    ++done;
+  }
+  cudaGetLastError();  // a not-ready query is not an error
+  // move the pending pairs to the front (event handles are swapped, not copied)
+  for (int i = done; i < used; ++i) {
+    std::swap(events[2 * (i - done)], events[2 * i]);
+    std::swap(events[2 * (i - done) + 1], events[2 * i + 1]);
+    kid[i - done] = kid[i];
+  }
+  used -= done;
+  return 0;
+}
+
 int Profiler::collect() {
   for (int i = 0; i < used; ++i) {
     float t = 0.f;
