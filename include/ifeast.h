@@ -129,6 +129,14 @@ typedef struct {
                            the quadrature on the fly, so Q is bit-identical to
                            the stored-basis mode. Workspace O(n m0) instead of
                            O(inner_max_iters n m0); about twice the inner time. */
+  double correction_rf; /* IFEAST_INNER_GMRES with IFEAST_FP32 only: once ||R_F|| of
+                           the previous iteration is <= correction_rf, the shifted
+                           systems are solved for the correction of the current
+                           Ritz pairs, (z B - A) e = A x_j - lambda_j B x_j, and
+                           y = (x_j + e) / (z - lambda_j) (an identity of the
+                           shifted systems; it lets FP32 inner solves reach FP64
+                           eigenpair residuals). Default 1e-3; 1 or more: from
+                           the second iteration on.                            */
 } ifeast_opts;
 
 typedef struct {
@@ -198,7 +206,9 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device);
  * may be NULL. *m_found gets the number inside (may exceed cap; then only the
  * first cap are copied). out_on_device != 0: outputs are device pointers. */
 /* Non-symmetric handles (opts.nonsymmetric = 1): the Ritz pairs inside the
- * circle |lambda - c| < r, ordered by real then imaginary part. evals: 2*cap
+ * circle |lambda - c| < r, ordered by real part, the two values of a complex
+ * conjugate pair adjacent with the negative imaginary part first (the pair
+ * shares one real-part key, the mean of its two computed real parts). evals: 2*cap
  * doubles (re, im); evecs: n x cap complex (re, im interleaved, row-major,
  * unit 2-norm); resid: cap relative residuals ||A x - lambda x|| / ||A x||.
  * Host or device outputs as ifeast_eigenpairs; any may be NULL.

@@ -17,6 +17,9 @@ Map to the paper:
                                         stopping rule ||x-(zI-A)y|| <= alpha*||R_F||)
   gmres .............................. GMRES of Section 2.2 (zero initial guess,
                                         modified Gram-Schmidt Arnoldi, Givens)
+  _filtered_subspace_gmres_correction  Alg. 2 step 1 solved for the correction of
+                                        the current Ritz pairs (an identity of the
+                                        shifted systems; reading in its docstring)
   gmres_shared_basis ................. Section 3, Eqs. (yz)-(contint_krylov):
                                         the Krylov basis does not depend on z
   rayleigh_ritz ...................... Algorithm 1/2 step 3 (B_Q = Q^T B Q for A x = lam B x)
@@ -284,6 +287,33 @@ def _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats, B=None):
     return Q.real if half else Q
 
 
+def _filtered_subspace_gmres_correction(A, X, lam, z, w, half, k, tol_rel, stats, B=None):
+    """The same filter from the current Ritz pairs (lam_j, x_j): with the residual
+    r_j = A x_j - lam_j B x_j the shifted solution is exactly
+    (z_k B - A)^{-1} B x_j = (x_j + e_kj) / (z_k - lam_j), (z_k B - A) e_kj = r_j,
+    so GMRES (zero initial guess) runs on the correction systems only. The stop
+    bound is the one of Alg. 2 on the original system, whose residual is the
+    correction's divided by |z_k - lam_j|: |g_{s+1}| <= tol_rel ||B x_j|| |z_k - lam_j|."""
+    n, m0 = X.shape
+    BX = X if B is None else B @ X
+    Rres = A @ X - BX * lam[None, :]
+    Q = np.zeros(X.shape, np.complex128)
+    for zk, wk in zip(z, w):
+        if B is None:
+            op = lambda v, zk=zk: shifted_apply(A, zk, v)
+        else:
+            op = lambda v, zk=zk: zk * (B @ v) - A @ v
+        for j in range(m0):
+            rn = np.linalg.norm(Rres[:, j])
+            tol_j = 0.0
+            if tol_rel > 0.0 and rn > 0.0:
+                tol_j = tol_rel * np.linalg.norm(BX[:, j]) * abs(zk - lam[j]) / rn
+            out = gmres(op, Rres[:, j], k, tol_j)
+            stats["inner_steps"].append(out["steps"])
+            Q[:, j] += wk * (X[:, j] + out["y"]) / (zk - lam[j])
+    return Q.real if half else Q
+
+
 def _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats):
     n, m0 = X.shape
     Q = np.zeros(X.shape, np.complex128)
@@ -296,7 +326,7 @@ def _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats):
 
 
 def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0,
-           tol=1e-10, max_outer=100, callback=None, B=None):
+           tol=1e-10, max_outer=100, callback=None, B=None, correction_rf=None):
     """Algorithm 2 (and, with inner="exact", Algorithm 1) for a real symmetric
     problem A x = lambda x, or A x = lambda B x with B symmetric positive
     definite (the generalized systems (z_k B - A) Y_k = B X of Section 2.2).
@@ -308,6 +338,10 @@ def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0
     ||x_j - (z_k I - A) y|| <= alpha * ||R_F|| * ||x_j|| (Alg. 2 step 1 with the
     residual measured relative to the right-hand side, ||R_F|| = 1 at the
     start); alpha <= 0: run exactly k steps.
+    correction_rf: None, or a bound: from the second iteration on, once the
+    previous ||R_F|| <= correction_rf, inner="gmres" solves for the correction
+    of the Ritz pairs of the previous iteration
+    (_filtered_subspace_gmres_correction; the same filter in exact arithmetic).
     ||R_F|| is the largest relative residual ||A x_j - lam_j x_j||/||A x_j||
     over Ritz values strictly inside (emin, emax).
 
@@ -332,6 +366,8 @@ def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0
                 if B is not None:
                     B_dense = B.toarray() if sp.issparse(B) else np.asarray(B)
             Q = _filtered_subspace_exact(A_dense, X, z, w, half, B_dense)
+        elif inner == "gmres" and correction_rf is not None and it > 1 and RF <= correction_rf:
+            Q = _filtered_subspace_gmres_correction(A, X, lam, z, w, half, k, tol_rel, stats, B)
         elif inner == "gmres":
             Q = _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats, B)
         elif inner == "shared":

@@ -40,10 +40,17 @@ struct ifeast_ctx {
   double2 *theta = nullptr, *Uc = nullptr;
   int *ridx = nullptr;
   double2 *z = nullptr, *w = nullptr;
-  double2 *V = nullptr, *W = nullptr, *part = nullptr, *H1 = nullptr, *H2 = nullptr;
+  void *V = nullptr, *W = nullptr;  // double2, or float2 for the FP32 basis
+  double2 *part = nullptr, *H1 = nullptr, *H2 = nullptr;
   double *inv_h = nullptr;
   double2 *CS = nullptr, *SN = nullptr, *R = nullptr, *G = nullptr, *Y = nullptr;
   int *steps = nullptr, *done = nullptr;
+  // per-node GMRES with the FP32 basis: FP32 values, FP32 weights, the
+  // per-system bounds and the residual form's filter values
+  float *valB32 = nullptr;
+  bool b_same_pattern = false;  // B stored on A's pattern
+  float2 *Yf = nullptr;
+  double *tolc = nullptr, *gcx = nullptr;
   double *X = nullptr, *Q = nullptr, *AQ = nullptr, *beta = nullptr;
   double *gram_part = nullptr, *Aq = nullptr, *Bq = nullptr, *L = nullptr, *Cm = nullptr,
          *U = nullptr, *XQ = nullptr, *lam = nullptr, *res_part = nullptr, *res = nullptr;
@@ -93,6 +100,7 @@ struct Offsets {
   size_t rowptrB, colidxB, valB, BQ, BX;
   size_t LinvT, theta, Uc, ridx;
   size_t Qf;
+  size_t valB32, tolc, Yf, gcx;
 };
 
 int device_sms() {
@@ -114,9 +122,21 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
   o.val = L.take<double>(nnz > 0 ? nnz : 1);
   o.z = L.take<double2>(nc);
   o.w = L.take<double2>(nc);
-  if (!minres) {  // per-node complex GMRES
-    o.V = L.take<double2>((size_t)(K + 1) * n * C);
-    o.W = L.take<double2>((size_t)n * C);
+  if (!minres) {  // per-node complex GMRES, FP64 or FP32 basis
+    const bool fp32 = prec == IFEAST_FP32;
+    const size_t es = fp32 ? sizeof(float2) : sizeof(double2);
+    if (fp32) {
+      o.val32 = L.take<float>(nnz > 0 ? nnz : 1);
+      if (nnzB >= 0) o.valB32 = L.take<float>(nnzB > 0 ? nnzB : 1);
+      o.Yf = L.take<float2>((size_t)K * C);
+      // residual form: right-hand sides A X - B X Lambda, their norms, filter values
+      o.Rres = L.take<double>((size_t)n * m0);
+      o.rnorm = L.take<double>(m0);
+      o.gcx = L.take<double>(m0);
+    }
+    o.tolc = L.take<double>(C);
+    o.V = L.take<char>((size_t)(K + 1) * n * C * es);
+    o.W = L.take<char>((size_t)n * C * es);
     o.part = L.take<double2>((size_t)tl.P * (K + 2) * C);
     o.H1 = L.take<double2>((size_t)(K + 2) * C);
     o.H2 = L.take<double2>((size_t)(K + 2) * C);
@@ -220,7 +240,9 @@ ifeast_contour effective_contour(const ifeast_contour &c) {
 int validate_opts(const ifeast_opts *o) {
   if (!o) return IFEAST_ERR_INVALID_ARG;
   if (o->inner_solver == IFEAST_INNER_GMRES) {
-    if (o->precision != IFEAST_FP64) return IFEAST_ERR_UNSUPPORTED;
+    if (o->precision != IFEAST_FP64 && o->precision != IFEAST_FP32) return IFEAST_ERR_UNSUPPORTED;
+    // the FP32 basis needs the residual form, which needs real Ritz pairs
+    if (o->precision == IFEAST_FP32 && o->nonsymmetric == 1) return IFEAST_ERR_UNSUPPORTED;
     if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxInner) return IFEAST_ERR_INVALID_ARG;
   } else if (o->inner_solver == IFEAST_INNER_MINRES) {
     if (o->precision != IFEAST_FP64 && o->precision != IFEAST_FP32 && o->precision != IFEAST_FP16)
@@ -231,6 +253,7 @@ int validate_opts(const ifeast_opts *o) {
   }
   if (o->max_outer < 1 || !(o->tol >= 0.0) || !std::isfinite(o->alpha))
     return IFEAST_ERR_INVALID_ARG;
+  if (!(o->correction_rf >= 0.0)) return IFEAST_ERR_INVALID_ARG;
   if (o->nonsymmetric != 0 && o->nonsymmetric != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->nonsymmetric && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (o->minres_two_pass != 0 && o->minres_two_pass != 1) return IFEAST_ERR_INVALID_ARG;
@@ -324,8 +347,24 @@ int ensure_device_init() {
     }                                             \
   } while (0)
 
-GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q) {
+// Per-node GMRES. correction = 0: right-hand sides X (or B X), norms in
+// h->beta; correction = 1: right-hand sides h->Rres = A X - B X Lambda of the
+// current Ritz pairs (norms h->rnorm, Ritz values h->lam, ||B x_j|| in h->beta).
+GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q, int correction = 0) {
   GmresArgs a{};
+  a.fp32 = h->fp32 ? 1 : 0;
+  a.val32 = h->val32;
+  a.valB32 = h->valB32;
+  a.b_same_pattern = h->b_same_pattern ? 1 : 0;
+  a.Yf = h->Yf;
+  a.tolc = h->tolc;
+  a.correction = correction;
+  if (correction) {
+    a.lam = h->lam;
+    a.xnorm = h->beta;
+    a.Xr = h->X;
+    a.cx = h->gcx;
+  }
   a.n = (int)h->n;
   a.m0 = h->m0;
   a.nc = h->nc;
@@ -348,7 +387,7 @@ GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q) {
   a.R = h->R;
   a.G = h->G;
   a.Y = h->Y;
-  a.beta = h->beta;
+  a.beta = correction ? h->rnorm : h->beta;
   a.steps = h->steps;
   a.done = h->done;
   a.Q = Q;
@@ -388,8 +427,8 @@ RRArgs rr_args(ifeast_ctx *h, const double *Q, double *X) {
   a.emax = h->contour.emax;
   a.alpha = h->opts.alpha;
   a.status = h->status;
-  a.Rres = h->minres ? h->Rres : nullptr;
-  a.rnorm = h->minres ? h->rnorm : nullptr;
+  a.Rres = h->Rres;  // null unless an inner solver takes the residual form
+  a.rnorm = h->rnorm;
   a.prof = h->profiling ? &h->prof : nullptr;
   a.rowptrB = h->rowptrB;
   a.colidxB = h->colidxB;
@@ -517,6 +556,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->verbose = 0;
   o->nonsymmetric = 0;
   o->minres_two_pass = 0;
+  o->correction_rf = 1e-3;
 }
 
 const char *ifeast_strerror(int code) {
@@ -671,8 +711,8 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->val = (double *)(b + off.val);
   h->z = (double2 *)(b + off.z);
   h->w = (double2 *)(b + off.w);
-  h->V = (double2 *)(b + off.V);
-  h->W = (double2 *)(b + off.W);
+  h->V = b + off.V;
+  h->W = b + off.W;
   h->part = (double2 *)(b + off.part);
   h->H1 = (double2 *)(b + off.H1);
   h->H2 = (double2 *)(b + off.H2);
@@ -684,6 +724,17 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->Y = (double2 *)(b + off.Y);
   h->steps = (int *)(b + off.steps);
   h->done = (int *)(b + off.done);
+  if (!h->minres) {
+    h->tolc = (double *)(b + off.tolc);
+    if (h->fp32) {
+      h->val32 = (float *)(b + off.val32);
+      if (B) h->valB32 = (float *)(b + off.valB32);
+      h->Yf = (float2 *)(b + off.Yf);
+      h->Rres = (double *)(b + off.Rres);
+      h->rnorm = (double *)(b + off.rnorm);
+      h->gcx = (double *)(b + off.gcx);
+    }
+  }
   h->X = (double *)(b + off.X);
   h->Q = (double *)(b + off.Q);
   h->AQ = (double *)(b + off.AQ);
@@ -707,6 +758,10 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   }
   if (B) {
     h->nnzB = nnzB;
+    h->b_same_pattern =
+        nnzB == nnz &&
+        std::equal(A->rowptr, A->rowptr + n + 1, B->rowptr) &&
+        (nnz == 0 || std::equal(A->colidx, A->colidx + nnz, B->colidx));
     h->rowptrB = (int32_t *)(b + off.rowptrB);
     h->colidxB = (int32_t *)(b + off.colidxB);
     h->valB = (double *)(b + off.valB);
@@ -764,6 +819,8 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   ok = ok && cudaMemcpyAsync(h->w, h->wh.data(), h->nc * sizeof(double2), cudaMemcpyHostToDevice,
                              h->stream) == cudaSuccess;
   if (h->fp32 && nnz > 0) ok = ok && convert_to_float(h->val, h->val32, nnz, h->stream) == cudaSuccess;
+  if (h->valB32 && nnzB > 0)
+    ok = ok && convert_to_float(h->valB, h->valB32, nnzB, h->stream) == cudaSuccess;
   if (h->fp32 && h->minres && m0 % 4 == 0) {
     // FP16 storage keeps w_s / ||A||_inf (|w_s| <= ||A||_inf ||v_s||_inf + |beta_s| ...)
     if (h->half) {
@@ -833,6 +890,8 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
     if (rc) return rc;
     if (h->minres)
       CK(minres_filter(minres_args(h, h->X, h->Q, it > 1 ? 1 : 0), h->stream));
+    else if (h->fp32 && it > 1 && h->stats.RF <= h->opts.correction_rf)  // FP32: residual form
+      CK(gmres_filter(gmres_args(h, h->Rres, h->Q, 1), h->stream));
     else  // right-hand sides X, or B X (norms in beta) from the previous Rayleigh-Ritz
       CK(gmres_filter(gmres_args(h, h->rowptrB ? h->BX : h->X, h->Q), h->stream));
     if (h->nonsym)
@@ -910,8 +969,27 @@ int ifeast_eigenpairs_complex(ifeast_t h, int cap, int *m_found, double *evals, 
   std::vector<int> idx;
   for (int j = 0; j < m0; ++j)
     if (std::hypot(th[j].x - cc, th[j].y) < rr) idx.push_back(j);
+  // Order: ascending real part, a conjugate pair adjacent with the negative
+  // imaginary part first. The reduced eigensolver works in complex arithmetic,
+  // so the two values of a pair agree only to rounding: both get the mean of
+  // their real parts as the sort key.
+  std::vector<double> key(m0);
+  for (int j = 0; j < m0; ++j) key[j] = th[j].x;
+  for (int j = 0; j < m0; ++j) {
+    if (th[j].y <= 0.0) continue;
+    int best = -1;
+    double bd = 0.0;
+    for (int k = 0; k < m0; ++k) {
+      if (th[k].y >= 0.0) continue;
+      const double d = std::hypot(th[k].x - th[j].x, th[k].y + th[j].y);
+      if (best < 0 || d < bd) best = k, bd = d;
+    }
+    if (best >= 0 && bd <= 1e-8 * std::hypot(th[j].x, th[j].y))
+      key[j] = key[best] = 0.5 * (th[std::min(j, best)].x + th[std::max(j, best)].x);
+  }
   std::sort(idx.begin(), idx.end(), [&](int a, int b) {
-    return th[a].x < th[b].x || (th[a].x == th[b].x && (th[a].y < th[b].y || (th[a].y == th[b].y && a < b)));
+    return key[a] < key[b] ||
+           (key[a] == key[b] && (th[a].y < th[b].y || (th[a].y == th[b].y && a < b)));
   });
   const int m = (int)idx.size();
   if (m_found) *m_found = m;

@@ -85,16 +85,18 @@ struct RowTiling {
 };
 RowTiling make_tiling(int64_t n, int ncols, int num_sms);
 
-// ---- inner solve (per-node complex GMRES, FP64) ---------------------------
+// ---- inner solve (per-node complex GMRES, FP64 or FP32) -------------------
 struct GmresArgs {
   int n, m0, nc, C, K;
+  int fp32;                 // 1: basis and work vector complex FP32, FP32 arithmetic
   const int32_t *rowptr, *colidx;
   const double *val;
+  const float *val32;       // FP32 copy of val (fp32)
   const double2 *z;         // [nc]
   const double2 *w;         // [nc] quadrature weights
-  const double *X;          // n x m0 right-hand sides (real)
-  double2 *V;               // (K+1) x n x C basis
-  double2 *W;               // n x C work vector
+  const double *X;          // n x m0 right-hand sides (real): X, B X, or the residuals
+  void *V;                  // (K+1) x n x C basis (double2, or float2 when fp32)
+  void *W;                  // n x C work vector (same type as V)
   double2 *part;            // P x (K+2) x C block partials
   double2 *H1;              // (K+1) x C first-pass coefficients of the current step
   double2 *H2;              // (K+1) x C second-pass coefficients of the current step
@@ -102,8 +104,10 @@ struct GmresArgs {
   double2 *CS, *SN;         // K x C Givens rotations
   double2 *R;               // K x K x C triangular factor, R[(l*K + s)*C + c]
   double2 *G;               // (K+1) x C rotated right-hand side
-  double2 *Y;               // K x C w_k-scaled least-squares solutions
-  double *beta;             // m0 column norms of X
+  double2 *Y;               // K x C weighted least-squares solutions
+  float2 *Yf;               // K x C FP32 copy of Y (fp32 quadrature)
+  double *beta;             // m0 norms of the right-hand sides
+  double *tolc;             // C   bound on |g_{s+1}| (0: run all K steps)
   int *steps;               // C   Krylov steps taken
   int *done;                // C   column finished (tolerance met or breakdown)
   double *Q;                // n x m0 output
@@ -112,6 +116,15 @@ struct GmresArgs {
   Profiler *prof;
   const int32_t *rowptrB, *colidxB;  // B of A x = lambda B x (null: B = I)
   const double *valB;
+  const float *valB32;      // FP32 copy of valB (fp32)
+  int b_same_pattern;       // 1: B has A's rowptr/colidx (valB indexed like val)
+  // residual form: right-hand sides r_j = A x_j - lambda_j B x_j (in X, norms in
+  // beta), y = (x_j + e) / (z_k - lambda_j), Q = cx X + Re sum_k w_k e_k / (z_k - lambda_j)
+  int correction;
+  const double *lam;        // [m0] Ritz values
+  const double *xnorm;      // [m0] ||B x_j||
+  const double *Xr;         // n x m0 the Ritz vectors x_j
+  double *cx;               // [m0] Re sum_k w_k / (z_k - lambda_j)
 };
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st);
 cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,

@@ -1,9 +1,14 @@
 // Inner solve of IFEAST (Algorithm 2, steps 1-2) on the GPU: for every contour
-// node z_k and every column x_j of X, GMRES on (z_k I - A) y = x_j with zero
-// initial guess (Section 2.2), all C = nc * m0 systems advanced together, then
-// the quadrature sum Q = Re sum_k w_k Y_k.
+// node z_k and every column b_j of the right-hand side block, GMRES on
+// (z_k B - A) y = b_j with zero initial guess (Section 2.2), all C = nc * m0
+// systems advanced together, then the quadrature sum Q = Re sum_k w_k Y_k.
+// The right-hand sides are X (B X for a generalized problem), or, in the
+// residual form, r_j = A x_j - lambda_j B x_j of the current Ritz pairs: then
+// (z B - A)^{-1} B x_j = (x_j + (z B - A)^{-1} r_j) / (z - lambda_j) and only
+// the correction is solved by GMRES.
 //
-// Data layout (all row-major, complex values interleaved as double2):
+// Data layout (all row-major, complex values interleaved as double2, or
+// float2 for the FP32 basis):
 //   V[s]  n x C basis vector s of every system, column c = k * m0 + j
 //   W     n x C work vector (A-product, then Gram-Schmidt in place)
 // One Arnoldi step s runs five kernels:
@@ -17,42 +22,73 @@
 // (classical Gram-Schmidt applied twice; the norm after the second pass
 // follows from the first-pass norm by Pythagoras because V_0..V_s are
 // orthonormal.) Every reduction sums block partials in a fixed order, so the
-// result does not depend on scheduling.
+// result does not depend on scheduling. With the FP32 basis the products, the
+// updates and each thread's dot sums are FP32; block partials, Hessenberg
+// columns, rotations and least-squares solutions stay FP64.
 #include "internal.h"
 
 namespace ifeast {
 
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+// Complex storage and arithmetic of the basis: double2 (FP64) or float2 (FP32).
+template <typename CT>
+struct Cx;
+template <>
+struct Cx<double2> {
+  using R = double;
+  __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+  __device__ static double fm(double a, double b, double c) { return fma(a, b, c); }
+};
+template <>
+struct Cx<float2> {
+  using R = float;
+  __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+  __device__ static float fm(float a, float b, float c) { return fmaf(a, b, c); }
+};
+
+template <typename CT>
+__device__ __forceinline__ CT cmul(CT a, CT b) {
+  return Cx<CT>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 // acc += conj(a) * b
-__device__ __forceinline__ void cjfma(double2 &acc, double2 a, double2 b) {
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+template <typename CT>
+__device__ __forceinline__ void cjfma(CT &acc, CT a, CT b) {
+  acc.x = Cx<CT>::fm(a.x, b.x, Cx<CT>::fm(a.y, b.y, acc.x));
+  acc.y = Cx<CT>::fm(a.x, b.y, Cx<CT>::fm(-a.y, b.x, acc.y));
 }
 // acc -= h * v
-__device__ __forceinline__ void cfms(double2 &acc, double2 h, double2 v) {
-  acc.x = fma(-h.x, v.x, fma(h.y, v.y, acc.x));
-  acc.y = fma(-h.x, v.y, fma(-h.y, v.x, acc.y));
+template <typename CT>
+__device__ __forceinline__ void cfms(CT &acc, CT h, CT v) {
+  acc.x = Cx<CT>::fm(-h.x, v.x, Cx<CT>::fm(h.y, v.y, acc.x));
+  acc.y = Cx<CT>::fm(-h.x, v.y, Cx<CT>::fm(-h.y, v.x, acc.y));
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
   return make_double2(a.x + b.x, a.y + b.y);
 }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = cabs2(b);
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+template <typename CT>
+__device__ __forceinline__ CT to_ct(double2 a) {
+  using R = typename Cx<CT>::R;
+  return Cx<CT>::make((R)a.x, (R)a.y);
+}
 
 // Sums LMAX register accumulators of the 8 warps of a block (lane = column)
-// and writes them as this block's partials part[(blk * K2 + l) * C + c], l <= s.
-template <int LMAX>
-__device__ __forceinline__ void block_store_partials(const double2 (&acc)[LMAX], int s, int C,
-                                                     int c, int K2, double2 *__restrict__ part) {
+// in FP64 and writes them as this block's partials part[(blk * K2 + l) * C + c],
+// l <= s. (FP32 accumulators are the per-thread sums of the FP32 kernels.)
+template <int LMAX, typename CT>
+__device__ __forceinline__ void block_store_partials(const CT (&acc)[LMAX], int s, int C, int c,
+                                                     int K2, double2 *__restrict__ part) {
   __shared__ double2 red[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     if (l <= s) {  // s is uniform over the block
-      red[warp][lane] = acc[l];
+      red[warp][lane] = make_double2((double)acc[l].x, (double)acc[l].y);
       __syncthreads();
       if (warp == 0) {
         double2 t = red[0][lane];
@@ -65,53 +101,89 @@ __device__ __forceinline__ void block_store_partials(const double2 (&acc)[LMAX],
   }
 }
 
-// W = z_{node(c)} B V_s - A V_s on every active column (B = I when rowptrB is
-// null); with DOTS also the block partials of <V_l, W>, l = 0..s.
-template <int LMAX, bool DOTS>
+// W = z_{node(c)} B V_s - A V_s on every active column; with DOTS also the
+// block partials of <V_l, W>, l = 0..s. CT: complex type of the basis (the
+// arithmetic is done in its precision). BM: B = I (0), B with a pattern of its
+// own (1), or B on A's pattern (2: one gather of V serves both products, valB
+// indexed like val). A row's non-zeros are taken in groups of kNG: the group's
+// indices and values are loaded together, then its gathers are issued before
+// they are used, so that kNG loads per warp are in flight.
+constexpr int kNG = 8;
+
+template <int LMAX, bool DOTS, typename CT, int BM>
 __global__ void __launch_bounds__(kThreads)
 k_spmm_shift_dot(int n, int C, int m0, const int32_t *__restrict__ rowptr,
-                 const int32_t *__restrict__ colidx, const double *__restrict__ val,
-                 const double2 *__restrict__ V, size_t vstride, int s,
-                 const double2 *__restrict__ z, const int *__restrict__ done,
-                 double2 *__restrict__ W, double2 *__restrict__ part, int rows, int K2,
-                 const int32_t *__restrict__ rowptrB, const int32_t *__restrict__ colidxB,
-                 const double *__restrict__ valB) {
+                 const int32_t *__restrict__ colidx, const typename Cx<CT>::R *__restrict__ val,
+                 const CT *__restrict__ V, size_t vstride, int s, const double2 *__restrict__ z,
+                 const int *__restrict__ done, CT *__restrict__ W, double2 *__restrict__ part,
+                 int rows, int K2, const int32_t *__restrict__ rowptrB,
+                 const int32_t *__restrict__ colidxB,
+                 const typename Cx<CT>::R *__restrict__ valB) {
+  using R = typename Cx<CT>::R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * 32 + lane;
   const bool active = c < C && (done == nullptr || done[c] == 0);
-  const double2 zc = (c < C) ? z[c / m0] : make_double2(0.0, 0.0);
-  const double2 *__restrict__ Vs = V + (size_t)s * vstride;
+  const CT zc = (c < C) ? to_ct<CT>(z[c / m0]) : Cx<CT>::make(0, 0);
+  const CT *__restrict__ Vs = V + (size_t)s * vstride;
   const int r0 = blockIdx.x * rows;
   const int r1 = min(n, r0 + rows);
-  double2 acc[LMAX];
+  const CT zero = Cx<CT>::make(0, 0);
+  CT acc[LMAX];
 #pragma unroll
-  for (int l = 0; l < LMAX; ++l) acc[l] = make_double2(0.0, 0.0);
+  for (int l = 0; l < LMAX; ++l) acc[l] = zero;
   if (active) {
     for (int r = r0 + warp; r < r1; r += kWarps) {
       const size_t rc = (size_t)r * C + c;
-      double2 bv;
-      if (rowptrB == nullptr) {
-        bv = Vs[rc];
-      } else {
-        bv = make_double2(0.0, 0.0);
+      CT bv = BM == 0 ? Vs[rc] : zero;  // (B V_s)[r]
+      CT av = zero;                      // (A V_s)[r]
+      if (BM == 1) {
         const int qb = rowptrB[r], qe = rowptrB[r + 1];
-#pragma unroll 4
-        for (int q = qb; q < qe; ++q) {
-          const double b = valB[q];
-          const double2 v = Vs[(size_t)colidxB[q] * C + c];
-          bv.x = fma(b, v.x, bv.x);
-          bv.y = fma(b, v.y, bv.y);
+        for (int q0 = qb; q0 < qe; q0 += kNG) {
+          int cb[kNG];
+          R b[kNG];
+#pragma unroll
+          for (int u = 0; u < kNG; ++u) {
+            const bool in = q0 + u < qe;
+            cb[u] = in ? colidxB[q0 + u] : r;
+            b[u] = in ? valB[q0 + u] : R(0);
+          }
+          CT v[kNG];
+#pragma unroll
+          for (int u = 0; u < kNG; ++u) v[u] = q0 + u < qe ? Vs[(size_t)cb[u] * C + c] : zero;
+#pragma unroll
+          for (int u = 0; u < kNG; ++u) {
+            bv.x = Cx<CT>::fm(b[u], v[u].x, bv.x);
+            bv.y = Cx<CT>::fm(b[u], v[u].y, bv.y);
+          }
         }
       }
-      double2 w = cmul(zc, bv);
       const int jb = rowptr[r], je = rowptr[r + 1];
-#pragma unroll 4
-      for (int j = jb; j < je; ++j) {
-        const double a = val[j];
-        const double2 v = Vs[(size_t)colidx[j] * C + c];
-        w.x = fma(-a, v.x, w.x);
-        w.y = fma(-a, v.y, w.y);
+      for (int j0 = jb; j0 < je; j0 += kNG) {
+        int cj[kNG];
+        R a[kNG], b[kNG];
+#pragma unroll
+        for (int u = 0; u < kNG; ++u) {
+          const bool in = j0 + u < je;
+          cj[u] = in ? colidx[j0 + u] : r;
+          a[u] = in ? val[j0 + u] : R(0);
+          if (BM == 2) b[u] = in ? valB[j0 + u] : R(0);
+        }
+        CT v[kNG];
+#pragma unroll
+        for (int u = 0; u < kNG; ++u) v[u] = j0 + u < je ? Vs[(size_t)cj[u] * C + c] : zero;
+#pragma unroll
+        for (int u = 0; u < kNG; ++u) {
+          av.x = Cx<CT>::fm(a[u], v[u].x, av.x);
+          av.y = Cx<CT>::fm(a[u], v[u].y, av.y);
+          if (BM == 2) {
+            bv.x = Cx<CT>::fm(b[u], v[u].x, bv.x);
+            bv.y = Cx<CT>::fm(b[u], v[u].y, bv.y);
+          }
+        }
       }
+      CT w = cmul(zc, bv);
+      w.x -= av.x;
+      w.y -= av.y;
       W[rc] = w;
       if (DOTS) {
 #pragma unroll
@@ -148,35 +220,36 @@ k_reduce_partials(int P, int C, int K2, const double2 *__restrict__ part,
 
 // First Gram-Schmidt pass: W -= sum_l h1_l V_l, then partials of h2_l =
 // <V_l, W> (l <= s) and of ||W||^2 (stored as the real part of slot s+1).
-template <int LMAX>
+template <int LMAX, typename CT>
 __global__ void __launch_bounds__(kThreads)
-k_orth_update_dot(int n, int C, const double2 *__restrict__ V, size_t vstride, int s,
+k_orth_update_dot(int n, int C, const CT *__restrict__ V, size_t vstride, int s,
                   const double2 *__restrict__ H1, const int *__restrict__ done,
-                  double2 *__restrict__ W, double2 *__restrict__ part, int rows, int K2) {
-  __shared__ double2 hs[LMAX][32];
+                  CT *__restrict__ W, double2 *__restrict__ part, int rows, int K2) {
+  using R = typename Cx<CT>::R;
+  __shared__ CT hs[LMAX][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * 32 + lane;
   const bool active = c < C && done[c] == 0;
   for (int l = warp; l <= s; l += kWarps)
-    hs[l][lane] = (c < C) ? H1[(size_t)l * C + c] : make_double2(0.0, 0.0);
+    hs[l][lane] = (c < C) ? to_ct<CT>(H1[(size_t)l * C + c]) : Cx<CT>::make(0, 0);
   __syncthreads();
-  double2 acc[LMAX + 1];
+  CT acc[LMAX + 1];
 #pragma unroll
-  for (int l = 0; l <= LMAX; ++l) acc[l] = make_double2(0.0, 0.0);
-  double nrm = 0.0;
+  for (int l = 0; l <= LMAX; ++l) acc[l] = Cx<CT>::make(0, 0);
+  R nrm = 0;
   const int r0 = blockIdx.x * rows;
   const int r1 = min(n, r0 + rows);
   if (active) {
     for (int r = r0 + warp; r < r1; r += kWarps) {
       const size_t rc = (size_t)r * C + c;
-      double2 w = W[rc];
+      CT w = W[rc];
 #pragma unroll
       for (int l = 0; l < LMAX; ++l)
         if (l <= s) cfms(w, hs[l][lane], V[(size_t)l * vstride + rc]);
 #pragma unroll
       for (int l = 0; l < LMAX; ++l)
         if (l <= s) cjfma(acc[l], V[(size_t)l * vstride + rc], w);
-      nrm = fma(w.x, w.x, fma(w.y, w.y, nrm));
+      nrm = Cx<CT>::fm(w.x, w.x, Cx<CT>::fm(w.y, w.y, nrm));
       W[rc] = w;
     }
   }
@@ -185,7 +258,8 @@ k_orth_update_dot(int n, int C, const double2 *__restrict__ V, size_t vstride, i
 #pragma unroll
   for (int l = 0; l <= LMAX; ++l) {
     if (l <= s + 1) {
-      red[warp][lane] = (l == s + 1) ? make_double2(nrm, 0.0) : acc[l];
+      red[warp][lane] = (l == s + 1) ? make_double2((double)nrm, 0.0)
+                                     : make_double2((double)acc[l].x, (double)acc[l].y);
       __syncthreads();
       if (warp == 0) {
         double2 t = red[0][lane];
@@ -200,13 +274,14 @@ k_orth_update_dot(int n, int C, const double2 *__restrict__ V, size_t vstride, i
 
 // Per system c: Hessenberg column h_{l,s} = h1_l + h2_l, h_{s+1,s} from
 // Pythagoras, previous Givens rotations, new rotation, rotated right-hand side
-// and the stop test |g_{s+1}| <= tol_rel * ||x_j||.
+// and the stop test |g_{s+1}| <= tolc[c]. h_{s+1,s} <= brk * ||b|| is a
+// breakdown (the Krylov space is invariant to the basis precision).
 __global__ void k_givens(int C, int m0, int K, int s, const double2 *__restrict__ H1,
                          const double2 *__restrict__ H2, const double *__restrict__ beta,
+                         const double *__restrict__ tolc, double brk,
                          double *__restrict__ inv_h, double2 *__restrict__ CS,
                          double2 *__restrict__ SN, double2 *__restrict__ R,
-                         double2 *__restrict__ G, int *__restrict__ steps, int *__restrict__ done,
-                         const DevStatus *__restrict__ status) {
+                         double2 *__restrict__ G, int *__restrict__ steps, int *__restrict__ done) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   if (done[c]) {
@@ -223,7 +298,7 @@ __global__ void k_givens(int C, int m0, int K, int s, const double2 *__restrict_
   const double nrm1 = H2[(size_t)(s + 1) * C + c].x;
   const double hs = sqrt(fmax(nrm1 - sum2, 0.0));
   const double b = beta[c % m0];
-  const bool happy = !(hs > 1e-14 * b);
+  const bool happy = !(hs > brk * b);
   inv_h[c] = happy ? 0.0 : 1.0 / hs;
   // apply the rotations of steps 0..s-1 (G_l = [[conj cs, conj sn], [-sn, cs]])
   for (int l = 0; l < s; ++l) {
@@ -255,65 +330,90 @@ __global__ void k_givens(int C, int m0, int K, int s, const double2 *__restrict_
   SN[(size_t)s * C + c] = sn;
   steps[c] = s + 1;
   const double res = sqrt(cabs2(G[(size_t)(s + 1) * C + c]));
-  const double tol = status->tol_rel;
-  if (happy || (tol > 0.0 && res <= tol * b)) done[c] = 1;
+  const double tol = tolc[c];
+  if (happy || (tol > 0.0 && res <= tol)) done[c] = 1;
 }
 
 // V_{s+1} = (W - sum_l h2_l V_l) * inv_h on systems still running.
-template <int LMAX>
+template <int LMAX, typename CT>
 __global__ void __launch_bounds__(kThreads)
-k_orth_finish(int n, int C, double2 *__restrict__ V, size_t vstride, int s,
+k_orth_finish(int n, int C, CT *__restrict__ V, size_t vstride, int s,
               const double2 *__restrict__ H2, const double *__restrict__ inv_h,
-              const int *__restrict__ done, const double2 *__restrict__ W, int rows) {
-  __shared__ double2 hs[LMAX][32];
+              const int *__restrict__ done, const CT *__restrict__ W, int rows) {
+  using R = typename Cx<CT>::R;
+  __shared__ CT hs[LMAX][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * 32 + lane;
   for (int l = warp; l <= s; l += kWarps)
-    hs[l][lane] = (c < C) ? H2[(size_t)l * C + c] : make_double2(0.0, 0.0);
+    hs[l][lane] = (c < C) ? to_ct<CT>(H2[(size_t)l * C + c]) : Cx<CT>::make(0, 0);
   __syncthreads();
   if (c >= C || done[c]) return;
-  const double ih = inv_h[c];
-  double2 *__restrict__ Vn = V + (size_t)(s + 1) * vstride;
+  const R ih = (R)inv_h[c];
+  CT *__restrict__ Vn = V + (size_t)(s + 1) * vstride;
   const int r0 = blockIdx.x * rows;
   const int r1 = min(n, r0 + rows);
   for (int r = r0 + warp; r < r1; r += kWarps) {
     const size_t rc = (size_t)r * C + c;
-    double2 w = W[rc];
+    CT w = W[rc];
 #pragma unroll
     for (int l = 0; l < LMAX; ++l)
       if (l <= s) cfms(w, hs[l][lane], V[(size_t)l * vstride + rc]);
-    Vn[rc] = make_double2(w.x * ih, w.y * ih);
+    Vn[rc] = Cx<CT>::make(w.x * ih, w.y * ih);
   }
 }
 
-// V_0[:, k*m0 + j] = x_j / ||x_j|| for all nodes k; least-squares state reset.
+// V_0[:, k*m0 + j] = b_j / ||b_j|| for all nodes k (b = X, B X, or the
+// residuals); least-squares state reset and the per-system bound on the
+// least-squares residual: tol_rel ||b_j||, or in the residual form
+// tol_rel ||B x_j|| |z_k - lambda_j| (the same bound on the original system,
+// whose residual is the correction's divided by |z_k - lambda_j|).
+template <typename CT>
 __global__ void k_prep(int n, int m0, int C, int K, const double *__restrict__ X,
-                       const double *__restrict__ beta, double2 *__restrict__ V0,
-                       double2 *__restrict__ G, int *__restrict__ steps, int *__restrict__ done) {
+                       const double *__restrict__ beta, CT *__restrict__ V0,
+                       double2 *__restrict__ G, int *__restrict__ steps, int *__restrict__ done,
+                       double *__restrict__ tolc, const DevStatus *__restrict__ status,
+                       const double2 *__restrict__ z, const double *__restrict__ lam,
+                       const double *__restrict__ xnorm, int correction) {
+  using R = typename Cx<CT>::R;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t total = (size_t)n * C;
   if (idx < total) {
     const int r = (int)(idx / C), c = (int)(idx % C), j = c % m0;
     const double b = beta[j];
-    V0[idx] = make_double2(b > 0.0 ? X[(size_t)r * m0 + j] / b : 0.0, 0.0);
+    V0[idx] = Cx<CT>::make((R)(b > 0.0 ? X[(size_t)r * m0 + j] / b : 0.0), 0);
   }
   if (idx < (size_t)C) {
-    const int c = (int)idx;
-    const double b = beta[c % m0];
+    const int c = (int)idx, j = c % m0, k = c / m0;
+    const double b = beta[j];
     G[c] = make_double2(b, 0.0);
     for (int l = 1; l <= K; ++l) G[(size_t)l * C + c] = make_double2(0.0, 0.0);
     steps[c] = 0;
     done[c] = (b > 0.0) ? 0 : 1;
+    const double tol_rel = status->tol_rel;
+    double t = 0.0;
+    if (tol_rel > 0.0) {
+      if (correction) {
+        const double2 d = make_double2(z[k].x - lam[j], z[k].y);
+        t = tol_rel * xnorm[j] * sqrt(cabs2(d));
+      } else {
+        t = tol_rel * b;
+      }
+    }
+    tolc[c] = t;
   }
 }
 
 // y = R^{-1} g for each system (back substitution over its steps), scaled by
-// the quadrature weight of its node: Y[l][c] = w_k * y_l. Step counts are
-// folded into the status record with integer atomics (order-independent).
-__global__ void k_solve_y(int C, int m0, int K, const double2 *__restrict__ R,
+// the system's weight: Y[l][c] = w_k y_l, or w_k / (z_k - lambda_j) y_l in the
+// residual form (Yf: the same in FP32 for the FP32 quadrature); cx[j] = Re
+// sum_k w_k / (z_k - lambda_j) (residual form) or 0. Step counts are folded
+// into the status record with integer atomics (order-independent).
+__global__ void k_solve_y(int C, int m0, int nc, int K, const double2 *__restrict__ R,
                           const double2 *__restrict__ G, const double2 *__restrict__ wq,
-                          const int *__restrict__ steps, double2 *__restrict__ Y,
-                          DevStatus *__restrict__ status) {
+                          const double2 *__restrict__ z, const double *__restrict__ lam,
+                          int correction, const int *__restrict__ steps,
+                          double2 *__restrict__ Y, float2 *__restrict__ Yf,
+                          double *__restrict__ cx, DevStatus *__restrict__ status) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const int m = steps[c];
@@ -329,64 +429,141 @@ __global__ void k_solve_y(int C, int m0, int K, const double2 *__restrict__ R,
     const double dd = cabs2(d);
     y[l] = make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd);
   }
-  const double2 wk = wq[c / m0];
-  for (int l = 0; l < K; ++l)
-    Y[(size_t)l * C + c] = (l < m) ? cmul(wk, y[l]) : make_double2(0.0, 0.0);
+  const int k = c / m0, j = c % m0;
+  double2 wk = wq[k];
+  if (correction) wk = cdiv(wk, make_double2(z[k].x - lam[j], z[k].y));
+  for (int l = 0; l < K; ++l) {
+    const double2 v = (l < m) ? cmul(wk, y[l]) : make_double2(0.0, 0.0);
+    Y[(size_t)l * C + c] = v;
+    if (Yf) Yf[(size_t)l * C + c] = make_float2((float)v.x, (float)v.y);
+  }
+  if (cx && c < m0) {
+    double t = 0.0;
+    if (correction)
+      for (int kk = 0; kk < nc; ++kk)
+        t += cdiv(wq[kk], make_double2(z[kk].x - lam[c], z[kk].y)).x;
+    cx[c] = t;
+  }
   atomicMax(&status->max_steps, m);
   atomicAdd((unsigned long long *)&status->total_steps, (unsigned long long)m);
 }
 
-// Q[r][j] = Re sum_k sum_{l < steps} (w_k y_{k,j,l}) V_l[r][k*m0 + j].
-__global__ void k_quadrature(int n, int m0, int nc, int C, const double2 *__restrict__ V,
+// Q[r][j] = cx[j] X[r][j] + Re sum_k sum_{l < steps} Y[l][k*m0 + j] V_l[r][k*m0 + j]
+// (cx null: no first term). FP64 basis: FP64 sums of the FP64 coefficients;
+// FP32 basis: FP32 sums of the FP32 coefficients.
+template <typename CT>
+__global__ void k_quadrature(int n, int m0, int nc, int C, const CT *__restrict__ V,
                              size_t vstride, const double2 *__restrict__ Y,
-                             const int *__restrict__ steps, double *__restrict__ Q) {
+                             const float2 *__restrict__ Yf, const int *__restrict__ steps,
+                             const double *__restrict__ cx, const double *__restrict__ Xr,
+                             double *__restrict__ Q) {
+  using R = typename Cx<CT>::R;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)n * m0) return;
   const int r = (int)(idx / m0), j = (int)(idx % m0);
-  double q = 0.0;
+  R q = 0;
   for (int k = 0; k < nc; ++k) {
     const int c = k * m0 + j;
     const int m = steps[c];
     const size_t rc = (size_t)r * C + c;
     for (int l = 0; l < m; ++l) {
-      const double2 yw = Y[(size_t)l * C + c];
-      const double2 v = V[(size_t)l * vstride + rc];
-      q = fma(yw.x, v.x, fma(-yw.y, v.y, q));
+      CT yw;
+      if constexpr (sizeof(R) == 8) {
+        yw = Y[(size_t)l * C + c];
+      } else {
+        yw = Yf[(size_t)l * C + c];
+      }
+      const CT v = V[(size_t)l * vstride + rc];
+      q = Cx<CT>::fm(yw.x, v.x, Cx<CT>::fm(-yw.y, v.y, q));
     }
   }
-  Q[idx] = q;
+  Q[idx] = cx ? cx[j] * Xr[idx] + (double)q : (double)q;
 }
 
-template <int LMAX>
+template <int LMAX, typename CT>
 cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
+  using R = typename Cx<CT>::R;
   const dim3 grid(a.tl.P, a.tl.tiles);
   const size_t vstride = (size_t)a.n * a.C;
   const int K2 = a.K + 2;
+  CT *V = static_cast<CT *>(a.V);
+  CT *W = static_cast<CT *>(a.W);
+  const R *val, *valB;
+  if constexpr (sizeof(R) == 8) {
+    val = a.val;
+    valB = a.valB;
+  } else {
+    val = a.val32;
+    valB = a.valB32;
+  }
   IFEAST_PROF_BEGIN(a.prof, K_GM_SPMM);
-  k_spmm_shift_dot<LMAX, true><<<grid, kThreads, 0, st>>>(
-      a.n, a.C, a.m0, a.rowptr, a.colidx, a.val, a.V, vstride, s, a.z, a.done, a.W, a.part,
-      a.tl.rows, K2, a.rowptrB, a.colidxB, a.valB);
+#define IFEAST_SPMM_LAUNCH(BM)                                                                 \
+  k_spmm_shift_dot<LMAX, true, CT, BM><<<grid, kThreads, 0, st>>>(                             \
+      a.n, a.C, a.m0, a.rowptr, a.colidx, val, V, vstride, s, a.z, a.done, W, a.part, a.tl.rows, \
+      K2, a.rowptrB, a.colidxB, valB)
+  if (!a.rowptrB)
+    IFEAST_SPMM_LAUNCH(0);
+  else if (a.b_same_pattern)
+    IFEAST_SPMM_LAUNCH(2);
+  else
+    IFEAST_SPMM_LAUNCH(1);
+#undef IFEAST_SPMM_LAUNCH
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 1, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H1);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_ORTH);
-  k_orth_update_dot<LMAX><<<grid, kThreads, 0, st>>>(a.n, a.C, a.V, vstride, s, a.H1, a.done,
-                                                     a.W, a.part, a.tl.rows, K2);
+  k_orth_update_dot<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.H1, a.done,
+                                                         W, a.part, a.tl.rows, K2);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 2, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H2);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_GIVENS);
-  k_givens<<<(a.C + 127) / 128, 128, 0, st>>>(a.C, a.m0, a.K, s, a.H1, a.H2, a.beta, a.inv_h,
-                                              a.CS, a.SN, a.R, a.G, a.steps, a.done, a.status);
+  // breakdown threshold: the basis precision's rounding level
+  const double brk = sizeof(R) == 8 ? 1e-14 : 1e-6;
+  k_givens<<<(a.C + 127) / 128, 128, 0, st>>>(a.C, a.m0, a.K, s, a.H1, a.H2, a.beta, a.tolc, brk,
+                                              a.inv_h, a.CS, a.SN, a.R, a.G, a.steps, a.done);
   IFEAST_PROF_END(a.prof);
   if (s + 1 < a.K) {  // the last step's basis vector is never used
     IFEAST_PROF_BEGIN(a.prof, K_GM_FINISH);
-    k_orth_finish<LMAX><<<grid, kThreads, 0, st>>>(a.n, a.C, a.V, vstride, s, a.H2, a.inv_h,
-                                                   a.done, a.W, a.tl.rows);
+    k_orth_finish<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.H2, a.inv_h,
+                                                       a.done, W, a.tl.rows);
     IFEAST_PROF_END(a.prof);
   }
+  return cudaGetLastError();
+}
+
+template <typename CT>
+cudaError_t run_gmres(const GmresArgs &a, cudaStream_t st) {
+  const size_t total = (size_t)a.n * a.C;
+  CT *V = static_cast<CT *>(a.V);
+  IFEAST_PROF_BEGIN(a.prof, K_PREP);
+  k_prep<CT><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      a.n, a.m0, a.C, a.K, a.X, a.beta, V, a.G, a.steps, a.done, a.tolc, a.status, a.z,
+      a.correction ? a.lam : nullptr, a.correction ? a.xnorm : nullptr, a.correction);
+  IFEAST_PROF_END(a.prof);
+  cudaError_t e = cudaGetLastError();
+  for (int s = 0; s < a.K && e == cudaSuccess; ++s) {
+    if (s + 1 <= 8)
+      e = launch_step<8, CT>(a, s, st);
+    else if (s + 1 <= 16)
+      e = launch_step<16, CT>(a, s, st);
+    else
+      e = launch_step<32, CT>(a, s, st);
+  }
+  if (e != cudaSuccess) return e;
+  IFEAST_PROF_BEGIN(a.prof, K_GM_SOLVE);
+  k_solve_y<<<(a.C + 127) / 128, 128, 0, st>>>(
+      a.C, a.m0, a.nc, a.K, a.R, a.G, a.w, a.z, a.correction ? a.lam : nullptr, a.correction,
+      a.steps, a.Y, a.fp32 ? a.Yf : nullptr, a.correction ? a.cx : nullptr, a.status);
+  IFEAST_PROF_END(a.prof);
+  IFEAST_PROF_BEGIN(a.prof, K_GM_QUAD);
+  const size_t nq = (size_t)a.n * a.m0;
+  k_quadrature<CT><<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
+      a.n, a.m0, a.nc, a.C, V, (size_t)a.n * a.C, a.Y, a.Yf, a.steps,
+      a.correction ? a.cx : nullptr, a.Xr, a.Q);
+  IFEAST_PROF_END(a.prof);
   return cudaGetLastError();
 }
 
@@ -408,40 +585,26 @@ RowTiling make_tiling(int64_t n, int ncols, int num_sms) {
 
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
   if (a.K < 1 || a.K > kMaxInner) return cudaErrorInvalidValue;
-  const size_t total = (size_t)a.n * a.C;
-  IFEAST_PROF_BEGIN(a.prof, K_PREP);
-  k_prep<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.C, a.K, a.X, a.beta, a.V,
-                                                           a.G, a.steps, a.done);
-  IFEAST_PROF_END(a.prof);
-  cudaError_t e = cudaGetLastError();
-  for (int s = 0; s < a.K && e == cudaSuccess; ++s) {
-    if (s + 1 <= 8)
-      e = launch_step<8>(a, s, st);
-    else if (s + 1 <= 16)
-      e = launch_step<16>(a, s, st);
-    else
-      e = launch_step<32>(a, s, st);
+  if (a.correction && (!a.lam || !a.xnorm || !a.Xr || !a.cx)) return cudaErrorInvalidValue;
+  if (a.fp32) {
+    if (!a.val32 || !a.Yf || (a.rowptrB && !a.valB32)) return cudaErrorInvalidValue;
+    return run_gmres<float2>(a, st);
   }
-  if (e != cudaSuccess) return e;
-  IFEAST_PROF_BEGIN(a.prof, K_GM_SOLVE);
-  k_solve_y<<<(a.C + 127) / 128, 128, 0, st>>>(a.C, a.m0, a.K, a.R, a.G, a.w, a.steps, a.Y,
-                                               a.status);
-  IFEAST_PROF_END(a.prof);
-  IFEAST_PROF_BEGIN(a.prof, K_GM_QUAD);
-  const size_t nq = (size_t)a.n * a.m0;
-  k_quadrature<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(a.n, a.m0, a.nc, a.C, a.V,
-                                                             (size_t)a.n * a.C, a.Y, a.steps, a.Q);
-  IFEAST_PROF_END(a.prof);
-  return cudaGetLastError();
+  return run_gmres<double2>(a, st);
 }
 
 cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
                             const double *val, const double2 *V, double2 *W, int ncols, int m0,
                             const double2 *z, RowTiling tl, cudaStream_t st,
                             const int32_t *rowptrB, const int32_t *colidxB, const double *valB) {
-  k_spmm_shift_dot<1, false><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
-      n, ncols, m0, rowptr, colidx, val, V, (size_t)n * ncols, 0, z, nullptr, W, nullptr, tl.rows,
-      0, rowptrB, colidxB, valB);
+  if (rowptrB)
+    k_spmm_shift_dot<1, false, double2, 1><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
+        n, ncols, m0, rowptr, colidx, val, V, (size_t)n * ncols, 0, z, nullptr, W, nullptr,
+        tl.rows, 0, rowptrB, colidxB, valB);
+  else
+    k_spmm_shift_dot<1, false, double2, 0><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
+        n, ncols, m0, rowptr, colidx, val, V, (size_t)n * ncols, 0, z, nullptr, W, nullptr,
+        tl.rows, 0, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

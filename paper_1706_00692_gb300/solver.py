@@ -49,7 +49,8 @@ class Solver:
                  alpha: float = 0.0, max_outer: int = 100, tol: float = 1e-10,
                  precision: str = "fp64", device: str | int = "cuda",
                  torch_workspace: bool = True, verbose: bool = False, B: CSR | None = None,
-                 nonsymmetric: bool = False, two_pass: bool = False):
+                 nonsymmetric: bool = False, two_pass: bool = False,
+                 correction_rf: float | None = None):
         torch = _torch()
         self.lib = _lib.load()
         self.torch = torch
@@ -68,6 +69,8 @@ class Solver:
         self.opts.verbose = 1 if verbose else 0
         self.opts.nonsymmetric = 1 if nonsymmetric else 0
         self.opts.minres_two_pass = 1 if two_pass else 0
+        if correction_rf is not None:
+            self.opts.correction_rf = correction_rf
         nbytes = ct.c_size_t(0)
         rc = self.lib.ifeast_workspace_bytes_generalized(
             self.n, A.nnz, -1 if B is None else B.nnz, self.m0, ct.byref(self.contour),

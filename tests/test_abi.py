@@ -72,7 +72,23 @@ def _opts(lib, **kw):
 def test_default_opts(lib):
     o = _opts(lib)
     assert (o.inner_solver, o.inner_max_iters, o.alpha, o.max_outer, o.tol, o.precision,
-            o.verbose, o.nonsymmetric) == (0, 10, 0.0, 100, 1e-10, 0, 0, 0)
+            o.verbose, o.nonsymmetric, o.minres_two_pass, o.correction_rf) == \
+        (0, 10, 0.0, 100, 1e-10, 0, 0, 0, 0, 1e-3)
+
+
+def test_fp32_gmres_workspace(lib):
+    """The FP32 GMRES basis and work vector take half the bytes of the FP64 ones
+    (plus FP32 copies of A, FP32 weights and the residual-form block)."""
+    c = _lib.Contour(0, 8, 0.0, 1.0)
+    n, nnz, m0, K = 4096, 20480, 16, 20
+    b64, b32 = ct.c_size_t(), ct.c_size_t()
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c), ct.byref(
+        _opts(lib, inner_max_iters=K)), ct.byref(b64)) == 0
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c), ct.byref(
+        _opts(lib, inner_max_iters=K, precision=1)), ct.byref(b32)) == 0
+    basis64 = (K + 2) * n * 8 * m0 * 16
+    extra32 = nnz * 4 + K * 8 * m0 * 8 + n * m0 * 8 + 2 * m0 * 8
+    assert abs((b64.value - b32.value) - (basis64 // 2 - extra32)) <= 16 * 256
 
 
 def test_workspace_bytes_grows_with_basis(lib):
@@ -118,8 +134,13 @@ def test_create_rejects_bad_options(lib):
     assert _create(lib, A, opts=_opts(lib, inner_max_iters=33))[0] == _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, opts=_opts(lib, max_outer=0))[0] == _lib.IFEAST_ERR_INVALID_ARG
     assert _create(lib, A, opts=_opts(lib, inner_solver=9))[0] == _lib.IFEAST_ERR_UNSUPPORTED
-    assert _create(lib, A, opts=_opts(lib, precision=1))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    # per-node GMRES: FP64 or FP32 basis (FP16 storage is the shared-basis solver's)
     assert _create(lib, A, opts=_opts(lib, precision=2))[0] == _lib.IFEAST_ERR_UNSUPPORTED
+    # the FP32 GMRES basis needs the residual form, i.e. real Ritz pairs
+    assert _create(lib, A, opts=_opts(lib, precision=1, nonsymmetric=1))[0] == \
+        _lib.IFEAST_ERR_UNSUPPORTED
+    for bad in (-1.0, float("nan")):
+        assert _create(lib, A, opts=_opts(lib, correction_rf=bad))[0] == _lib.IFEAST_ERR_INVALID_ARG
     # FP16 storage needs the four-column kernels (m0 % 4 == 0)
     assert _create(lib, A, m0=7, opts=_opts(lib, inner_solver=1, inner_max_iters=8,
                                             precision=2))[0] == _lib.IFEAST_ERR_UNSUPPORTED

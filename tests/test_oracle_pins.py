@@ -349,3 +349,74 @@ def test_generalized_ifeast_exact_inner_reproduces_feast():
     for a, b in zip(h1, h2):
         ins = (a > emin) & (a < emax)
         assert np.abs(a[ins] - b[ins]).max() < 1e-9 * np.abs(a).max()
+
+
+# ---------------------------------------------------------------- residual form of the GMRES filter
+
+def _correction_case(B_too):
+    if B_too:
+        A, B = inputs.fem_q1((6, 5))
+        Bs = B.to_scipy()
+    else:
+        A, Bs = inputs.add_diagonal(inputs.laplacian((6, 5)), inputs.random_potential(30, 4)), None
+    As = A.to_scipy()
+    X = inputs.initial_subspace(30, 4, 8)
+    lam = np.array([0.3, 1.7, 2.2, 9.0])  # any scalars off the contour
+    return As, Bs, X, lam
+
+
+@pytest.mark.parametrize("B_too", [False, True])
+def test_gmres_correction_filter_equals_plain_filter_with_exact_solves(B_too):
+    """With GMRES run to n steps (an exact solve), the residual-form filter
+    sum_k w_k (x_j + (z_k B - A)^{-1} r_j) / (z_k - lam_j) equals the plain
+    filter sum_k w_k (z_k B - A)^{-1} B x_j (dense LU) for every lam_j: the
+    identity (z B - A)^{-1} B x = (x + (z B - A)^{-1}(A x - lam B x)) / (z - lam)."""
+    As, Bs, X, lam = _correction_case(B_too)
+    z, w = orc.contour_nodes("gl_half", 5, 0.0, 4.0 if not B_too else 400.0)
+    ref = orc._filtered_subspace_exact(As.toarray(), X, z, w, True,
+                                       None if Bs is None else Bs.toarray())
+    got = orc._filtered_subspace_gmres_correction(As, X, lam, z, w, True, 30, 0.0,
+                                                  {"inner_steps": []}, Bs)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_gmres_correction_filter_mutations_fail():
+    """A dropped x_j term or a sign error in the residual is caught by the
+    exact-solve identity."""
+    As, Bs, X, lam = _correction_case(False)
+    z, w = orc.contour_nodes("gl_half", 5, 0.0, 4.0)
+    ref = orc._filtered_subspace_exact(As.toarray(), X, z, w, True)
+    scale = np.abs(ref).max()
+    # mutation 1: correction only (no x_j / (z - lam) term)
+    Rres = As @ X - X * lam[None, :]
+    Q1 = np.zeros(X.shape, np.complex128)
+    Q2 = np.zeros(X.shape, np.complex128)
+    for zk, wk in zip(z, w):
+        M = zk * np.eye(30) - As.toarray()
+        for j in range(4):
+            e = np.linalg.solve(M, Rres[:, j])
+            Q1[:, j] += wk * e / (zk - lam[j])
+            e2 = np.linalg.solve(M, -Rres[:, j])  # mutation 2: residual sign
+            Q2[:, j] += wk * (X[:, j] + e2) / (zk - lam[j])
+    assert np.abs(Q1.real - ref).max() > 1e-3 * scale
+    assert np.abs(Q2.real - ref).max() > 1e-3 * scale
+
+
+def test_ifeast_correction_converges_to_closed_form_generalized():
+    """IFEAST with the GMRES residual form on the Q1 FEM pencil reaches the
+    closed-form eigenvalues; the plain form with the same k also converges
+    (the two differ only in the inner solver's starting point)."""
+    grid = (12, 10)
+    K, M = inputs.fem_q1(grid)
+    ev = inputs.fem_q1_eigs(grid)
+    cnt = 5
+    emin, emax = 0.0, 0.5 * (ev[cnt - 1] + ev[cnt])
+    z, w = orc.contour_nodes("gl_half", 8, emin, emax)
+    X0 = inputs.initial_subspace(K.n, 10, 0)
+    for corr in (np.inf, 1e-3, None):
+        out = orc.ifeast(K.to_scipy(), X0, emin, emax, z, w, inner="gmres", k=12, alpha=1e-2,
+                         max_outer=40, B=M.to_scipy(), correction_rf=corr)
+        assert out["converged"], corr
+        lam = out["lam"][out["inside"]]
+        assert lam.size == cnt
+        assert np.abs(lam - ev[:cnt]).max() <= 1e-10 * ev[cnt - 1]
