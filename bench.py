@@ -1,13 +1,16 @@
 """Benchmark of the IFEAST hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload lap2d_50|lap3d_64]
+                    [--workload lap3d_64|lap3d_64_fp16|lap3d_64_twopass|lap3d_64_fp64|
+                                lap2d_50|fem3d_64|fem3d_64_fp64|fem3d_48|serve]
 
 One step = one full IFEAST solve (Algorithm 2 from the seeded initial subspace
 until ||R_F|| <= 1e-10) of the workload, inputs resident on the device. The
 default workload is the 3D 7-point Laplacian on 64^3 plus a U[0,1) potential
-(n = 262,144), interior window with 52 eigenvalues, m0 = 80, 8 contour nodes,
+(n = 262,144), interior window with 56 eigenvalues, m0 = 80, 8 contour nodes,
 shared-basis MINRES inner solves in FP32 with the FP64 outer iteration. The
+fem3d workloads are generalized problems (Q1 finite elements, K x = lambda M x,
+lowest eigenvalues) with per-node GMRES inner solves. The
 metric is converged eigenpairs per second (pairs inside the interval with
 relative residual <= 1e-10, times steps, over the device time of the steps).
 Under torchrun every rank solves its own replica of the workload (no data
@@ -46,7 +49,8 @@ def parse():
     p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp16",
                                                                  "lap3d_64_twopass",
                                                                  "lap3d_64_fp64", "lap2d_50",
-                                                                 "serve"])
+                                                                 "fem3d_64", "fem3d_64_fp64",
+                                                                 "fem3d_48", "serve"])
     p.add_argument("--requests", type=int, default=64, help="serving stream length")
     p.add_argument("--rate", type=float, default=8.0, help="serving arrivals per second")
     p.add_argument("--n-max", type=float, default=1e6, help="largest serving request size")
@@ -66,6 +70,12 @@ def make_workload(name):
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp16")
     if name == "lap3d_64_twopass":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp32", two_pass=True)
+    if name == "fem3d_64":  # generalized K x = lambda M x, per-node FP32 GMRES
+        return inputs.workload_fem3d(64, 50, precision="fp32")
+    if name == "fem3d_64_fp64":
+        return inputs.workload_fem3d(64, 50, precision="fp64")
+    if name == "fem3d_48":
+        return inputs.workload_fem3d(48, 40, precision="fp32")
     raise ValueError(name)
 
 
@@ -172,6 +182,28 @@ def oracle_sample(wl, budget_s=20.0, gpu_stats=None):
     from oracle import ifeast_oracle as orc
     z, w = orc.contour_nodes(wl.rule, wl.nc, wl.emin, wl.emax)
     A = wl.A.to_scipy()
+    if wl.B is not None:
+        # generalized problem: the oracle's per-node GMRES on (z_k B - A) y = B x_j,
+        # timed on a bounded number of (node, column) systems and scaled to the
+        # Krylov steps the GPU solve took (all of its systems and iterations)
+        B = wl.B.to_scipy()
+        BX = B @ wl.X0()
+        done, steps_done, t0 = 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s and done < 64:
+            k, j = done % wl.nc, done // wl.nc
+            out = orc.gmres(lambda v, zk=z[k]: zk * (B @ v) - A @ v, BX[:, j], wl.inner_iters)
+            steps_done += out["steps"]
+            done += 1
+        dt = time.perf_counter() - t0
+        per_step = dt / max(steps_done, 1)
+        total_steps = (gpu_stats or {}).get("total_matvecs") or \
+            wl.inner_iters * wl.nc * wl.m0 * 10
+        est = per_step * total_steps
+        pairs = wl.expected_count or 0
+        return pairs / est, (f"oracle per-node GMRES on {wl.name}: {done} (node, column) systems, "
+                             f"{steps_done} Krylov steps in {dt:.1f} s = {per_step*1e3:.2f} ms "
+                             f"per step; scaled to {total_steps} Krylov steps of a full solve "
+                             f"({est/3600:.1f} h) for {pairs} pairs")
     if wl.A.n > 100000:
         X = wl.X0()
         steps, pairs_done, t0 = 60, 0, time.perf_counter()
@@ -252,7 +284,8 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     X0 = torch.as_tensor(wl.X0(), device=dev)
     skw = dict(nc=wl.nc, rule=wl.rule, inner=wl.inner, inner_iters=wl.inner_iters,
-               alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass, device=dev)
+               alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass, B=wl.B,
+               device=dev)
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, **skw)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -300,7 +333,8 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: create (A host->device),
     # solve (X0 host->device), eigenpairs (device->host), destroy
     X0h = torch.from_numpy(wl.X0()).pin_memory().numpy()
-    csr_bytes = wl.A.rowptr.nbytes + wl.A.colidx.nbytes + wl.A.val.nbytes
+    csr_bytes = sum(M.rowptr.nbytes + M.colidx.nbytes + M.val.nbytes
+                    for M in (wl.A, wl.B) if M is not None)
     e2e_times = []
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()

@@ -12,7 +12,7 @@
 //   V[s]  n x C basis vector s of every system, column c = k * m0 + j
 //   W     n x C work vector (A-product, then Gram-Schmidt in place)
 // One Arnoldi step s runs five kernels:
-//   spmm_shift_dot   W = z V_s - A V_s and block partials of h1_l = <V_l, W>
+//   spmm_shift, dots W = z B V_s - A V_s, then block partials of h1_l = <V_l, W>
 //   reduce           h1 (fixed-order sum of the block partials)
 //   orth_update_dot  W -= sum_l h1_l V_l and partials of h2_l = <V_l, W>, ||W||^2
 //   reduce           h2, ||W||^2
@@ -193,6 +193,35 @@ k_spmm_shift_dot(int n, int C, int m0, const int32_t *__restrict__ rowptr,
     }
   }
   if (DOTS) block_store_partials<LMAX>(acc, s, C, c, K2, part);
+}
+
+// Block partials of h1_l = <V_l, W>, l = 0..s, for the columns still running
+// (the first Gram-Schmidt pass's coefficients). Kept out of the SpMM so that
+// the SpMM's gathers run at full occupancy: the s + 1 accumulators per thread
+// would otherwise hold registers through the whole gather loop.
+template <int LMAX, typename CT>
+__global__ void __launch_bounds__(kThreads)
+k_dots(int n, int C, const CT *__restrict__ V, size_t vstride, int s,
+       const int *__restrict__ done, const CT *__restrict__ W, double2 *__restrict__ part,
+       int rows, int K2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.y * 32 + lane;
+  const bool active = c < C && done[c] == 0;
+  CT acc[LMAX];
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) acc[l] = Cx<CT>::make(0, 0);
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(n, r0 + rows);
+  if (active) {
+    for (int r = r0 + warp; r < r1; r += kWarps) {
+      const size_t rc = (size_t)r * C + c;
+      const CT w = W[rc];
+#pragma unroll
+      for (int l = 0; l < LMAX; ++l)
+        if (l <= s) cjfma(acc[l], V[(size_t)l * vstride + rc], w);
+    }
+  }
+  block_store_partials<LMAX>(acc, s, C, c, K2, part);
 }
 
 // out[l * C + c] = sum over blocks b (in order) of part[(b * K2 + l) * C + c].
@@ -498,7 +527,7 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
   }
   IFEAST_PROF_BEGIN(a.prof, K_GM_SPMM);
 #define IFEAST_SPMM_LAUNCH(BM)                                                                 \
-  k_spmm_shift_dot<LMAX, true, CT, BM><<<grid, kThreads, 0, st>>>(                             \
+  k_spmm_shift_dot<1, false, CT, BM><<<grid, kThreads, 0, st>>>(                               \
       a.n, a.C, a.m0, a.rowptr, a.colidx, val, V, vstride, s, a.z, a.done, W, a.part, a.tl.rows, \
       K2, a.rowptrB, a.colidxB, valB)
   if (!a.rowptrB)
@@ -508,6 +537,8 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
   else
     IFEAST_SPMM_LAUNCH(1);
 #undef IFEAST_SPMM_LAUNCH
+  k_dots<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.done, W, a.part,
+                                              a.tl.rows, K2);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 1, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H1);

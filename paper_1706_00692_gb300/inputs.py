@@ -250,6 +250,7 @@ class Workload:
     inner: str = "gmres"
     precision: str = "fp64"
     two_pass: bool = False  # shared-basis solver without the stored basis
+    B: CSR | None = None  # generalized problem A x = lambda B x (None: B = I)
     # Krylov steps over all (node, column) pairs of one full solve, as measured
     # on the GPU path; scales timed samples of the CPU oracle to a full solve
     krylov_steps_full_solve: int | None = None
@@ -311,6 +312,35 @@ def workload_lap3d_64_interior(seed: int = 0, precision: str = "fp32", alpha: fl
     wl.two_pass = two_pass
     if two_pass:
         wl.name += "_twopass"
+    return wl
+
+
+def _gap_count(ev: np.ndarray, target: int, rel: float = 1e-3) -> int:
+    """Smallest count >= target whose next eigenvalue lies rel * ev[count] or
+    more above the last one (an interval endpoint in a spectral gap)."""
+    for c in range(target, len(ev) - 1):
+        if ev[c] - ev[c - 1] > rel * ev[c]:
+            return c
+    raise ValueError("no gap")
+
+
+def workload_fem3d(N: int = 64, target: int = 50, precision: str = "fp32") -> Workload:
+    """Generalized problem K x = lambda M x of Q1 trilinear finite elements on an
+    N^3 interior grid (27-point K and M on one pattern; closed-form spectrum),
+    the lowest eigenvalues up to the first spectral gap at or after `target`
+    (54 pairs at N = 64), m0 = 1.5 count + 2, 12 Gauss-Legendre nodes on the
+    upper half circle, per-node GMRES with at most 32 steps and alpha = 1e-2
+    (FP32 basis with the residual form, or FP64)."""
+    K, M = fem_q1((N, N, N))
+    ev = fem_q1_eigs((N, N, N))
+    cnt = _gap_count(ev, target)
+    emax = 0.5 * (ev[cnt - 1] + ev[cnt])
+    m0 = int(1.5 * cnt) + 2
+    wl = Workload(f"fem3d_{N}^3_lowest{cnt}_m0_{m0}_gl12_gmres32_{precision}", K, 0.0, emax,
+                  m0=m0, nc=12, rule="gl_half", inner_iters=32, alpha=1e-2, seed=0,
+                  expected_count=cnt)
+    wl.precision = precision
+    wl.B = M
     return wl
 
 
