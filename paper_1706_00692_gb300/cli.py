@@ -1,6 +1,7 @@
 """Run one IFEAST solve of a named synthetic workload and report the result.
 
-    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_twopass|lap3d_64_fp64|lap2d_50]
+    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_twopass|lap3d_64_fp64|lap2d_50|
+                                                     fem3d_64|fem3d_64_fp64|fem3d_48]
                                          [--max-outer M] [--inner-iters K] [--verbose]
 
 Prints one JSON line: status, eigenpairs found, largest residual, outer
@@ -28,6 +29,12 @@ def workload(name: str):
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp16")
     if name == "lap3d_64_twopass":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp32", two_pass=True)
+    if name == "fem3d_64":
+        return inputs.workload_fem3d(64, 50, precision="fp32")
+    if name == "fem3d_64_fp64":
+        return inputs.workload_fem3d(64, 50, precision="fp64")
+    if name == "fem3d_48":
+        return inputs.workload_fem3d(48, 40, precision="fp32")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -43,7 +50,7 @@ def main(argv=None) -> int:
     k = a.inner_iters or wl.inner_iters
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
                inner_iters=k, alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass,
-               max_outer=a.max_outer,
+               max_outer=a.max_outer, B=wl.B,
                verbose=a.verbose)
     X0 = torch.as_tensor(wl.X0(), device="cuda")
     torch.cuda.synchronize()

@@ -195,33 +195,54 @@ k_spmm_shift_dot(int n, int C, int m0, const int32_t *__restrict__ rowptr,
   if (DOTS) block_store_partials<LMAX>(acc, s, C, c, K2, part);
 }
 
-// Block partials of h1_l = <V_l, W>, l = 0..s, for the columns still running
-// (the first Gram-Schmidt pass's coefficients). Kept out of the SpMM so that
-// the SpMM's gathers run at full occupancy: the s + 1 accumulators per thread
-// would otherwise hold registers through the whole gather loop.
-template <int LMAX, typename CT>
+// Block partials of h1_l = <V_l, W> for l in chunk blockIdx.z (l = 8 z ..
+// 8 z + 7, l <= s), for the columns still running: the first Gram-Schmidt
+// pass's coefficients. They run in their own kernel, in chunks of 8 basis
+// vectors, so that each thread holds 8 accumulators instead of s + 1 and many
+// blocks stay resident (the kernel streams the basis: its speed is the number
+// of loads in flight), and so that the SpMM's gathers run at full occupancy.
+constexpr int kDotChunk = 8;
+
+template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 k_dots(int n, int C, const CT *__restrict__ V, size_t vstride, int s,
        const int *__restrict__ done, const CT *__restrict__ W, double2 *__restrict__ part,
        int rows, int K2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * 32 + lane;
+  const int l0 = blockIdx.z * kDotChunk;
   const bool active = c < C && done[c] == 0;
-  CT acc[LMAX];
+  CT acc[kDotChunk];
 #pragma unroll
-  for (int l = 0; l < LMAX; ++l) acc[l] = Cx<CT>::make(0, 0);
+  for (int l = 0; l < kDotChunk; ++l) acc[l] = Cx<CT>::make(0, 0);
   const int r0 = blockIdx.x * rows;
   const int r1 = min(n, r0 + rows);
+  const CT *__restrict__ Vc = V + (size_t)l0 * vstride;
   if (active) {
     for (int r = r0 + warp; r < r1; r += kWarps) {
       const size_t rc = (size_t)r * C + c;
       const CT w = W[rc];
 #pragma unroll
-      for (int l = 0; l < LMAX; ++l)
-        if (l <= s) cjfma(acc[l], V[(size_t)l * vstride + rc], w);
+      for (int l = 0; l < kDotChunk; ++l)
+        if (l0 + l <= s) cjfma(acc[l], Vc[(size_t)l * vstride + rc], w);
     }
   }
-  block_store_partials<LMAX>(acc, s, C, c, K2, part);
+  // fixed-order block sums (warp order) in FP64, one slot at a time
+  __shared__ double2 red[kWarps][32];
+#pragma unroll
+  for (int l = 0; l < kDotChunk; ++l) {
+    if (l0 + l <= s) {  // uniform over the block
+      red[warp][lane] = make_double2((double)acc[l].x, (double)acc[l].y);
+      __syncthreads();
+      if (warp == 0) {
+        double2 t = red[0][lane];
+#pragma unroll
+        for (int q = 1; q < kWarps; ++q) t = cadd(t, red[q][lane]);
+        if (c < C) part[((size_t)blockIdx.x * K2 + l0 + l) * C + c] = t;
+      }
+      __syncthreads();
+    }
+  }
 }
 
 // out[l * C + c] = sum over blocks b (in order) of part[(b * K2 + l) * C + c].
@@ -537,8 +558,9 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
   else
     IFEAST_SPMM_LAUNCH(1);
 #undef IFEAST_SPMM_LAUNCH
-  k_dots<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.done, W, a.part,
-                                              a.tl.rows, K2);
+  const dim3 gdots(a.tl.P, a.tl.tiles, (s + 1 + kDotChunk - 1) / kDotChunk);
+  k_dots<CT><<<gdots, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.done, W, a.part,
+                                                a.tl.rows, K2);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 1, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H1);
