@@ -407,7 +407,10 @@ def run_serve(args):
     whose stored Lanczos basis would exceed 8 GB runs in the two-pass mode
     (three basis vectors). Reports converged eigenpairs/s over the makespan and
     p50/p99 request latency, and the same stream served one request at a time
-    for comparison."""
+    for comparison. A second, smaller stream (16 requests, n up to 5e4) is run
+    three ways: served (mixed precision, 8 at once), one at a time in the same
+    form, and one at a time in the plain FP64 form of Algorithm 2 (per-node
+    GMRES, at most 32 steps, alpha = 1e-2), all to residual 1e-10."""
     import torch
     from paper_1706_00692_gb300 import Server, inputs
     from paper_1706_00692_gb300.build import build
@@ -422,10 +425,13 @@ def run_serve(args):
     two_pass = [(K + 1) * r.A.n * r.m0 * 4 > (8 << 30) for r in reqs]
     warm = inputs.serving_requests(3, seed=999, n_max=2e4)
 
-    def serve(max_active, timed_arrivals):
+    mixed = dict(inner="minres", inner_iters=K, alpha=3e-2, precision="fp32")
+    plain = dict(inner="gmres", inner_iters=32, alpha=1e-2, precision="fp64")
+
+    def serve(max_active, timed_arrivals, reqs=reqs, two_pass=two_pass, form=mixed):
         srv = Server(160 << 30, max_active=max_active, device=local)
         for r in warm:  # load kernels, warm the allocator
-            srv.wait(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half"))
+            srv.wait(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half", **form))
         ids = []
         t0 = time.perf_counter()
         for r, tp in zip(reqs, two_pass):
@@ -434,7 +440,7 @@ def run_serve(args):
                 if dt > 0:
                     time.sleep(dt)
             ids.append(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half",
-                                  inner_iters=K, two_pass=tp))
+                                  two_pass=tp, **form))
         outs = [srv.wait(i) for i in ids]
         span = time.perf_counter() - t0
         srv.close()
@@ -449,6 +455,17 @@ def run_serve(args):
     with ClockSampler(local) as clk:
         pairs, span, lat, failed = serve(8, True)
     pairs1, span1, lat1, failed1 = serve(1, False)
+    # the mixed-precision served form against the plain FP64 form, one request at a time
+    small = inputs.serving_requests(16, seed=1234, rate=args.rate, n_max=5e4)
+    nosplit = [False] * len(small)
+    cmp = {}
+    for name, ma, timed, form in [("served_mixed", 8, True, mixed),
+                                  ("one_at_a_time_mixed", 1, False, mixed),
+                                  ("one_at_a_time_plain_fp64", 1, False, plain)]:
+        pr, sp, la, fa = serve(ma, timed, small, nosplit, form)
+        cmp[name] = {"value": pr / sp, "pairs": pr, "makespan_s": sp, "failed": fa,
+                     "p50_ms": float(np.percentile(la, 50)),
+                     "p99_ms": float(np.percentile(la, 99))}
     from paper_1706_00692_gb300.replicas import job_throughput
     _, _, value = job_throughput(pairs, span, device=torch.device("cuda", local))
     if rank == 0:
@@ -468,6 +485,10 @@ def run_serve(args):
                 "failed": failed, "pairs": pairs, "requests": len(reqs),
                 "one_at_a_time": {"value": pairs1 / span1, "makespan_s": span1,
                                   "failed": failed1},
+                "vs_plain_fp64": {"stream": "16 requests, n 1e3-5e4, m0 16-128, seed 1234",
+                                  "plain_form": "per-node GMRES FP64, <= 32 steps, alpha 1e-2",
+                                  "mixed_form": "shared-basis MINRES FP32, <= 300 steps, "
+                                                "alpha 3e-2", **cmp},
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:
