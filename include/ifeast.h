@@ -295,19 +295,29 @@ int ifeast_rayleigh_ritz_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr,
                                  void *stream);
 
 /* ---------------------------------------------------------------------------
- * Kernel timing. When on, every kernel launch of the handle is bracketed by
+ * Kernel timing. on = 1: every kernel launch of the handle is bracketed by
  * CUDA events on the handle's stream (a few microseconds of overhead per
  * launch); the durations are summed per kernel class when the library next
- * synchronises its stream.
+ * synchronises its stream. on = N >= 2: the same, except that only launches
+ * 1, 1 + N, 1 + 2N, ... of the Lanczos step and Givens kernels are timed: an
+ * event between two of those kernels stops the second from launching while the
+ * first runs (programmatic dependent launch), so timing all of them slows the
+ * solve being timed. on = 0: off. A negative on returns IFEAST_ERR_INVALID_ARG.
  * ------------------------------------------------------------------------- */
 int ifeast_set_profiling(ifeast_t h, int on);
 
-/* Copies the summed milliseconds and launch counts of the first cap kernel
- * classes (device time between the bracketing events) into ms[] and
+/* Copies the summed milliseconds and the counts of timed launches of the first
+ * cap kernel classes (device time between the bracketing events) into ms[] and
  * launches[] (either may be NULL); reset != 0 clears them afterwards.
  * Returns the number of kernel classes (21; each class is one kernel) on success; a NULL handle or a
  * negative cap returns IFEAST_ERR_INVALID_ARG (1). */
 int ifeast_kernel_times(ifeast_t h, int cap, double *ms, int64_t *launches, int reset);
+
+/* All launches (timed or not) of the first cap kernel classes since profiling
+ * was switched on or last reset; reset != 0 clears them afterwards. Returns the
+ * number of kernel classes, or IFEAST_ERR_INVALID_ARG for a NULL handle or a
+ * negative cap. */
+int ifeast_kernel_launches(ifeast_t h, int cap, int64_t *launches, int reset);
 
 /* Name of kernel class k (static storage), "unknown" out of range. */
 const char *ifeast_kernel_name(int k);

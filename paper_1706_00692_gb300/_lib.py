@@ -91,6 +91,7 @@ SIGNATURES = {
                                      ct.c_void_p]),
     "ifeast_set_profiling": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "ifeast_kernel_times": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "ifeast_kernel_launches": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int]),
     "ifeast_kernel_name": (ct.c_char_p, [ct.c_int]),
     "ifeast_server_create": (ct.c_int, [ct.POINTER(ServerOpts), ct.POINTER(ct.c_void_p)]),
     "ifeast_server_submit": (ct.c_int, [ct.c_void_p, ct.POINTER(Csr), ct.POINTER(Contour), ct.c_int,

@@ -1134,7 +1134,7 @@ int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0,
 }
 
 int ifeast_set_profiling(ifeast_t h, int on) {
-  if (!h) return IFEAST_ERR_INVALID_ARG;
+  if (!h || on < 0) return IFEAST_ERR_INVALID_ARG;
   if (on && !h->prof.events) {
     const int cap = 4096;
     h->prof.events = new (std::nothrow) cudaEvent_t[2 * cap];
@@ -1153,6 +1153,10 @@ int ifeast_set_profiling(ifeast_t h, int on) {
   }
   h->prof.stream = h->stream;
   h->prof.used = 0;
+  h->prof.sample_every = on > 1 ? on : 1;
+  h->prof.skipping = false;
+  if (on)
+    for (long long &c : h->prof.launches) c = 0;
   h->profiling = on != 0;
   return IFEAST_OK;
 }
@@ -1168,6 +1172,15 @@ int ifeast_kernel_times(ifeast_t h, int cap, double *ms, int64_t *launches, int 
       h->prof.ms[k] = 0.0;
       h->prof.count[k] = 0;
     }
+  return K_COUNT;
+}
+
+int ifeast_kernel_launches(ifeast_t h, int cap, int64_t *launches, int reset) {
+  if (!h || cap < 0) return IFEAST_ERR_INVALID_ARG;
+  for (int k = 0; k < K_COUNT && k < cap; ++k)
+    if (launches) launches[k] = h->prof.launches[k];
+  if (reset)
+    for (int k = 0; k < K_COUNT; ++k) h->prof.launches[k] = 0;
   return K_COUNT;
 }
 

@@ -48,7 +48,12 @@ struct Profiler {
   int cap = 0, used = 0;
   int *kid = nullptr;             // kernel class of each pending pair
   double ms[K_COUNT] = {0};
-  long long count[K_COUNT] = {0};
+  long long count[K_COUNT] = {0};     // timed launches
+  long long launches[K_COUNT] = {0};  // all launches
+  // > 1: only every sample_every-th launch of the Lanczos step and Givens
+  // kernels is timed (events between them stop their programmatic overlap)
+  int sample_every = 1;
+  bool skipping = false;
   void begin(int k);
   void end();
   int collect();                  // after a stream synchronisation

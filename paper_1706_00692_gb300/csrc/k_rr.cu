@@ -1231,12 +1231,20 @@ cudaError_t spmm_block(int n, int m, const int32_t *rowptr, const int32_t *colid
 }
 
 void Profiler::begin(int k) {
-  if (used >= cap) return;  // pool full: the launch goes untimed
+  ++launches[k];
+  // sampling: time launch 1, 1 + N, 1 + 2N, ... of the per-step Lanczos kernels
+  skipping = sample_every > 1 && (k == K_LZ_STEP || k == K_LZ_GIVENS) &&
+             (launches[k] - 1) % sample_every != 0;
+  if (skipping || used >= cap) return;  // pool full: the launch goes untimed
   kid[used] = k;
   cudaEventRecord(events[2 * used], stream);
 }
 
 void Profiler::end() {
+  if (skipping) {
+    skipping = false;
+    return;
+  }
   if (used >= cap) return;
   cudaEventRecord(events[2 * used + 1], stream);
   ++used;

@@ -226,18 +226,27 @@ class Solver:
         return W
 
     # ------------------------------------------------------------------ timing
-    def set_profiling(self, on: bool = True):
-        rc = self.lib.ifeast_set_profiling(self.h, 1 if on else 0)
+    def set_profiling(self, on: bool | int = True):
+        """True/1: time every launch; N >= 2: time every N-th launch of the
+        Lanczos step and Givens kernels (and every other launch); False: off."""
+        rc = self.lib.ifeast_set_profiling(self.h, int(on))
         if rc:
             raise IFEASTError(rc, "ifeast_set_profiling")
 
     def kernel_times(self, reset: bool = False) -> dict:
-        """{kernel class: (launches, total ms)} measured with CUDA events."""
+        """{kernel class: (timed launches, their total ms)} measured with CUDA events."""
         ms = np.zeros(32)
         cnt = np.zeros(32, dtype=np.int64)
         k = self.lib.ifeast_kernel_times(self.h, 32, ms.ctypes.data, cnt.ctypes.data,
                                          1 if reset else 0)
         return {self.lib.ifeast_kernel_name(i).decode(): (int(cnt[i]), float(ms[i]))
+                for i in range(k) if cnt[i] > 0}
+
+    def kernel_launches(self, reset: bool = False) -> dict:
+        """{kernel class: launches} since profiling was switched on (timed or not)."""
+        cnt = np.zeros(32, dtype=np.int64)
+        k = self.lib.ifeast_kernel_launches(self.h, 32, cnt.ctypes.data, 1 if reset else 0)
+        return {self.lib.ifeast_kernel_name(i).decode(): int(cnt[i])
                 for i in range(k) if cnt[i] > 0}
 
     def close(self):

@@ -257,3 +257,28 @@ def test_two_pass_solve_is_bit_identical(torch):
     assert np.array_equal(res[0][0], res[1][0])
     assert np.array_equal(res[0][1], res[1][1])
     assert np.abs(res[1][0] - ev[i0:i0 + cnt]).max() / np.abs(ev).max() <= 1e-10
+
+
+def test_sampled_profiling_counts(torch):
+    """set_profiling(N): the Lanczos step and Givens kernels are timed in one
+    step of N (launches 1, 1 + N, ...), every other kernel at every launch, and
+    all launches are counted."""
+    from paper_1706_00692_gb300 import Solver
+    A, ev, emin, emax, i0, cnt = _interior_problem()
+    S = Solver(A, emin, emax, 2 * cnt, nc=8, rule="trap_half", inner="minres", inner_iters=300,
+               alpha=3e-2, precision="fp32", max_outer=3)
+    S.set_profiling(4)
+    S.kernel_times(reset=True)
+    S.kernel_launches(reset=True)
+    S.solve(inputs.initial_subspace(A.n, 2 * cnt, 0))
+    timed = S.kernel_times(reset=True)
+    launches = S.kernel_launches(reset=True)
+    S.set_profiling(False)
+    for k, n in launches.items():
+        c = timed[k][0]
+        if k in ("lanczos_step", "lanczos_givens"):
+            assert c == (n + 3) // 4, (k, n, c)
+        else:
+            assert c == n, (k, n, c)
+    assert launches["lanczos_step"] > 8
+    S.close()
