@@ -282,3 +282,32 @@ def test_sampled_profiling_counts(torch):
             assert c == n, (k, n, c)
     assert launches["lanczos_step"] > 8
     S.close()
+
+
+def test_full_size_lap3d_64_properties(torch):
+    """The bench's 64^3 workload in the bench's configuration (n = 262,144,
+    m0 = 80, 8 trapezoid nodes, FP32 shared-basis MINRES): a full oracle solve
+    takes hours, so the returned pairs are checked by properties that hold at
+    any size. Every pair inside the window has an independent FP64 residual
+    ||A x - lam x|| / ||A x|| <= 2e-10 recomputed on the CPU, the vectors are
+    orthonormal, the values are inside the window and inside the Weyl bounds
+    of the potential (eigenvalues of L + V lie in [lam_min(L), lam_max(L) + 1]),
+    and the 56 eigenvalues the window holds are all found."""
+    from paper_1706_00692_gb300 import Solver
+    wl = inputs.workload_lap3d_64_interior()
+    S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
+               inner_iters=wl.inner_iters, alpha=wl.alpha, precision=wl.precision)
+    rc = S.solve(wl.X0())
+    lam, X, res = S.eigenpairs()
+    S.close()
+    assert rc == 0, rc
+    assert lam.size == wl.expected_count == 56
+    assert ((lam > wl.emin) & (lam < wl.emax)).all()
+    assert res.max() <= 1e-10
+    As = wl.A.to_scipy()
+    AX = As @ X
+    r = np.linalg.norm(AX - X * lam[None, :], axis=0) / np.linalg.norm(AX, axis=0)
+    assert r.max() <= 2e-10
+    assert np.abs(X.T @ X - np.eye(lam.size)).max() <= 1e-9
+    evL = inputs.laplacian_eigs((64, 64, 64))
+    assert evL[0] <= lam.min() and lam.max() <= evL[-1] + 1.0
