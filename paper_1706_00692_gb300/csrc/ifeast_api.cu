@@ -81,6 +81,15 @@ struct ifeast_ctx {
 
 namespace {
 
+// out[r * ld + q] = X[r * m0 + j0 + q], q < cnt: the in-interval Ritz vectors
+__global__ void k_gather_columns(int64_t n, int m0, int j0, int cnt, int ld,
+                                 const double *__restrict__ X, double *__restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)n * cnt) return;
+  const size_t r = i / cnt, q = i % cnt;
+  out[r * ld + q] = X[r * m0 + j0 + q];
+}
+
 struct Layout {
   size_t off = 0;
   template <typename T>
@@ -1078,10 +1087,23 @@ int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *
   if (resid && cnt) CK(cudaMemcpy(resid, rs.data(), cnt * sizeof(double), kind));
   if (evecs && cnt) {
     // the in-interval columns are contiguous in the ascending order: idx[0]..idx[cnt-1]
-    const cudaMemcpyKind k2 = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    CK(cudaMemcpy2DAsync(evecs, (size_t)cap * sizeof(double), h->X + idx[0],
-                         (size_t)h->m0 * sizeof(double), cnt * sizeof(double), (size_t)h->n, k2,
+    const size_t total = (size_t)h->n * cnt;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (out_on_device) {  // gathered straight into the caller's n x cap block
+      k_gather_columns<<<blocks, 256, 0, h->stream>>>(h->n, h->m0, idx[0], cnt, cap, h->X, evecs);
+      CK(cudaGetLastError());
+    } else if (cap == cnt) {
+      // gathered into the A Q scratch block (free after the solve), then one
+      // contiguous copy: a strided copy of 8 cnt bytes per row is far slower
+      k_gather_columns<<<blocks, 256, 0, h->stream>>>(h->n, h->m0, idx[0], cnt, cnt, h->X, h->AQ);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(evecs, h->AQ, total * sizeof(double), cudaMemcpyDeviceToHost,
                          h->stream));
+    } else {  // wider host block: only the cnt columns may be written
+      CK(cudaMemcpy2DAsync(evecs, (size_t)cap * sizeof(double), h->X + idx[0],
+                           (size_t)h->m0 * sizeof(double), cnt * sizeof(double), (size_t)h->n,
+                           cudaMemcpyDeviceToHost, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
   }
   return IFEAST_OK;
