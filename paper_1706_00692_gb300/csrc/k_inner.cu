@@ -77,60 +77,31 @@ __device__ __forceinline__ CT to_ct(double2 a) {
   return Cx<CT>::make((R)a.x, (R)a.y);
 }
 
-// Sums LMAX register accumulators of the 8 warps of a block (lane = column)
-// in FP64 and writes them as this block's partials part[(blk * K2 + l) * C + c],
-// l <= s. (FP32 accumulators are the per-thread sums of the FP32 kernels.)
-template <int LMAX, typename CT>
-__device__ __forceinline__ void block_store_partials(const CT (&acc)[LMAX], int s, int C, int c,
-                                                     int K2, double2 *__restrict__ part) {
-  __shared__ double2 red[kWarps][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int l = 0; l < LMAX; ++l) {
-    if (l <= s) {  // s is uniform over the block
-      red[warp][lane] = make_double2((double)acc[l].x, (double)acc[l].y);
-      __syncthreads();
-      if (warp == 0) {
-        double2 t = red[0][lane];
-#pragma unroll
-        for (int w = 1; w < kWarps; ++w) t = cadd(t, red[w][lane]);
-        if (c < C) part[((size_t)blockIdx.x * K2 + l) * C + c] = t;
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// W = z_{node(c)} B V_s - A V_s on every active column; with DOTS also the
-// block partials of <V_l, W>, l = 0..s. CT: complex type of the basis (the
-// arithmetic is done in its precision). BM: B = I (0), B with a pattern of its
+// W = z_{node(c)} B V_s - A V_s on every active column (the first-pass dots
+// follow in k_dots). CT: complex type of the basis (the arithmetic is done in
+// its precision). BM: B = I (0), B with a pattern of its
 // own (1), or B on A's pattern (2: one gather of V serves both products, valB
 // indexed like val). A row's non-zeros are taken in groups of kNG: the group's
 // indices and values are loaded together, then its gathers are issued before
 // they are used, so that kNG loads per warp are in flight.
 constexpr int kNG = 8;
 
-template <int LMAX, bool DOTS, typename CT, int BM>
+template <typename CT, int BM>
 __global__ void __launch_bounds__(kThreads)
-k_spmm_shift_dot(int n, int C, int m0, const int32_t *__restrict__ rowptr,
-                 const int32_t *__restrict__ colidx, const typename Cx<CT>::R *__restrict__ val,
-                 const CT *__restrict__ V, size_t vstride, int s, const double2 *__restrict__ z,
-                 const int *__restrict__ done, CT *__restrict__ W, double2 *__restrict__ part,
-                 int rows, int K2, const int32_t *__restrict__ rowptrB,
-                 const int32_t *__restrict__ colidxB,
-                 const typename Cx<CT>::R *__restrict__ valB) {
+k_spmm_shift(int n, int C, int m0, const int32_t *__restrict__ rowptr,
+             const int32_t *__restrict__ colidx, const typename Cx<CT>::R *__restrict__ val,
+             const CT *__restrict__ Vs, const double2 *__restrict__ z,
+             const int *__restrict__ done, CT *__restrict__ W, int rows,
+             const int32_t *__restrict__ rowptrB, const int32_t *__restrict__ colidxB,
+             const typename Cx<CT>::R *__restrict__ valB) {
   using R = typename Cx<CT>::R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * 32 + lane;
   const bool active = c < C && (done == nullptr || done[c] == 0);
   const CT zc = (c < C) ? to_ct<CT>(z[c / m0]) : Cx<CT>::make(0, 0);
-  const CT *__restrict__ Vs = V + (size_t)s * vstride;
   const int r0 = blockIdx.x * rows;
   const int r1 = min(n, r0 + rows);
   const CT zero = Cx<CT>::make(0, 0);
-  CT acc[LMAX];
-#pragma unroll
-  for (int l = 0; l < LMAX; ++l) acc[l] = zero;
   if (active) {
     for (int r = r0 + warp; r < r1; r += kWarps) {
       const size_t rc = (size_t)r * C + c;
@@ -185,14 +156,8 @@ k_spmm_shift_dot(int n, int C, int m0, const int32_t *__restrict__ rowptr,
       w.x -= av.x;
       w.y -= av.y;
       W[rc] = w;
-      if (DOTS) {
-#pragma unroll
-        for (int l = 0; l < LMAX; ++l)
-          if (l <= s) cjfma(acc[l], V[(size_t)l * vstride + rc], w);
-      }
     }
   }
-  if (DOTS) block_store_partials<LMAX>(acc, s, C, c, K2, part);
 }
 
 // Block partials of h1_l = <V_l, W> for l in chunk blockIdx.z (l = 8 z ..
@@ -547,10 +512,10 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
     valB = a.valB32;
   }
   IFEAST_PROF_BEGIN(a.prof, K_GM_SPMM);
-#define IFEAST_SPMM_LAUNCH(BM)                                                                 \
-  k_spmm_shift_dot<1, false, CT, BM><<<grid, kThreads, 0, st>>>(                               \
-      a.n, a.C, a.m0, a.rowptr, a.colidx, val, V, vstride, s, a.z, a.done, W, a.part, a.tl.rows, \
-      K2, a.rowptrB, a.colidxB, valB)
+#define IFEAST_SPMM_LAUNCH(BM)                                                            \
+  k_spmm_shift<CT, BM><<<grid, kThreads, 0, st>>>(a.n, a.C, a.m0, a.rowptr, a.colidx, val,   \
+                                                  V + (size_t)s * vstride, a.z, a.done, W,  \
+                                                  a.tl.rows, a.rowptrB, a.colidxB, valB)
   if (!a.rowptrB)
     IFEAST_SPMM_LAUNCH(0);
   else if (a.b_same_pattern)
@@ -651,13 +616,11 @@ cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
                             const double2 *z, RowTiling tl, cudaStream_t st,
                             const int32_t *rowptrB, const int32_t *colidxB, const double *valB) {
   if (rowptrB)
-    k_spmm_shift_dot<1, false, double2, 1><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
-        n, ncols, m0, rowptr, colidx, val, V, (size_t)n * ncols, 0, z, nullptr, W, nullptr,
-        tl.rows, 0, rowptrB, colidxB, valB);
+    k_spmm_shift<double2, 1><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
+        n, ncols, m0, rowptr, colidx, val, V, z, nullptr, W, tl.rows, rowptrB, colidxB, valB);
   else
-    k_spmm_shift_dot<1, false, double2, 0><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
-        n, ncols, m0, rowptr, colidx, val, V, (size_t)n * ncols, 0, z, nullptr, W, nullptr,
-        tl.rows, 0, nullptr, nullptr, nullptr);
+    k_spmm_shift<double2, 0><<<dim3(tl.P, tl.tiles), kThreads, 0, st>>>(
+        n, ncols, m0, rowptr, colidx, val, V, z, nullptr, W, tl.rows, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
