@@ -779,24 +779,32 @@ __device__ __forceinline__ void load_column_mask(int m0, int nc, const int *__re
   __syncthreads();
 }
 
-// Q accumulation of the second pass: Qacc[r][j] += cf[s][j] v_s[r][j] in FP32
-// fused multiply-adds, in step order (the same sums as k_lz_quadrature4).
+// Q accumulation of the second pass: Qacc[r][j] += cf[l][j] v_l[r][j] in FP32
+// fused multiply-adds, in step order (the same sums as k_lz_quadrature4). The
+// terms are added two steps at a time, at odd s (v_{s-1} is the row's own
+// value the step already loaded), and at a column's last step when that step
+// is even: one read-modify-write of Qacc per two steps.
 __device__ __forceinline__ void accumulate_q(const Pass2 &p2, int m0, int s, size_t off, int q4,
-                                             const float (&v)[4], const bool (&act)[4],
-                                             bool all4) {
-  const float *c = p2.cf + (size_t)s * m0 + q4;
-  if (all4) {
-    float4 qv = *reinterpret_cast<const float4 *>(p2.Qacc + off);
-    qv.x = fmaf(c[0], v[0], qv.x);
-    qv.y = fmaf(c[1], v[1], qv.y);
-    qv.z = fmaf(c[2], v[2], qv.z);
-    qv.w = fmaf(c[3], v[3], qv.w);
-    *reinterpret_cast<float4 *>(p2.Qacc + off) = qv;
-  } else {
+                                             const float (&v)[4], const float (&vprev)[4],
+                                             const bool (&act)[4]) {
+  const bool odd = s & 1;
+  bool cur[4], any = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (act[i]) p2.Qacc[off + i] = fmaf(c[i], v[i], p2.Qacc[off + i]);
+  for (int i = 0; i < 4; ++i) {
+    cur[i] = act[i] && (odd || s == p2.Sj[q4 + i] - 1);
+    any = any || cur[i];
   }
+  if (!any) return;
+  const float *c = p2.cf + (size_t)s * m0 + q4;
+  float4 qv = *reinterpret_cast<const float4 *>(p2.Qacc + off);
+  float q[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!cur[i]) continue;
+    if (odd) q[i] = fmaf(c[i - m0], vprev[i], q[i]);  // step s - 1 (active: s - 1 < s < Sj)
+    q[i] = fmaf(c[i], v[i], q[i]);
+  }
+  *reinterpret_cast<float4 *>(p2.Qacc + off) = make_float4(q[0], q[1], q[2], q[3]);
 }
 
 template <typename S, bool FIRST>
@@ -879,7 +887,10 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
       float vo[4];
       finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout, off, vv, vw,
                            ww, vo);
-      if (p2.Qacc != nullptr) accumulate_q(p2, m0, s, off, 4 * q, vo, act, all4);
+      if (p2.Qacc != nullptr) {
+        const float vp[4] = {o2.x, o2.y, o2.z, o2.w};
+        accumulate_q(p2, m0, s, off, 4 * q, vo, vp, act);
+      }
     }
   }
   store_partials_f(vv, vw, ww, m0, stride_items, part);
@@ -998,7 +1009,10 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
       float vo[4];
       finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout,
                            (size_t)(r * m0 + q4), vv, vw, ww, vo);
-      if (p2.Qacc != nullptr) accumulate_q(p2, m0, s, (size_t)(r * m0 + q4), q4, vo, act, all4);
+      if (p2.Qacc != nullptr) {
+        const float vp[4] = {o2.x, o2.y, o2.z, o2.w};
+        accumulate_q(p2, m0, s, (size_t)(r * m0 + q4), q4, vo, vp, act);
+      }
     }
   }
   store_partials_f(vv, vw, ww, m0, stride_items, part);
