@@ -200,7 +200,18 @@ def test_strerror_and_null_handles(lib):
         assert lib.ifeast_strerror(code)
     assert lib.ifeast_solve(None, None, 0) == _lib.IFEAST_ERR_INVALID_ARG
     assert lib.ifeast_get_stats(None, None) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_set_profiling(None, 1) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_kernel_times(None, 4, None, None, 0) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_kernel_launches(None, 4, None, 0) == _lib.IFEAST_ERR_INVALID_ARG
     lib.ifeast_destroy(None)
+
+
+def test_kernel_class_names(lib):
+    """21 kernel classes with distinct names; the profiler's sampled classes exist."""
+    names = [lib.ifeast_kernel_name(k).decode() for k in range(21)]
+    assert len(set(names)) == 21 and "unknown" not in names
+    assert {"lanczos_step", "lanczos_givens", "gmres_spmm_dot"} <= set(names)
+    assert lib.ifeast_kernel_name(21).decode() == "unknown"
 
 
 def test_product_path_has_no_oracle_import():

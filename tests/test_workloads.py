@@ -1,0 +1,43 @@
+"""Host-side checks of the synthetic workloads the bench and the CLI use: the
+interval endpoints sit in spectral gaps of the closed-form spectra, and the
+counts, subspace sizes and names are the ones the bench reports."""
+import numpy as np
+
+from paper_1706_00692_gb300 import inputs
+
+
+def test_fem3d_workload_interval_and_sizes():
+    wl = inputs.workload_fem3d(64, 50, precision="fp32")
+    ev = inputs.fem_q1_eigs((64, 64, 64))
+    inside = (ev > wl.emin) & (ev < wl.emax)
+    assert inside.sum() == wl.expected_count == 54
+    assert wl.m0 == int(1.5 * 54) + 2 == 83
+    # the upper endpoint is the midpoint of a gap of at least 1e-3 relative
+    k = wl.expected_count
+    assert ev[k] - ev[k - 1] > 1e-3 * ev[k]
+    assert abs(wl.emax - 0.5 * (ev[k - 1] + ev[k])) <= 1e-12 * ev[k]
+    assert wl.A.n == wl.B.n == 64 ** 3 and wl.A.nnz == wl.B.nnz
+    assert (wl.A.rowptr == wl.B.rowptr).all() and (wl.A.colidx == wl.B.colidx).all()
+    assert wl.name.startswith("fem3d_64^3_lowest54_m0_83")
+
+
+def test_fem3d_small_gap_count():
+    wl = inputs.workload_fem3d(12, 10, precision="fp64")
+    ev = inputs.fem_q1_eigs((12, 12, 12))
+    assert ((ev > wl.emin) & (ev < wl.emax)).sum() == wl.expected_count >= 10
+    assert wl.precision == "fp64"
+
+
+def test_lap3d_64_window_parameters():
+    """The bench window of the 64^3 Laplacian + U[0,1) potential: its 56
+    eigenvalues come from converged solves (the GPU test of the full-size
+    workload checks them); here the window lies in the part of the spectrum
+    the potential can reach (Weyl: every eigenvalue of L + V is within
+    [lam_min(L), lam_max(L) + 1]) and the solver parameters are the bench's."""
+    wl = inputs.workload_lap3d_64_interior()
+    evL = inputs.laplacian_eigs((64, 64, 64))
+    assert evL[0] < wl.emin < wl.emax < evL[-1] + 1.0
+    assert wl.expected_count == 56
+    assert wl.m0 == 80 and wl.nc == 8 and wl.rule == "trap_half"
+    assert wl.inner == "minres" and wl.inner_iters == 1500 and wl.alpha == 3e-2
+    assert np.isclose(wl.emax - wl.emin, 0.91001238 - 0.89754658)
