@@ -178,6 +178,17 @@ def test_solve_from_device_input_and_workspace_owned_by_library(torch):
     assert lam.is_cuda and X.shape == (wl.A.n, 10)
     ref = np.loadtxt(os.path.join(GOLDEN, "lap2d_50x50_lowest11.txt"))[:10]
     assert np.abs(lam.cpu().numpy() - ref).max() / ref.max() <= 1e-10
+    # the three output paths give the same vectors: device block, host block of
+    # exactly cnt columns, and a wider host block whose extra columns stay untouched
+    lam_h, X_h, res_h = S.eigenpairs()
+    assert (X.cpu().numpy() == X_h).all() and (res.cpu().numpy() == res_h).all()
+    import ctypes as ct
+    cap = 13
+    wide = np.full((wl.A.n, cap), 7.5)
+    m = ct.c_int(0)
+    rc = S.lib.ifeast_eigenpairs(S.h, cap, ct.byref(m), None, wide.ctypes.data, None, 0)
+    assert rc == 0 and m.value == 10
+    assert (wide[:, :10] == X_h).all() and (wide[:, 10:] == 7.5).all()
     S.close()
 
 
