@@ -65,7 +65,8 @@ typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } 
 /* Inner solver for Alg. 2 step 1.
  *   GMRES:  one complex GMRES per (node, column) pair, zero initial guess,
  *           classical Gram-Schmidt applied twice, Givens least squares
- *           (Sec. 2.2). inner_max_iters <= 32. FP64 only.
+ *           (Sec. 2.2). inner_max_iters <= 32. FP64, or FP32 (FP32 basis;
+ *           with the residual form below opts.correction_rf).
  *   MINRES: one real Lanczos basis per column of X, shared by all nc shifts
  *           (Sec. 3: the Krylov basis of (z I - A) does not depend on z); each
  *           (node, column) pair takes the minimal-residual solution on it
@@ -79,7 +80,9 @@ typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } 
 typedef enum { IFEAST_INNER_GMRES = 0, IFEAST_INNER_MINRES = 1 } ifeast_inner;
 
 /* Arithmetic of the inner solve (Krylov vectors, sparse products and their
- * inner products; FP32 and FP16 are accepted with IFEAST_INNER_MINRES only).
+ * inner products; FP32 with either inner solver, FP16 with IFEAST_INNER_MINRES
+ * only; FP32 GMRES needs a symmetric A, since its residual form takes real
+ * Ritz pairs).
  *   FP64: FP64 vectors and arithmetic.
  *   FP32: FP32 vectors and arithmetic.
  *   FP16: FP16 storage of the Lanczos vectors (half the bytes of FP32),
