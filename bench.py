@@ -111,6 +111,32 @@ def step_bytes(wl, elem):
     return 4 * n * m0 * elem + 4 * (n + 1) + nnz * (4 + val_elem)
 
 
+def kernel_stats(ktimes, klaunch):
+    """{class: (all launches, timed launches, ms per timed launch)} from the
+    library's timed launches and their summed ms, and its launch counts."""
+    return {k: (klaunch.get(k, c), c, t / c) for k, (c, t) in ktimes.items() if c > 0}
+
+
+def lanczos_roofline(kstat, wl, peak, peak_kind):
+    """Roofline entry of the Lanczos step kernel when it is the class with the
+    most estimated device time (all launches x ms per timed launch), else None:
+    algorithmic bytes per launch over the mean timed launch, against the peak."""
+    top = max(kstat.items(), key=lambda kv: kv[1][0] * kv[1][2]) if kstat else None
+    if top is None or top[0] != "lanczos_step":
+        return None
+    elem = {"fp16": 2, "fp32": 4}.get(wl.precision, 8)
+    launches, timed, ms_each = top[1]
+    nbytes = step_bytes(wl, elem)
+    achieved = nbytes / (ms_each * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "k_lanczos_step", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"{peak_kind} copy bandwidth",
+            "traffic": (ELL_STEP_TRAFFIC_LAP3D64
+                        if wl.name.startswith("lap3d_64") and wl.precision == "fp32" else None),
+            "bytes_per_launch": nbytes, "launches": launches,
+            "launches_timed": timed, "us_per_launch": 1e3 * ms_each}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -326,8 +352,7 @@ def run_ours(args):
     ktimes = S.kernel_times(reset=True)
     klaunch = S.kernel_launches(reset=True)
     S.set_profiling(False)
-    # per class: (all launches, timed launches, ms per timed launch)
-    kstat = {k: (klaunch.get(k, c), c, t / c) for k, (c, t) in ktimes.items() if c > 0}
+    kstat = kernel_stats(ktimes, klaunch)
     lam, X, res = S.eigenpairs()
     pairs = int((res <= 1e-10).sum())
     # replicas: converged pairs of every rank over the slowest rank's time
@@ -361,21 +386,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel class, from the live event timings
     peak, peak_kind = measured_peaks()
-    top = max(kstat.items(), key=lambda kv: kv[1][0] * kv[1][2]) if kstat else None
-    roofline = None
-    if top is not None and top[0] == "lanczos_step":
-        elem = {"fp16": 2, "fp32": 4}.get(wl.precision, 8)
-        launches, timed, ms_each = top[1]
-        nbytes = step_bytes(wl, elem)
-        achieved = nbytes / (ms_each * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_lanczos_step", "achieved": achieved,
-                    "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_source": f"{peak_kind} copy bandwidth",
-                    "traffic": (ELL_STEP_TRAFFIC_LAP3D64
-                                if wl.name.startswith("lap3d_64") and wl.precision == "fp32"
-                                else None),
-                    "bytes_per_launch": nbytes, "launches": launches,
-                    "launches_timed": timed, "us_per_launch": 1e3 * ms_each}
+    roofline = lanczos_roofline(kstat, wl, peak, peak_kind)
     gpu_launches = int(sum(klaunch.values()))
     if rank == 0:
         st = stats[-1]
