@@ -41,3 +41,18 @@ def test_lap3d_64_window_parameters():
     assert wl.m0 == 80 and wl.nc == 8 and wl.rule == "trap_half"
     assert wl.inner == "minres" and wl.inner_iters == 1500 and wl.alpha == 3e-2
     assert np.isclose(wl.emax - wl.emin, 0.91001238 - 0.89754658)
+
+
+def test_serving_requests_counts_match_dense_spectra():
+    """Each request's interval holds exactly its stated count of eigenvalues of
+    A = L + V (dense eigh on small requests): the potential is below a quarter
+    of the gap at the upper end, so by Weyl's bounds no eigenvalue crosses it;
+    m0 is a multiple of 4 at least the count; arrivals increase."""
+    reqs = inputs.serving_requests(12, seed=77, n_min=200, n_max=1500)
+    for r in reqs:
+        ev = np.linalg.eigvalsh(r.A.to_scipy().toarray())
+        inside = (ev > r.emin) & (ev < r.emax)
+        assert inside.sum() == r.count
+        assert r.m0 >= r.count and r.m0 % 4 == 0
+        assert r.X0.shape == (r.A.n, r.m0)
+    assert all(b.arrival > a.arrival for a, b in zip(reqs, reqs[1:]))
