@@ -1,7 +1,8 @@
 """Benchmark of the IFEAST hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload lap3d_64|lap3d_64_fp16|lap3d_64_twopass|lap3d_64_fp64|
+                    [--workload lap3d_64|lap3d_64_fp16|lap3d_64_bf16|lap3d_64_twopass|
+                                lap3d_64_fp64|
                                 lap2d_50|fem3d_64|fem3d_64_fp64|fem3d_48|serve]
 
 One step = one full IFEAST solve (Algorithm 2 from the seeded initial subspace
@@ -47,6 +48,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="lap3d_64", choices=["lap3d_64", "lap3d_64_fp16",
+                                                                 "lap3d_64_bf16",
                                                                  "lap3d_64_twopass",
                                                                  "lap3d_64_fp64", "lap2d_50",
                                                                  "fem3d_64", "fem3d_64_fp64",
@@ -68,6 +70,8 @@ def make_workload(name):
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp64")
     if name == "lap3d_64_fp16":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp16")
+    if name == "lap3d_64_bf16":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="bf16")
     if name == "lap3d_64_twopass":
         return inputs.workload_lap3d_64_interior(seed=0, precision="fp32", two_pass=True)
     if name == "fem3d_64":  # generalized K x = lambda M x, per-node FP32 GMRES
@@ -91,10 +95,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per launch of k_lanczos_step_ell<float, false, 8> on the 64^3 workload
-# (m0 = 80, FP32), dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture (profiles/k_lanczos_step_ell_lap3d64.md). Re-measure when that kernel
-# changes; None when unknown for the workload.
+# DRAM bytes per launch of the FP32 fixed-width Lanczos step kernel on the 64^3
+# workload (m0 = 80): dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture of that kernel at the bench's launch shape. Re-measure when the
+# kernel changes (None: not measured for the workload).
 ELL_STEP_TRAFFIC_LAP3D64 = 314.7e6
 
 # the Lanczos step and Givens kernels are timed in one step of PROFILE_EVERY
@@ -124,7 +128,7 @@ def lanczos_roofline(kstat, wl, peak, peak_kind):
     top = max(kstat.items(), key=lambda kv: kv[1][0] * kv[1][2]) if kstat else None
     if top is None or top[0] != "lanczos_step":
         return None
-    elem = {"fp16": 2, "fp32": 4}.get(wl.precision, 8)
+    elem = {"fp16": 2, "bf16": 2, "fp32": 4}.get(wl.precision, 8)
     launches, timed, ms_each = top[1]
     nbytes = step_bytes(wl, elem)
     achieved = nbytes / (ms_each * 1e-3) / 1e9
@@ -200,73 +204,117 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
-def oracle_sample(wl, budget_s=20.0, gpu_stats=None):
-    """Times the CPU oracle on the workload. For the 50x50 workload it runs the
-    oracle's Algorithm 2 to convergence. For the 64^3 workload a full oracle
-    solve takes hours, so it times the oracle's shared-basis GMRES
-    (gmres_shared_basis: Arnoldi with MGS + least squares, Section 3) on a
-    bounded number of (node, column) pairs and Krylov steps, and scales the
-    time per Krylov step to the Krylov steps a full solve takes (the workload's
-    recorded count from a GPU solve). Returns (pairs/s, text)."""
-    from oracle import ifeast_oracle as orc
-    z, w = orc.contour_nodes(wl.rule, wl.nc, wl.emin, wl.emax)
-    A = wl.A.to_scipy()
+def reduced_instance(wl):
+    """The oracle's sample of a workload too large for it: the same generator
+    at a size the CPU oracle solves completely in seconds. lap3d: the 3D 7-point
+    Laplacian + U[0,1) potential on 10^3 with the window at the same relative
+    position (first eigenvalue 0.4% into the spectrum; endpoints at the widest
+    gap within three eigenvalues of the targets), 10 pairs, m0 = 16, 8
+    trapezoid half-circle nodes, alpha = 3e-2, inner solves of at most 150
+    steps in residual form from the second iteration on. fem3d: the Q1 pencil
+    on 10^3, lowest eigenvalues to the first gap at or after 8, 12 GL nodes,
+    per-node GMRES (32 steps, alpha = 1e-2), residual form below ||R_F|| = 1e-3.
+    The window endpoints come from a dense eigvalsh of the small matrix."""
+    from paper_1706_00692_gb300 import inputs
     if wl.B is not None:
-        # generalized problem: the oracle's per-node GMRES on (z_k B - A) y = B x_j,
-        # timed on a bounded number of (node, column) systems and scaled to the
-        # Krylov steps the GPU solve took (all of its systems and iterations)
-        B = wl.B.to_scipy()
-        BX = B @ wl.X0()
-        done, steps_done, t0 = 0, 0, time.perf_counter()
-        while time.perf_counter() - t0 < budget_s and done < 64:
-            k, j = done % wl.nc, done // wl.nc
-            out = orc.gmres(lambda v, zk=z[k]: zk * (B @ v) - A @ v, BX[:, j], wl.inner_iters)
-            steps_done += out["steps"]
-            done += 1
-        dt = time.perf_counter() - t0
-        per_step = dt / max(steps_done, 1)
-        total_steps = (gpu_stats or {}).get("total_matvecs") or \
-            wl.inner_iters * wl.nc * wl.m0 * 10
-        est = per_step * total_steps
-        pairs = wl.expected_count or 0
-        return pairs / est, (f"oracle per-node GMRES on {wl.name}: {done} (node, column) systems, "
-                             f"{steps_done} Krylov steps in {dt:.1f} s = {per_step*1e3:.2f} ms "
-                             f"per step; scaled to {total_steps} Krylov steps of a full solve "
-                             f"({est/3600:.1f} h) for {pairs} pairs")
+        K, M = inputs.fem_q1((10, 10, 10))
+        ev = inputs.fem_q1_eigs((10, 10, 10))
+        cnt = inputs._gap_count(ev, 8)
+        emin, emax = 0.0, 0.5 * (ev[cnt - 1] + ev[cnt])
+        m0 = int(1.5 * cnt) + 2
+        return dict(name=f"fem3d_10^3_lowest{cnt}_m0_{m0}_gl12_gmres32", A=K, B=M, emin=emin,
+                    emax=emax, m0=m0, rule="gl_half", nc=12, k=32, alpha=1e-2,
+                    correction_rf=1e-3, count=cnt)
+    N = 10
+    A = inputs.add_diagonal_fast(inputs.laplacian((N, N, N)), inputs.random_potential(N ** 3, 1))
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+
+    def gap_at(i):
+        g = max(range(max(1, i - 3), i + 4), key=lambda c: ev[c] - ev[c - 1])
+        return g, 0.5 * (ev[g - 1] + ev[g])
+
+    i0, emin = gap_at(4)
+    i1, emax = gap_at(12)
+    m0 = int(np.ceil(1.43 * (i1 - i0) / 4) * 4)
+    return dict(name=f"lap3d_10^3_pot_interior{i1 - i0}_m0_{m0}_trap8", A=A, B=None, emin=emin,
+                emax=emax, m0=m0, rule="trap_half", nc=8, k=150, alpha=3e-2,
+                correction_rf=np.inf, count=i1 - i0)
+
+
+def oracle_sample(wl):
+    """Times the CPU oracle (the plain FP64 numpy/scipy Algorithm 2) on one
+    complete solve, from the seeded initial subspace to ||R_F|| <= 1e-10:
+    of the workload itself when it is the 50x50 one, else of its reduced
+    instance (reduced_instance). The per-node GMRES inner solver of the
+    oracle equals the shared-basis solver in exact arithmetic (Section 3).
+    Returns (converged pairs/s, text)."""
+    from oracle import ifeast_oracle as orc
     if wl.A.n > 100000:
-        X = wl.X0()
-        steps, pairs_done, t0 = 60, 0, time.perf_counter()
-        while time.perf_counter() - t0 < budget_s and pairs_done < 64:
-            k = pairs_done % wl.nc
-            j = pairs_done // wl.nc
-            orc.gmres_shared_basis(A, X[:, j], z[k], steps)
-            pairs_done += 1
-        dt = time.perf_counter() - t0
-        per_step = dt / (pairs_done * steps)
-        total_steps = wl.krylov_steps_full_solve or 16 * 1500 * wl.nc * wl.m0
-        est = per_step * total_steps
-        pairs = wl.expected_count or 0
-        return pairs / est, (f"oracle gmres_shared_basis on {wl.name}: {pairs_done} (node, column) "
-                             f"pairs x {steps} Krylov steps in {dt:.1f} s = {per_step*1e3:.2f} ms "
-                             f"per step; scaled to {total_steps} Krylov steps of a full solve "
-                             f"({est/3600:.1f} h) for {pairs} pairs")
-    t0 = time.perf_counter()
-    iters = [0]
-
-    def cb(it, lam, X, res, ins):
-        iters[0] = it
-        if time.perf_counter() - t0 > budget_s:
-            raise TimeoutError
-
-    try:
-        out = orc.ifeast(A, wl.X0(), wl.emin, wl.emax, z, w, inner="gmres", k=wl.inner_iters,
-                         alpha=wl.alpha, tol=1e-10, max_outer=200, callback=cb)
+        r = reduced_instance(wl)
+        A = r["A"].to_scipy()
+        B = None if r["B"] is None else r["B"].to_scipy()
+        z, w = orc.contour_nodes(r["rule"], r["nc"], r["emin"], r["emax"])
+        X0 = inputs_subspace(A.shape[0], r["m0"], 0)
+        t0 = time.perf_counter()
+        out = orc.ifeast(A, X0, r["emin"], r["emax"], z, w, inner="gmres", k=r["k"],
+                         alpha=r["alpha"], tol=1e-10, max_outer=60, B=B,
+                         correction_rf=r["correction_rf"])
         dt = time.perf_counter() - t0
         pairs = int((out["inside"] & (out["res"] <= 1e-10)).sum()) if out["converged"] else 0
-        return pairs / dt, f"full solve of {wl.name}: {iters[0]} outer iterations, {pairs} pairs, {dt:.1f} s"
-    except TimeoutError:
-        dt = time.perf_counter() - t0
-        return 0.0, f"{wl.name}: {iters[0]} outer iterations in {dt:.1f} s without converging"
+        return pairs / dt, (f"complete oracle solve of the reduced instance {r['name']} "
+                            f"(n = {A.shape[0]}; the {wl.A.n}-row workload takes the oracle days): "
+                            f"{out['iters']} outer iterations, {pairs} pairs, {dt:.1f} s")
+    z, w = orc.contour_nodes(wl.rule, wl.nc, wl.emin, wl.emax)
+    A = wl.A.to_scipy()
+    t0 = time.perf_counter()
+    out = orc.ifeast(A, wl.X0(), wl.emin, wl.emax, z, w, inner="gmres", k=wl.inner_iters,
+                     alpha=wl.alpha, tol=1e-10, max_outer=200)
+    dt = time.perf_counter() - t0
+    pairs = int((out["inside"] & (out["res"] <= 1e-10)).sum()) if out["converged"] else 0
+    return pairs / dt, (f"complete oracle solve of {wl.name}: {out['iters']} outer iterations, "
+                        f"{pairs} pairs, {dt:.1f} s")
+
+
+def oracle_reference_eigs(wl):
+    """The eigenvalues the workload's interval holds, from outside the CUDA
+    path: the oracle-written golden file for the 64^3 window (shift-invert
+    Lanczos), the closed-form spectra for the 50x50 Laplacian and the Q1
+    pencils. (values, source) or (None, reason)."""
+    from paper_1706_00692_gb300 import inputs
+    if wl.name.startswith("lap3d_64"):
+        path = os.path.join(ROOT, "tests", "golden", "lap3d64_window.txt")
+        try:
+            data = np.loadtxt(path)
+        except OSError:
+            return None, "golden file missing"
+        return data[data[:, 2] == 1, 0], "CPU oracle, shift-invert Lanczos (tests/golden/lap3d64_window.txt)"
+    if wl.name.startswith("lap2d_50"):
+        ev = inputs.laplacian_eigs((50, 50))
+        return ev[(ev > wl.emin) & (ev < wl.emax)], "closed form"
+    if wl.B is not None and wl.name.startswith("fem3d_"):
+        N = round(wl.A.n ** (1.0 / 3.0))
+        ev = inputs.fem_q1_eigs((N, N, N))
+        return ev[(ev > wl.emin) & (ev < wl.emax)], "closed form"
+    return None, "no reference for this workload"
+
+
+def error_vs_reference(wl, lam, res):
+    ref, source = oracle_reference_eigs(wl)
+    out = {"pairs": int(lam.size), "max_resid": float(res.max()) if res.size else None,
+           "source": source}
+    if ref is None:
+        return out
+    out["reference_pairs"] = int(ref.size)
+    if ref.size == lam.size and ref.size:
+        err = np.abs(lam - ref) / np.abs(ref)
+        out["max_rel_eig_err"] = float(err.max())
+        out["per_pair_rel_eig_err"] = [float(f"{e:.2e}") for e in err]
+    return out
+
+
+def inputs_subspace(n, m0, seed):
+    from paper_1706_00692_gb300 import inputs
+    return inputs.initial_subspace(n, m0, seed)
 
 
 def run_reference(args):
@@ -277,9 +325,9 @@ def run_reference(args):
     vals = []
     sample = ""
     for _ in range(args.warmup):
-        oracle_sample(wl, budget_s=3.0)
+        oracle_sample(wl)
     for _ in range(args.steps):
-        v, sample = oracle_sample(wl, budget_s=15.0)
+        v, sample = oracle_sample(wl)
         vals.append(v)
     value = float(np.mean(vals))
     cores = cpu_threads()
@@ -355,6 +403,7 @@ def run_ours(args):
     kstat = kernel_stats(ktimes, klaunch)
     lam, X, res = S.eigenpairs()
     pairs = int((res <= 1e-10).sum())
+    accuracy = error_vs_reference(wl, lam, res)
     # replicas: converged pairs of every rank over the slowest rank's time
     from paper_1706_00692_gb300.replicas import job_throughput
     _, total_s, value = job_throughput(pairs * args.steps, float(sum(times)) / 1e3, device=dev)
@@ -398,7 +447,8 @@ def run_ours(args):
                 "config": {"workload": wl.name, "n": wl.A.n, "nnz": wl.A.nnz, "m0": wl.m0,
                            "nc": wl.nc, "contour": wl.rule, "inner": wl.inner,
                            "inner_precision": wl.precision,
-                           "inner_storage": {"fp16": "f16", "fp32": "f32"}.get(wl.precision, "f64"),
+                           "inner_storage": {"fp16": "f16", "bf16": "bf16",
+                                             "fp32": "f32"}.get(wl.precision, "f64"),
                            "inner_iters": wl.inner_iters,
                            "alpha": wl.alpha, "l2": "flushed between steps (256 MB write)",
                            "outer_iters": st["outer_iters"], "pairs": pairs,
@@ -411,11 +461,13 @@ def run_ours(args):
                 "roofline": roofline,
                 "kernel_ms": {k: {"launches": n, "timed": c, "ms_per_launch": round(e, 6),
                                   "ms": round(n * e, 3)} for k, (n, c, e) in kstat.items()},
-                "kernel_timing": f"CUDA events per launch; Lanczos step and Givens kernels "
-                                 f"timed in one step of {PROFILE_EVERY}",
+                "kernel_timing": f"CUDA events per launch; the per-step Lanczos kernels "
+                                 f"(step, coefficient reduction) timed in one step of "
+                                 f"{PROFILE_EVERY}",
+                "error_vs_reference": accuracy,
                 "clocks": clk.summary()}
         if not args.no_cpu_baseline and world == 1:
-            v, sample = oracle_sample(wl, budget_s=20.0, gpu_stats=st)
+            v, sample = oracle_sample(wl)
             line["cpu_baseline"] = {"value": v, "unit": "eigenpairs/s", "cores": cpu_threads(),
                                     "kind": "oracle", "sample": sample}
         print(json.dumps(line), flush=True)

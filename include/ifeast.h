@@ -46,7 +46,7 @@ typedef enum {
   IFEAST_ERR_M0_TOO_SMALL = 5,   /* m0 Ritz values inside the interval: m0 <= m  */
   IFEAST_STATUS_NO_EIGENVALUES = 6, /* no Ritz value inside the interval         */
   IFEAST_ERR_BREAKDOWN = 7,      /* B_Q not positive definite even after a shift */
-  IFEAST_ERR_TIMEOUT = 8,        /* a bounded device-side wait ran out           */
+  IFEAST_ERR_TIMEOUT = 8,        /* opts.time_limit_ms ran out; last iterate kept  */
   IFEAST_ERR_STATE = 9,          /* call out of order (e.g. eigenpairs before solve) */
   IFEAST_ERR_UNSUPPORTED = 10    /* option combination not built                 */
 } ifeast_status;
@@ -60,7 +60,18 @@ typedef enum {
  *             (nc even). A is real and X real, so the solutions at conjugate
  *             nodes are conjugate: the library runs the equal TRAP_HALF sum
  *             over the nc/2 upper nodes.                                     */
-typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } ifeast_rule;
+/*   USER      nc caller-given nodes and weights (ifeast_contour.user_zw). The
+ *             library forms the filter as Re sum_k w_k / (z_k - lambda) like
+ *             the *_HALF rules, so a rule for a real problem is given by its
+ *             upper-half nodes with the factor 2 of the mirrored lower half
+ *             folded into the weights (the form ifeast_contour_nodes returns).
+ *             Every node needs Im z_k != 0 (a real node can hit the spectrum). */
+typedef enum {
+  IFEAST_GL_HALF = 0,
+  IFEAST_TRAP_HALF = 1,
+  IFEAST_TRAP_FULL = 2,
+  IFEAST_USER = 3
+} ifeast_rule;
 
 /* Inner solver for Alg. 2 step 1.
  *   GMRES:  one complex GMRES per (node, column) pair, zero initial guess,
@@ -80,17 +91,19 @@ typedef enum { IFEAST_GL_HALF = 0, IFEAST_TRAP_HALF = 1, IFEAST_TRAP_FULL = 2 } 
 typedef enum { IFEAST_INNER_GMRES = 0, IFEAST_INNER_MINRES = 1 } ifeast_inner;
 
 /* Arithmetic of the inner solve (Krylov vectors, sparse products and their
- * inner products; FP32 with either inner solver, FP16 with IFEAST_INNER_MINRES
- * only; FP32 GMRES needs a symmetric A, since its residual form takes real
- * Ritz pairs).
+ * inner products; FP32 with either inner solver, FP16 and BF16 with
+ * IFEAST_INNER_MINRES only; FP32 GMRES needs a symmetric A, since its residual
+ * form takes real Ritz pairs).
  *   FP64: FP64 vectors and arithmetic.
  *   FP32: FP32 vectors and arithmetic.
  *   FP16: FP16 storage of the Lanczos vectors (half the bytes of FP32),
  *         FP32 arithmetic; needs m0 % 4 == 0. The work vectors are stored
  *         scaled by 1/||A||_inf to stay in FP16 range.
+ *   BF16: BF16 storage of the Lanczos vectors (8-bit exponent, so no
+ *         scaling), FP32 arithmetic; needs m0 % 4 == 0.
  * The quadrature weights, least-squares updates, reduced eigenproblem,
  * Rayleigh-Ritz products and residual check are FP64 in every mode. */
-typedef enum { IFEAST_FP64 = 0, IFEAST_FP32 = 1, IFEAST_FP16 = 2 } ifeast_precision;
+typedef enum { IFEAST_FP64 = 0, IFEAST_FP32 = 1, IFEAST_FP16 = 2, IFEAST_BF16 = 3 } ifeast_precision;
 
 typedef struct {
   int64_t n;
@@ -103,8 +116,11 @@ typedef struct {
 typedef struct {
   int rule;       /* ifeast_rule                        */
   int nc;         /* number of nodes (upper half for *_HALF rules) */
-  double emin;    /* interval (emin, emax), open         */
+  double emin;    /* interval (emin, emax), open; the wanted eigenvalues, and
+                     the circle of the built-in rules                        */
   double emax;
+  const double *user_zw; /* IFEAST_USER only (else ignored): host array of nc x
+                     {Re z_k, Im z_k, Re w_k, Im w_k}, copied by ifeast_create */
 } ifeast_contour;
 
 typedef struct {
@@ -140,6 +156,13 @@ typedef struct {
                            shifted systems; it lets FP32 inner solves reach FP64
                            eigenpair residuals). Default 1e-3; 1 or more: from
                            the second iteration on.                            */
+  double time_limit_ms; /* > 0: ifeast_solve stops once this much wall time has
+                           passed: between outer iterations, and inside the
+                           Lanczos loop at its lagged early-exit checks (the
+                           filter then uses the steps run so far), followed by
+                           that iteration's Rayleigh-Ritz. It returns
+                           IFEAST_ERR_TIMEOUT with the last iterate kept (pairs
+                           retrievable as after NOT_CONVERGED). <= 0: no limit. */
 } ifeast_opts;
 
 typedef struct {
@@ -151,16 +174,17 @@ typedef struct {
   int max_inner;              /* largest per-(node, column) step count seen    */
   int shifted_cholesky;       /* times B_Q needed the diagonal shift           */
   double solve_ms;            /* wall time of the last ifeast_solve (host clock) */
-} ifeast_stats;
+} ifeast_stats_t;
 
 /* Fills *o with the defaults: GMRES, k = 10, alpha = 0 (fixed k), max_outer =
- * 100, tol = 1e-10, FP64, verbose = 0. */
+ * 100, tol = 1e-10, FP64, verbose = 0, correction_rf = 1e-3, no time limit. */
 void ifeast_default_opts(ifeast_opts *o);
 
 /* Contour nodes and weights (Eq. contour_int_quad with the rules above) on the
  * host: zw[4*k + {0,1,2,3}] = {Re z_k, Im z_k, Re w_k, Im w_k}, k < c->nc. For
  * *_HALF rules the weights already include the factor 2 of the conjugate
- * lower half, so the filter is rho(lambda) = Re sum_k w_k / (z_k - lambda). */
+ * lower half, so the filter is rho(lambda) = Re sum_k w_k / (z_k - lambda).
+ * IFEAST_USER: the given nodes, validated (finite, Im z_k != 0). */
 int ifeast_contour_nodes(const ifeast_contour *c, double *zw);
 
 /* Device bytes a handle needs for (n, nnz, m0, contour, opts), B = I. */
@@ -196,12 +220,28 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
                   ifeast_t *out);
 
 /* Runs Algorithm 2 from the initial subspace X0 (n x m0, row-major float64;
- * x0_on_device != 0: device pointer, else host pointer, copied in). Returns
- * OK on convergence, NOT_CONVERGED after max_outer iterations (the last
- * iterate is kept), M0_TOO_SMALL if all m0 Ritz values fall inside the
+ * x0_on_device != 0: device pointer, else host pointer, copied in). X0 = NULL
+ * starts from a random subspace (Alg. 1 input: "random" X^(0)) drawn on the
+ * device from seed, as ifeast_initial_subspace below. stream: the
+ * cudaStream_t (as void*) this solve runs on; NULL: the stream given to
+ * ifeast_create. Returns OK on convergence, NOT_CONVERGED after max_outer
+ * iterations (the last iterate is kept), TIMEOUT once opts.time_limit_ms has
+ * run out (likewise), M0_TOO_SMALL if all m0 Ritz values fall inside the
  * interval, NO_EIGENVALUES if none does, BREAKDOWN if B_Q cannot be factored.
  * Blocks the calling host thread until the solve ends. */
-int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device);
+int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device, uint64_t seed, void *stream);
+
+/* The seeded random subspace of ifeast_solve(X0 = NULL): X (n x m0 row-major
+ * float64, DEVICE, caller-owned) gets i.i.d. N(0, 1) values. Element pair
+ * e = 2p, 2p + 1 (row-major index) comes from one Philox4x32-10 block
+ * (Salmon et al., SC'11) with counter (p mod 2^32, p div 2^32, 0, 0) and key
+ * (seed mod 2^32, seed div 2^32): its words x0..x3 give the 53-bit uniforms
+ * u1 = (2^26 (x0 >> 5) + (x1 >> 6) + 1) 2^-53 in (0, 1] and
+ * u2 = (2^26 (x2 >> 5) + (x3 >> 6)) 2^-53 in [0, 1), and Box-Muller gives
+ * X[2p] = sqrt(-2 ln u1) cos(2 pi u2), X[2p + 1] = sqrt(-2 ln u1) sin(2 pi u2).
+ * Runs on stream and returns when it finished. INVALID_ARG for n < 1, m0 < 1
+ * or X = NULL. */
+int ifeast_initial_subspace(int64_t n, int m0, uint64_t seed, double *X, void *stream);
 
 /* Copies the Ritz pairs with lambda inside (emin, emax), ascending:
  * evals[m], evecs (n x cap row-major: column j of the block is the j-th pair,
@@ -226,7 +266,8 @@ int ifeast_eigenpairs(ifeast_t h, int cap, int *m_found, double *evals, double *
  * device or host pointers as flagged. */
 int ifeast_ritz_all(ifeast_t h, double *lam, double *resid, int out_on_device);
 
-int ifeast_get_stats(ifeast_t h, ifeast_stats *s);
+/* Counters of the last ifeast_solve. */
+int ifeast_stats(ifeast_t h, ifeast_stats_t *s);
 
 /* Human-readable name of a status code (static storage). */
 const char *ifeast_strerror(int code);
@@ -247,6 +288,23 @@ void ifeast_destroy(ifeast_t h);
  * X, Q: n x m0 float64 device. steps (optional, device int32[nc*m0], column
  * c = k*m0 + j) receives the Krylov steps taken by each (node, column). */
 int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32_t *steps);
+
+/* Alg. 2 steps 1-2 in residual form (the right-hand sides ifeast_solve uses
+ * from its second outer iteration on with IFEAST_INNER_MINRES, and with
+ * IFEAST_INNER_GMRES + IFEAST_FP32 once ||R_F|| <= opts.correction_rf): for
+ * the pairs (lam_j, x_j) given, r_j = A x_j - lam_j B x_j, the systems
+ * (z_k B - A) e = r_j are solved by the inner solver (stop test
+ * ||r_j - (z_k B - A) e|| <= alpha RF ||B x_j|| |z_k - lam_j|, Alg. 2's test on
+ * the original system), and
+ *   Q_j = Re sum_k w_k (x_j + e_kj) / (z_k - lam_j)
+ *       = rho(lam_j) x_j + Re sum_k w_k e_kj / (z_k - lam_j),
+ * which equals ifeast_apply_filter's Q in exact arithmetic (an identity of the
+ * shifted systems). X, Q: n x m0 float64 device; lam: m0 float64 device;
+ * steps as ifeast_apply_filter. UNSUPPORTED for GMRES handles in FP64 and for
+ * non-symmetric handles. Overwrites the handle's last iterate: call
+ * ifeast_solve again before ifeast_eigenpairs. */
+int ifeast_apply_filter_residual(ifeast_t h, const double *X, const double *lam, double *Q,
+                                 double RF, int32_t *steps);
 
 /* Alg. 2 steps 3-4 on a given Q (n x m0 float64 device): Rayleigh-Ritz with
  * B_Q = Q^T B Q, A_Q = Q^T A Q, then X = Q X_Q (n x m0 device, B-orthonormal
@@ -280,7 +338,9 @@ int ifeast_spmm_shift(ifeast_t h, const double *V, double *W, int ncols, int m0,
  * Same outputs (X = Q X_Q, lam ascending, resid) for the matrix given as
  * caller-owned DEVICE CSR arrays (rowptr int32[n+1], colidx int32[nnz],
  * val float64[nnz]; not validated: the caller passes a well-formed matrix)
- * and device Q, X (n x m0 row-major), lam[m0], resid[m0].
+ * and device Q, X (n x m0 row-major), lam[m0], resid[m0]. X must not overlap
+ * Q (X = Q X_Q reads every column of a row of Q while it writes that row of
+ * X): overlapping ranges return INVALID_ARG before any device work.
  *   - No handle and no workspace: intermediates live in one file-scope
  *     device array of about 4.5 MiB that every GPU loading the library keeps
  *     until the process exits. m0 must be <= 64 (larger: INVALID_ARG).
@@ -302,7 +362,8 @@ int ifeast_rayleigh_ritz_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr,
  * CUDA events on the handle's stream (a few microseconds of overhead per
  * launch); the durations are summed per kernel class when the library next
  * synchronises its stream. on = N >= 2: the same, except that only launches
- * 1, 1 + N, 1 + 2N, ... of the Lanczos step and Givens kernels are timed: an
+ * 1, 1 + N, 1 + 2N, ... of the per-step Lanczos kernels (the step kernel and
+ * the kernel that reduces its partials to alpha_s, beta_{s+1}) are timed: an
  * event between two of those kernels stops the second from launching while the
  * first runs (programmatic dependent launch), so timing all of them slows the
  * solve being timed. on = 0: off. A negative on returns IFEAST_ERR_INVALID_ARG.
@@ -312,7 +373,7 @@ int ifeast_set_profiling(ifeast_t h, int on);
 /* Copies the summed milliseconds and the counts of timed launches of the first
  * cap kernel classes (device time between the bracketing events) into ms[] and
  * launches[] (either may be NULL); reset != 0 clears them afterwards.
- * Returns the number of kernel classes (21; each class is one kernel) on success; a NULL handle or a
+ * Returns the number of kernel classes (22; each class is one kernel) on success; a NULL handle or a
  * negative cap returns IFEAST_ERR_INVALID_ARG (1). */
 int ifeast_kernel_times(ifeast_t h, int cap, double *ms, int64_t *launches, int reset);
 

@@ -18,7 +18,7 @@ Map to the paper:
   gmres .............................. GMRES of Section 2.2 (zero initial guess,
                                         modified Gram-Schmidt Arnoldi, Givens)
   _filtered_subspace_gmres_correction  Alg. 2 step 1 solved for the correction of
-                                        the current Ritz pairs (an identity of the
+  _filtered_subspace_shared_correction  the current Ritz pairs (an identity of the
                                         shifted systems; reading in its docstring)
   gmres_shared_basis ................. Section 3, Eqs. (yz)-(contint_krylov):
                                         the Krylov basis does not depend on z
@@ -27,6 +27,10 @@ Map to the paper:
   convergence_bound .................. Eq. (upperbound), Eq. (deltadef)
   ifeast_nonsym / rayleigh_ritz_nonsym  non-Hermitian extension (stated without
                                         steps in the paper; readings in the docstring)
+  seeded_normal_block ................ the random X^(0) (Alg. 1 input), Philox4x32-10
+                                        + Box-Muller from their published definitions
+  eigenvalues_in_interval ............ the eigenvalues an interval holds (problem
+                                        statement, Section 1) by shift-invert Lanczos
 """
 from __future__ import annotations
 
@@ -315,6 +319,10 @@ def _filtered_subspace_gmres_correction(A, X, lam, z, w, half, k, tol_rel, stats
 
 
 def _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats):
+    """Sum_k w_k y_kj with y_kj the GMRES iterate of (z_k I - A) y = x_j on the
+    real Krylov basis of K(A, x_j), which every node shares (Section 3,
+    Eqs. yz-contint_krylov); stop per (node, column) once the least-squares
+    residual is <= tol_rel ||x_j|| (Alg. 2 step 1)."""
     n, m0 = X.shape
     Q = np.zeros(X.shape, np.complex128)
     for zk, wk in zip(z, w):
@@ -322,6 +330,35 @@ def _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats):
             out = gmres_shared_basis(A, X[:, j], zk, k, tol_rel)
             stats["inner_steps"].append(out["steps"])
             Q[:, j] += wk * out["y"]
+    return Q.real if half else Q
+
+
+def _filtered_subspace_shared_correction(A, X, lam, z, w, half, k, tol_rel, stats):
+    """The shared-basis filter (Section 3) solved for the correction of the
+    current Ritz pairs (lam_j, x_j), B = I. With r_j = A x_j - lam_j x_j the
+    shifted solution is exactly
+        (z_k I - A)^{-1} x_j = (x_j + y'_kj) / (z_k - lam_j),  (z_k I - A) y'_kj = r_j,
+    so every node's system is solved on the one real basis of K(A, r_j) and
+        Q_j = rho(lam_j) x_j + sum_k w_k y'_kj / (z_k - lam_j)
+    (rho of Eq. rhoh; real part for a half contour). The stop test is Alg. 2's
+    on the original system, whose residual is the correction's divided by
+    |z_k - lam_j|: least-squares residual <= tol_rel ||x_j|| |z_k - lam_j|."""
+    n, m0 = X.shape
+    Rres = A @ X - X * lam[None, :]
+    rho = filter_rho(lam, z, w, half)
+    Q = X * rho[None, :] + 0j
+    for zk, wk in zip(z, w):
+        for j in range(m0):
+            rn = np.linalg.norm(Rres[:, j])
+            if rn == 0.0:
+                stats["inner_steps"].append(0)
+                continue
+            tol_j = 0.0
+            if tol_rel > 0.0:
+                tol_j = tol_rel * np.linalg.norm(X[:, j]) * abs(zk - lam[j]) / rn
+            out = gmres_shared_basis(A, Rres[:, j], zk, k, tol_j)
+            stats["inner_steps"].append(out["steps"])
+            Q[:, j] += wk * out["y"] / (zk - lam[j])
     return Q.real if half else Q
 
 
@@ -339,9 +376,11 @@ def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0
     residual measured relative to the right-hand side, ||R_F|| = 1 at the
     start); alpha <= 0: run exactly k steps.
     correction_rf: None, or a bound: from the second iteration on, once the
-    previous ||R_F|| <= correction_rf, inner="gmres" solves for the correction
-    of the Ritz pairs of the previous iteration
-    (_filtered_subspace_gmres_correction; the same filter in exact arithmetic).
+    previous ||R_F|| <= correction_rf, inner="gmres" (and inner="shared")
+    solves for the correction of the Ritz pairs of the previous iteration
+    (_filtered_subspace_gmres_correction, _filtered_subspace_shared_correction;
+    the same filter in exact arithmetic). correction_rf = inf: from the second
+    iteration on, whatever ||R_F||.
     ||R_F|| is the largest relative residual ||A x_j - lam_j x_j||/||A x_j||
     over Ritz values strictly inside (emin, emax).
 
@@ -370,6 +409,8 @@ def ifeast(A, X0, emin, emax, z, w, *, half=True, inner="gmres", k=10, alpha=0.0
             Q = _filtered_subspace_gmres_correction(A, X, lam, z, w, half, k, tol_rel, stats, B)
         elif inner == "gmres":
             Q = _filtered_subspace_gmres(A, X, z, w, half, k, tol_rel, stats, B)
+        elif inner == "shared" and correction_rf is not None and it > 1 and RF <= correction_rf:
+            Q = _filtered_subspace_shared_correction(A, X, lam, z, w, half, k, tol_rel, stats)
         elif inner == "shared":
             Q = _filtered_subspace_shared(A, X, z, w, half, k, tol_rel, stats)
         else:
@@ -509,13 +550,15 @@ def filter_step_spectral(A_dense, X, z, w, half=True, B_dense=None):
 
 
 def convergence_bound_delta(lam_all, z, w, half=True):
-    """Delta = sum_k ||w_k (z_k I - A)^{-1}|| (Eq. deltadef) for normal A with
-    spectrum lam_all; for a half contour the mirrored lower-half nodes are
-    counted too, since the filter uses both halves."""
+    """Delta = sum_k ||w_k (z_k I - A)^{-1}|| (Eq. deltadef) over the nodes of the
+    whole contour, for normal A with spectrum lam_all, where the resolvent's
+    2-norm is 1 / min |z_k - lambda|. A half rule's weights hold the factor 2
+    of the mirrored lower-half node (weight w_k / 2 at z_k and at conj(z_k),
+    whose resolvents have the same norm), so both rules sum |w_k| / min|z_k - lambda|
+    over the given nodes."""
     d = 0.0
     for zk, wk in zip(z, w):
-        t = abs(wk) / np.min(np.abs(zk - lam_all))
-        d += 2.0 * t if half else t
+        d += abs(wk) / np.min(np.abs(zk - lam_all))
     return d
 
 
@@ -528,26 +571,142 @@ def ref_spmm_shift(A, V, zcol):
     return V * zcol[None, :] - A @ V
 
 
-def ref_arnoldi_step(V_basis, W):
-    """Orthogonalise W (n x C) against V_basis (s+1, n, C) column by column
-    with MGS; returns (h (s+2, C), V_next (n, C))."""
-    sp1 = V_basis.shape[0]
-    C = W.shape[1]
-    h = np.zeros((sp1 + 1, C), np.complex128)
-    Vn = np.zeros_like(W)
-    for c in range(C):
-        w = W[:, c].copy()
-        for l in range(sp1):
-            h[l, c] = np.vdot(V_basis[l, :, c], w)
-            w = w - h[l, c] * V_basis[l, :, c]
-        nr = np.linalg.norm(w)
-        h[sp1, c] = nr
-        Vn[:, c] = w / nr
-    return h, Vn
+# ---------------------------------------------------------------------------
+# Seeded random initial subspace (Alg. 1/2 input X^(0), "random"): the
+# counter-based generator Philox4x32-10 from its published definition
+# (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+# SC'11) and the Box-Muller transform
+# ---------------------------------------------------------------------------
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57      # round multipliers
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85      # key increments (Weyl sequence)
 
 
-def ref_gram(Q, AQ):
-    return Q.conj().T @ AQ, Q.conj().T @ Q
+def philox4x32_10(counter, key):
+    """Philox4x32 with 10 rounds on arrays of counters: counter (4, N) and key
+    (2, N) unsigned 32-bit words; returns the (4, N) output words. One round:
+    (hi0, lo0) = M0 * c0 and (hi1, lo1) = M1 * c2 as 64-bit products, then
+    c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key is bumped by
+    (W0, W1) before every round but the first."""
+    mask = np.uint64(0xFFFFFFFF)
+    c = [np.asarray(counter[i], dtype=np.uint64) & mask for i in range(4)]
+    k0 = np.asarray(key[0], dtype=np.uint64) & mask
+    k1 = np.asarray(key[1], dtype=np.uint64) & mask
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + np.uint64(_PHILOX_W0)) & mask
+            k1 = (k1 + np.uint64(_PHILOX_W1)) & mask
+        p0 = np.uint64(_PHILOX_M0) * c[0]   # < 2^64: exact in uint64
+        p1 = np.uint64(_PHILOX_M1) * c[2]
+        c = [(p1 >> np.uint64(32)) ^ c[1] ^ k0, p1 & mask,
+             (p0 >> np.uint64(32)) ^ c[3] ^ k1, p0 & mask]
+    return np.stack(c).astype(np.uint32)
+
+
+def seeded_normal_block(n, m0, seed):
+    """X^(0): n x m0 (row-major) i.i.d. N(0,1). Element pair e = 2p, 2p + 1
+    takes the Philox4x32-10 block of counter (p mod 2^32, p div 2^32, 0, 0)
+    under key (seed mod 2^32, seed div 2^32); its words x0..x3 make the 53-bit
+    uniforms u1 = (2^26 (x0 >> 5) + (x1 >> 6) + 1) / 2^53 in (0, 1] and
+    u2 = (2^26 (x2 >> 5) + (x3 >> 6)) / 2^53 in [0, 1), and Box-Muller gives
+    sqrt(-2 ln u1) cos(2 pi u2) and sqrt(-2 ln u1) sin(2 pi u2)."""
+    total = n * m0
+    pairs = (total + 1) // 2
+    p = np.arange(pairs, dtype=np.uint64)
+    zero = np.zeros(pairs, dtype=np.uint64)
+    ctr = [p & np.uint64(0xFFFFFFFF), p >> np.uint64(32), zero, zero]
+    key = [np.full(pairs, seed & 0xFFFFFFFF, dtype=np.uint64),
+           np.full(pairs, (seed >> 32) & 0xFFFFFFFF, dtype=np.uint64)]
+    x = philox4x32_10(ctr, key).astype(np.uint64)
+    a = (x[0] >> np.uint64(5)) * np.uint64(1 << 26) + (x[1] >> np.uint64(6))
+    b = (x[2] >> np.uint64(5)) * np.uint64(1 << 26) + (x[3] >> np.uint64(6))
+    u1 = (a.astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = b.astype(np.float64) * 2.0 ** -53
+    rad = np.sqrt(-2.0 * np.log(u1))
+    t = (2.0 * math.pi) * u2
+    out = np.empty(2 * pairs)
+    out[0::2] = rad * np.cos(t)
+    out[1::2] = rad * np.sin(t)
+    return out[:total].reshape(n, m0)
+
+
+# ---------------------------------------------------------------------------
+# Eigenpairs an interval holds, from the plain definition (the problem
+# statement of Section 1): for checks at sizes a dense solver cannot reach
+# ---------------------------------------------------------------------------
+
+def grid_nested_dissection(shape):
+    """A fill-reducing symmetric ordering of the unknowns of a grid (last
+    index fastest) for the sparse LU below: geometric nested dissection,
+    i.e. split the box at the middle plane of its longest side, order the two
+    halves recursively and the separating plane last. Returns a permutation
+    of range(prod(shape))."""
+    idx = np.arange(int(np.prod(shape))).reshape(shape)
+    out = []
+
+    def rec(block):
+        if block.size <= 64:
+            out.append(block.ravel())
+            return
+        ax = int(np.argmax(block.shape))
+        m = block.shape[ax] // 2
+        rec(block.take(range(0, m), axis=ax))
+        rec(block.take(range(m + 1, block.shape[ax]), axis=ax))
+        out.append(block.take([m], axis=ax).ravel())
+
+    rec(idx)
+    return np.concatenate(out)
+
+
+def eigenpairs_near(A, sigma, k, perm=None):
+    """The k eigenpairs of the real symmetric sparse A whose eigenvalues lie
+    closest to sigma, by shift-invert Lanczos (ARPACK through
+    scipy.sparse.linalg.eigsh with a sparse LU of A - sigma I: eigenvalues nu
+    of (A - sigma I)^{-1}, lambda = sigma + 1/nu), one library step. perm: an
+    optional symmetric ordering applied before the LU (fill only; the
+    operator is the same). Returns (lam ascending, X unit columns, res) with
+    res_j = ||A x_j - lam_j x_j||; for symmetric A an exact eigenvalue lies
+    within res_j of lam_j."""
+    import scipy.sparse.linalg as spla
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    M = (A - sigma * sp.identity(n, format="csr")).tocsr()
+    if perm is None:
+        lu = spla.splu(M.tocsc(), permc_spec="MMD_AT_PLUS_A")
+        solve = lu.solve
+    else:
+        perm = np.asarray(perm)
+        lu = spla.splu(M[perm][:, perm].tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.1,
+                       options=dict(SymmetricMode=True))
+
+        def solve(b):
+            y = np.empty_like(b)
+            y[perm] = lu.solve(b[perm])
+            return y
+    op = spla.LinearOperator(A.shape, matvec=solve, dtype=np.float64)
+    lam, X = spla.eigsh(A, k=k, sigma=sigma, which="LM", OPinv=op, tol=0.0)
+    order = np.argsort(lam)
+    lam, X = lam[order], X[:, order]
+    X = X / np.linalg.norm(X, axis=0)[None, :]
+    res = np.linalg.norm(A @ X - X * lam[None, :], axis=0)
+    return lam, X, res
+
+
+def eigenvalues_in_interval(A, emin, emax, k, perm=None):
+    """All eigenvalues of the real symmetric A inside the open interval (emin,
+    emax), with their residual bounds, from the k eigenvalues closest to the
+    centre: the set is complete when the farthest of the k lies at or beyond
+    the half-width on each side of the centre found (then no eigenvalue of
+    the interval is left out); raises otherwise. Also returns the nearest
+    eigenvalue found below emin and above emax (the gaps at the ends)."""
+    c, r = 0.5 * (emin + emax), 0.5 * (emax - emin)
+    lam, _, res = eigenpairs_near(A, c, k, perm)
+    if not (lam.min() <= emin and lam.max() >= emax):
+        raise ValueError("k too small: the eigenvalues found do not reach both interval ends")
+    inside = (lam > emin) & (lam < emax)
+    below = lam[lam <= emin].max()
+    above = lam[lam >= emax].min()
+    return lam[inside], res[inside], below, above
 
 
 # ---------------------------------------------------------------------------

@@ -9,7 +9,7 @@ from . import inputs  # noqa: F401  (seeded synthetic workloads; no solver arith
 
 
 def __getattr__(name):
-    if name in ("Solver", "Server", "IFEASTError", "contour_nodes"):
+    if name in ("Solver", "Server", "IFEASTError", "contour_nodes", "initial_subspace"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

@@ -19,13 +19,13 @@ IFEAST_ERR_TIMEOUT = 8
 IFEAST_ERR_STATE = 9
 IFEAST_ERR_UNSUPPORTED = 10
 
-GL_HALF, TRAP_HALF, TRAP_FULL = 0, 1, 2
+GL_HALF, TRAP_HALF, TRAP_FULL, USER = 0, 1, 2, 3
 INNER_GMRES, INNER_MINRES = 0, 1
-FP64, FP32, FP16 = 0, 1, 2
+FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 INNERS = {"gmres": INNER_GMRES, "minres": INNER_MINRES}
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16}
 
-RULES = {"gl_half": GL_HALF, "trap_half": TRAP_HALF, "trap_full": TRAP_FULL}
+RULES = {"gl_half": GL_HALF, "trap_half": TRAP_HALF, "trap_full": TRAP_FULL, "user": USER}
 
 
 class Csr(ct.Structure):
@@ -34,14 +34,15 @@ class Csr(ct.Structure):
 
 
 class Contour(ct.Structure):
-    _fields_ = [("rule", ct.c_int), ("nc", ct.c_int), ("emin", ct.c_double), ("emax", ct.c_double)]
+    _fields_ = [("rule", ct.c_int), ("nc", ct.c_int), ("emin", ct.c_double), ("emax", ct.c_double),
+                ("user_zw", ct.c_void_p)]
 
 
 class Opts(ct.Structure):
     _fields_ = [("inner_solver", ct.c_int), ("inner_max_iters", ct.c_int), ("alpha", ct.c_double),
                 ("max_outer", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
                 ("verbose", ct.c_int), ("nonsymmetric", ct.c_int), ("minres_two_pass", ct.c_int),
-                ("correction_rf", ct.c_double)]
+                ("correction_rf", ct.c_double), ("time_limit_ms", ct.c_double)]
 
 
 class Stats(ct.Structure):
@@ -72,7 +73,9 @@ SIGNATURES = {
     "ifeast_create": (ct.c_int, [ct.POINTER(Csr), ct.c_void_p, ct.POINTER(Contour), ct.c_int,
                                  ct.POINTER(Opts), ct.c_void_p, ct.c_size_t, ct.c_void_p,
                                  ct.POINTER(ct.c_void_p)]),
-    "ifeast_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "ifeast_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_uint64, ct.c_void_p]),
+    "ifeast_initial_subspace": (ct.c_int, [ct.c_int64, ct.c_int, ct.c_uint64, ct.c_void_p,
+                                           ct.c_void_p]),
     "ifeast_eigenpairs": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.c_void_p,
                                      ct.c_void_p, ct.c_void_p, ct.c_int]),
     "ifeast_ritz_all": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
@@ -80,11 +83,13 @@ SIGNATURES = {
                                              ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "ifeast_rayleigh_ritz_nonsym": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                                ct.c_void_p, ct.c_void_p]),
-    "ifeast_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(Stats)]),
+    "ifeast_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(Stats)]),
     "ifeast_strerror": (ct.c_char_p, [ct.c_int]),
     "ifeast_destroy": (None, [ct.c_void_p]),
     "ifeast_apply_filter": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_double,
                                        ct.c_void_p]),
+    "ifeast_apply_filter_residual": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                                ct.c_void_p, ct.c_double, ct.c_void_p]),
     "ifeast_rayleigh_ritz": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                         ct.c_void_p]),
     "ifeast_spmm_shift": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int,

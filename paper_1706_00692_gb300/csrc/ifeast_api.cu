@@ -57,15 +57,18 @@ struct ifeast_ctx {
   DevStatus *status = nullptr;
   DevStatus *status_host = nullptr;  // pinned
   // shared-basis (MINRES) mode
-  bool minres = false, fp32 = false, half = false;  // fp32: FP32 arithmetic (FP32 or FP16 storage)
+  // fp32: FP32 arithmetic (FP32, FP16 or BF16 storage); half / bf16: 16-bit storage
+  bool minres = false, fp32 = false, half = false, bf16 = false;
   float wscale = 1.f;
   float *val32 = nullptr;
   void *LV = nullptr, *LW0 = nullptr, *LW1 = nullptr;
   bool two_pass = false;
   float *Qf = nullptr;
   double *lpart = nullptr, *lalpha = nullptr, *lbeta = nullptr, *ltol = nullptr;
+  float4 *lcf32 = nullptr;
   double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
-  int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lactive = nullptr, *lSj = nullptr;
+  int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lndone = nullptr,
+      *lactive = nullptr, *lSj = nullptr;
   double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
   int *active_host = nullptr;  // pinned, kCheckLag + 1 slots
   cudaEvent_t check_events[kCheckLag + 1] = {};
@@ -76,8 +79,89 @@ struct ifeast_ctx {
   bool profiling = false;
   // results
   bool solved = false;
-  ifeast_stats stats{};
+  ifeast_stats_t stats{};
+  std::vector<double> user_zw;  // IFEAST_USER nodes (the contour points here)
 };
+
+namespace ifeast {
+
+namespace rng_detail {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): ten rounds of two 32 x 32 -> 64-bit products with the
+// multipliers 0xD2511F53 and 0xCD9E8D57, the key bumped by the Weyl constants
+// 0x9E3779B9 and 0xBB67AE85 between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = (uint32_t)p1;
+    c[2] = n2;
+    c[3] = (uint32_t)p0;
+  }
+}
+
+// One thread per element pair 2p, 2p + 1: 53-bit uniforms from the block's
+// words, Box-Muller.
+__global__ void k_seeded_normal(uint64_t total, uint32_t k0, uint32_t k1, double *__restrict__ X) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * p >= total) return;
+  uint32_t c[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u};
+  philox4x32_10(c, k0, k1);
+  const double inv53 = 1.0 / 9007199254740992.0;  // 2^-53
+  const double u1 = ((double)(((uint64_t)(c[0] >> 5) << 26) + (c[1] >> 6)) + 1.0) * inv53;
+  const double u2 = (double)(((uint64_t)(c[2] >> 5) << 26) + (c[3] >> 6)) * inv53;
+  const double rad = sqrt(-2.0 * log(u1));
+  const double t = 6.283185307179586 * u2;  // the double nearest 2 pi, times u2
+  X[2 * p] = rad * cos(t);
+  if (2 * p + 1 < total) X[2 * p + 1] = rad * sin(t);
+}
+
+// R[r][j] = (A X)[r][j] - lam[j] BX[r][j], one thread per entry.
+__global__ void k_residual_block(int n, int m, const int32_t *__restrict__ rowptr,
+                                 const int32_t *__restrict__ colidx,
+                                 const double *__restrict__ val, const double *__restrict__ X,
+                                 const double *__restrict__ BX, const double *__restrict__ lam,
+                                 double *__restrict__ R) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * m) return;
+  const int r = (int)(idx / m), j = (int)(idx % m);
+  double acc = 0.0;
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) acc = fma(val[p], X[(size_t)colidx[p] * m + j], acc);
+  R[idx] = acc - lam[j] * BX[idx];
+}
+
+}  // namespace rng_detail
+
+using rng_detail::k_residual_block;
+using rng_detail::k_seeded_normal;
+
+cudaError_t seeded_normal(int64_t n, int m0, uint64_t seed, double *X, cudaStream_t st) {
+  const uint64_t total = (uint64_t)n * (uint64_t)m0;
+  const uint64_t pairs = (total + 1) / 2;
+  k_seeded_normal<<<(unsigned)((pairs + 255) / 256), 256, 0, st>>>(
+      total, (uint32_t)seed, (uint32_t)(seed >> 32), X);
+  return cudaGetLastError();
+}
+
+cudaError_t residual_block(int n, int m0, const int32_t *rowptr, const int32_t *colidx,
+                           const double *val, const double *X, const double *BX,
+                           const double *lam, double *R, cudaStream_t st) {
+  const size_t total = (size_t)n * m0;
+  k_residual_block<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, m0, rowptr, colidx, val, X,
+                                                                    BX, lam, R);
+  return cudaGetLastError();
+}
+
+}  // namespace ifeast
 
 namespace {
 
@@ -104,8 +188,8 @@ struct Layout {
 struct Offsets {
   size_t rowptr, colidx, val, z, w, V, W, part, H1, H2, inv_h, CS, SN, R, G, Y, steps, done, X, Q,
       AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
-  size_t val32, LV, LW0, LW1, lpart, lalpha, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
-      lcoldone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
+  size_t val32, LV, LW0, LW1, lpart, lalpha, lcf32, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
+      lcoldone, lndone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
   size_t rowptrB, colidxB, valB, BQ, BX;
   size_t LinvT, theta, Uc, ridx;
   size_t Qf;
@@ -159,7 +243,8 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.done = L.take<int>(C);
   } else {  // shared Lanczos basis, tl tiles the n x m0 block
     const bool fp32 = prec != IFEAST_FP64;
-    const size_t es = prec == IFEAST_FP16 ? 2 : (fp32 ? sizeof(float) : sizeof(double));
+    const size_t es = (prec == IFEAST_FP16 || prec == IFEAST_BF16)
+                          ? 2 : (fp32 ? sizeof(float) : sizeof(double));
     if (fp32) {
       o.val32 = L.take<float>(nnz > 0 ? nnz : 1);
       // fixed-width copy of A for rows of at most 16 non-zeros
@@ -174,6 +259,7 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     // partials of the step kernels: tl.P blocks (generic) or up to 2 per SM (FP32)
     o.lpart = L.take<double>((size_t)std::max(std::max(tl.P, 2 * sms_for_plan), 4) * 3 * m0);
     o.lalpha = L.take<double>((size_t)K * m0);
+    o.lcf32 = L.take<float4>((size_t)(K + 1) * m0);
     o.lbeta = L.take<double>((size_t)(K + 1) * m0);
     o.ltol = L.take<double>(C);
     o.lg = L.take<double2>(C * (K + 1));
@@ -181,8 +267,9 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.lrot = L.take<double2>(C * 4);
     o.lYc = L.take<double2>(C * K);
     o.lsteps = L.take<int>(C);
-    o.ldone = L.take<int>(2 * C);  // pair done flags, two parity buffers
+    o.ldone = L.take<int>(C);  // pair done flags
     o.lcoldone = L.take<int>(m0);
+    o.lndone = L.take<int>(m0);
     o.lactive = L.take<int>(1);
     o.lSj = L.take<int>(m0);
     o.lcoef = L.take<double>((size_t)K * m0 + ((size_t)K * m0 + 1) / 2);  // FP64 + FP32 copy
@@ -226,6 +313,15 @@ int validate_contour(const ifeast_contour *c) {
   if (!c) return IFEAST_ERR_INVALID_ARG;
   if (!(c->emin < c->emax) || !std::isfinite(c->emin) || !std::isfinite(c->emax))
     return IFEAST_ERR_INVALID_ARG;
+  if (c->rule == IFEAST_USER) {
+    if (c->nc < 1 || c->nc > kMaxNodes || !c->user_zw) return IFEAST_ERR_INVALID_ARG;
+    for (int k = 0; k < c->nc; ++k) {
+      for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(c->user_zw[4 * k + q])) return IFEAST_ERR_INVALID_ARG;
+      if (c->user_zw[4 * k + 1] == 0.0) return IFEAST_ERR_INVALID_ARG;
+    }
+    return IFEAST_OK;
+  }
   if (c->rule == IFEAST_TRAP_FULL) {
     if (c->nc < 2 || c->nc % 2 != 0 || c->nc / 2 > kMaxNodes) return IFEAST_ERR_INVALID_ARG;
     return IFEAST_OK;
@@ -254,7 +350,8 @@ int validate_opts(const ifeast_opts *o) {
     if (o->precision == IFEAST_FP32 && o->nonsymmetric == 1) return IFEAST_ERR_UNSUPPORTED;
     if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxInner) return IFEAST_ERR_INVALID_ARG;
   } else if (o->inner_solver == IFEAST_INNER_MINRES) {
-    if (o->precision != IFEAST_FP64 && o->precision != IFEAST_FP32 && o->precision != IFEAST_FP16)
+    if (o->precision != IFEAST_FP64 && o->precision != IFEAST_FP32 &&
+        o->precision != IFEAST_FP16 && o->precision != IFEAST_BF16)
       return IFEAST_ERR_UNSUPPORTED;
     if (o->inner_max_iters < 1 || o->inner_max_iters > kMaxLanczos) return IFEAST_ERR_INVALID_ARG;
   } else {
@@ -263,6 +360,7 @@ int validate_opts(const ifeast_opts *o) {
   if (o->max_outer < 1 || !(o->tol >= 0.0) || !std::isfinite(o->alpha))
     return IFEAST_ERR_INVALID_ARG;
   if (!(o->correction_rf >= 0.0)) return IFEAST_ERR_INVALID_ARG;
+  if (std::isnan(o->time_limit_ms)) return IFEAST_ERR_INVALID_ARG;
   if (o->nonsymmetric != 0 && o->nonsymmetric != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->nonsymmetric && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (o->minres_two_pass != 0 && o->minres_two_pass != 1) return IFEAST_ERR_INVALID_ARG;
@@ -317,7 +415,12 @@ void contour_host(const ifeast_contour *c, std::vector<double2> &z, std::vector<
   const double ctr = 0.5 * (c->emin + c->emax), r = 0.5 * (c->emax - c->emin);
   z.resize(c->nc);
   w.resize(c->nc);
-  if (c->rule == IFEAST_GL_HALF) {
+  if (c->rule == IFEAST_USER) {
+    for (int k = 0; k < c->nc; ++k) {
+      z[k] = make_double2(c->user_zw[4 * k], c->user_zw[4 * k + 1]);
+      w[k] = make_double2(c->user_zw[4 * k + 2], c->user_zw[4 * k + 3]);
+    }
+  } else if (c->rule == IFEAST_GL_HALF) {
     std::vector<double> x, g;
     gauss_legendre(c->nc, x, g);
     for (int k = 0; k < c->nc; ++k) {
@@ -486,6 +589,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.K = h->K;
   a.fp32 = h->fp32 ? 1 : 0;
   a.half = h->half ? 1 : 0;
+  a.bf16 = h->bf16 ? 1 : 0;
   a.wscale = h->wscale;
   a.rowptr = h->rowptr;
   a.colidx = h->colidx;
@@ -499,6 +603,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.part = h->lpart;
   a.alpha = h->lalpha;
   a.beta = h->lbeta;
+  a.cf32 = h->lcf32;
   a.Yc = h->lYc;
   a.coef = h->lcoef;
   a.cx = h->lcx;
@@ -528,6 +633,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   m.steps = h->lsteps;
   m.done = h->ldone;
   m.coldone = h->lcoldone;
+  m.ndone = h->lndone;
   m.active = h->lactive;
   m.status = h->status;
   return a;
@@ -566,6 +672,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->nonsymmetric = 0;
   o->minres_two_pass = 0;
   o->correction_rf = 1e-3;
+  o->time_limit_ms = 0.0;
 }
 
 const char *ifeast_strerror(int code) {
@@ -588,8 +695,10 @@ const char *ifeast_strerror(int code) {
 int ifeast_contour_nodes(const ifeast_contour *c, double *zw) {
   if (!c || !zw) return IFEAST_ERR_INVALID_ARG;
   if (c->nc < 1 || c->nc > kMaxNodes || !(c->emin < c->emax)) return IFEAST_ERR_INVALID_ARG;
-  if (c->rule != IFEAST_GL_HALF && c->rule != IFEAST_TRAP_HALF && c->rule != IFEAST_TRAP_FULL)
+  if (c->rule != IFEAST_GL_HALF && c->rule != IFEAST_TRAP_HALF && c->rule != IFEAST_TRAP_FULL &&
+      c->rule != IFEAST_USER)
     return IFEAST_ERR_INVALID_ARG;
+  if (c->rule == IFEAST_USER && validate_contour(c) != IFEAST_OK) return IFEAST_ERR_INVALID_ARG;
   std::vector<double2> z, w;
   contour_host(c, z, w);
   for (int k = 0; k < c->nc; ++k) {
@@ -614,8 +723,9 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   if (nnz_b >= 0 && o && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   // the non-symmetric extension: standard problem, m0 within the reduced solver's limit
   if (o && o->nonsymmetric == 1 && (nnz_b >= 0 || m0 > kNonsymMaxM0)) return IFEAST_ERR_UNSUPPORTED;
-  // FP16 storage and the two-pass mode run on the four-column kernels only
-  if (o && (o->precision == IFEAST_FP16 || o->minres_two_pass == 1) && m0 % 4 != 0)
+  // 16-bit storage and the two-pass mode run on the four-column kernels only
+  if (o && (o->precision == IFEAST_FP16 || o->precision == IFEAST_BF16 ||
+            o->minres_two_pass == 1) && m0 % 4 != 0)
     return IFEAST_ERR_UNSUPPORTED;
   if (n > (int64_t)INT32_MAX - 1 || nnz > (int64_t)INT32_MAX) return IFEAST_ERR_INVALID_ARG;
   int rc = validate_contour(c);
@@ -673,12 +783,18 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
   h->K = o->inner_max_iters;
   h->opts = *o;
   h->contour = ce;
+  if (ce.rule == IFEAST_USER) {  // the caller's array may be freed after create
+    h->user_zw.assign(ce.user_zw, ce.user_zw + 4 * (size_t)ce.nc);
+    h->contour.user_zw = h->user_zw.data();
+  }
   h->nonsym = o->nonsymmetric == 1;
   h->stream = (cudaStream_t)stream;
   h->num_sms = device_sms();
   h->minres = o->inner_solver == IFEAST_INNER_MINRES;
-  h->fp32 = o->precision == IFEAST_FP32 || o->precision == IFEAST_FP16;
+  h->fp32 = o->precision == IFEAST_FP32 || o->precision == IFEAST_FP16 ||
+            o->precision == IFEAST_BF16;
   h->half = o->precision == IFEAST_FP16;
+  h->bf16 = o->precision == IFEAST_BF16;
   h->tl = make_tiling(n, h->minres ? 32 : h->C, h->num_sms);
   if (h->minres) h->tl.tiles = (m0 + 31) / 32;
   h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
@@ -789,6 +905,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->LW1 = b + off.LW1;
     h->lpart = (double *)(b + off.lpart);
     h->lalpha = (double *)(b + off.lalpha);
+    h->lcf32 = (float4 *)(b + off.lcf32);
     h->lbeta = (double *)(b + off.lbeta);
     h->ltol = (double *)(b + off.ltol);
     h->lg = (double2 *)(b + off.lg);
@@ -798,6 +915,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->lsteps = (int *)(b + off.lsteps);
     h->ldone = (int *)(b + off.ldone);
     h->lcoldone = (int *)(b + off.lcoldone);
+    h->lndone = (int *)(b + off.lndone);
     h->lactive = (int *)(b + off.lactive);
     h->lSj = (int *)(b + off.lSj);
     h->lcoef = (double *)(b + off.lcoef);
@@ -880,14 +998,40 @@ void ifeast_destroy(ifeast_t h) {
   delete h;
 }
 
-int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
-  if (!h || !X0) return IFEAST_ERR_INVALID_ARG;
+int ifeast_initial_subspace(int64_t n, int m0, uint64_t seed, double *X, void *stream) {
+  if (n < 1 || m0 < 1 || !X) return IFEAST_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(seeded_normal(n, m0, seed, X, st));
+  CK(cudaStreamSynchronize(st));
+  return IFEAST_OK;
+}
+
+int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device, uint64_t seed, void *stream) {
+  if (!h) return IFEAST_ERR_INVALID_ARG;
+  // this solve's stream (the handle's own when NULL); restored on return
+  struct StreamScope {
+    ifeast_ctx *h;
+    cudaStream_t saved, saved_prof;
+    ~StreamScope() {
+      h->stream = saved;
+      h->prof.stream = saved_prof;
+    }
+  } scope{h, h->stream, h->prof.stream};
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+    h->prof.stream = h->stream;
+  }
   const auto t0 = std::chrono::steady_clock::now();
+  const double limit_ms = h->opts.time_limit_ms;
   h->solved = false;
-  h->stats = ifeast_stats{};
+  h->stats = ifeast_stats_t{};
   const size_t xbytes = (size_t)h->n * h->m0 * sizeof(double);
-  CK(cudaMemcpyAsync(h->X, X0, xbytes,
-                     x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  if (X0)
+    CK(cudaMemcpyAsync(h->X, X0, xbytes,
+                       x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream));
+  else
+    CK(seeded_normal(h->n, h->m0, seed, h->X, h->stream));
   const double *rhs = nullptr;
   int rc = prepare_rhs(h, h->X, &rhs);
   if (rc) return rc;
@@ -897,12 +1041,18 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
   for (int it = 1; it <= h->opts.max_outer; ++it) {
     rc = clear_step_counters(h);
     if (rc) return rc;
-    if (h->minres)
-      CK(minres_filter(minres_args(h, h->X, h->Q, it > 1 ? 1 : 0), h->stream));
-    else if (h->fp32 && it > 1 && h->stats.RF <= h->opts.correction_rf)  // FP32: residual form
+    bool cut = false;  // the Lanczos loop stopped at the time limit
+    if (h->minres) {
+      MinresArgs ma = minres_args(h, h->X, h->Q, it > 1 ? 1 : 0);
+      ma.t0 = t0;
+      ma.time_limit_ms = limit_ms;
+      ma.cut = &cut;
+      CK(minres_filter(ma, h->stream));
+    } else if (h->fp32 && it > 1 && h->stats.RF <= h->opts.correction_rf) {  // FP32: residual form
       CK(gmres_filter(gmres_args(h, h->Rres, h->Q, 1), h->stream));
-    else  // right-hand sides X, or B X (norms in beta) from the previous Rayleigh-Ritz
+    } else {  // right-hand sides X, or B X (norms in beta) from the previous Rayleigh-Ritz
       CK(gmres_filter(gmres_args(h, h->rowptrB ? h->BX : h->X, h->Q), h->stream));
+    }
     if (h->nonsym)
       CK(rayleigh_ritz_nonsym(rr_args(h, h->Q, h->X), ns_args(h), h->stream));
     else
@@ -920,11 +1070,11 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
     h->stats.max_inner = std::max(h->stats.max_inner, s.max_steps);
     h->stats.shifted_cholesky += s.shifted;
     h->solved = true;
+    const double elapsed =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (h->opts.verbose)
       std::fprintf(stderr, "ifeast: iter %3d  inside %4d  RF %.3e  inner max %5d total %9lld  %.1f ms\n",
-                   it, s.count, s.RF, s.max_steps, s.total_steps,
-                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
-                       .count());
+                   it, s.count, s.RF, s.max_steps, s.total_steps, elapsed);
     if (s.breakdown) {
       result = IFEAST_ERR_BREAKDOWN;
       h->solved = false;
@@ -932,6 +1082,10 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
     }
     if (s.count > 0 && s.RF <= h->opts.tol) {
       result = IFEAST_OK;
+      break;
+    }
+    if (cut || (limit_ms > 0.0 && elapsed >= limit_ms)) {
+      result = IFEAST_ERR_TIMEOUT;
       break;
     }
   }
@@ -944,7 +1098,7 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device) {
   return result;
 }
 
-int ifeast_get_stats(ifeast_t h, ifeast_stats *s) {
+int ifeast_stats(ifeast_t h, ifeast_stats_t *s) {
   if (!h || !s) return IFEAST_ERR_INVALID_ARG;
   *s = h->stats;
   return IFEAST_OK;
@@ -1128,6 +1282,40 @@ int ifeast_apply_filter(ifeast_t h, const double *X, double *Q, double RF, int32
   return IFEAST_OK;
 }
 
+int ifeast_apply_filter_residual(ifeast_t h, const double *X, const double *lam, double *Q,
+                                 double RF, int32_t *steps) {
+  if (!h || !X || !lam || !Q || !(RF >= 0.0)) return IFEAST_ERR_INVALID_ARG;
+  if (h->nonsym || (!h->minres && !h->fp32)) return IFEAST_ERR_UNSUPPORTED;
+  h->solved = false;
+  Profiler *pf = h->profiling ? &h->prof : nullptr;
+  const size_t nm = (size_t)h->n * h->m0;
+  CK(cudaMemcpyAsync(h->X, X, nm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->lam, lam, h->m0 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  // B x_j (x_j for B = I), its norms (the stop test's scale), r_j and ||r_j||
+  const double *bx = h->X;
+  if (h->rowptrB) {
+    CK(spmm_block((int)h->n, h->m0, h->rowptrB, h->colidxB, h->valB, h->X, h->BX, h->Pg,
+                  h->stream));
+    bx = h->BX;
+  }
+  CK(column_norms((int)h->n, h->m0, bx, h->res_part, h->Pr, h->beta, h->stream, pf));
+  CK(residual_block((int)h->n, h->m0, h->rowptr, h->colidx, h->val, h->X, bx, h->lam, h->Rres,
+                    h->stream));
+  CK(column_norms((int)h->n, h->m0, h->Rres, h->res_part, h->Pr, h->rnorm, h->stream, pf));
+  int rc = set_tolerance(h, RF);
+  if (rc) return rc;
+  if (h->minres)
+    CK(minres_filter(minres_args(h, h->X, Q, 1), h->stream));
+  else
+    CK(gmres_filter(gmres_args(h, h->Rres, Q, 1), h->stream));
+  if (steps)
+    CK(cudaMemcpyAsync(steps, h->minres ? h->lsteps : h->steps, h->C * sizeof(int),
+                       cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->profiling && h->prof.collect()) return IFEAST_ERR_CUDA;
+  return IFEAST_OK;
+}
+
 int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, double *resid) {
   if (!h || !Q || !X) return IFEAST_ERR_INVALID_ARG;
   int rc = set_tolerance(h, 1.0);
@@ -1213,7 +1401,7 @@ const char *ifeast_kernel_name(int k) {
       "gmres_solve",    "gmres_quadrature", "lanczos_step",   "lanczos_givens",
       "lanczos_solve",  "lanczos_coef",     "lanczos_quadrature", "rr_spmm",
       "rr_gram",        "rr_gram_reduce",   "rr_eig",         "rr_update_resid",
-      "rr_resid_reduce"};
+      "rr_resid_reduce", "lanczos_reduce"};
   return (k >= 0 && k < K_COUNT) ? names[k] : "unknown";
 }
 

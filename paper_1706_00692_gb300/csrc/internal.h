@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <chrono>
 #include <cstddef>
 #include <cstdint>
 
@@ -39,6 +40,7 @@ enum KernelId {
   K_RR_EIG,        // reduced generalised eigenproblem (one CTA)
   K_RR_UPDATE,     // X = Q X_Q and residual partials
   K_RR_RESID,      // residuals, interval count, ||R_F||
+  K_LZ_REDUCE,     // shared basis, FP32 steps: alpha_s, beta_{s+1} from the step's partials
   K_COUNT
 };
 
@@ -148,8 +150,9 @@ struct MinresState {
   double2 *rot;             // [nc*m0][4] last two Givens rotations
   double *tol;              // [nc*m0] bound on |g_{s+1}|
   int *steps;               // [nc*m0]
-  int *done;                // [nc*m0] (FP32 step kernels: two buffers, by step parity)
-  int *coldone;             // [m0]
+  int *done;                // [nc*m0]
+  int *coldone;             // [m0] column finished (all pairs done, or a breakdown)
+  int *ndone;               // [m0] pairs of the column done (FP32 step kernels)
   int *active;              // [1] columns still running at the last checked step
   DevStatus *status;
 };
@@ -170,6 +173,7 @@ struct MinresArgs {
   int n, m0, nc, K;
   int fp32;                 // FP32 arithmetic in the Krylov kernels
   int half;                 // FP16 storage of the Krylov vectors (with fp32)
+  int bf16;                 // BF16 storage of the Krylov vectors (with fp32)
   float wscale;             // FP16: w_s is stored as w_s / wscale (||A||_inf); else 1
   const int32_t *rowptr, *colidx;
   const void *val_t;        // float or double values of A
@@ -179,6 +183,7 @@ struct MinresArgs {
   void *V, *W0, *W1;        // basis and double-buffered work vectors (T)
   double *part;             // P x 3 x m0
   double *alpha, *beta;     // [K][m0], [K+1][m0]
+  float4 *cf32;             // [K+1][m0] FP32 {alpha_{s-1}, beta_s, 1/beta_s, 0} for step s
   double2 *Yc;              // [nc][K][m0]
   double *coef, *cx;        // [K][m0] (+ an FP32 copy after it), [m0]
   int *Sj;                  // [m0]
@@ -195,12 +200,25 @@ struct MinresArgs {
   const float *valE;        // n x ell_w values (padded with zero)
   int two_pass;             // 1: three basis slots and a second pass (FP32 kernels only)
   float *Qf;                // n x m0 FP32 accumulator of the second pass
+  // wall-time limit, checked at the lagged early-exit checks of the Lanczos
+  // loop: past it the loop stops (the filter uses the steps run) and *cut is set
+  std::chrono::steady_clock::time_point t0{};
+  double time_limit_ms = 0.0;  // <= 0: none
+  bool *cut = nullptr;
 };
 cudaError_t build_ell(int n, int W, const int32_t *rowptr, const int32_t *colidx, const float *val,
                       int32_t *colE, float *valE, cudaStream_t st);
 cudaError_t minres_init();  // once per device: opt-in shared-memory sizes
 cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st);
 cudaError_t convert_to_float(const double *a, float *b, size_t n, cudaStream_t st);
+
+// X (n x m0 row-major) = i.i.d. N(0,1) from Philox4x32-10 blocks keyed by seed
+// (element pair 2p, 2p+1 from counter p, Box-Muller; layout in ifeast.h).
+cudaError_t seeded_normal(int64_t n, int m0, uint64_t seed, double *X, cudaStream_t st);
+// R = A X - BX diag(lam) for n x m0 row-major blocks (BX = X for B = I), FP64.
+cudaError_t residual_block(int n, int m0, const int32_t *rowptr, const int32_t *colidx,
+                           const double *val, const double *X, const double *BX,
+                           const double *lam, double *R, cudaStream_t st);
 
 // ---- Rayleigh-Ritz and residual -------------------------------------------
 struct RRArgs {

@@ -21,6 +21,7 @@
 // <v,w>^2/<v,v> (the squared norm of w_s - alpha_s v_s, using the actual
 // <v,v> so that rounding in earlier normalisations does not feed back), and
 // advances every node's Givens QR.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -66,6 +67,8 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
     const double x = b > 0.0 ? rhs[idx] / b : 0.0;
     if constexpr (std::is_same_v<T, __half>)
       V0[idx] = __float2half_rn((float)x);
+    else if constexpr (std::is_same_v<T, __nv_bfloat16>)
+      V0[idx] = __float2bfloat16_rn((float)x);
     else
       V0[idx] = (T)x;
   }
@@ -90,6 +93,7 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
   }
   if (idx < (size_t)m0) {
     st.coldone[idx] = rnorm[idx] > 0.0 ? 0 : 1;
+    st.ndone[idx] = rnorm[idx] > 0.0 ? 0 : nc;  // pairs of the column already done
     beta[idx] = 0.0;  // beta_0
   }
   if (idx == 0) st.active[0] = 0;
@@ -106,6 +110,8 @@ __global__ void k_lz_v0(int n, int m0, const double *__restrict__ rhs,
   const double x = b > 0.0 ? rhs[idx] / b : 0.0;
   if constexpr (std::is_same_v<T, __half>)
     V0[idx] = __float2half_rn((float)x);
+  else if constexpr (std::is_same_v<T, __nv_bfloat16>)
+    V0[idx] = __float2bfloat16_rn((float)x);
   else
     V0[idx] = (T)x;
 }
@@ -453,60 +459,36 @@ k_lanczos_givens(int P, int m0, int nc, int K, int s, const double *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Coefficient and Givens step after an FP32 Lanczos step (k_lanczos_step_vec,
-// k_lanczos_step_ell), whose blocks leave FP32 partials part[b][3][m0].
-// One block per (32-column tile, node k), so the FP64 Givens arithmetic of the
-// nc x m0 pairs is spread over tiles x nc blocks instead of one block per tile.
-// The pairs' done flags are double-buffered by step parity: step s reads
-// done[s & 1] and writes done[(s + 1) & 1], and a column is finished when all
-// of its pairs are done, so no block reads a flag another block of the same
-// launch writes.
-//  1. every block of a tile sums the P partials of its 32 columns: warp w takes
-//     the rows b = w (mod NW) with compensated (Kahan) FP32 sums, then warp 0
-//     adds the warp sums (and compensations) in warp order, again
-//     compensated. The order is the same in every block, so all nodes see
-//     bit-identical alpha_s and beta_{s+1}; node 0's block stores them.
-//  2. warp 0 advances the QR of the tridiagonal (z_k I - Tbar_s) for its 32
-//     pairs (same rotations as givens_tile; the rotation is formed from
-//     rsqrt of rho^2, and the stop test compares |g_{s+1}|^2 with tol^2),
-//     writes the pairs' new done flags and raises *active for a pair that
-//     still runs.
-// Launched with programmatic dependent launch after the step kernel: the
-// pair state is loaded before waiting for the step kernel to finish.
+// After an FP32 Lanczos step (k_lanczos_step_vec, k_lanczos_step_ell), whose
+// blocks leave FP32 partials part[b][3][m0], only the reduction that gives
+// alpha_s and beta_{s+1} stays between two consecutive step kernels
+// (k_lanczos_coef_f). The Givens QR of every (node, column) pair does not feed
+// the next step, so it runs in batches of kGivensBatch steps
+// (k_lanczos_givens_batch): the columns' stop flags then lag by less than one
+// batch, and a finished column runs at most that many extra Lanczos steps,
+// whose vectors no solution uses (each pair keeps its own step count).
 // ---------------------------------------------------------------------------
 constexpr int kGfThreads = 512;
+constexpr int kGivensBatch = 16;
 
+// One block per 32-column tile: warp w sums the partial rows b = w (mod NW)
+// with compensated (Kahan) FP32 sums, warp 0 adds the warp sums and their
+// compensations in warp order, again compensated, and converts once to FP64:
+// alpha_s = <v,w>/<v,v>, beta_{s+1}^2 = <w,w> - alpha_s <v,w> (0 below the
+// breakdown threshold, which finishes the column). Only columns still running
+// (coldone[j] == 0) get coefficients. active_reset (check steps): cleared here
+// so that the Givens batch that follows can raise it.
 __global__ void __launch_bounds__(kGfThreads)
-k_lanczos_givens_f(int P, int m0, int nc, int K, int s, const float *__restrict__ part,
-                   double *__restrict__ alpha, double *__restrict__ beta, const MinresState st,
-                   double brk2) {
+k_lanczos_coef_f(int P, int m0, int s, const float *__restrict__ part, double *__restrict__ alpha,
+                 double *__restrict__ beta, float4 *__restrict__ cf, int *__restrict__ coldone,
+                 double brk2, int *__restrict__ active_reset) {
   constexpr int NW = kGfThreads / 32;
   __shared__ float red[3][2][NW][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int tile = blockIdx.x, k = blockIdx.y;
-  const int j = tile * 32 + lane;
-  const int p = k * m0 + j;
-  const size_t C = (size_t)nc * m0;
-  const int *__restrict__ done_r = st.done + (size_t)(s & 1) * C;
-  int *__restrict__ done_w = st.done + (size_t)((s + 1) & 1) * C;
-  // warp 0: the pair's state and the column's flags, in flight during the reduction
-  int cd = 1, pdone = 1;
-  double2 rr[4];
-  double2 gs = make_double2(0.0, 0.0);
-  double tol = 0.0, b0 = 0.0;
-  if (warp == 0 && j < m0) {
-    pdone = done_r[p];
-    for (int kk = 0; kk < nc; ++kk) cd &= done_r[(size_t)kk * m0 + j];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) rr[u] = st.rot[(size_t)p * 4 + u];
-    gs = st.g[(size_t)p * (K + 1) + s];
-    tol = st.tol[p];
-    b0 = beta[(size_t)s * m0 + j];
-  }
-  // the state above was written by the previous Givens step, which finished
-  // before the step kernel passed its wait; the partials need the step kernel
-  pdl_wait();
+  const int j = blockIdx.x * 32 + lane;
+  pdl_wait();  // the partials of the step kernel
   pdl_launch_next();
+  if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   {
     float sm[3] = {0.f, 0.f, 0.f}, cp[3] = {0.f, 0.f, 0.f};
     if (j < m0) {
@@ -538,10 +520,7 @@ k_lanczos_givens_f(int P, int m0, int nc, int K, int s, const float *__restrict_
     }
   }
   __syncthreads();
-  if (warp != 0 || j >= m0) return;
-  // warp sums and their compensations, combined in FP32 with the same
-  // compensated sum, then one conversion to FP64 (FP64 instructions are the
-  // slow part of this kernel)
+  if (warp != 0 || j >= m0 || coldone[j]) return;
   double tot[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -557,60 +536,100 @@ k_lanczos_givens_f(int P, int m0, int nc, int K, int s, const float *__restrict_
     tot[q] = (double)S - (double)Cc;
   }
   const double vv = tot[0], vw = tot[1], ww = tot[2];
-  int nd = 1;  // the pair's done flag after this step
-  if (!cd) {
-    const double a = vv > 0.0 ? vw / vv : 0.0;
-    const double b2 = ww - a * vw;
-    const double b1 = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
-    if (k == 0) {
-      alpha[(size_t)s * m0 + j] = a;
-      beta[(size_t)(s + 1) * m0 + j] = b1;
+  const double a = vv > 0.0 ? vw / vv : 0.0;
+  const double b2 = ww - a * vw;
+  const double b1 = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
+  alpha[(size_t)s * m0 + j] = a;
+  beta[(size_t)(s + 1) * m0 + j] = b1;
+  // FP32 copies for the next step kernel: alpha_s, beta_{s+1}, 1 / beta_{s+1}
+  cf[(size_t)(s + 1) * m0 + j] =
+      make_float4((float)a, (float)b1, b1 != 0.0 ? (float)(1.0 / b1) : 0.f, 0.f);
+  if (b1 == 0.0) coldone[j] = 1;
+}
+
+// Givens QR of the shifted tridiagonals (z_k I - Tbar) for steps s0 .. s1 - 1
+// of every pair still running; grid (tiles, nc), one thread per (node k,
+// column j). Per step: column s of (z_k I - Tbar) is (fill, -beta_s,
+// z_k - alpha_s, -beta_{s+1}) in rows s-2 .. s+1; the two previous rotations
+// act on it, a new rotation (formed from rsqrt of rho^2) annihilates
+// -beta_{s+1}, and the rotated right-hand side gives the residual |g_{s+1}|.
+// A pair stops at its tolerance (|g_{s+1}|^2 <= tol^2) or at a breakdown
+// (beta_{s+1} = 0); the last pair of a column to stop finishes the column.
+// Any pair still running raises *active.
+__global__ void __launch_bounds__(32)
+k_lanczos_givens_batch(int m0, int nc, int K, int s0, int s1, const double *__restrict__ alpha,
+                       const double *__restrict__ beta, const MinresState st) {
+  const int j = blockIdx.x * 32 + threadIdx.x, k = blockIdx.y;
+  const int p = k * m0 + j;
+  pdl_wait();  // alpha, beta of the batch's steps
+  pdl_launch_next();
+  if (j >= m0 || st.done[p]) return;
+  // the last two rotations [cs, sn] by step parity, in registers
+  double2 c0 = st.rot[(size_t)p * 4 + 0], s0r = st.rot[(size_t)p * 4 + 1];
+  double2 c1 = st.rot[(size_t)p * 4 + 2], s1r = st.rot[(size_t)p * 4 + 3];
+  double2 *g = st.g + (size_t)p * (K + 1);
+  double2 gs = g[s0];
+  const double tol = st.tol[p];
+  const double2 zk = st.z[k];
+  bool fin = false;
+  for (int s = s0; s < s1 && !fin; ++s) {
+    const double a = alpha[(size_t)s * m0 + j];
+    const double b0 = beta[(size_t)s * m0 + j], b1 = beta[(size_t)(s + 1) * m0 + j];
+    double2 e2 = make_double2(0.0, 0.0);
+    double2 e1 = make_double2(-b0, 0.0);
+    double2 e0 = make_double2(zk.x - a, zk.y);
+    // rotation of step s - 2 sits in the parity slot of s, that of step s - 1 in the other
+    const bool odd = s & 1;
+    if (s >= 2) {
+      const double2 cs = odd ? c1 : c0, sn = odd ? s1r : s0r;
+      e2 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
+      e1 = cmul(cs, e1);
     }
-    if (!pdone) {
-      // column s of (z I - Tbar): rows s-2 (fill), s-1, s, s+1
-      double2 e2 = make_double2(0.0, 0.0);
-      double2 e1 = make_double2(-b0, 0.0);
-      double2 e0 = make_double2(st.z[k].x - a, st.z[k].y);
-      // rotation of step s - 2 sits in slots (s & 1) * 2, that of step s - 1 in the other
-      const bool odd = s & 1;
-      if (s >= 2) {
-        const double2 cs = odd ? rr[2] : rr[0], sn = odd ? rr[3] : rr[1];
-        e2 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
-        e1 = cmul(cs, e1);
-      }
-      if (s >= 1) {
-        const double2 cs = odd ? rr[0] : rr[2], sn = odd ? rr[1] : rr[3];
-        const double2 x = e1, y = e0;
-        e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
-                          cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
-        const double2 sx = cmul(sn, x), cy = cmul(cs, y);
-        e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
-      }
-      const double rho2 = cabs2(e0) + b1 * b1;
-      if (rho2 > 0.0) {
-        const double inv = rsqrt(rho2);
-        const double rho = rho2 * inv;
-        // rotation annihilating the subdiagonal entry -beta_{s+1} below e0
-        const double2 cs = make_double2(e0.x * inv, e0.y * inv);
-        const double2 sn = make_double2(-b1 * inv, 0.0);
-        double2 *R = st.R + ((size_t)p * K + s) * 3;
-        R[0] = make_double2(rho, 0.0);
-        R[1] = e1;
-        R[2] = e2;
-        double2 *rot = st.rot + (size_t)p * 4;
-        rot[(s & 1) * 2] = cs;
-        rot[(s & 1) * 2 + 1] = sn;
-        const double2 gn = make_double2(-sn.x * gs.x, -sn.x * gs.y);  // sn is real
-        double2 *g = st.g + (size_t)p * (K + 1);
-        g[s + 1] = gn;
-        g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
-        st.steps[p] = s + 1;
-        nd = (b1 == 0.0 || (tol > 0.0 && cabs2(gn) <= tol * tol)) ? 1 : 0;
-      }
+    if (s >= 1) {
+      const double2 cs = odd ? c0 : c1, sn = odd ? s0r : s1r;
+      const double2 x = e1, y = e0;
+      e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
+                        cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
+      const double2 sx = cmul(sn, x), cy = cmul(cs, y);
+      e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
     }
+    const double rho2 = cabs2(e0) + b1 * b1;
+    if (!(rho2 > 0.0)) {
+      fin = true;
+      break;
+    }
+    const double inv = rsqrt(rho2);
+    const double rho = rho2 * inv;
+    const double2 cs = make_double2(e0.x * inv, e0.y * inv);
+    const double2 sn = make_double2(-b1 * inv, 0.0);
+    double2 *R = st.R + ((size_t)p * K + s) * 3;
+    R[0] = make_double2(rho, 0.0);
+    R[1] = e1;
+    R[2] = e2;
+    if (odd) {
+      c1 = cs;
+      s1r = sn;
+    } else {
+      c0 = cs;
+      s0r = sn;
+    }
+    const double2 gn = make_double2(-sn.x * gs.x, -sn.x * gs.y);  // sn is real
+    g[s + 1] = gn;
+    g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
+    gs = gn;
+    st.steps[p] = s + 1;
+    fin = b1 == 0.0 || (tol > 0.0 && cabs2(gn) <= tol * tol);
   }
-  done_w[p] = nd;
-  if (!nd) *st.active = 1;
+  st.rot[(size_t)p * 4 + 0] = c0;
+  st.rot[(size_t)p * 4 + 1] = s0r;
+  st.rot[(size_t)p * 4 + 2] = c1;
+  st.rot[(size_t)p * 4 + 3] = s1r;
+  if (fin) {
+    st.done[p] = 1;
+    if (atomicAdd(&st.ndone[j], 1) == nc - 1) st.coldone[j] = 1;
+  } else {
+    *st.active = 1;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -640,6 +659,7 @@ struct Store4;
 template <>
 struct Store4<float> {
   static constexpr bool kHalf = false;
+  static constexpr bool kScaled = false;
   using Raw = float4;  // four stored values as loaded
   __device__ static Raw load_raw(const float *p) { return *reinterpret_cast<const float4 *>(p); }
   __device__ static float4 cvt(Raw r) { return r; }
@@ -651,6 +671,7 @@ struct Store4<float> {
 template <>
 struct Store4<__half> {
   static constexpr bool kHalf = true;
+  static constexpr bool kScaled = true;  // w_s stored divided by wsc
   using Raw = uint2;
   __device__ static Raw load_raw(const __half *p) { return *reinterpret_cast<const uint2 *>(p); }
   __device__ static float4 cvt(Raw u) {
@@ -679,6 +700,35 @@ struct Store4<__half> {
   __device__ static float rnd(float x) { return __half2float(__float2half_rn(x)); }
 };
 
+// BF16: the exponent range of FP32, so the work vectors are stored unscaled
+// (the kernels pass wsc = 1 and skip the scaling when kScaled is false).
+template <>
+struct Store4<__nv_bfloat16> {
+  static constexpr bool kHalf = true;
+  static constexpr bool kScaled = false;
+  using Raw = uint2;
+  __device__ static float4 cvt(Raw u) {
+    __nv_bfloat162 h0, h1;
+    memcpy(&h0, &u.x, 4);
+    memcpy(&h1, &u.y, 4);
+    const float2 a = __bfloat1622float2(h0), b = __bfloat1622float2(h1);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  __device__ static Raw load_raw(const __nv_bfloat16 *p) {
+    return *reinterpret_cast<const uint2 *>(p);
+  }
+  __device__ static float4 load(const __nv_bfloat16 *p) { return cvt(load_raw(p)); }
+  __device__ static void store(__nv_bfloat16 *p, float4 v) {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    memcpy(&u.x, &h0, 4);
+    memcpy(&u.y, &h1, 4);
+    *reinterpret_cast<uint2 *>(p) = u;
+  }
+  __device__ static void store1(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+  __device__ static float rnd(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+};
+
 // Row epilogue of the FP32-arithmetic step kernels. From the row's own
 // gathered values o1 (w_{s-1}, or v_0 at s = 0) and o2 (v_{s-1}) and the row
 // products acc1 = (A G1)[r], acc2 = (A v_{s-1})[r]: v_s = (w_{s-1} -
@@ -692,7 +742,7 @@ __device__ __forceinline__ void finish_row(float4 o1, float4 o2, float4 acc1, fl
                                            size_t off, float (&vv)[4], float (&vw)[4],
                                            float (&ww)[4], float (&vout)[4]) {
   using St = Store4<S>;
-  if (St::kHalf && !FIRST) {  // w_{s-1} is stored divided by wsc
+  if (St::kScaled && !FIRST) {  // w_{s-1} is stored divided by wsc
     o1 = make_float4(o1.x * wsc, o1.y * wsc, o1.z * wsc, o1.w * wsc);
     acc1 = make_float4(acc1.x * wsc, acc1.y * wsc, acc1.z * wsc, acc1.w * wsc);
   }
@@ -709,10 +759,14 @@ __device__ __forceinline__ void finish_row(float4 o1, float4 o2, float4 acc1, fl
       w[i] = (a1a[i] - ap[i] * a2a[i]) * ib[i] - bs[i] * o2a[i];
     }
     wst[i] = w[i];
-    if constexpr (St::kHalf) {
+    if constexpr (St::kScaled) {
       v[i] = St::rnd(v[i]);
       wst[i] = St::rnd(w[i] / wsc);
       w[i] = wst[i] * wsc;
+    } else if constexpr (St::kHalf) {
+      v[i] = St::rnd(v[i]);
+      wst[i] = St::rnd(w[i]);
+      w[i] = wst[i];
     }
     if (act[i]) {
       vv[i] = fmaf(v[i], v[i], vv[i]);
@@ -762,20 +816,14 @@ __device__ __forceinline__ void store_partials_f(const float (&vv)[4], const flo
   }
 }
 
-// Column mask of an FP32 step kernel: column j still runs while some node's
-// pair (k, j) is not done (flags left by the previous Givens step); in the
-// second pass of the two-pass mode, while s < Sj[j] (the steps its solves took).
-__device__ __forceinline__ void load_column_mask(int m0, int nc, const int *__restrict__ done_r,
+// Column mask of an FP32 step kernel: column j still runs while coldone[j] is
+// 0 (set once the last Givens batch found all of its pairs done, or at a
+// breakdown); in the second pass of the two-pass mode, while s < Sj[j] (the
+// steps its solves took).
+__device__ __forceinline__ void load_column_mask(int m0, const int *__restrict__ coldone,
                                                  int *cdone, const int *__restrict__ Sj, int s) {
-  if (Sj != nullptr) {
-    for (int j = threadIdx.x; j < m0; j += kVThreads) cdone[j] = s < Sj[j] ? 0 : 1;
-    __syncthreads();
-    return;
-  }
-  for (int j = threadIdx.x; j < m0; j += kVThreads) cdone[j] = 1;
-  __syncthreads();
-  for (int t = threadIdx.x; t < nc * m0; t += kVThreads)
-    if (done_r[t] == 0) cdone[t % m0] = 0;  // every writer stores the same value
+  for (int j = threadIdx.x; j < m0; j += kVThreads)
+    cdone[j] = Sj != nullptr ? (s < Sj[j] ? 0 : 1) : coldone[j];
   __syncthreads();
 }
 
@@ -812,14 +860,11 @@ __global__ void __launch_bounds__(kVThreads, 2)
 k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
                    const int32_t *__restrict__ colidx, const float *__restrict__ val,
                    S *__restrict__ V, const S *__restrict__ Wprev, S *__restrict__ Wout,
-                   const double *__restrict__ alpha, const double *__restrict__ beta,
-                   const int *__restrict__ done_r, int nc, float *__restrict__ part,
-                   int stride_items, float wsc, int *__restrict__ active_reset,
-                   const Pass2 p2) {
+                   const float4 *__restrict__ cf, const int *__restrict__ coldone,
+                   float *__restrict__ part, int stride_items, float wsc, const Pass2 p2) {
   using St = Store4<S>;
   pdl_wait();
   pdl_launch_next();
-  if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
   // basis slot of step s: the stored basis, or a ring of three in the two-pass mode
@@ -835,15 +880,14 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
   if (!FIRST && thr) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int j = 4 * q + i;
-      const double bj = beta[(size_t)s * m0 + j];
-      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
-      bs[i] = (float)bj;
-      ib[i] = bj != 0.0 ? (float)(1.0 / bj) : 0.f;
+      const float4 c = cf[(size_t)s * m0 + 4 * q + i];  // alpha_{s-1}, beta_s, 1 / beta_s
+      ap[i] = c.x;
+      bs[i] = c.y;
+      ib[i] = c.z;
     }
   }
   __shared__ int cdone[1024];
-  load_column_mask(m0, nc, done_r, cdone, p2.Sj, s);
+  load_column_mask(m0, coldone, cdone, p2.Sj, s);
   bool act[4];
   bool qact = false;
 #pragma unroll
@@ -912,14 +956,11 @@ __global__ void __launch_bounds__(kVThreads, 2)
 k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
                    const float *__restrict__ valE, S *__restrict__ V,
                    const S *__restrict__ Wprev, S *__restrict__ Wout,
-                   const double *__restrict__ alpha, const double *__restrict__ beta,
-                   const int *__restrict__ done_r, int nc, float *__restrict__ part,
-                   int stride_items, float wsc, int *__restrict__ active_reset,
-                   const Pass2 p2) {
+                   const float4 *__restrict__ cf, const int *__restrict__ coldone,
+                   float *__restrict__ part, int stride_items, float wsc, const Pass2 p2) {
   using St = Store4<S>;
   pdl_wait();
   pdl_launch_next();
-  if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   const int MQ = m0 >> 2;
   const size_t vs = (size_t)n * m0;
   // basis slot of step s: the stored basis, or a ring of three in the two-pass mode
@@ -936,15 +977,14 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
   if (!FIRST && thr) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int j = q4 + i;
-      const double bj = beta[(size_t)s * m0 + j];
-      ap[i] = (float)alpha[(size_t)(s - 1) * m0 + j];
-      bs[i] = (float)bj;
-      ib[i] = bj != 0.0 ? (float)(1.0 / bj) : 0.f;
+      const float4 c = cf[(size_t)s * m0 + q4 + i];  // alpha_{s-1}, beta_s, 1 / beta_s
+      ap[i] = c.x;
+      bs[i] = c.y;
+      ib[i] = c.z;
     }
   }
   __shared__ int cdone[1024];
-  load_column_mask(m0, nc, done_r, cdone, p2.Sj, s);
+  load_column_mask(m0, coldone, cdone, p2.Sj, s);
   bool act[4];
   bool qact = false;
 #pragma unroll
@@ -954,25 +994,30 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
   }
   const bool all4 = act[0] && act[1] && act[2] && act[3];
   float vv[4] = {0.f, 0.f, 0.f, 0.f}, vw[4] = {0.f, 0.f, 0.f, 0.f}, ww[4] = {0.f, 0.f, 0.f, 0.f};
+  // odd steps walk the rows backwards: the first rows they read are the last
+  // ones the previous step wrote, still in L2
+  const bool rev = s & 1;
   int r = gt / MQ;
   if (qact && r < n) {
     int cn[W];
+    const int r0m = rev ? n - 1 - r : r;
 #pragma unroll
     for (int u = 0; u < W; u += 4) {
-      const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)r * W + u);
+      const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)r0m * W + u);
       cn[u] = c4.x;
       cn[u + 1] = c4.y;
       cn[u + 2] = c4.z;
       cn[u + 3] = c4.w;
     }
     for (; r < n; r += rstep) {
+      const int rm = rev ? n - 1 - r : r;  // the row this iteration takes
       int c[W];
 #pragma unroll
       for (int u = 0; u < W; ++u) c[u] = cn[u];
       float a[W];
 #pragma unroll
       for (int u = 0; u < W; u += 4) {
-        const float4 a4 = *reinterpret_cast<const float4 *>(valE + (size_t)r * W + u);
+        const float4 a4 = *reinterpret_cast<const float4 *>(valE + (size_t)rm * W + u);
         a[u] = a4.x;
         a[u + 1] = a4.y;
         a[u + 2] = a4.z;
@@ -984,15 +1029,16 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
 #pragma unroll
       for (int u = 0; u < W; ++u) {
         const int co = c[u] * m0 + q4;
-        const bool ld = u == 0 || c[u] != r;
+        const bool ld = u == 0 || c[u] != rm;
         g1[u] = ld ? St::load_raw(G1 + co) : zr;
         if (!FIRST) g2[u] = ld ? St::load_raw(G2 + co) : zr;
       }
       const int rn = r + rstep;  // next row's indices, in flight with the gathers
       if (rn < n) {
+        const int rnm = rev ? n - 1 - rn : rn;
 #pragma unroll
         for (int u = 0; u < W; u += 4) {
-          const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)rn * W + u);
+          const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)rnm * W + u);
           cn[u] = c4.x;
           cn[u + 1] = c4.y;
           cn[u + 2] = c4.z;
@@ -1008,10 +1054,10 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
       const float4 o1 = St::cvt(g1[0]), o2 = FIRST ? z4 : St::cvt(g2[0]);
       float vo[4];
       finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout,
-                           (size_t)(r * m0 + q4), vv, vw, ww, vo);
+                           (size_t)(rm * m0 + q4), vv, vw, ww, vo);
       if (p2.Qacc != nullptr) {
         const float vp[4] = {o2.x, o2.y, o2.z, o2.w};
-        accumulate_q(p2, m0, s, (size_t)(r * m0 + q4), q4, vo, vp, act);
+        accumulate_q(p2, m0, s, (size_t)(rm * m0 + q4), q4, vo, vp, act);
       }
     }
   }
@@ -1250,9 +1296,12 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
 }
 
 // Lanczos breakdown threshold on beta^2 / ||w||^2 for the storage precision
+// ((16 u)^2 for the storage's unit roundoff u: below it the new direction is
+// not resolved by the stored vectors)
 template <typename T>
 double brk2_of() {
   if constexpr (std::is_same_v<T, __half>) return 1e-4;
+  if constexpr (std::is_same_v<T, __nv_bfloat16>) return 4e-3;
   return sizeof(T) == 4 ? 1e-6 : 1e-16;
 }
 
@@ -1277,19 +1326,16 @@ void vec_grid(const MinresArgs &a, int &blocks, int &stride_items) {
 
 template <typename T>
 cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T *Wo,
-                                const ValOf<T> *val, int *active_reset, const Pass2 &p2,
-                                cudaStream_t st) {
+                                const ValOf<T> *val, const Pass2 &p2, cudaStream_t st) {
   if constexpr (sizeof(T) <= 4) {
-    // pair done flags of the previous Givens step (double-buffered by parity)
-    const int *done_r = a.ms.done + (size_t)(s & 1) * a.nc * a.m0;
+    const int *coldone = a.ms.coldone;  // columns finished by the Givens batches
     float *part = reinterpret_cast<float *>(a.part);
     if (use_ell_step(a)) {
       int blocks, stride_items;
       vec_grid(a, blocks, stride_items);
 #define IFEAST_ELL_LAUNCH(F, WW)                                                              \
   launch_pdl(k_lanczos_step_ell<T, F, WW>, dim3(blocks), dim3(kVThreads), st, a.n, a.m0, s,     \
-             a.colE, a.valE, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc, part, stride_items,     \
-             a.wscale, active_reset, p2)
+             a.colE, a.valE, V, Wp, Wo, a.cf32, coldone, part, stride_items, a.wscale, p2)
       if (a.ell_w == 8)
         return s == 0 ? IFEAST_ELL_LAUNCH(true, 8) : IFEAST_ELL_LAUNCH(false, 8);
       return s == 0 ? IFEAST_ELL_LAUNCH(true, 16) : IFEAST_ELL_LAUNCH(false, 16);
@@ -1300,15 +1346,15 @@ cudaError_t launch_lanczos_step(const MinresArgs &a, int s, T *V, const T *Wp, T
       vec_grid(a, blocks, stride_items);
       if (s == 0)
         return launch_pdl(k_lanczos_step_vec<T, true>, dim3(blocks), dim3(kVThreads), st, a.n,
-                          a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, done_r,
-                          a.nc, part, stride_items, a.wscale, active_reset, p2);
+                          a.m0, s, a.rowptr, a.colidx, val, V, Wp, Wo, a.cf32, coldone, part,
+                          stride_items, a.wscale, p2);
       return launch_pdl(k_lanczos_step_vec<T, false>, dim3(blocks), dim3(kVThreads), st, a.n, a.m0,
-                        s, a.rowptr, a.colidx, val, V, Wp, Wo, a.alpha, a.beta, done_r, a.nc,
-                        part, stride_items, a.wscale, active_reset, p2);
+                        s, a.rowptr, a.colidx, val, V, Wp, Wo, a.cf32, coldone, part,
+                        stride_items, a.wscale, p2);
     }
   }
-  if constexpr (std::is_same_v<T, __half>) {
-    return cudaErrorInvalidValue;  // FP16 storage needs m0 % 4 == 0 (checked at create)
+  if constexpr (std::is_same_v<T, __half> || std::is_same_v<T, __nv_bfloat16>) {
+    return cudaErrorInvalidValue;  // 16-bit storage needs m0 % 4 == 0 (checked at create)
   } else {
     const int nj = (a.m0 + 31) / 32;
     switch (nj) {
@@ -1341,7 +1387,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   IFEAST_PROF_END(a.prof);
   const double brk2 = brk2_of<T>();
   int step_blocks = a.tl.P;
-  // the FP32-arithmetic vec / ELL step kernels leave FP32 partials for k_lanczos_givens_f
+  // the FP32-arithmetic vec / ELL step kernels leave FP32 partials for k_lanczos_coef_f
   const bool f32_partials = sizeof(T) <= 4 && use_vec_step(a);
   if (f32_partials) {
     int stride_items;
@@ -1351,27 +1397,40 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   const Pass2 pass1 = {nullptr, nullptr, nullptr, a.two_pass ? 3 : 0};
   cudaError_t e = cudaGetLastError();
   int s = 0, ck = 0;  // ck: checkpoints enqueued
+  int s0 = 0;         // first step not yet taken by a Givens batch (FP32 kernels)
   for (; s < a.K && e == cudaSuccess; ++s) {
     const bool check = a.check_every > 0 && (s + 1) % a.check_every == 0 && s + 1 < a.K;
     IFEAST_PROF_BEGIN(a.prof, K_LZ_STEP);
-    // on a checked step the FP32 step kernels clear *active themselves (no
-    // memset between the step and Givens kernels breaks their launch overlap)
-    e = launch_lanczos_step<T>(a, s, V, W[(s + 1) & 1], W[s & 1], val,
-                               (check && f32_partials) ? a.ms.active : nullptr, pass1, st);
+    e = launch_lanczos_step<T>(a, s, V, W[(s + 1) & 1], W[s & 1], val, pass1, st);
     IFEAST_PROF_END(a.prof);
     if (check && !f32_partials && e == cudaSuccess)
       e = cudaMemsetAsync(a.ms.active, 0, sizeof(int), st);
-    IFEAST_PROF_BEGIN(a.prof, K_LZ_GIVENS);
     if (e == cudaSuccess) {
-      if (f32_partials)
-        e = launch_pdl(k_lanczos_givens_f, dim3(a.tl.tiles, a.nc), dim3(kGfThreads), st,
-                       step_blocks, a.m0, a.nc, a.K, s, reinterpret_cast<const float *>(a.part),
-                       a.alpha, a.beta, a.ms, brk2);
-      else
+      if (f32_partials) {
+        // alpha_s, beta_{s+1}; then, at batch ends and checks, the Givens QR of
+        // the steps since the last batch (no memset between the step and
+        // coefficient kernels breaks their launch overlap: on a checked step
+        // the coefficient kernel clears *active itself)
+        const bool batch = (s + 1) % kGivensBatch == 0 || check || s + 1 == a.K;
+        IFEAST_PROF_BEGIN(a.prof, K_LZ_REDUCE);
+        e = launch_pdl(k_lanczos_coef_f, dim3(a.tl.tiles), dim3(kGfThreads), st, step_blocks, a.m0,
+                       s, reinterpret_cast<const float *>(a.part), a.alpha, a.beta, a.cf32,
+                       a.ms.coldone, brk2, batch ? a.ms.active : nullptr);
+        IFEAST_PROF_END(a.prof);
+        if (batch && e == cudaSuccess) {
+          IFEAST_PROF_BEGIN(a.prof, K_LZ_GIVENS);
+          e = launch_pdl(k_lanczos_givens_batch, dim3(a.tl.tiles, a.nc), dim3(32), st, a.m0, a.nc,
+                         a.K, s0, s + 1, a.alpha, a.beta, a.ms);
+          IFEAST_PROF_END(a.prof);
+          s0 = s + 1;
+        }
+      } else {
+        IFEAST_PROF_BEGIN(a.prof, K_LZ_GIVENS);
         k_lanczos_givens<<<a.tl.tiles, kThreads, 0, st>>>(step_blocks, a.m0, a.nc, a.K, s,
                                                           a.part, a.alpha, a.beta, a.ms, brk2);
+        IFEAST_PROF_END(a.prof);
+      }
     }
-    IFEAST_PROF_END(a.prof);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (check && e == cudaSuccess) {
       // stop early once no column is still running: this checkpoint's flag is
@@ -1388,6 +1447,12 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
         e = cudaEventSynchronize(a.check_events[old]);
         if (e == cudaSuccess && a.prof && a.prof->collect_ready()) e = cudaErrorUnknown;
         if (e == cudaSuccess && a.active_host[old] == 0) break;
+        if (e == cudaSuccess && a.time_limit_ms > 0.0 &&
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a.t0)
+                    .count() >= a.time_limit_ms) {
+          if (a.cut) *a.cut = true;  // the steps run so far make the filter
+          break;
+        }
       }
     }
   }
@@ -1418,7 +1483,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
                            a.Sj, 3};
       for (int s2 = 0; s2 < S && e == cudaSuccess; ++s2) {
         IFEAST_PROF_BEGIN(a.prof, K_LZ_STEP);
-        e = launch_lanczos_step<T>(a, s2, V, W[(s2 + 1) & 1], W[s2 & 1], val, nullptr, pass2, st);
+        e = launch_lanczos_step<T>(a, s2, V, W[(s2 + 1) & 1], W[s2 & 1], val, pass2, st);
         IFEAST_PROF_END(a.prof);
       }
       if (e != cudaSuccess) return e;
@@ -1434,7 +1499,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
       k_lz_quadrature4<T><<<(unsigned)((nm / 4 + 255) / 256), 256, 0, st>>>(
           a.n, a.m0, a.K, V, a.coef, a.cx, a.Sj, a.X, a.Q);
   }
-  if constexpr (!std::is_same_v<T, __half>) {
+  if constexpr (!std::is_same_v<T, __half> && !std::is_same_v<T, __nv_bfloat16>) {
     if (sizeof(T) == 8 || a.m0 % 4 != 0)
       k_lz_quadrature<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(a.n, a.m0, V, a.coef, a.cx,
                                                                        a.Sj, a.X, a.Q);
@@ -1449,6 +1514,7 @@ cudaError_t minres_init() { return cudaSuccess; }
 
 cudaError_t minres_filter(const MinresArgs &a, cudaStream_t st) {
   if (a.half) return run_minres<__half>(a, st);
+  if (a.bf16) return run_minres<__nv_bfloat16>(a, st);
   if (a.fp32) return run_minres<float>(a, st);
   return run_minres<double>(a, st);
 }

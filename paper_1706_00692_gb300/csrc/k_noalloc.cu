@@ -225,6 +225,11 @@ extern "C" int ifeast_rayleigh_ritz_noalloc(int64_t n, int64_t nnz, const int32_
       !X || !lam || !resid || m0 < 1 || m0 > n)
     return IFEAST_ERR_INVALID_ARG;
   if (m0 > kNaMaxM0) return IFEAST_ERR_INVALID_ARG;  // beyond the fixed scratch
+  {  // X = Q X_Q reads all of a row of Q while it writes that row of X
+    const uintptr_t q0 = (uintptr_t)Q, x0 = (uintptr_t)X;
+    const uintptr_t len = (uintptr_t)n * (uintptr_t)m0 * sizeof(double);
+    if (q0 < x0 + len && x0 < q0 + len) return IFEAST_ERR_INVALID_ARG;
+  }
   double *sc = nullptr;
   int rc = scratch_for_current_device(&sc);
   if (rc) return rc;

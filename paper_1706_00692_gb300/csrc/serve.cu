@@ -23,6 +23,7 @@ struct Request {
   std::vector<int32_t> rowptr, colidx;
   std::vector<double> val;
   ifeast_contour contour{};
+  std::vector<double> user_zw;  // IFEAST_USER nodes (contour.user_zw points here)
   ifeast_opts opts{};
   int m0 = 0;
   std::vector<double> X0;
@@ -30,7 +31,7 @@ struct Request {
   Clock::time_point t_submit, t_start, t_done;
   bool done = false;
   int status = IFEAST_OK;
-  ifeast_stats stats{};
+  ifeast_stats_t stats{};
   int found = 0;
   std::vector<double> evals, evecs, resid;  // evecs n x found row-major
 };
@@ -72,8 +73,8 @@ void run_request(const ifeast_server_opts &so, Request &r) {
   ifeast_t h = nullptr;
   int rc = ifeast_create(&A, nullptr, &r.contour, r.m0, &r.opts, ws, r.ws_bytes, st, &h);
   if (rc == IFEAST_OK) {
-    rc = ifeast_solve(h, r.X0.data(), 0);
-    ifeast_get_stats(h, &r.stats);
+    rc = ifeast_solve(h, r.X0.data(), 0, 0, nullptr);
+    ifeast_stats(h, &r.stats);
     if (rc == IFEAST_OK || rc == IFEAST_ERR_NOT_CONVERGED || rc == IFEAST_ERR_M0_TOO_SMALL) {
       int m = 0;
       if (ifeast_eigenpairs(h, 0, &m, nullptr, nullptr, nullptr, 0) == IFEAST_OK && m > 0) {
@@ -160,6 +161,10 @@ int ifeast_server_submit(ifeast_server_t s, const ifeast_csr *A, const ifeast_co
     r->val.assign(A->val, A->val + A->nnz);
   }
   r->contour = *c;
+  if (c->rule == IFEAST_USER) {  // the caller's node array may be freed on return
+    r->user_zw.assign(c->user_zw, c->user_zw + 4 * (size_t)c->nc);
+    r->contour.user_zw = r->user_zw.data();
+  }
   r->opts = *o;
   r->m0 = m0;
   r->X0.assign(X0, X0 + (size_t)A->n * m0);

@@ -40,9 +40,29 @@ def contour_nodes(rule: str, nc: int, emin: float, emax: float):
     return zw[:, 0] + 1j * zw[:, 1], zw[:, 2] + 1j * zw[:, 3]
 
 
+def initial_subspace(n: int, m0: int, seed: int, device="cuda"):
+    """The library's seeded random subspace (i.i.d. N(0,1), Philox4x32-10 +
+    Box-Muller, drawn on the device) as a CUDA float64 (n, m0) tensor."""
+    torch = _torch()
+    lib = _lib.load()
+    X = torch.empty((n, m0), dtype=torch.float64, device=device)
+    rc = lib.ifeast_initial_subspace(n, m0, seed, X.data_ptr(),
+                                     ct.c_void_p(torch.cuda.current_stream(X.device).cuda_stream))
+    if rc:
+        raise IFEASTError(rc, "ifeast_initial_subspace")
+    return X
+
+
+def _user_zw(nodes):
+    """(z, w) complex arrays -> the nc x 4 float64 array of IFEAST_USER."""
+    z, w = (np.asarray(a, dtype=np.complex128).ravel() for a in nodes)
+    return np.ascontiguousarray(np.stack([z.real, z.imag, w.real, w.imag], axis=1))
+
+
 class Solver:
     """One IFEAST problem (A, optional SPD B, interval, m0, contour, options)
-    bound to a handle."""
+    bound to a handle. rule="user" takes the nodes and weights from
+    user_nodes=(z, w) (filter Re sum_k w_k / (z_k - lambda))."""
 
     def __init__(self, A: CSR, emin: float, emax: float, m0: int, *, nc: int = 8,
                  rule: str = "gl_half", inner: str = "gmres", inner_iters: int = 10,
@@ -50,14 +70,21 @@ class Solver:
                  precision: str = "fp64", device: str | int = "cuda",
                  torch_workspace: bool = True, verbose: bool = False, B: CSR | None = None,
                  nonsymmetric: bool = False, two_pass: bool = False,
-                 correction_rf: float | None = None):
+                 correction_rf: float | None = None, user_nodes=None,
+                 time_limit_ms: float = 0.0):
         torch = _torch()
         self.lib = _lib.load()
         self.torch = torch
         self.device = torch.device(device)
-        self.n, self.m0, self.nc = int(A.n), int(m0), int(nc)
+        self.n, self.m0 = int(A.n), int(m0)
         self.emin, self.emax = float(emin), float(emax)
-        self.contour = _lib.Contour(_lib.RULES[rule], nc, emin, emax)
+        self._zw = None
+        if rule == "user":
+            self._zw = _user_zw(user_nodes)
+            nc = self._zw.shape[0]
+        self.nc = int(nc)
+        self.contour = _lib.Contour(_lib.RULES[rule], nc, emin, emax,
+                                    None if self._zw is None else self._zw.ctypes.data)
         self.opts = _lib.Opts()
         self.lib.ifeast_default_opts(ct.byref(self.opts))
         self.opts.inner_max_iters = inner_iters
@@ -71,6 +98,7 @@ class Solver:
         self.opts.minres_two_pass = 1 if two_pass else 0
         if correction_rf is not None:
             self.opts.correction_rf = correction_rf
+        self.opts.time_limit_ms = float(time_limit_ms)
         nbytes = ct.c_size_t(0)
         rc = self.lib.ifeast_workspace_bytes_generalized(
             self.n, A.nnz, -1 if B is None else B.nnz, self.m0, ct.byref(self.contour),
@@ -105,17 +133,20 @@ class Solver:
             self.h = h
 
     # ------------------------------------------------------------------ full solve
-    def solve(self, X0) -> int:
+    def solve(self, X0=None, seed: int = 0) -> int:
         """Algorithm 2 from X0 (numpy (n, m0) float64 on the host, or a CUDA
-        float64 tensor). Returns the library status (0 = converged)."""
+        float64 tensor; None: the library's seeded random subspace from seed).
+        Returns the library status (0 = converged)."""
         torch = self.torch
+        if X0 is None:
+            return int(self.lib.ifeast_solve(self.h, None, 0, int(seed), None))
         if isinstance(X0, np.ndarray):
             x = np.ascontiguousarray(X0, dtype=np.float64)
             assert x.shape == (self.n, self.m0)
-            return int(self.lib.ifeast_solve(self.h, x.ctypes.data, 0))
+            return int(self.lib.ifeast_solve(self.h, x.ctypes.data, 0, 0, None))
         assert X0.is_cuda and X0.dtype == torch.float64 and X0.shape == (self.n, self.m0)
         X0 = X0.contiguous()
-        return int(self.lib.ifeast_solve(self.h, X0.data_ptr(), 1))
+        return int(self.lib.ifeast_solve(self.h, X0.data_ptr(), 1, 0, None))
 
     def eigenpairs(self, on_device: bool = False):
         """(lam, X, res) for the Ritz pairs inside the interval, ascending."""
@@ -179,9 +210,9 @@ class Solver:
 
     def stats(self) -> dict:
         s = _lib.Stats()
-        rc = self.lib.ifeast_get_stats(self.h, ct.byref(s))
+        rc = self.lib.ifeast_stats(self.h, ct.byref(s))
         if rc:
-            raise IFEASTError(rc, "ifeast_get_stats")
+            raise IFEASTError(rc, "ifeast_stats")
         return {f: getattr(s, f) for f, _ in _lib.Stats._fields_}
 
     # ------------------------------------------------------------------ steps
@@ -195,6 +226,20 @@ class Solver:
                                           steps.data_ptr())
         if rc:
             raise IFEASTError(rc, "ifeast_apply_filter")
+        return Q, steps
+
+    def apply_filter_residual(self, X, lam, RF: float = 1.0):
+        """Alg. 2 steps 1-2 in residual form for the pairs (lam_j, x_j): X a CUDA
+        float64 (n, m0) tensor, lam (m0,). Returns (Q, steps)."""
+        torch = self.torch
+        X = X.contiguous()
+        lam = torch.as_tensor(lam, dtype=torch.float64, device=self.device).contiguous()
+        Q = torch.empty_like(X)
+        steps = torch.empty(self.nc * self.m0, dtype=torch.int32, device=self.device)
+        rc = self.lib.ifeast_apply_filter_residual(self.h, X.data_ptr(), lam.data_ptr(),
+                                                   Q.data_ptr(), float(RF), steps.data_ptr())
+        if rc:
+            raise IFEASTError(rc, "ifeast_apply_filter_residual")
         return Q, steps
 
     def rayleigh_ritz(self, Q):
@@ -282,8 +327,11 @@ class Server:
     def submit(self, A: CSR, emin: float, emax: float, m0: int, X0: np.ndarray, *, nc: int = 8,
                rule: str = "gl_half", inner: str = "minres", inner_iters: int = 300,
                alpha: float = 3e-2, max_outer: int = 100, tol: float = 1e-10,
-               precision: str = "fp32", two_pass: bool = False) -> int:
-        c = _lib.Contour(_lib.RULES[rule], nc, emin, emax)
+               precision: str = "fp32", two_pass: bool = False, user_nodes=None) -> int:
+        zw = _user_zw(user_nodes) if rule == "user" else None
+        if zw is not None:
+            nc = zw.shape[0]
+        c = _lib.Contour(_lib.RULES[rule], nc, emin, emax, None if zw is None else zw.ctypes.data)
         o = _lib.Opts()
         self.lib.ifeast_default_opts(ct.byref(o))
         o.inner_solver = _lib.INNERS[inner]

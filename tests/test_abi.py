@@ -198,8 +198,12 @@ def test_create_checks_B(lib):
 def test_strerror_and_null_handles(lib):
     for code in range(11):
         assert lib.ifeast_strerror(code)
-    assert lib.ifeast_solve(None, None, 0) == _lib.IFEAST_ERR_INVALID_ARG
-    assert lib.ifeast_get_stats(None, None) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_solve(None, None, 0, 0, None) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_stats(None, None) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_apply_filter_residual(None, None, None, None, 1.0, None) == \
+        _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_initial_subspace(0, 4, 1, None, None) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_initial_subspace(10, 4, 1, None, None) == _lib.IFEAST_ERR_INVALID_ARG
     assert lib.ifeast_set_profiling(None, 1) == _lib.IFEAST_ERR_INVALID_ARG
     assert lib.ifeast_kernel_times(None, 4, None, None, 0) == _lib.IFEAST_ERR_INVALID_ARG
     assert lib.ifeast_kernel_launches(None, 4, None, 0) == _lib.IFEAST_ERR_INVALID_ARG
@@ -207,11 +211,11 @@ def test_strerror_and_null_handles(lib):
 
 
 def test_kernel_class_names(lib):
-    """21 kernel classes with distinct names; the profiler's sampled classes exist."""
-    names = [lib.ifeast_kernel_name(k).decode() for k in range(21)]
-    assert len(set(names)) == 21 and "unknown" not in names
-    assert {"lanczos_step", "lanczos_givens", "gmres_spmm_dot"} <= set(names)
-    assert lib.ifeast_kernel_name(21).decode() == "unknown"
+    """22 kernel classes with distinct names; the profiler's sampled classes exist."""
+    names = [lib.ifeast_kernel_name(k).decode() for k in range(22)]
+    assert len(set(names)) == 22 and "unknown" not in names
+    assert {"lanczos_step", "lanczos_reduce", "lanczos_givens", "gmres_spmm_dot"} <= set(names)
+    assert lib.ifeast_kernel_name(22).decode() == "unknown"
 
 
 def test_product_path_has_no_oracle_import():
@@ -234,3 +238,63 @@ def test_two_pass_workspace_drops_the_basis(lib):
     assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c), ct.byref(o2), ct.byref(b2)) == 0
     # K + 1 FP32 basis vectors become three slots plus one FP32 accumulator
     assert b1.value - b2.value >= (K + 1 - 4) * n * m0 * 4
+
+
+def test_user_contour_nodes_and_validation(lib):
+    """IFEAST_USER: the given nodes come back unchanged; a missing array, a
+    non-finite entry or a node on the real axis is rejected."""
+    z, w = orc.contour_nodes("gl_half", 6, 0.2, 1.4)
+    zw = np.ascontiguousarray(np.stack([z.real, z.imag, w.real, w.imag], axis=1))
+    c = _lib.Contour(_lib.USER, 6, 0.2, 1.4, zw.ctypes.data)
+    out = np.zeros(24)
+    assert lib.ifeast_contour_nodes(ct.byref(c), out.ctypes.data) == 0
+    assert np.array_equal(out.reshape(6, 4), zw)
+    for bad in (None, "nan", "real"):
+        zb = zw.copy()
+        if bad == "nan":
+            zb[2, 2] = np.nan
+        elif bad == "real":
+            zb[4, 1] = 0.0
+        cb = _lib.Contour(_lib.USER, 6, 0.2, 1.4, None if bad is None else zb.ctypes.data)
+        assert lib.ifeast_contour_nodes(ct.byref(cb), out.ctypes.data) == _lib.IFEAST_ERR_INVALID_ARG
+    # the workspace query validates the same way
+    nb = ct.c_size_t()
+    cb = _lib.Contour(_lib.USER, 6, 0.2, 1.4, None)
+    assert lib.ifeast_workspace_bytes(100, 300, 4, ct.byref(cb), ct.byref(_opts(lib)),
+                                      ct.byref(nb)) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_workspace_bytes(100, 300, 4, ct.byref(c), ct.byref(_opts(lib)),
+                                      ct.byref(nb)) == 0
+
+
+def test_bf16_and_time_limit_options(lib):
+    """BF16 storage exists for the shared-basis solver (m0 % 4 == 0) only; a NaN
+    time limit is invalid."""
+    c = _lib.Contour(1, 8, 0.0, 1.0)
+    nb = ct.c_size_t()
+    ok = _opts(lib, inner_solver=1, inner_max_iters=100, precision=_lib.BF16)
+    assert lib.ifeast_workspace_bytes(1000, 7000, 8, ct.byref(c), ct.byref(ok), ct.byref(nb)) == 0
+    f32 = ct.c_size_t()
+    o32 = _opts(lib, inner_solver=1, inner_max_iters=100, precision=_lib.FP32)
+    assert lib.ifeast_workspace_bytes(1000, 7000, 8, ct.byref(c), ct.byref(o32), ct.byref(f32)) == 0
+    assert f32.value - nb.value >= 2 * 101 * 1000 * 8  # half the basis bytes
+    assert lib.ifeast_workspace_bytes(1000, 7000, 6, ct.byref(c), ct.byref(ok), ct.byref(nb)) == \
+        _lib.IFEAST_ERR_UNSUPPORTED
+    gm = _opts(lib, precision=_lib.BF16)
+    assert lib.ifeast_workspace_bytes(1000, 7000, 8, ct.byref(c), ct.byref(gm), ct.byref(nb)) == \
+        _lib.IFEAST_ERR_UNSUPPORTED
+    bad = _opts(lib, time_limit_ms=float("nan"))
+    assert lib.ifeast_workspace_bytes(1000, 7000, 8, ct.byref(c), ct.byref(bad), ct.byref(nb)) == \
+        _lib.IFEAST_ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_overlapping_x_and_q(lib):
+    """X = Q X_Q is not formed in place: an X range overlapping Q's returns
+    INVALID_ARG before any device work (the pointers are never dereferenced)."""
+    n, m0 = 1000, 8
+    rp = ct.c_void_p(0x10000)
+    base = 0x7f0000000000
+    nbytes = n * m0 * 8
+    for off in (0, 8, nbytes - 8, -(nbytes - 8)):
+        rc = lib.ifeast_rayleigh_ritz_noalloc(n, 3000, rp, rp, rp, m0, ct.c_void_p(base),
+                                              ct.c_void_p(base + off), rp, rp, None)
+        assert rc == _lib.IFEAST_ERR_INVALID_ARG, off

@@ -420,3 +420,214 @@ def test_ifeast_correction_converges_to_closed_form_generalized():
         lam = out["lam"][out["inside"]]
         assert lam.size == cnt
         assert np.abs(lam - ev[:cnt]).max() <= 1e-10 * ev[cnt - 1]
+
+
+# ---------------------------------------------------------------- shared basis: plain and residual form
+
+# Krylov steps allowed for an exact solve at n = 30: the MGS Arnoldi basis loses
+# orthogonality near step n, so the invariant subspace is reached a step or two
+# later (the breakdown test then ends the run)
+KFULL = 40
+
+
+def _shared_case():
+    A = inputs.add_diagonal(inputs.laplacian((6, 5)), inputs.random_potential(30, 11))
+    X = inputs.initial_subspace(30, 4, 12)
+    lam = np.array([1.1, 2.9, 3.3, 6.5])  # any scalars off the contour
+    z, w = orc.contour_nodes("trap_half", 6, 0.5, 4.0)
+    return A.to_scipy(), X, lam, z, w
+
+
+def test_shared_filter_full_dimension_equals_exact_filter():
+    """At k >= n the shared-basis GMRES iterate of every node is the exact solve,
+    so the filter equals dense LU (Alg. 1 steps 1-2) and U rho(Lambda) U^T X."""
+    As, X, lam, z, w = _shared_case()
+    got = orc._filtered_subspace_shared(As, X, z, w, True, KFULL, 0.0, {"inner_steps": []})
+    ref = orc._filtered_subspace_exact(As.toarray(), X, z, w, True)
+    spec = orc.filter_step_spectral(As.toarray(), X, z, w, True)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.abs(got - spec).max() <= 1e-10 * np.abs(spec).max()
+
+
+def test_shared_correction_filter_full_dimension_equals_exact_filter():
+    """Residual form of the shared-basis filter (right-hand sides r_j = A x_j -
+    lam_j x_j, Q_j = rho(lam_j) x_j + Re sum_k w_k y'_kj / (z_k - lam_j)): at k >= n
+    it equals the exact filter for any lam_j (an identity of the shifted
+    systems), half and full contour."""
+    As, X, lam, z, w = _shared_case()
+    got = orc._filtered_subspace_shared_correction(As, X, lam, z, w, True, KFULL, 0.0,
+                                                   {"inner_steps": []})
+    ref = orc._filtered_subspace_exact(As.toarray(), X, z, w, True)
+    spec = orc.filter_step_spectral(As.toarray(), X, z, w, True)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.abs(got - spec).max() <= 1e-10 * np.abs(spec).max()
+    zf, wf = orc.contour_nodes("trap_full", 8, 0.5, 4.0)
+    gotf = orc._filtered_subspace_shared_correction(As, X, lam, zf, wf, False, KFULL, 0.0,
+                                                    {"inner_steps": []})
+    reff = orc._filtered_subspace_exact(As.toarray(), X, zf, wf, False)
+    assert np.abs(gotf - reff).max() <= 1e-10 * np.abs(reff).max()
+
+
+def test_shared_correction_filter_mutations_fail():
+    """Planted mistakes in the residual form are caught by the exact-solve
+    identity: the rho(lam_j) x_j term dropped, the residual's sign flipped, the
+    weights not divided by z_k - lam_j."""
+    As, X, lam, z, w = _shared_case()
+    ref = orc._filtered_subspace_exact(As.toarray(), X, z, w, True)
+    scale = np.abs(ref).max()
+    Rres = As @ X - X * lam[None, :]
+    rho = orc.filter_rho(lam, z, w, True)
+    q_nox = np.zeros(X.shape, np.complex128)
+    q_sign = X * rho[None, :] + 0j
+    q_wt = X * rho[None, :] + 0j
+    for zk, wk in zip(z, w):
+        for j in range(4):
+            y = orc.gmres_shared_basis(As, Rres[:, j], zk, KFULL)["y"]
+            ym = orc.gmres_shared_basis(As, -Rres[:, j], zk, KFULL)["y"]
+            q_nox[:, j] += wk * y / (zk - lam[j])
+            q_sign[:, j] += wk * ym / (zk - lam[j])
+            q_wt[:, j] += wk * y
+    for bad in (q_nox, q_sign, q_wt):
+        assert np.abs(bad.real - ref).max() > 1e-3 * scale
+
+
+def test_shared_correction_stop_bound_is_first_step_below():
+    """The residual-form stop bound: a (node, column) pair stops at the first
+    step whose least-squares residual of the correction system is within
+    tol ||x_j|| |z_k - lam_j|, i.e. the original system's residual within
+    tol ||x_j|| (Alg. 2 step 1). Brute force: the minimal residual over an
+    explicitly orthonormalised Krylov space (Gram-Schmidt applied twice)."""
+    As, X, lam, z, w = _shared_case()
+    Ad = As.toarray()
+    tol = 3e-2
+    stats = {"inner_steps": []}
+    orc._filtered_subspace_shared_correction(As, X, lam, z, w, True, 30, tol, stats)
+    Rres = As @ X - X * lam[None, :]
+
+    def min_res(M, r, d):
+        Qb = np.zeros((30, d))
+        q = r / np.linalg.norm(r)
+        for i in range(d):
+            Qb[:, i] = q
+            v = Ad @ q
+            for _ in range(2):
+                v = v - Qb[:, :i + 1] @ (Qb[:, :i + 1].T @ v)
+            q = v / np.linalg.norm(v)
+        c = np.linalg.lstsq(M @ Qb, r + 0j, rcond=None)[0]
+        return np.linalg.norm(r - M @ Qb @ c)
+
+    steps = iter(stats["inner_steps"])
+    for zk in z:
+        M = zk * np.eye(30) - Ad
+        for j in range(4):
+            s = next(steps)
+            assert 1 <= s <= 20
+            bound = tol * np.linalg.norm(X[:, j]) * abs(zk - lam[j])
+            assert min_res(M, Rres[:, j], s) <= bound * (1 + 1e-6)
+            if s > 1:
+                assert min_res(M, Rres[:, j], s - 1) > bound * (1 - 1e-6)
+
+
+def test_shared_correction_ifeast_converges_to_brute_force():
+    """IFEAST with the shared basis and the residual form from the second
+    iteration on (the GPU solver's schedule) reaches the brute-force
+    eigenvalues of an interior window."""
+    A = inputs.add_diagonal(inputs.laplacian((6, 5, 4)), inputs.random_potential(120, 3))
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+    i0, cnt = 12, 4
+    emin, emax = 0.5 * (ev[i0 - 1] + ev[i0]), 0.5 * (ev[i0 + cnt - 1] + ev[i0 + cnt])
+    z, w = orc.contour_nodes("trap_half", 6, emin, emax)
+    out = orc.ifeast(A.to_scipy(), inputs.initial_subspace(A.n, 8, 0), emin, emax, z, w,
+                     inner="shared", k=40, alpha=1e-2, max_outer=30, correction_rf=np.inf)
+    assert out["converged"]
+    lam = out["lam"][out["inside"]]
+    assert lam.size == cnt
+    assert np.abs(lam - ev[i0:i0 + cnt]).max() <= 1e-10 * np.abs(ev).max()
+
+
+# ---------------------------------------------------------------- step-level references
+
+def test_ref_spmm_shift_matches_dense_shifted_matrix():
+    """W[:, c] = (z_c I - A) V[:, c], checked against the dense shifted matrix
+    built entry by entry, on complex columns; a flipped sign (A - z I) fails."""
+    A = inputs.random_sparse_symmetric(40, 3, 2)
+    Ad = A.to_scipy().toarray()
+    g = np.random.default_rng(5)
+    V = g.standard_normal((40, 6)) + 1j * g.standard_normal((40, 6))
+    zcol = np.array([0.3 + 0.1j, 1.5 - 0.2j, 2.0, -0.7 + 2j, 0.0, 5.0 + 0.5j])
+    got = orc.ref_spmm_shift(A.to_scipy(), V, zcol)
+    for c in range(6):
+        M = np.array([[(zcol[c] if i == j else 0.0) - Ad[i, j] for j in range(40)]
+                      for i in range(40)])
+        ref = M @ V[:, c]
+        assert np.abs(got[:, c] - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert np.abs(-got[:, c] - ref).max() > 0.1 * np.abs(ref).max()
+
+
+def test_convergence_bound_delta_matches_resolvent_norms():
+    """Delta = sum_k ||w_k (z_k I - A)^{-1}||_2 (Eq. deltadef) over the full
+    circle, from the dense resolvents' spectral norms: a half rule's weights
+    hold the factor 2 of the mirrored lower-half node (w/2 at z and at conj z)."""
+    A = inputs.add_diagonal(inputs.laplacian((5, 4)), inputs.random_potential(20, 2))
+    Ad = A.to_scipy().toarray()
+    ev = np.linalg.eigvalsh(Ad)
+    z, w = orc.contour_nodes("gl_half", 5, 1.0, 3.0)
+    ref = 0.0
+    for zk, wk in zip(list(z) + list(z.conj()), list(w / 2) + list(w.conj() / 2)):
+        ref += np.linalg.norm(wk * np.linalg.inv(zk * np.eye(20) - Ad), 2)
+    assert abs(orc.convergence_bound_delta(ev, z, w, True) - ref) <= 1e-12 * ref
+
+
+# ---------------------------------------------------------------- seeded initial subspace
+
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the generator's published known-answer vectors."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = orc.philox4x32_10([np.array([c]) for c in v[:4]], [np.array([k]) for k in v[4:6]])
+        assert [int(o[0]) for o in out] == v[6:]
+
+
+def test_seeded_normal_block_layout_and_distribution():
+    """Pair p of the row-major block comes from counter p (so a larger block
+    extends a smaller one), different seeds give different blocks, and the
+    values are standard normal (Kolmogorov-Smirnov against the normal CDF,
+    moments)."""
+    from scipy import stats
+    X = orc.seeded_normal_block(2001, 7, 123)
+    Y = orc.seeded_normal_block(3001, 7, 123)
+    assert np.array_equal(X.ravel(), Y.ravel()[: X.size])
+    assert not np.allclose(X, orc.seeded_normal_block(2001, 7, 124))
+    assert not np.allclose(X, orc.seeded_normal_block(2001, 7, 123 + (1 << 32)))
+    x = Y.ravel()
+    assert abs(x.mean()) < 4.0 / np.sqrt(x.size)
+    assert abs(x.var() - 1.0) < 6.0 * np.sqrt(2.0 / x.size)
+    assert stats.kstest(x, "norm").pvalue > 1e-3
+    # the cosine and sine halves of Box-Muller are independent N(0,1)
+    assert abs(np.corrcoef(x[0::2][:10000], x[1::2][:10000])[0, 1]) < 0.05
+
+
+# ---------------------------------------------------------------- eigenvalues an interval holds
+
+def test_eigenvalues_in_interval_matches_dense():
+    """Shift-invert Lanczos around the interval centre returns exactly the
+    dense eigvalsh eigenvalues inside the interval, with their neighbours
+    outside, and raises when k does not reach both ends."""
+    A = inputs.add_diagonal(inputs.laplacian((11, 10, 9)), inputs.random_potential(990, 4))
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+    emin, emax = 0.5 * (ev[99] + ev[100]), 0.5 * (ev[129] + ev[130])
+    lam, res, below, above = orc.eigenvalues_in_interval(A.to_scipy(), emin, emax, 40)
+    assert lam.size == 30
+    assert np.abs(lam - ev[100:130]).max() <= 1e-12 * np.abs(ev).max()
+    assert res.max() <= 1e-10
+    assert below == pytest.approx(ev[99], abs=1e-12) and above == pytest.approx(ev[130], abs=1e-12)
+    with pytest.raises(ValueError):
+        orc.eigenvalues_in_interval(A.to_scipy(), emin, emax, 20)
+    # a fill-reducing ordering changes the factorisation only
+    perm = orc.grid_nested_dissection((11, 10, 9))
+    assert np.array_equal(np.sort(perm), np.arange(990))
+    lam2, res2, _, _ = orc.eigenvalues_in_interval(A.to_scipy(), emin, emax, 40, perm)
+    assert np.abs(lam2 - ev[100:130]).max() <= 1e-12 * np.abs(ev).max()

@@ -56,3 +56,34 @@ def test_serving_requests_counts_match_dense_spectra():
         assert r.m0 >= r.count and r.m0 % 4 == 0
         assert r.X0.shape == (r.A.n, r.m0)
     assert all(b.arrival > a.arrival for a, b in zip(reqs, reqs[1:]))
+
+
+def test_lap3d64_window_comes_from_the_oracle_spectrum():
+    """The 64^3 workload's window and count are those of the oracle-written
+    golden file: the stored endpoints follow the file's gap rule applied to its
+    eigenvalues, the constants equal them, 56 eigenvalues lie inside, the
+    nearest ones outside are on both sides, and every stored eigenvalue has a
+    residual small enough to fix it to 1e-11 relative (an exact eigenvalue lies
+    within the residual norm; ten times tighter than the GPU comparison's 1e-10)."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    path = os.path.join(here, "lap3d64_window.txt")
+    header = [l.split() for l in open(path) if l.startswith("# window")][0]
+    emin, emax = float(header[2]), float(header[3])
+    data = np.loadtxt(path)
+    lam, res, ins = data[:, 0], data[:, 1], data[:, 2].astype(bool)
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(here, "make_lap3d64_window.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    evL = inputs.laplacian_eigs((64, 64, 64))
+    assert mk.window_from_gaps(lam, evL[1000] + 0.5) == emin
+    assert mk.window_from_gaps(lam, evL[1050] + 0.5) == emax
+    assert inputs.LAP3D_64_WINDOW == (emin, emax)
+    wl = inputs.workload_lap3d_64_interior()
+    assert (wl.emin, wl.emax) == (emin, emax)
+    assert ins.sum() == wl.expected_count == 56
+    assert np.array_equal(ins, (lam > emin) & (lam < emax))
+    assert (lam < emin).any() and (lam > emax).any()
+    assert np.all(np.diff(lam) > 0)
+    assert res.max() <= 1e-11 * lam.min()
