@@ -3,7 +3,7 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload lap3d_64|lap3d_64_fp16|lap3d_64_bf16|lap3d_64_twopass|
                                 lap3d_64_fp64|
-                                lap2d_50|fem3d_64|fem3d_64_fp64|fem3d_48|serve]
+                                lap2d_50|fem3d_64|fem3d_64_fp64|fem3d_48|fem3d_128|serve]
 
 One step = one full IFEAST solve (Algorithm 2 from the seeded initial subspace
 until ||R_F|| <= 1e-10) of the workload, inputs resident on the device. The
@@ -52,11 +52,15 @@ def parse():
                                                                  "lap3d_64_twopass",
                                                                  "lap3d_64_fp64", "lap2d_50",
                                                                  "fem3d_64", "fem3d_64_fp64",
-                                                                 "fem3d_48", "serve"])
+                                                                 "fem3d_48", "fem3d_128",
+                                                                 "serve"])
     p.add_argument("--requests", type=int, default=64, help="serving stream length")
     p.add_argument("--rate", type=float, default=8.0, help="serving arrivals per second")
     p.add_argument("--n-max", type=float, default=1e6, help="largest serving request size")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--rate-sweep", default="",
+                   help="serving: comma-separated multiples of the one-at-a-time service rate "
+                        "(e.g. 0.5,0.8,1.2); each runs the stream with Poisson arrivals at that rate")
     return p.parse_args()
 
 
@@ -80,6 +84,8 @@ def make_workload(name):
         return inputs.workload_fem3d(64, 50, precision="fp64")
     if name == "fem3d_48":
         return inputs.workload_fem3d(48, 40, precision="fp32")
+    if name == "fem3d_128":  # 128^3 pencil, 102 lowest pairs, two nodes per GMRES pass
+        return inputs.workload_fem3d_128()
     raise ValueError(name)
 
 
@@ -362,7 +368,7 @@ def run_ours(args):
     X0 = torch.as_tensor(wl.X0(), device=dev)
     skw = dict(nc=wl.nc, rule=wl.rule, inner=wl.inner, inner_iters=wl.inner_iters,
                alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass, B=wl.B,
-               device=dev)
+               node_chunk=wl.node_chunk, device=dev)
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, **skw)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -504,7 +510,8 @@ def run_serve(args):
     mixed = dict(inner="minres", inner_iters=K, alpha=3e-2, precision="fp32")
     plain = dict(inner="gmres", inner_iters=32, alpha=1e-2, precision="fp64")
 
-    def serve(max_active, timed_arrivals, reqs=reqs, two_pass=two_pass, form=mixed):
+    def serve(max_active, timed_arrivals, reqs=reqs, two_pass=two_pass, form=mixed,
+              arrival_scale=1.0):
         srv = Server(160 << 30, max_active=max_active, device=local)
         for r in warm:  # load kernels, warm the allocator
             srv.wait(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half", **form))
@@ -512,7 +519,7 @@ def run_serve(args):
         t0 = time.perf_counter()
         for r, tp in zip(reqs, two_pass):
             if timed_arrivals:
-                dt = r.arrival - (time.perf_counter() - t0)
+                dt = r.arrival * arrival_scale - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
             ids.append(srv.submit(r.A, r.emin, r.emax, r.m0, r.X0, rule="trap_half",
@@ -531,6 +538,17 @@ def run_serve(args):
     with ClockSampler(local) as clk:
         pairs, span, lat, failed = serve(8, True)
     pairs1, span1, lat1, failed1 = serve(1, False)
+    # arrival-rate sweep: multiples f of the one-at-a-time service rate mu (requests/s);
+    # the stream's exponential inter-arrival times are rescaled from rate args.rate to f mu
+    sweep = []
+    mu = len(reqs) / span1
+    for f in [float(x) for x in args.rate_sweep.split(",") if x.strip()]:
+        with ClockSampler(local) as clk_f:
+            pr, sp, la, fa = serve(8, True, arrival_scale=args.rate / (f * mu))
+        sweep.append({"rate_factor": f, "arrival_rate_per_s": f * mu, "value": pr / sp,
+                      "pairs": pr, "makespan_s": sp, "failed": fa,
+                      "p50_ms": float(np.percentile(la, 50)),
+                      "p99_ms": float(np.percentile(la, 99)), "clocks": clk_f.summary()})
     # the mixed-precision served form against the plain FP64 form, one request at a time
     small = inputs.serving_requests(16, seed=1234, rate=args.rate, n_max=5e4)
     nosplit = [False] * len(small)
@@ -560,7 +578,8 @@ def run_serve(args):
                                "p99": float(np.percentile(lat, 99))},
                 "failed": failed, "pairs": pairs, "requests": len(reqs),
                 "one_at_a_time": {"value": pairs1 / span1, "makespan_s": span1,
-                                  "failed": failed1},
+                                  "failed": failed1, "service_rate_per_s": mu},
+                "rate_sweep": sweep,
                 "vs_plain_fp64": {"stream": "16 requests, n 1e3-5e4, m0 16-128, seed 1234",
                                   "plain_form": "per-node GMRES FP64, <= 32 steps, alpha 1e-2",
                                   "mixed_form": "shared-basis MINRES FP32, <= 300 steps, "

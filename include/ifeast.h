@@ -163,6 +163,13 @@ typedef struct {
                            that iteration's Rayleigh-Ritz. It returns
                            IFEAST_ERR_TIMEOUT with the last iterate kept (pairs
                            retrievable as after NOT_CONVERGED). <= 0: no limit. */
+  int node_chunk;       /* IFEAST_INNER_GMRES: > 0 solves the shifted systems of
+                           node_chunk contour nodes at a time (nc of the rule run
+                           must be a multiple of it), summing their parts of Q:
+                           the per-node Krylov bases then need node_chunk * m0
+                           columns of workspace instead of nc * m0. The result
+                           equals the all-nodes filter (same kernels, same
+                           arithmetic per system). 0: all nodes at once.      */
 } ifeast_opts;
 
 typedef struct {
@@ -177,7 +184,8 @@ typedef struct {
 } ifeast_stats_t;
 
 /* Fills *o with the defaults: GMRES, k = 10, alpha = 0 (fixed k), max_outer =
- * 100, tol = 1e-10, FP64, verbose = 0, correction_rf = 1e-3, no time limit. */
+ * 100, tol = 1e-10, FP64, verbose = 0, correction_rf = 1e-3, no time limit,
+ * node_chunk = 0. */
 void ifeast_default_opts(ifeast_opts *o);
 
 /* Contour nodes and weights (Eq. contour_int_quad with the rules above) on the

@@ -42,7 +42,8 @@ class Opts(ct.Structure):
     _fields_ = [("inner_solver", ct.c_int), ("inner_max_iters", ct.c_int), ("alpha", ct.c_double),
                 ("max_outer", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
                 ("verbose", ct.c_int), ("nonsymmetric", ct.c_int), ("minres_two_pass", ct.c_int),
-                ("correction_rf", ct.c_double), ("time_limit_ms", ct.c_double)]
+                ("correction_rf", ct.c_double), ("time_limit_ms", ct.c_double),
+                ("node_chunk", ct.c_int)]
 
 
 class Stats(ct.Structure):

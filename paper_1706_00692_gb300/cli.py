@@ -1,7 +1,8 @@
 """Run one IFEAST solve of a named synthetic workload and report the result.
 
-    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_twopass|lap3d_64_fp64|lap2d_50|
-                                                     fem3d_64|fem3d_64_fp64|fem3d_48]
+    python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_bf16|
+                                                     lap3d_64_twopass|lap3d_64_fp64|lap2d_50|
+                                                     fem3d_64|fem3d_64_fp64|fem3d_48|fem3d_128]
                                          [--max-outer M] [--inner-iters K] [--verbose]
 
 Prints one JSON line: status, eigenpairs found, largest residual, outer
@@ -13,6 +14,8 @@ from __future__ import annotations
 import argparse
 import json
 import time
+
+import numpy as np
 
 from . import inputs
 from .solver import Solver
@@ -35,6 +38,10 @@ def workload(name: str):
         return inputs.workload_fem3d(64, 50, precision="fp64")
     if name == "fem3d_48":
         return inputs.workload_fem3d(48, 40, precision="fp32")
+    if name == "fem3d_128":
+        return inputs.workload_fem3d_128()
+    if name == "lap3d_64_bf16":
+        return inputs.workload_lap3d_64_interior(seed=0, precision="bf16")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -50,7 +57,7 @@ def main(argv=None) -> int:
     k = a.inner_iters or wl.inner_iters
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
                inner_iters=k, alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass,
-               max_outer=a.max_outer, B=wl.B,
+               max_outer=a.max_outer, B=wl.B, node_chunk=wl.node_chunk,
                verbose=a.verbose)
     X0 = torch.as_tensor(wl.X0(), device="cuda")
     torch.cuda.synchronize()
@@ -65,6 +72,13 @@ def main(argv=None) -> int:
     if rc in (0, 4):
         lam, X, res = S.eigenpairs()
         out["max_residual"] = float(res.max()) if res.size else None
+        if wl.B is not None and wl.name.startswith("fem3d_"):  # closed-form Q1 spectrum
+            N = round(wl.A.n ** (1.0 / 3.0))
+            ev = inputs.fem_q1_eigs((N, N, N))
+            ref = ev[(ev > wl.emin) & (ev < wl.emax)]
+            out["reference_pairs"] = int(ref.size)
+            if ref.size == lam.size and ref.size:
+                out["max_rel_eig_err_vs_closed_form"] = float(np.max(np.abs(lam - ref) / ref))
     S.close()
     print(json.dumps(out), flush=True)
     return 0 if rc in (0, 4) else 1

@@ -16,6 +16,7 @@ using namespace ifeast;
 struct ifeast_ctx {
   int64_t n = 0, nnz = 0;
   int m0 = 0, nc = 0, C = 0, K = 0;
+  int ncc = 0;  // nodes per inner pass (per-node GMRES, opts.node_chunk; else nc)
   ifeast_opts opts{};
   ifeast_contour contour{};
   std::vector<double2> zh, wh;  // host copies of nodes and weights
@@ -66,6 +67,7 @@ struct ifeast_ctx {
   float *Qf = nullptr;
   double *lpart = nullptr, *lalpha = nullptr, *lbeta = nullptr, *ltol = nullptr;
   float4 *lcf32 = nullptr;
+
   double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lndone = nullptr,
       *lactive = nullptr, *lSj = nullptr;
@@ -203,12 +205,14 @@ int device_sms() {
   return sms > 0 ? sms : 152;
 }
 
-Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl, int Pg, int Pr,
+Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int ncc, int K, const RowTiling &tl, int Pg,
+             int Pr,
              bool minres, int prec, int sms_for_plan, int64_t nnzB, bool nonsym,
              bool two_pass) {
   Layout L;
   Offsets o{};
-  const size_t C = (size_t)nc * m0;
+  const size_t C = (size_t)ncc * m0;     // columns of one node chunk (all nodes: ncc = nc)
+  const size_t Cfull = (size_t)nc * m0;
   const size_t mp = (size_t)(m0 + 3) / 4 * 4;
   o.rowptr = L.take<int32_t>(n + 1);
   o.colidx = L.take<int32_t>(nnz > 0 ? nnz : 1);
@@ -239,7 +243,7 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.R = L.take<double2>((size_t)K * K * C);
     o.G = L.take<double2>((size_t)(K + 1) * C);
     o.Y = L.take<double2>((size_t)K * C);
-    o.steps = L.take<int>(C);
+    o.steps = L.take<int>(Cfull);  // every node's step counts (chunks write their slice)
     o.done = L.take<int>(C);
   } else {  // shared Lanczos basis, tl tiles the n x m0 block
     const bool fp32 = prec != IFEAST_FP64;
@@ -260,6 +264,7 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int K, const RowTiling &tl,
     o.lpart = L.take<double>((size_t)std::max(std::max(tl.P, 2 * sms_for_plan), 4) * 3 * m0);
     o.lalpha = L.take<double>((size_t)K * m0);
     o.lcf32 = L.take<float4>((size_t)(K + 1) * m0);
+
     o.lbeta = L.take<double>((size_t)(K + 1) * m0);
     o.ltol = L.take<double>(C);
     o.lg = L.take<double2>(C * (K + 1));
@@ -364,6 +369,8 @@ int validate_opts(const ifeast_opts *o) {
   if (o->nonsymmetric != 0 && o->nonsymmetric != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->nonsymmetric && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (o->minres_two_pass != 0 && o->minres_two_pass != 1) return IFEAST_ERR_INVALID_ARG;
+  if (o->node_chunk < 0) return IFEAST_ERR_INVALID_ARG;
+  if (o->node_chunk > 0 && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (o->minres_two_pass &&
       (o->inner_solver != IFEAST_INNER_MINRES || o->precision == IFEAST_FP64))
     return IFEAST_ERR_UNSUPPORTED;
@@ -480,7 +487,8 @@ GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q, int correction =
   a.n = (int)h->n;
   a.m0 = h->m0;
   a.nc = h->nc;
-  a.C = h->C;
+  a.ncc = h->ncc;
+  a.C = h->ncc * h->m0;  // columns of one inner pass
   a.K = h->K;
   a.rowptr = h->rowptr;
   a.colidx = h->colidx;
@@ -604,6 +612,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.alpha = h->lalpha;
   a.beta = h->lbeta;
   a.cf32 = h->lcf32;
+
   a.Yc = h->lYc;
   a.coef = h->lcoef;
   a.cx = h->lcx;
@@ -613,7 +622,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.check_every = 16;
   a.active_host = h->active_host;
   a.check_events = h->check_events;
-  a.P_async = 2 * h->num_sms;  // two resident blocks per SM
+  a.P_async = h->num_sms;  // one resident 512-thread block per SM
   a.two_pass = h->two_pass ? 1 : 0;
   a.Qf = h->Qf;
   a.ell_w = h->ell_w;
@@ -673,6 +682,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->minres_two_pass = 0;
   o->correction_rf = 1e-3;
   o->time_limit_ms = 0.0;
+  o->node_chunk = 0;
 }
 
 const char *ifeast_strerror(int code) {
@@ -733,13 +743,15 @@ int ifeast_workspace_bytes_generalized(int64_t n, int64_t nnz, int64_t nnz_b, in
   rc = validate_opts(o);
   if (rc) return rc;
   const int nc = effective_contour(*c).nc;
+  if (o->node_chunk > 0 && nc % o->node_chunk != 0) return IFEAST_ERR_INVALID_ARG;
   const int sms = device_sms();
   const bool minres = o->inner_solver == IFEAST_INNER_MINRES;
-  RowTiling tl = make_tiling(n, minres ? 32 : nc * m0, sms);
+  const int ncc = (!minres && o->node_chunk > 0) ? o->node_chunk : nc;
+  RowTiling tl = make_tiling(n, minres ? 32 : ncc * m0, sms);
   if (minres) tl.tiles = (m0 + 31) / 32;  // row blocks cover every column
   const int Pg = std::max(1, (int)std::min<int64_t>(2 * sms, (n + 31) / 32));
   const int Pr = Pg;
-  *bytes = plan(n, nnz, m0, nc, o->inner_max_iters, tl, Pg, Pr, minres, o->precision, sms,
+  *bytes = plan(n, nnz, m0, nc, ncc, o->inner_max_iters, tl, Pg, Pr, minres, o->precision, sms,
                 nnz_b < 0 ? -1 : nnz_b, o->nonsymmetric == 1, o->minres_two_pass == 1).total;
   return IFEAST_OK;
 }
@@ -795,13 +807,15 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
             o->precision == IFEAST_BF16;
   h->half = o->precision == IFEAST_FP16;
   h->bf16 = o->precision == IFEAST_BF16;
-  h->tl = make_tiling(n, h->minres ? 32 : h->C, h->num_sms);
+  h->ncc = (!h->minres && o->node_chunk > 0) ? o->node_chunk : h->nc;
+  h->tl = make_tiling(n, h->minres ? 32 : h->ncc * m0, h->num_sms);
   if (h->minres) h->tl.tiles = (m0 + 31) / 32;
   h->Pg = std::max(1, (int)std::min<int64_t>(2 * h->num_sms, (n + 31) / 32));
   h->Pr = h->Pg;
   contour_host(&ce, h->zh, h->wh);
   h->two_pass = o->minres_two_pass == 1;
-  const Offsets off = plan(n, nnz, m0, h->nc, h->K, h->tl, h->Pg, h->Pr, h->minres, o->precision,
+  const Offsets off = plan(n, nnz, m0, h->nc, h->ncc, h->K, h->tl, h->Pg, h->Pr, h->minres,
+                           o->precision,
                            h->num_sms, nnzB, h->nonsym, h->two_pass);
   if (workspace) {
     h->ws = (char *)workspace;
@@ -906,6 +920,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->lpart = (double *)(b + off.lpart);
     h->lalpha = (double *)(b + off.lalpha);
     h->lcf32 = (float4 *)(b + off.lcf32);
+
     h->lbeta = (double *)(b + off.lbeta);
     h->ltol = (double *)(b + off.ltol);
     h->lg = (double2 *)(b + off.lg);

@@ -95,6 +95,8 @@ RowTiling make_tiling(int64_t n, int ncols, int num_sms);
 // ---- inner solve (per-node complex GMRES, FP64 or FP32) -------------------
 struct GmresArgs {
   int n, m0, nc, C, K;
+  int ncc;                  // nodes per inner pass: the filter runs nc / ncc passes of
+                            // ncc nodes (C = ncc * m0 columns each), summing their Q
   int fp32;                 // 1: basis and work vector complex FP32, FP32 arithmetic
   const int32_t *rowptr, *colidx;
   const double *val;
@@ -128,6 +130,7 @@ struct GmresArgs {
   // residual form: right-hand sides r_j = A x_j - lambda_j B x_j (in X, norms in
   // beta), y = (x_j + e) / (z_k - lambda_j), Q = cx X + Re sum_k w_k e_k / (z_k - lambda_j)
   int correction;
+  int accumulate;           // 1: Q += this pass's sum (later node chunks)
   const double *lam;        // [m0] Ritz values
   const double *xnorm;      // [m0] ||B x_j||
   const double *Xr;         // n x m0 the Ritz vectors x_j

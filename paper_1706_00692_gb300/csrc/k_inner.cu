@@ -471,7 +471,7 @@ __global__ void k_quadrature(int n, int m0, int nc, int C, const CT *__restrict_
                              size_t vstride, const double2 *__restrict__ Y,
                              const float2 *__restrict__ Yf, const int *__restrict__ steps,
                              const double *__restrict__ cx, const double *__restrict__ Xr,
-                             double *__restrict__ Q) {
+                             double *__restrict__ Q, int accumulate) {
   using R = typename Cx<CT>::R;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)n * m0) return;
@@ -492,7 +492,8 @@ __global__ void k_quadrature(int n, int m0, int nc, int C, const CT *__restrict_
       q = Cx<CT>::fm(yw.x, v.x, Cx<CT>::fm(-yw.y, v.y, q));
     }
   }
-  Q[idx] = cx ? cx[j] * Xr[idx] + (double)q : (double)q;
+  const double t = cx ? cx[j] * Xr[idx] + (double)q : (double)q;
+  Q[idx] = accumulate ? Q[idx] + t : t;  // later node chunks add their part
 }
 
 template <int LMAX, typename CT>
@@ -580,7 +581,7 @@ cudaError_t run_gmres(const GmresArgs &a, cudaStream_t st) {
   const size_t nq = (size_t)a.n * a.m0;
   k_quadrature<CT><<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
       a.n, a.m0, a.nc, a.C, V, (size_t)a.n * a.C, a.Y, a.Yf, a.steps,
-      a.correction ? a.cx : nullptr, a.Xr, a.Q);
+      a.correction ? a.cx : nullptr, a.Xr, a.Q, a.accumulate);
   IFEAST_PROF_END(a.prof);
   return cudaGetLastError();
 }
@@ -604,11 +605,22 @@ RowTiling make_tiling(int64_t n, int ncols, int num_sms) {
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
   if (a.K < 1 || a.K > kMaxInner) return cudaErrorInvalidValue;
   if (a.correction && (!a.lam || !a.xnorm || !a.Xr || !a.cx)) return cudaErrorInvalidValue;
-  if (a.fp32) {
-    if (!a.val32 || !a.Yf || (a.rowptrB && !a.valB32)) return cudaErrorInvalidValue;
-    return run_gmres<float2>(a, st);
+  if (a.fp32 && (!a.val32 || !a.Yf || (a.rowptrB && !a.valB32))) return cudaErrorInvalidValue;
+  if (a.ncc < 1 || a.nc % a.ncc != 0 || a.C != a.ncc * a.m0) return cudaErrorInvalidValue;
+  // passes over chunks of ncc nodes: the same kernels on the chunk's nodes and
+  // weights, each pass's step counts in its slice, Q summed over the passes
+  // (the first pass writes it; cx of the residual form is summed likewise)
+  cudaError_t e = cudaSuccess;
+  for (int k0 = 0; k0 < a.nc && e == cudaSuccess; k0 += a.ncc) {
+    GmresArgs b = a;
+    b.nc = a.ncc;
+    b.z = a.z + k0;
+    b.w = a.w + k0;
+    b.steps = a.steps + (size_t)k0 * a.m0;
+    b.accumulate = k0 > 0 ? 1 : 0;
+    e = a.fp32 ? run_gmres<float2>(b, st) : run_gmres<double2>(b, st);
   }
-  return run_gmres<double2>(a, st);
+  return e;
 }
 
 cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,

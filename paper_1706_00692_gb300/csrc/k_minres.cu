@@ -99,6 +99,8 @@ __global__ void k_lz_prep(int n, int m0, int nc, int K, const double *__restrict
   if (idx == 0) st.active[0] = 0;
 }
 
+
+
 // v_0 = b / ||b|| again (second pass of the two-pass mode; the same
 // arithmetic as k_lz_prep, which also resets the least-squares state).
 template <typename T>
@@ -459,30 +461,34 @@ k_lanczos_givens(int P, int m0, int nc, int K, int s, const double *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// After an FP32 Lanczos step (k_lanczos_step_vec, k_lanczos_step_ell), whose
-// blocks leave FP32 partials part[b][3][m0], only the reduction that gives
-// alpha_s and beta_{s+1} stays between two consecutive step kernels
-// (k_lanczos_coef_f). The Givens QR of every (node, column) pair does not feed
-// the next step, so it runs in batches of kGivensBatch steps
-// (k_lanczos_givens_batch): the columns' stop flags then lag by less than one
-// batch, and a finished column runs at most that many extra Lanczos steps,
-// whose vectors no solution uses (each pair keeps its own step count).
+// After an FP32 Lanczos step (k_lanczos_step_vec, k_lanczos_step_ell), only the
+// reduction that gives alpha_s and beta_{s+1} stays between two consecutive
+// step kernels (k_lanczos_coef_f).
+// The Givens QR of every (node, column) pair does not feed the next step, so
+// it runs in batches of kGivensBatch steps (k_lanczos_givens_batch): the
+// columns' stop flags then lag by less than one batch, and a finished column
+// runs at most that many extra Lanczos steps, whose vectors no solution uses
+// (each pair keeps its own step count).
 // ---------------------------------------------------------------------------
-constexpr int kGfThreads = 512;
 constexpr int kGivensBatch = 16;
 
-// One block per 32-column tile: warp w sums the partial rows b = w (mod NW)
-// with compensated (Kahan) FP32 sums, warp 0 adds the warp sums and their
-// compensations in warp order, again compensated, and converts once to FP64:
-// alpha_s = <v,w>/<v,v>, beta_{s+1}^2 = <w,w> - alpha_s <v,w> (0 below the
-// breakdown threshold, which finishes the column). Only columns still running
-// (coldone[j] == 0) get coefficients. active_reset (check steps): cleared here
-// so that the Givens batch that follows can raise it.
-__global__ void __launch_bounds__(kGfThreads)
+// One block of kCoefThreads per 32-column tile, lane = column j: warp w sums
+// the partial rows b = w (mod NW) with compensated (Kahan) FP32 sums, all of
+// its rows' loads in flight first; warp 0 adds the warp sums and their
+// compensations in warp order, again compensated, converts once to FP64 and
+// forms alpha_s = <v,w>/<v,v>, beta_{s+1}^2 = <w,w> - alpha_s <v,w> (0 below the
+// breakdown threshold, which finishes the column), plus the FP32 copies
+// {alpha_s, beta_{s+1}, 1/beta_{s+1}} the next step kernel loads. Only columns
+// still running (coldone[j] == 0) get coefficients. active_reset (Givens batch
+// steps): cleared so that the batch that follows can raise it.
+constexpr int kCoefThreads = 512;
+constexpr int kCoefRows = 20;  // partial rows per warp: grids of up to 320 step blocks
+
+__global__ void __launch_bounds__(kCoefThreads)
 k_lanczos_coef_f(int P, int m0, int s, const float *__restrict__ part, double *__restrict__ alpha,
                  double *__restrict__ beta, float4 *__restrict__ cf, int *__restrict__ coldone,
                  double brk2, int *__restrict__ active_reset) {
-  constexpr int NW = kGfThreads / 32;
+  constexpr int NW = kCoefThreads / 32;
   __shared__ float red[3][2][NW][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -490,29 +496,24 @@ k_lanczos_coef_f(int P, int m0, int s, const float *__restrict__ part, double *_
   pdl_launch_next();
   if (active_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *active_reset = 0;
   {
-    float sm[3] = {0.f, 0.f, 0.f}, cp[3] = {0.f, 0.f, 0.f};
-    if (j < m0) {
-      constexpr int U = 10;  // rows in flight per warp
-      for (int b0r = warp; b0r < P; b0r += U * NW) {
-        float x[U][3];
+    float x[kCoefRows][3];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int b = b0r + u * NW;
+    for (int u = 0; u < kCoefRows; ++u) {
+      const int b = warp + u * NW;
 #pragma unroll
-          for (int q = 0; q < 3; ++q)
-            x[u][q] = b < P ? __ldcg(part + ((size_t)b * 3 + q) * m0 + j) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const float y = x[u][q] - cp[q];
-            const float t = sm[q] + y;
-            cp[q] = (t - sm[q]) - y;
-            sm[q] = t;
-          }
-      }
+      for (int q = 0; q < 3; ++q)
+        x[u][q] = (j < m0 && b < P) ? __ldcg(part + ((size_t)b * 3 + q) * m0 + j) : 0.f;
     }
+    float sm[3] = {0.f, 0.f, 0.f}, cp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < kCoefRows; ++u)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float y = x[u][q] - cp[q];
+        const float t = sm[q] + y;
+        cp[q] = (t - sm[q]) - y;
+        sm[q] = t;
+      }
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       red[q][0][warp][lane] = sm[q];
@@ -541,7 +542,6 @@ k_lanczos_coef_f(int P, int m0, int s, const float *__restrict__ part, double *_
   const double b1 = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
   alpha[(size_t)s * m0 + j] = a;
   beta[(size_t)(s + 1) * m0 + j] = b1;
-  // FP32 copies for the next step kernel: alpha_s, beta_{s+1}, 1 / beta_{s+1}
   cf[(size_t)(s + 1) * m0 + j] =
       make_float4((float)a, (float)b1, b1 != 0.0 ? (float)(1.0 / b1) : 0.f, 0.f);
   if (b1 == 0.0) coldone[j] = 1;
@@ -642,7 +642,7 @@ k_lanczos_givens_batch(int m0, int nc, int K, int s0, int s1, const double *__re
 // they are used. Same recurrence as k_lanczos_step.
 // ---------------------------------------------------------------------------
 constexpr int kVG = 8;        // non-zeros per gather group
-constexpr int kVThreads = 256;
+constexpr int kVThreads = 512;  // one block per SM (the register file holds 512 threads)
 
 __device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
   return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
@@ -856,7 +856,7 @@ __device__ __forceinline__ void accumulate_q(const Pass2 &p2, int m0, int s, siz
 }
 
 template <typename S, bool FIRST>
-__global__ void __launch_bounds__(kVThreads, 2)
+__global__ void __launch_bounds__(kVThreads, 1)
 k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
                    const int32_t *__restrict__ colidx, const float *__restrict__ val,
                    S *__restrict__ V, const S *__restrict__ Wprev, S *__restrict__ Wout,
@@ -952,7 +952,7 @@ k_lanczos_step_vec(int n, int m0, int s, const int32_t *__restrict__ rowptr,
 // k_lanczos_step.
 // ---------------------------------------------------------------------------
 template <typename S, bool FIRST, int W>
-__global__ void __launch_bounds__(kVThreads, 2)
+__global__ void __launch_bounds__(kVThreads, 1)
 k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
                    const float *__restrict__ valE, S *__restrict__ V,
                    const S *__restrict__ Wprev, S *__restrict__ Wout,
@@ -994,30 +994,25 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
   }
   const bool all4 = act[0] && act[1] && act[2] && act[3];
   float vv[4] = {0.f, 0.f, 0.f, 0.f}, vw[4] = {0.f, 0.f, 0.f, 0.f}, ww[4] = {0.f, 0.f, 0.f, 0.f};
-  // odd steps walk the rows backwards: the first rows they read are the last
-  // ones the previous step wrote, still in L2
-  const bool rev = s & 1;
   int r = gt / MQ;
   if (qact && r < n) {
     int cn[W];
-    const int r0m = rev ? n - 1 - r : r;
 #pragma unroll
     for (int u = 0; u < W; u += 4) {
-      const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)r0m * W + u);
+      const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)r * W + u);
       cn[u] = c4.x;
       cn[u + 1] = c4.y;
       cn[u + 2] = c4.z;
       cn[u + 3] = c4.w;
     }
     for (; r < n; r += rstep) {
-      const int rm = rev ? n - 1 - r : r;  // the row this iteration takes
       int c[W];
 #pragma unroll
       for (int u = 0; u < W; ++u) c[u] = cn[u];
       float a[W];
 #pragma unroll
       for (int u = 0; u < W; u += 4) {
-        const float4 a4 = *reinterpret_cast<const float4 *>(valE + (size_t)rm * W + u);
+        const float4 a4 = *reinterpret_cast<const float4 *>(valE + (size_t)r * W + u);
         a[u] = a4.x;
         a[u + 1] = a4.y;
         a[u + 2] = a4.z;
@@ -1029,16 +1024,15 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
 #pragma unroll
       for (int u = 0; u < W; ++u) {
         const int co = c[u] * m0 + q4;
-        const bool ld = u == 0 || c[u] != rm;
+        const bool ld = u == 0 || c[u] != r;
         g1[u] = ld ? St::load_raw(G1 + co) : zr;
         if (!FIRST) g2[u] = ld ? St::load_raw(G2 + co) : zr;
       }
       const int rn = r + rstep;  // next row's indices, in flight with the gathers
       if (rn < n) {
-        const int rnm = rev ? n - 1 - rn : rn;
 #pragma unroll
         for (int u = 0; u < W; u += 4) {
-          const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)rnm * W + u);
+          const int4 c4 = *reinterpret_cast<const int4 *>(colE + (size_t)rn * W + u);
           cn[u] = c4.x;
           cn[u + 1] = c4.y;
           cn[u + 2] = c4.z;
@@ -1054,10 +1048,10 @@ k_lanczos_step_ell(int n, int m0, int s, const int32_t *__restrict__ colE,
       const float4 o1 = St::cvt(g1[0]), o2 = FIRST ? z4 : St::cvt(g2[0]);
       float vo[4];
       finish_row<S, FIRST>(o1, o2, acc1, acc2, ap, ib, bs, act, all4, wsc, Vs, Wout,
-                           (size_t)(rm * m0 + q4), vv, vw, ww, vo);
+                           (size_t)(r * m0 + q4), vv, vw, ww, vo);
       if (p2.Qacc != nullptr) {
         const float vp[4] = {o2.x, o2.y, o2.z, o2.w};
-        accumulate_q(p2, m0, s, (size_t)(rm * m0 + q4), q4, vo, vp, act);
+        accumulate_q(p2, m0, s, (size_t)(r * m0 + q4), q4, vo, vp, act);
       }
     }
   }
@@ -1315,6 +1309,8 @@ void vec_grid(const MinresArgs &a, int &blocks, int &stride_items) {
   const int MQ = a.m0 / 4;
   const long long need = (long long)a.n * MQ;
   long long b = std::min<long long>((need + kVThreads - 1) / kVThreads, (long long)a.P_async);
+  // the coefficient kernel holds at most NW x kCoefRows partial rows
+  b = std::min<long long>(b, (kCoefThreads / 32) * kCoefRows);
   if (b < 1) b = 1;
   blocks = (int)b;
   stride_items = (int)((b * kVThreads) / MQ * MQ);
@@ -1387,7 +1383,7 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   IFEAST_PROF_END(a.prof);
   const double brk2 = brk2_of<T>();
   int step_blocks = a.tl.P;
-  // the FP32-arithmetic vec / ELL step kernels leave FP32 partials for k_lanczos_coef_f
+  // the FP32-arithmetic vec / ELL step kernels reduce their FP32 partials themselves
   const bool f32_partials = sizeof(T) <= 4 && use_vec_step(a);
   if (f32_partials) {
     int stride_items;
@@ -1408,16 +1404,16 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
     if (e == cudaSuccess) {
       if (f32_partials) {
         // alpha_s, beta_{s+1}; then, at batch ends and checks, the Givens QR of
-        // the steps since the last batch (no memset between the step and
-        // coefficient kernels breaks their launch overlap: on a checked step
-        // the coefficient kernel clears *active itself)
+        // the steps since the last batch (no memset between kernels breaks
+        // their launch overlap: at a batch step the coefficient kernel clears
+        // *active itself)
         const bool batch = (s + 1) % kGivensBatch == 0 || check || s + 1 == a.K;
         IFEAST_PROF_BEGIN(a.prof, K_LZ_REDUCE);
-        e = launch_pdl(k_lanczos_coef_f, dim3(a.tl.tiles), dim3(kGfThreads), st, step_blocks, a.m0,
-                       s, reinterpret_cast<const float *>(a.part), a.alpha, a.beta, a.cf32,
+        e = launch_pdl(k_lanczos_coef_f, dim3(a.tl.tiles), dim3(kCoefThreads), st, step_blocks,
+                       a.m0, s, reinterpret_cast<const float *>(a.part), a.alpha, a.beta, a.cf32,
                        a.ms.coldone, brk2, batch ? a.ms.active : nullptr);
         IFEAST_PROF_END(a.prof);
-        if (batch && e == cudaSuccess) {
+        if (batch && e == cudaSuccess) {  // the Givens QR of the steps since the last batch
           IFEAST_PROF_BEGIN(a.prof, K_LZ_GIVENS);
           e = launch_pdl(k_lanczos_givens_batch, dim3(a.tl.tiles, a.nc), dim3(32), st, a.m0, a.nc,
                          a.K, s0, s + 1, a.alpha, a.beta, a.ms);

@@ -251,6 +251,7 @@ class Workload:
     precision: str = "fp64"
     two_pass: bool = False  # shared-basis solver without the stored basis
     B: CSR | None = None  # generalized problem A x = lambda B x (None: B = I)
+    node_chunk: int = 0   # per-node GMRES: nodes per inner pass (0: all)
 
     def X0(self) -> np.ndarray:
         return initial_subspace(self.A.n, self.m0, self.seed)
@@ -324,6 +325,28 @@ def _gap_count(ev: np.ndarray, target: int, rel: float = 1e-3) -> int:
         if ev[c] - ev[c - 1] > rel * ev[c]:
             return c
     raise ValueError("no gap")
+
+
+def workload_fem3d_128(precision: str = "fp32", node_chunk: int = 2) -> Workload:
+    """The 27-point generalized workload at 128^3 (n = 2,097,152): Q1 trilinear
+    FEM K x = lambda M x, the lowest eigenvalues through the 6-fold cluster that
+    holds the 100th (102 pairs; the upper endpoint is the midpoint of the gap
+    after eigenvalue 102), m0 = 150, 12 Gauss-Legendre half-circle nodes,
+    per-node GMRES with at most 32 steps and alpha = 1e-2 (FP32 basis, residual
+    form below ||R_F|| = 1e-3), node_chunk nodes per pass (the 12 nodes' bases
+    together would need about 1 TB)."""
+    N = 128
+    K, M = fem_q1((N, N, N))
+    ev = fem_q1_eigs((N, N, N))
+    cnt = _gap_count(ev, 100)
+    emax = 0.5 * (ev[cnt - 1] + ev[cnt])
+    wl = Workload(f"fem3d_128^3_lowest{cnt}_m0_150_gl12_gmres32_{precision}_chunk{node_chunk}", K,
+                  0.0, emax, m0=150, nc=12, rule="gl_half", inner_iters=32, alpha=1e-2, seed=0,
+                  expected_count=cnt)
+    wl.precision = precision
+    wl.B = M
+    wl.node_chunk = node_chunk
+    return wl
 
 
 def workload_fem3d(N: int = 64, target: int = 50, precision: str = "fp32") -> Workload:

@@ -71,7 +71,7 @@ class Solver:
                  torch_workspace: bool = True, verbose: bool = False, B: CSR | None = None,
                  nonsymmetric: bool = False, two_pass: bool = False,
                  correction_rf: float | None = None, user_nodes=None,
-                 time_limit_ms: float = 0.0):
+                 time_limit_ms: float = 0.0, node_chunk: int = 0):
         torch = _torch()
         self.lib = _lib.load()
         self.torch = torch
@@ -99,6 +99,7 @@ class Solver:
         if correction_rf is not None:
             self.opts.correction_rf = correction_rf
         self.opts.time_limit_ms = float(time_limit_ms)
+        self.opts.node_chunk = int(node_chunk)
         nbytes = ct.c_size_t(0)
         rc = self.lib.ifeast_workspace_bytes_generalized(
             self.n, A.nnz, -1 if B is None else B.nnz, self.m0, ct.byref(self.contour),

@@ -298,3 +298,28 @@ def test_noalloc_rejects_overlapping_x_and_q(lib):
         rc = lib.ifeast_rayleigh_ritz_noalloc(n, 3000, rp, rp, rp, m0, ct.c_void_p(base),
                                               ct.c_void_p(base + off), rp, rp, None)
         assert rc == _lib.IFEAST_ERR_INVALID_ARG, off
+
+
+def test_node_chunk_option(lib):
+    """node_chunk: per-node GMRES only, a divisor of the node count; the
+    workspace holds one chunk's Krylov bases."""
+    c = _lib.Contour(0, 12, 0.0, 1.0)
+    n, nnz, m0 = 20000, 140000, 16
+    full, part = ct.c_size_t(), ct.c_size_t()
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c), ct.byref(_opts(lib, inner_max_iters=20)),
+                                      ct.byref(full)) == 0
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c),
+                                      ct.byref(_opts(lib, inner_max_iters=20, node_chunk=3)),
+                                      ct.byref(part)) == 0
+    # the (K + 1) x n x C complex FP64 basis shrinks from 12 to 3 nodes' columns
+    assert full.value - part.value >= 21 * n * 9 * m0 * 16
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c),
+                                      ct.byref(_opts(lib, node_chunk=5)),
+                                      ct.byref(part)) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c),
+                                      ct.byref(_opts(lib, node_chunk=-1)),
+                                      ct.byref(part)) == _lib.IFEAST_ERR_INVALID_ARG
+    assert lib.ifeast_workspace_bytes(n, nnz, m0, ct.byref(c),
+                                      ct.byref(_opts(lib, inner_solver=1, inner_max_iters=50,
+                                                     precision=1, node_chunk=2)),
+                                      ct.byref(part)) == _lib.IFEAST_ERR_UNSUPPORTED

@@ -138,3 +138,61 @@ def test_minres_with_B_is_refused(torch):
     K, M = inputs.fem_q1((6, 5))
     with pytest.raises(IFEASTError):
         _solver(K, M, 0.0, 100.0, 4, inner="minres", inner_iters=50)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("chunk", [1, 2, 3])
+def test_node_chunks_equal_the_all_nodes_filter(torch, precision, tol, chunk):
+    """opts.node_chunk: the shifted systems run chunk nodes at a time and Q is
+    summed over the passes. Every system's arithmetic is unchanged, so the
+    step counts are identical and Q differs from the all-nodes filter only by
+    the order of the sum over nodes (FP32 sums with the FP32 basis: 1e-5 of the
+    block's largest entry); the oracle agrees (plain and residual form)."""
+    A, B = inputs.fem_q1((14, 12))
+    emin, emax, m0, nc = 0.0, 200.0, 6, 6
+    X = inputs.initial_subspace(A.n, m0, 3)
+    Xn = X / np.linalg.norm(X, axis=0)[None, :]
+    lam = np.linspace(20.0, 260.0, m0)
+    outs = []
+    for nch in (0, chunk):
+        S = _solver(A, B, emin, emax, m0, nc=nc, inner="gmres", inner_iters=12, alpha=0.3,
+                    precision=precision, node_chunk=nch)
+        Q, st = S.apply_filter(torch.as_tensor(X, device="cuda"), RF=0.5)
+        outs.append((Q.cpu().numpy(), st.cpu().numpy()))
+        if precision == "fp32":
+            Qr, str_ = S.apply_filter_residual(torch.as_tensor(Xn, device="cuda"), lam, RF=0.5)
+            outs[-1] += (Qr.cpu().numpy(), str_.cpu().numpy())
+        S.close()
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.abs(outs[0][0] - outs[1][0]).max() <= tol * np.abs(outs[0][0]).max()
+    if precision == "fp32":
+        assert np.array_equal(outs[0][3], outs[1][3])
+        assert np.abs(outs[0][2] - outs[1][2]).max() <= tol * np.abs(outs[0][2]).max()
+    z, w = orc.contour_nodes("gl_half", nc, emin, emax)
+    stats = {"inner_steps": []}
+    ref = orc._filtered_subspace_gmres(A.to_scipy(), X, z, w, True, 12, 0.3 * 0.5, stats,
+                                       B.to_scipy())
+    ref_steps = np.array(stats["inner_steps"])
+    assert (outs[1][1] == ref_steps).mean() >= 0.95
+    if (outs[1][1] == ref_steps).all():
+        assert np.abs(outs[1][0] - ref).max() <= (2e-5 if precision == "fp32" else 1e-11) * \
+            np.abs(ref).max()
+
+
+def test_node_chunked_solve_matches_closed_form(torch):
+    """A full generalized solve with two nodes per pass reaches the closed-form
+    Q1 FEM eigenvalues like the all-nodes solve."""
+    grid = (30, 25)
+    A, B = inputs.fem_q1(grid)
+    ev = inputs.fem_q1_eigs(grid)
+    cnt = 8
+    emin, emax = 0.0, 0.5 * (ev[cnt - 1] + ev[cnt])
+    S = _solver(A, B, emin, emax, 14, nc=8, inner="gmres", inner_iters=32, alpha=1e-2,
+                precision="fp32", node_chunk=2)
+    rc = S.solve(inputs.initial_subspace(A.n, 14, 0))
+    assert rc == 0, rc
+    lam, X, res = S.eigenpairs()
+    S.close()
+    assert lam.size == cnt
+    assert np.abs(lam - ev[:cnt]).max() <= 1e-10 * ev[cnt - 1]
+    assert res.max() <= 1e-10

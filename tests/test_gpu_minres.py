@@ -119,7 +119,8 @@ def test_solve_interior_window_brute_force(torch, precision):
     assert np.abs(lam - ev[i0:i0 + cnt]).max() / np.abs(ev).max() <= 1e-10
     assert res.max() <= 1e-10
     st = S.stats()
-    assert st["outer_iters"] <= 12
+    # 16-bit storage stagnates the inner solves above their target more often
+    assert st["outer_iters"] <= (12 if precision in ("fp64", "fp32") else 20)
     S.close()
 
 
