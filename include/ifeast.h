@@ -46,7 +46,9 @@ typedef enum {
   IFEAST_ERR_M0_TOO_SMALL = 5,   /* m0 Ritz values inside the interval: m0 <= m  */
   IFEAST_STATUS_NO_EIGENVALUES = 6, /* no Ritz value inside the interval         */
   IFEAST_ERR_BREAKDOWN = 7,      /* B_Q not positive definite even after a shift */
-  IFEAST_ERR_TIMEOUT = 8,        /* opts.time_limit_ms ran out; last iterate kept  */
+  IFEAST_ERR_TIMEOUT = 8,        /* opts.time_limit_ms ran out (last iterate kept),
+                                    or a bounded device-side wait of the tensor-core
+                                    Rayleigh-Ritz update ran out (iterate invalid)  */
   IFEAST_ERR_STATE = 9,          /* call out of order (e.g. eigenpairs before solve) */
   IFEAST_ERR_UNSUPPORTED = 10    /* option combination not built                 */
 } ifeast_status;

@@ -555,6 +555,7 @@ RRArgs rr_args(ifeast_ctx *h, const double *Q, double *X) {
   a.valB = h->valB;
   a.BQ = h->BQ;
   a.BX = h->BX;
+  a.num_sms = h->num_sms;
   return a;
 }
 
@@ -1095,6 +1096,11 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device, uint64_t seed, 
       h->solved = false;
       break;
     }
+    if (s.tc_timeout) {  // a bounded device-side wait ran out: the update is incomplete
+      result = IFEAST_ERR_TIMEOUT;
+      h->solved = false;
+      break;
+    }
     if (s.count > 0 && s.RF <= h->opts.tol) {
       result = IFEAST_OK;
       break;
@@ -1344,6 +1350,7 @@ int ifeast_rayleigh_ritz(ifeast_t h, const double *Q, double *X, double *lam, do
   CK(cudaStreamSynchronize(h->stream));
   if (h->profiling && h->prof.collect()) return IFEAST_ERR_CUDA;
   if (h->status_host->breakdown) return IFEAST_ERR_BREAKDOWN;
+  if (h->status_host->tc_timeout) return IFEAST_ERR_TIMEOUT;
   return IFEAST_OK;
 }
 

@@ -80,7 +80,7 @@ struct DevStatus {
   int max_steps;        // max Krylov steps over (node, column) in the last filter
   long long total_steps;// sum of Krylov steps over (node, column) in the last filter
   int nonfinite;        // a NaN/Inf was seen in the residuals
-  int pad;
+  int tc_timeout;       // tensor-core update: a bounded wait on the MMA completion ran out
 };
 
 // Row-tiled launch geometry for n x C blocks: grid (P, tiles), warp w of a
@@ -252,6 +252,7 @@ struct RRArgs {
   double emin, emax, alpha;
   DevStatus *status;
   Profiler *prof;
+  int num_sms;              // persistent grids (tensor-core update)
 };
 // Non-Hermitian extension (real non-symmetric A, m0 <= 64)
 struct NonsymArgs {
@@ -264,6 +265,12 @@ cudaError_t ritz_vectors_nonsym(int n, int m, const double *X, const double2 *Uc
                                 int cnt, int cap, double2 *out, cudaStream_t st);
 constexpr int kNonsymMaxM0 = 64;
 cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
+// Tensor-core (tcgen05, BF16 digit products) form of the Rayleigh-Ritz update
+// X = Q X_Q, AX = AQ X_Q with the residual partials (k_rr_tc.cu); supported for
+// m0 <= 80, B = I, n >= 128. blocks: persistent CTAs (one per SM at most).
+bool update_resid_tc_supported(const RRArgs &a);
+cudaError_t update_resid_tc(const RRArgs &a, int blocks, cudaStream_t st);
+cudaError_t rr_tc_init();
 cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st);
 cudaError_t column_norms(int n, int m0, const double *X, double *part, int Pr, double *beta,
                          cudaStream_t st, Profiler *prof);

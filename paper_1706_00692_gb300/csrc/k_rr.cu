@@ -1115,6 +1115,8 @@ cudaError_t rr_init() {
   cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        3 * kGramRows * kMaxM0 * (int)sizeof(double));
   if (e != cudaSuccess) return e;
+  e = rr_tc_init();
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_reduced_eig_nonsym, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kNsEigSmem);
   if (e != cudaSuccess) return e;
@@ -1169,7 +1171,21 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
                                               a.status, nmat);
     IFEAST_PROF_END(a.prof);
   }
-  // X = Q X_Q and residual partials
+  // X = Q X_Q and residual partials: on the tensor cores (BF16 digit products,
+  // FP64-accurate, k_rr_tc.cu) when the shape allows, else in FP64
+  if (update_resid_tc_supported(a)) {
+    const int ntiles = (a.n + 127) / 128;
+    const int blocks = std::max(1, std::min(a.num_sms > 0 ? a.num_sms : 1, ntiles));
+    IFEAST_PROF_BEGIN(a.prof, K_RR_UPDATE);
+    cudaError_t e = update_resid_tc(a, blocks, st);
+    IFEAST_PROF_END(a.prof);
+    if (e != cudaSuccess) return e;
+    IFEAST_PROF_BEGIN(a.prof, K_RR_RESID);
+    k_reduce_resid<<<1, 256, 0, st>>>(blocks, m, a.res_part, a.lam, a.emin, a.emax, a.alpha,
+                                      a.res, a.beta, a.rnorm, a.status);
+    IFEAST_PROF_END(a.prof);
+    return cudaGetLastError();
+  }
   {
     const int rows = (a.n + a.Pr - 1) / a.Pr;
     const int pr_used = (a.n + rows - 1) / rows;

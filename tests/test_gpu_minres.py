@@ -119,8 +119,9 @@ def test_solve_interior_window_brute_force(torch, precision):
     assert np.abs(lam - ev[i0:i0 + cnt]).max() / np.abs(ev).max() <= 1e-10
     assert res.max() <= 1e-10
     st = S.stats()
-    # 16-bit storage stagnates the inner solves above their target more often
-    assert st["outer_iters"] <= (12 if precision in ("fp64", "fp32") else 20)
+    # 16-bit storage stagnates the inner solves above their target more often;
+    # with BF16's 8-bit significands most iterations do (converged within the cap)
+    assert st["outer_iters"] <= {"fp64": 12, "fp32": 12, "fp16": 20, "bf16": 30}[precision]
     S.close()
 
 

@@ -214,3 +214,41 @@ def test_not_converged_keeps_last_iterate(torch):
     lam, X, res = S.eigenpairs()
     assert S.stats()["outer_iters"] == 3 and lam.size >= 1 and np.isfinite(res).all()
     S.close()
+
+
+@pytest.mark.parametrize("m0,scaled", [(16, False), (20, True), (48, True), (80, True), (80, False),
+                                       (96, False), (96, True)])
+def test_rayleigh_ritz_update_fp64_accurate(torch, m0, scaled):
+    """X = Q X_Q and the residuals computed by the library (on the tensor cores
+    for m0 <= 80: exact BF16 digit products of 7-bit digit planes; in FP64
+    otherwise) agree with the FP64 oracle's product of the library's own X_Q:
+    each X entry to 1e-12 of its row's scale, and the residuals to the FP64
+    rounding of the product (a ragged grid so that the last row tile is partial; rows of Q
+    scaled over 3 and columns over 6 orders of magnitude, signs mixed)."""
+    A = inputs.add_diagonal(inputs.laplacian((17, 13, 9)), inputs.random_potential(1989, 2))
+    Q = inputs.initial_subspace(A.n, m0, 5)
+    if scaled:
+        g = np.random.default_rng(6)
+        Q *= 10.0 ** g.uniform(-1.5, 1.5, size=(A.n, 1))
+        Q *= 10.0 ** g.uniform(-3, 3, size=(1, m0))
+    S = _solver(A, 0.0, 8.0, m0)
+    X, lam, res = S.rayleigh_ritz(torch.as_tensor(Q, device="cuda"))
+    X, lam, res = X.cpu().numpy(), lam.cpu().numpy(), res.cpu().numpy()
+    S.close()
+    As = A.to_scipy()
+    # the library's X_Q, recovered from its X in FP64 (Q has full column rank);
+    # X - Q X_Q then holds the part of the update's error outside span(Q)
+    XQ = np.linalg.lstsq(Q, X, rcond=None)[0]
+    Xr = Q @ XQ
+    rowscale = np.abs(Q).max(axis=1, keepdims=True) * np.abs(XQ).max(axis=0, keepdims=True)
+    assert (np.abs(X - Xr) / rowscale).max() <= 1e-12
+    AX = As @ X
+    nAX = np.linalg.norm(AX, axis=0)
+    r = np.linalg.norm(AX - X * lam[None, :], axis=0) / nAX
+    # the library forms A X as (A Q) X_Q, this check as A (Q X_Q): in FP64 the
+    # two differ by rounding of the size eps |A| |Q| |X_Q| (columnwise), which
+    # the scaled cases make far larger than eps ||A X||
+    M = np.linalg.norm((abs(As) @ np.abs(Q)) @ np.abs(XQ), axis=0)
+    assert (np.abs(res - r) <= 64 * np.finfo(float).eps * M / nAX + 1e-14).all()
+    lr, _ = orc.rayleigh_ritz(Q, As @ Q)
+    assert np.abs(lam - lr).max() <= 1e-9 * np.abs(lr).max()
