@@ -16,21 +16,25 @@
 // summed over the at most 8 pairs (a, b) of one level a + b, stay below 2^24:
 // the FP32 accumulator of each level is an exact integer. Levels 2..9 are
 // kept (pairs with a + b > 9 weigh below 2^-63 of the scales, like the 56-bit
-// truncation), combined exactly as two 64-bit integers and converted to FP64
-// once:
-//     (Q X_Q)[r][j] = 2^{e_r + f_j} (H 2^-35 + L 2^-63),
-//     H = sum_{d=2..5} acc_d 2^{7(5-d)},  L = sum_{d=6..9} acc_d 2^{7(9-d)}.
-// The result carries the 56-bit truncation of the operands and one FP64
-// rounding, i.e. FP64 accuracy, with no FP64 multiply on the products.
+// truncation) and combined exactly in integers,
+//     (Q X_Q)[r][j] = 2^{e_r + f_j - 63} T,   T = sum_{d=2..9} acc_d 2^{7(9-d)}  (|T| < 2^75),
+// then rounded once to FP64 (to nearest) by integer operations. The result
+// carries the 56-bit truncation of the operands and one rounding: FP64
+// accuracy, with the FP64 pipe (1/64 of the FP32 rate on this GPU) used only
+// for the residual sums.
 //
 // Layout (tcgen05.mma kind::f16, BF16 operands, FP32 accumulators in TMEM,
-// cta_group::1, M = 128 rows of the tile, N = a 32-column (or 16-column) chunk
-// of the output, K = m0 padded to a multiple of 16): operands in shared memory
-// in the no-swizzle K-major layout of 8 x 16-byte core matrices (leading byte
-// offset 128 B between core matrices along K, stride byte offset (K/8) x 128 B
-// between groups of 8 rows). Shared memory holds the 8 digit planes of one
-// 128-row tile of Q (then of A Q) and the 8 digit planes of the 32 columns of
-// X_Q of the chunk; TMEM holds 2 outputs x 8 levels x 32 columns (512 columns).
+// cta_group::1, M = 128 rows of the tile, K = m0 padded to a multiple of 16):
+// operands in shared memory in the no-swizzle K-major layout of 8 x 16-byte
+// core matrices (leading byte offset 128 B between core matrices along K,
+// stride byte offset (K/8) x 128 B between groups of 8 rows). Output columns
+// go in chunks of wc = 32 (the last one 16 when K is an odd multiple of 16).
+// The 8 digit planes of a chunk of D^-1 X_Q are stored back to back, so the
+// planes b = 1 .. 9 - a form one B operand of N = wc (9 - a) rows: one MMA per
+// 16-wide K step writes every level a + b of digit a of the A operand, into
+// TMEM columns that are contiguous when level d sits at (d - 2) wc. Shared
+// memory holds the 8 digit planes of one 128-row tile of Q (then of A Q) and
+// the 8 planes of the chunk; TMEM holds 2 outputs x 8 levels x wc columns.
 // One persistent CTA of 512 threads per SM walks (column chunk, row tile)
 // items. Every wait on the mbarrier is bounded: a wait that runs out sets
 // status->tc_timeout, and the CTA stops issuing work, waits (bounded) for its
@@ -50,8 +54,9 @@ constexpr int kTcRows = 128;      // M: rows of one tile (TMEM lanes)
 constexpr int kTcDigits = 8;      // digits per operand value (56 bits)
 constexpr int kTcLevels = 8;      // levels d = 2..9
 constexpr int kTcMaxK = 80;       // m0 padded, at most (digit sums stay below 2^24)
-constexpr int kTcChunk = 32;      // output columns per item (N)
+constexpr int kTcChunk = 32;      // output columns per item (N of one level)
 constexpr long kTcSpin = 1L << 26;  // try_wait polls before a wait gives up
+constexpr int kNoExp = -(1 << 20);  // exponent of 0 (and of denormals)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -114,8 +119,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
       : "r"(taddr));
 }
 
-constexpr int kNoExp = -(1 << 20);  // exponent of 0 (and of denormals)
-
 // exponent e with 2^(e-1) <= |x| < 2^e for normal x; kNoExp for 0 and denormals
 __device__ __forceinline__ int scale_exp(double x) {
   const long long b = __double_as_longlong(x);
@@ -144,27 +147,121 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int e) {
   return m >> (-sh);
 }
 
-// signed digit t (1..8) of a fixed-point magnitude, as BF16 (|d| <= 127: exact)
-__device__ __forceinline__ __nv_bfloat16 digit_bf16(unsigned long long f, int t, bool neg) {
-  const int d = (int)((f >> (56 - 7 * t)) & 0x7F);
-  return __float2bfloat16_rn((float)(neg ? -d : d));
+__device__ __forceinline__ bool sign_bit(double x) { return __double_as_longlong(x) < 0; }
+
+// BF16 bits of the integer d in [0, 127]: 2^23 + d is exact in FP32 and
+// (2^23 + d) - 2^23 = d exactly; its low 16 bits are zero, so the upper half
+// is the BF16 value
+__device__ __forceinline__ uint32_t digit_bits(uint32_t d) {
+  const float f = __int_as_float((int)(0x4B000000u | d)) - 8388608.0f;
+  return (uint32_t)__float_as_int(f) >> 16;
 }
 
-// Digits of D^-1 X_Q for the B operand: column j (the output column) has the
-// scale f_j (2^f_j > max_i |X_Q[i][j]| 2^c_i); Bd[(c * 8 + t - 1) * 32 * kp +
-// core_off(j - 32 c, i, kp)] = digit t of X_Q[i][j] 2^c_i (signed), 0 in the
-// padding. Block 0 also writes the balancing exponents cexp[i] = c_i.
-__global__ void k_tc_bdigits(int m, int kp, const double *__restrict__ XQ,
-                             const double *__restrict__ Bq, __nv_bfloat16 *__restrict__ Bd,
-                             int *__restrict__ fexp, int *__restrict__ cexp) {
-  const int j = blockIdx.x;  // one block per output column, padding columns included
+// signed digit t (1..8) of a fixed-point magnitude, as BF16 (|d| <= 127: exact)
+__device__ __forceinline__ __nv_bfloat16 digit_bf16(unsigned long long f, int t, bool neg) {
+  const uint32_t d = (uint32_t)((f >> (56 - 7 * t)) & 0x7F);
+  return __ushort_as_bfloat16((unsigned short)(digit_bits(d) | (neg && d ? 0x8000u : 0u)));
+}
+
+// (-1)^neg |T| 2^e2 rounded to the nearest FP64 (ties to even), T given as the
+// 128-bit magnitude hi 2^64 + lo; integer operations only while the result is
+// a normal number (ldexp of the rounded significand otherwise)
+__device__ __forceinline__ double int128_to_double(unsigned long long hi, unsigned long long lo,
+                                                   bool neg, int e2) {
+  if (hi == 0 && lo == 0) return 0.0;
+  const int lz = hi ? __clzll(hi) : 64 + __clzll(lo);
+  unsigned long long top, rest;  // the magnitude shifted left by lz: top = bits 127..64
+  if (lz == 0) {
+    top = hi;
+    rest = lo;
+  } else if (lz < 64) {
+    top = (hi << lz) | (lo >> (64 - lz));
+    rest = lo << lz;
+  } else {
+    top = lo << (lz - 64);
+    rest = 0;
+  }
+  unsigned long long mant = top >> 11;  // 53 bits, leading bit set
+  const bool rbit = (top >> 10) & 1ull;
+  const bool sticky = (top & 0x3FFull) != 0 || rest != 0;
+  int p = 127 - lz;  // position of the leading bit of T
+  if (rbit && (sticky || (mant & 1ull))) {
+    ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++p;
+    }
+  }
+  const int be = p + e2 + 1023;  // biased exponent of the result
+  if (be > 0 && be < 2047) {
+    const unsigned long long bits = ((unsigned long long)neg << 63) |
+                                    ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+  }
+  const double v = ldexp((double)mant, p - 52 + e2);
+  return neg ? -v : v;
+}
+
+constexpr int kTcPrepRows = 32;  // rows per row-exponent block of k_tc_prep
+
+// Operand preparation, one launch with two kinds of blocks (blockDim =
+// 32 * kp / 8 threads; every block first forms the balancing exponents c_i):
+//  * blocks 0 .. kp - 1, one per output column j (padding included): the digits
+//    of D^-1 X_Q for the B operand. Column j has the scale f_j (2^f_j >
+//    max_i |X_Q[i][j]| 2^c_i). Chunk c holds columns 32 c .. 32 c + wc - 1
+//    (wc = min(32, kp - 32 c)); its planes t = 1..8 follow each other:
+//    Bd[32 c * 8 * kp + (t - 1) * wc * kp + core_off(j - 32 c, i, kp)] = digit t
+//    of X_Q[i][j] 2^c_i (signed), 0 in the padding. Block 0 also writes
+//    cexp[i] = c_i.
+//  * the following blocks, 32 rows each: the row exponents of Q D and A Q D,
+//    rexp[o * n + r] = the e with 2^e > max_k |M[r][k]| 2^-c_k (0 for a zero
+//    row), one thread per 8 consecutive columns of a row, all 8 loads in
+//    flight.
+__global__ void k_tc_prep(int n, int m, int kp, const double *__restrict__ XQ,
+                          const double *__restrict__ Bq, const double *__restrict__ Q,
+                          const double *__restrict__ AQ, __nv_bfloat16 *__restrict__ Bd,
+                          int *__restrict__ fexp, int *__restrict__ cexp,
+                          int *__restrict__ rexp) {
   __shared__ int se;
   __shared__ int sc[kTcMaxK];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    sc[i] = balance_exp(Bq, m, i);
-    if (j == 0) cexp[i] = sc[i];
+  __shared__ int srow[2][kTcPrepRows];
+  for (int i = threadIdx.x; i < kp; i += blockDim.x) {
+    sc[i] = i < m ? balance_exp(Bq, m, i) : 0;
+    if (blockIdx.x == 0 && i < m) cexp[i] = sc[i];
   }
+  if (threadIdx.x < 2 * kTcPrepRows) srow[threadIdx.x / kTcPrepRows][threadIdx.x % kTcPrepRows] = kNoExp;
   __syncthreads();
+  if ((int)blockIdx.x >= kp) {  // row exponents
+    const int groups = kp >> 3;
+    const int lr = threadIdx.x / groups, g = threadIdx.x % groups;
+    const int r = (blockIdx.x - kp) * kTcPrepRows + lr;
+    if (r < n) {
+      for (int o = 0; o < 2; ++o) {
+        const double *M = o == 0 ? Q : AQ;
+        double x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int k = 8 * g + e;
+          x[e] = k < m ? M[(size_t)r * m + k] : 0.0;
+        }
+        int ex = kNoExp;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int ek = scale_exp(x[e]);
+          if (ek != kNoExp) ex = max(ex, ek - sc[8 * g + e]);
+        }
+        atomicMax(&srow[o][lr], ex);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kTcPrepRows) {
+      const int o = threadIdx.x / kTcPrepRows, l = threadIdx.x % kTcPrepRows;
+      const int rr = (blockIdx.x - kp) * kTcPrepRows + l;
+      if (rr < n) rexp[(size_t)o * n + rr] = srow[o][l] == kNoExp ? 0 : srow[o][l];
+    }
+    return;
+  }
+  const int j = blockIdx.x;  // B digits of output column j
   if (threadIdx.x == 0) {
     int e = kNoExp;  // max_i of the exponent of X_Q[i][j] 2^c_i
     if (j < m)
@@ -177,15 +274,16 @@ __global__ void k_tc_bdigits(int m, int kp, const double *__restrict__ XQ,
   }
   __syncthreads();
   const int c = j / kTcChunk, jj = j % kTcChunk;
+  const int wc = min(kTcChunk, kp - kTcChunk * c);
+  __nv_bfloat16 *Bc = Bd + (size_t)kTcChunk * c * kTcDigits * kp;
   for (int i = threadIdx.x; i < kp; i += blockDim.x) {
     const bool in = j < m && i < m;
     const double x = in ? XQ[(size_t)i * m + j] : 0.0;
     // |X_Q[i][j] 2^c_i| < 2^se, i.e. |X_Q[i][j]| < 2^(se - c_i)
     const unsigned long long f = in ? fixed56(x, se - sc[i]) : 0ull;
-    const bool neg = x < 0.0;
+    const bool neg = sign_bit(x);
     for (int t = 1; t <= kTcDigits; ++t)
-      Bd[((size_t)c * kTcDigits + (t - 1)) * kTcChunk * kp + core_off(jj, i, kp)] =
-          digit_bf16(f, t, neg);
+      Bc[(size_t)(t - 1) * wc * kp + core_off(jj, i, kp)] = digit_bf16(f, t, neg);
   }
 }
 
@@ -196,19 +294,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
             const double *__restrict__ AQ, const __nv_bfloat16 *__restrict__ Bd,
             const int *__restrict__ fexp, const int *__restrict__ cexp,
-            const double *__restrict__ lam, double *__restrict__ X,
+            const int *__restrict__ rexp_g, const double *__restrict__ lam, double *__restrict__ X,
             double *__restrict__ Rres, double *__restrict__ part, DevStatus *__restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // A digit planes [8] (128 x kp each), then B digit planes [8] (32 x kp each)
+  // A digit planes [8] (128 x kp each), then the chunk's B digit planes [8] (wc x kp each)
   __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
   __nv_bfloat16 *sB = sA + (size_t)kTcDigits * kTcRows * kp;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tbase;
   __shared__ int rexp[2][kTcRows];
   __shared__ int sc[kTcMaxK];  // balancing exponents c_i (0 in the padding)
+  __shared__ int sf[kTcMaxK];  // column scales f_j
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = (n + kTcRows - 1) / kTcRows;
-  for (int i = tid; i < kp; i += kTcThreads) sc[i] = i < m ? cexp[i] : 0;
+  for (int i = tid; i < kp; i += kTcThreads) {
+    sc[i] = i < m ? cexp[i] : 0;
+    sf[i] = i < m ? fexp[i] : 0;
+  }
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -224,20 +326,18 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
   uint32_t commits = 0, waited = 0;  // commits on mbar issued / waited for (uniform)
   bool fail = false;
   const int groups = kp >> 3;        // groups of 8 consecutive K columns per row
-  const int kq = kp >> 2;            // row-scale pass: 4 threads per row, kq columns each
   // epilogue mapping: warp w -> TMEM lanes 32 (w & 3) .. + 31, columns 8 (w >> 2) .. + 7
   const int erow = 32 * (warp & 3) + lane, ecol = 8 * (warp >> 2);
   const uint32_t sbo = (uint32_t)(kp >> 3) * 128u;
   for (int c = 0; c < nchunks && !fail; ++c) {
-    const int nc = (kp - c * kTcChunk) >= kTcChunk ? kTcChunk : 16;  // N of this chunk
+    const int wc = min(kTcChunk, kp - c * kTcChunk);  // output columns of this chunk
     const int j0 = c * kTcChunk;
-    const uint32_t idesc = idesc_bf16(nc);
     // B digits of this chunk to shared memory (16-byte copies); every MMA of the
     // previous chunk completed (the item loop waits for every commit)
     {
-      const uint4 *src = reinterpret_cast<const uint4 *>(Bd + (size_t)c * kTcDigits * kTcChunk * kp);
+      const uint4 *src = reinterpret_cast<const uint4 *>(Bd + (size_t)j0 * kTcDigits * kp);
       uint4 *dst = reinterpret_cast<uint4 *>(sB);
-      const int words = kTcDigits * kTcChunk * kp * 2 / 16;
+      const int words = kTcDigits * wc * kp * 2 / 16;
       for (int e = tid; e < words; e += kTcThreads) dst[e] = src[e];
     }
     double pe[8], pa[8], px[8];  // residual partial sums of this thread's columns
@@ -247,20 +347,8 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
       const int r0 = tile * kTcRows;
       for (int o = 0; o < 2 && !fail; ++o) {
         const double *Mt = o == 0 ? Q : AQ;
-        {  // row scales of M D: 4 threads per row, kq columns each
-          const int row = tid >> 2, qtr = tid & 3, gr = r0 + row;
-          int ex = kNoExp;  // max_k of the exponent of M[r][k] 2^-c_k
-          for (int q = 0; q < kq; ++q) {
-            const int k = qtr * kq + q;
-            if (gr < n && k < m) {
-              const int ek = scale_exp(Mt[(size_t)gr * m + k]);
-              if (ek != kNoExp) ex = max(ex, ek - sc[k]);
-            }
-          }
-          ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, 1));
-          ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, 2));
-          if (qtr == 0) rexp[o][row] = ex == kNoExp ? 0 : ex;
-        }
+        if (tid < kTcRows)  // row exponents of M D (k_tc_prep)
+          rexp[o][tid] = r0 + tid < n ? rexp_g[(size_t)o * n + r0 + tid] : 0;
         // the MMAs of the previous matrix read the digit planes: wait for them
         bool gave_up = false;
         if (waited < commits) {
@@ -270,27 +358,43 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
         fail = __syncthreads_or(gave_up) != 0;  // rexp visible; the same decision in every thread
         if (fail) break;
         // digit planes: one unit = 8 consecutive K columns of one row, one
-        // 16-byte store per plane (they form one row of a core matrix)
+        // 16-byte store per plane (they form one row of a core matrix); the 8
+        // rows of a core matrix are 8 consecutive threads, whose stores fill
+        // 128 contiguous bytes
         for (int u = tid; u < kTcRows * groups; u += kTcThreads) {
-          const int row = u / groups, g = u % groups, gr = r0 + row;
+          const int rem = u % (8 * groups);
+          const int row = 8 * (u / (8 * groups)) + (rem & 7), g = rem >> 3, gr = r0 + row;
           const int er = rexp[o][row];
-          unsigned long long f[8];
-          unsigned neg = 0u;
+          uint32_t hi[8], lo[8];  // the 56-bit magnitudes as two 28-bit halves
+          uint32_t sg[4];         // sign bits of the packed element pairs
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int k = 8 * g + e;
             const double x = (gr < n && k < m) ? Mt[(size_t)gr * m + k] : 0.0;
-            f[e] = fixed56(x, er + sc[k]);  // |M[r][k] 2^-c_k| < 2^er
-            neg |= (x < 0.0 ? 1u : 0u) << e;
+            const unsigned long long f = fixed56(x, er + sc[k]);  // |M[r][k] 2^-c_k| < 2^er
+            hi[e] = (uint32_t)(f >> 28);
+            lo[e] = (uint32_t)(f & 0xFFFFFFFull);
+            if (e & 1)
+              sg[e >> 1] |= sign_bit(x) ? 0x80000000u : 0u;
+            else
+              sg[e >> 1] = sign_bit(x) ? 0x8000u : 0u;
           }
           const int off = core_off(row, 8 * g, kp);
 #pragma unroll
           for (int t = 1; t <= kTcDigits; ++t) {
-            __align__(16) __nv_bfloat16 dg[8];
+            uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) dg[e] = digit_bf16(f[e], t, (neg >> e) & 1u);
+            for (int e2 = 0; e2 < 4; ++e2) {
+              // digit t: bits 28 - 7t .. of hi for t <= 4, bits 56 - 7t .. of lo for t > 4
+              const uint32_t d0 = t <= 4 ? (hi[2 * e2] >> (28 - 7 * t)) & 0x7Fu
+                                         : (lo[2 * e2] >> (56 - 7 * t)) & 0x7Fu;
+              const uint32_t d1 = t <= 4 ? (hi[2 * e2 + 1] >> (28 - 7 * t)) & 0x7Fu
+                                         : (lo[2 * e2 + 1] >> (56 - 7 * t)) & 0x7Fu;
+              const uint32_t s = sg[e2] & ((d0 ? 0x8000u : 0u) | (d1 ? 0x80000000u : 0u));
+              w[e2] = (digit_bits(d0) | (digit_bits(d1) << 16)) | s;
+            }
             *reinterpret_cast<uint4 *>(sA + (size_t)(t - 1) * kTcRows * kp + off) =
-                *reinterpret_cast<const uint4 *>(dg);
+                make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -298,16 +402,17 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
         if (tid == 0) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t abase = smem_u32(sA), bbase = smem_u32(sB);
-          for (int a = 1; a <= kTcDigits; ++a)
-            for (int b = 1; a + b <= kTcLevels + 1; ++b) {
-              const int d = a + b;  // level 2..9, first written by the pair (1, d - 1)
-              const uint32_t dcol = tmem + (uint32_t)((o * kTcLevels + (d - 2)) * kTcChunk);
-              const uint32_t ap = abase + (uint32_t)((a - 1) * kTcRows * kp * 2);
-              const uint32_t bp = bbase + (uint32_t)((b - 1) * kTcChunk * kp * 2);
-              for (int kk = 0; kk < kp / 16; ++kk)
-                mma_bf16(dcol, smem_desc(ap + kk * 256u, sbo), smem_desc(bp + kk * 256u, sbo),
-                         idesc, (a > 1 || kk > 0) ? 1u : 0u);
-            }
+          // digit a of A against planes b = 1 .. 9 - a of B: one MMA of
+          // N = wc (9 - a) per K step, into levels a + 1 .. 9
+          for (int a = 1; a <= kTcDigits; ++a) {
+            const int nb = kTcLevels + 1 - a;
+            const uint32_t idesc = idesc_bf16(wc * nb);
+            const uint32_t dcol = tmem + (uint32_t)((o * kTcLevels + (a - 1)) * wc);
+            const uint32_t ap = abase + (uint32_t)((a - 1) * kTcRows * kp * 2);
+            for (int kk = 0; kk < kp / 16; ++kk)
+              mma_bf16(dcol, smem_desc(ap + kk * 256u, sbo), smem_desc(bbase + kk * 256u, sbo),
+                       idesc, (a > 1 || kk > 0) ? 1u : 0u);
+          }
           mma_commit(&mbar);
         }
         ++commits;
@@ -328,27 +433,31 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
       // output 0 (X) first, then output 1 (A X) with the residual
       const int gr = r0 + erow;
       double xv[8];
-      if (ecol < nc) {
+      if (ecol < wc) {
 #pragma unroll
         for (int o = 0; o < 2; ++o) {
-          long long H[8], L[8];
+          long long S1[8], S2[8];  // levels 2..5 and 6..9, each below 2^46
 #pragma unroll
-          for (int q = 0; q < 8; ++q) H[q] = L[q] = 0;
+          for (int half = 0; half < 2; ++half) {
+            uint32_t uu[4][8];
 #pragma unroll
-          for (int d = 2; d <= 9; ++d) {
-            uint32_t uu[8];
-            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
-                                (uint32_t)((o * kTcLevels + (d - 2)) * kTcChunk + ecol);
-            tmem_ld8(ta, uu);
+            for (int l = 0; l < 4; ++l) {
+              const int d = 2 + 4 * half + l;
+              const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                                  (uint32_t)((o * kTcLevels + (d - 2)) * wc + ecol);
+              tmem_ld8(ta, uu[l]);
+            }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const long long w = d <= 5 ? (1LL << (7 * (5 - d))) : (1LL << (7 * (9 - d)));
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const long long iv = __float2ll_rn(__uint_as_float(uu[q]));  // an exact integer
-              if (d <= 5)
-                H[q] += iv * w;
+              long long s = 0;
+#pragma unroll
+              for (int l = 0; l < 4; ++l)  // weight 2^{7(3 - l)} within the half
+                s += (long long)__float2int_rn(__uint_as_float(uu[l][q])) << (7 * (3 - l));
+              if (half == 0)
+                S1[q] = s;
               else
-                L[q] += iv * w;
+                S2[q] = s;
             }
           }
           const int er = rexp[o][erow];
@@ -356,14 +465,24 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
           for (int q = 0; q < 8; ++q) {
             const int j = j0 + ecol + q;
             if (gr >= n || j >= m) continue;
-            const double val = ldexp(fma((double)L[q], 0x1p-63, (double)H[q] * 0x1p-35),
-                                     er + fexp[j]);
+            // T = S1 2^28 + S2 as a signed 128-bit value (hi, lo)
+            const unsigned long long s1lo = (unsigned long long)S1[q] << 28;
+            unsigned long long lo = s1lo + (unsigned long long)S2[q];
+            const unsigned long long carry = lo < s1lo ? 1ull : 0ull;
+            unsigned long long hi = (unsigned long long)(S1[q] >> 36) +
+                                    (unsigned long long)(S2[q] >> 63) + carry;
+            const bool neg = (long long)hi < 0;
+            if (neg) {  // magnitude of the two's complement value
+              lo = ~lo + 1ull;
+              hi = ~hi + (lo == 0 ? 1ull : 0ull);
+            }
+            const double val = int128_to_double(hi, lo, neg, er + sf[j] - 63);
             if (o == 0) {
               xv[q] = val;
               X[(size_t)gr * m + j] = val;
             } else {
               const double x = xv[q], ax = val;
-              const double dd = ax - lam[j] * x;
+              const double dd = fma(-lam[j], x, ax);
               if (Rres) Rres[(size_t)gr * m + j] = dd;
               pe[q] = fma(dd, dd, pe[q]);
               pa[q] = fma(ax, ax, pa[q]);
@@ -389,7 +508,7 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
         if (tid < kTcChunk) {
           const int cg = tid / 8, q = tid % 8;
           const int j = j0 + tid;
-          if (j < m && tid < nc) {
+          if (j < m && tid < wc) {
             double sum = 0.0;
             for (int w = 0; w < 4; ++w)
               for (int l = 0; l < 32; ++l) sum += dred[((cg * 4 + w) * 32 + l) * 9 + q];
@@ -420,18 +539,18 @@ size_t tc_smem_bytes(int kp) {
   return need > floor_bytes ? need : floor_bytes;
 }
 
-size_t tc_bdigit_bytes(int m0) {
+// B digit planes of all chunks (kp columns x 8 planes x kp), f_j, c_i, and
+// the row exponents of Q D and A Q D
+size_t tc_scratch_bytes(int64_t n, int m0) {
   const int kp = (m0 + 15) / 16 * 16;
-  const int nchunks = (kp + kTcChunk - 1) / kTcChunk;
-  return (size_t)nchunks * kTcDigits * kTcChunk * kp * 2 +
-         (size_t)(nchunks * kTcChunk + kTcMaxK) * sizeof(int);
+  return (size_t)kp * kTcDigits * kp * 2 + (size_t)(2 * kTcMaxK + 2 * n) * sizeof(int);
 }
 
 }  // namespace
 
 bool update_resid_tc_supported(const RRArgs &a) {
   const size_t gram_bytes = (size_t)a.Pg * 2 * ((a.m0 + 3) / 4 * 4) * ((a.m0 + 3) / 4 * 4) * 8;
-  return a.m0 <= kTcMaxK && a.rowptrB == nullptr && tc_bdigit_bytes(a.m0) <= gram_bytes &&
+  return a.m0 <= kTcMaxK && a.rowptrB == nullptr && tc_scratch_bytes(a.n, a.m0) <= gram_bytes &&
          a.n >= kTcRows;
 }
 
@@ -442,12 +561,15 @@ cudaError_t update_resid_tc(const RRArgs &a, int blocks, cudaStream_t st) {
   // B digits and column scales in the Gram partials buffer, which the reduced
   // eigensolver has finished with
   __nv_bfloat16 *Bd = reinterpret_cast<__nv_bfloat16 *>(a.gram_part);
-  int *fexp = reinterpret_cast<int *>(Bd + (size_t)nchunks * kTcDigits * kTcChunk * kp);
-  int *cexp = fexp + (size_t)nchunks * kTcChunk;
-  k_tc_bdigits<<<nchunks * kTcChunk, 128, 0, st>>>(m, kp, a.XQ, a.Bq, Bd, fexp, cexp);
+  int *fexp = reinterpret_cast<int *>(Bd + (size_t)kp * kTcDigits * kp);
+  int *cexp = fexp + kTcMaxK;
+  int *rexp = cexp + kTcMaxK;
+  const int prep_blocks = kp + (a.n + kTcPrepRows - 1) / kTcPrepRows;
+  k_tc_prep<<<prep_blocks, kTcPrepRows * (kp >> 3), 0, st>>>(a.n, m, kp, a.XQ, a.Bq, a.Q, a.AQ,
+                                                              Bd, fexp, cexp, rexp);
   k_tc_update<<<blocks, kTcThreads, tc_smem_bytes(kp), st>>>(a.n, m, kp, nchunks, a.Q, a.AQ, Bd,
-                                                              fexp, cexp, a.lam, a.X, a.Rres,
-                                                              a.res_part, a.status);
+                                                              fexp, cexp, rexp, a.lam, a.X,
+                                                              a.Rres, a.res_part, a.status);
   return cudaGetLastError();
 }
 
