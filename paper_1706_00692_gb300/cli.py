@@ -4,10 +4,14 @@
                                                      lap3d_64_twopass|lap3d_64_fp64|lap2d_50|
                                                      fem3d_64|fem3d_64_fp64|fem3d_48|fem3d_128]
                                          [--max-outer M] [--inner-iters K] [--verbose]
+                                         [--rr-calls R]
 
 Prints one JSON line: status, eigenpairs found, largest residual, outer
 iterations, Krylov steps and wall time. Exit status 0 whenever the library
 calls succeed (a solve stopped by --max-outer before convergence included).
+With --rr-calls R it runs no solve: R Rayleigh-Ritz calls (Algorithm 2, steps
+3-4) on the workload's matrix and a seeded random subspace of its m0 columns,
+and prints the per-kernel CUDA-event times of those calls.
 """
 from __future__ import annotations
 
@@ -51,9 +55,13 @@ def main(argv=None) -> int:
     p.add_argument("--max-outer", type=int, default=100)
     p.add_argument("--inner-iters", type=int, default=0, help="override the workload's cap")
     p.add_argument("--verbose", action="store_true")
+    p.add_argument("--rr-calls", type=int, default=0,
+                   help="time this many Rayleigh-Ritz calls instead of a solve")
     a = p.parse_args(argv)
     import torch
     wl = workload(a.workload)
+    if a.rr_calls > 0:
+        return rr_calls(wl, a.rr_calls)
     k = a.inner_iters or wl.inner_iters
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
                inner_iters=k, alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass,
@@ -82,6 +90,25 @@ def main(argv=None) -> int:
     S.close()
     print(json.dumps(out), flush=True)
     return 0 if rc in (0, 4) else 1
+
+
+def rr_calls(wl, calls: int) -> int:
+    """Time `calls` Rayleigh-Ritz calls on a seeded N(0,1) subspace."""
+    import torch
+    S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
+               inner_iters=wl.inner_iters, alpha=wl.alpha, precision=wl.precision, B=wl.B)
+    Q = torch.as_tensor(inputs.initial_subspace(wl.A.n, wl.m0, 3), device="cuda")
+    S.set_profiling(True)
+    for _ in range(calls):
+        X, lam, res = S.rayleigh_ritz(Q)
+    torch.cuda.synchronize()
+    kt = S.kernel_times()
+    out = {"workload": wl.name, "rr_calls": calls,
+           "ms_per_call": {k: t / c for k, (c, t) in kt.items()},
+           "res_range": [float(res.min()), float(res.max())]}
+    S.close()
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -68,7 +68,7 @@ struct ifeast_ctx {
   double *lpart = nullptr, *lalpha = nullptr, *lbeta = nullptr, *ltol = nullptr;
   float4 *lcf32 = nullptr;
 
-  double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr;
+  double2 *lg = nullptr, *lR = nullptr, *lrot = nullptr, *lYc = nullptr, *lwt = nullptr;
   int *lsteps = nullptr, *ldone = nullptr, *lcoldone = nullptr, *lndone = nullptr,
       *lactive = nullptr, *lSj = nullptr;
   double *lcoef = nullptr, *lcx = nullptr, *Rres = nullptr, *rnorm = nullptr;
@@ -190,7 +190,7 @@ struct Layout {
 struct Offsets {
   size_t rowptr, colidx, val, z, w, V, W, part, H1, H2, inv_h, CS, SN, R, G, Y, steps, done, X, Q,
       AQ, beta, gram_part, Aq, Bq, L, Cm, U, XQ, lam, res_part, res, status, total;
-  size_t val32, LV, LW0, LW1, lpart, lalpha, lcf32, lbeta, ltol, lg, lR, lrot, lYc, lsteps, ldone,
+  size_t val32, LV, LW0, LW1, lpart, lalpha, lcf32, lbeta, ltol, lg, lR, lrot, lYc, lwt, lsteps, ldone,
       lcoldone, lndone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
   size_t rowptrB, colidxB, valB, BQ, BX;
   size_t LinvT, theta, Uc, ridx;
@@ -271,6 +271,7 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int ncc, int K, const RowTi
     o.lR = L.take<double2>(C * K * 3);
     o.lrot = L.take<double2>(C * 4);
     o.lYc = L.take<double2>(C * K);
+    o.lwt = L.take<double2>(C);
     o.lsteps = L.take<int>(C);
     o.ldone = L.take<int>(C);  // pair done flags
     o.lcoldone = L.take<int>(m0);
@@ -615,6 +616,7 @@ MinresArgs minres_args(ifeast_ctx *h, const double *X, double *Q, int correction
   a.cf32 = h->lcf32;
 
   a.Yc = h->lYc;
+  a.wt = h->lwt;
   a.coef = h->lcoef;
   a.cx = h->lcx;
   a.Sj = h->lSj;
@@ -928,6 +930,7 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->lR = (double2 *)(b + off.lR);
     h->lrot = (double2 *)(b + off.lrot);
     h->lYc = (double2 *)(b + off.lYc);
+    h->lwt = (double2 *)(b + off.lwt);
     h->lsteps = (int *)(b + off.lsteps);
     h->ldone = (int *)(b + off.ldone);
     h->lcoldone = (int *)(b + off.lcoldone);

@@ -188,6 +188,7 @@ struct MinresArgs {
   double *alpha, *beta;     // [K][m0], [K+1][m0]
   float4 *cf32;             // [K+1][m0] FP32 {alpha_{s-1}, beta_s, 1/beta_s, 0} for step s
   double2 *Yc;              // [nc][K][m0]
+  double2 *wt;              // [nc][m0] quadrature weight of each (node, column) pair
   double *coef, *cx;        // [K][m0] (+ an FP32 copy after it), [m0]
   int *Sj;                  // [m0]
   double *Q;

@@ -1089,9 +1089,38 @@ __global__ void k_build_ell(int n, int W, const int32_t *__restrict__ rowptr,
   }
 }
 
-// y = R^{-1} g for each (node, column) pair (banded back substitution), then
-// Yc[k][l][j] = wt_{k,j} y_l with wt = w_k (plain) or w_k / (z_k - lambda_j)
+// Back substitution y = R^{-1} g for each (node, column) pair, R upper
+// triangular with bandwidth 3: y_l = (g_l - r_{l,l+1} y_{l+1} - r_{l,l+2}
+// y_{l+2}) / r_{l,l}. The divisions do not depend on y, so they run first, in
+// parallel over (pair, l), in place: g_l <- g_l / r_{l,l}, r_{l,l+1} <-
+// r_{l,l+1} / r_{l,l}, r_{l,l+2} <- r_{l,l+2} / r_{l,l} (each entry is read and
+// written by the thread of its row l only); the dependent recurrence is then
+// two complex multiply-adds per row. Thread 0 of each pair's first block also
+// forms the pair's quadrature weight wt = w_k (plain) or w_k / (z_k - lambda_j)
 // (residual form).
+__global__ void k_lz_solve_prep(int m0, int K, const MinresState st, double2 *__restrict__ wt) {
+  const int p = blockIdx.y;
+  const int k = p / m0, j = p % m0;
+  const int m = st.steps[p];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double2 w = st.w[k];
+    if (st.correction) w = cdiv(w, make_double2(st.z[k].x - st.lam[j], st.z[k].y));
+    wt[p] = w;
+  }
+  if (l >= m) return;
+  double2 *R = st.R + (size_t)p * K * 3;
+  double2 *g = st.g + (size_t)p * (K + 1);
+  const double2 r0 = R[(size_t)l * 3];
+  const double d = r0.x * r0.x + r0.y * r0.y;
+  const double2 inv = make_double2(r0.x / d, -r0.y / d);  // 1 / r_{l,l}
+  g[l] = cmul(g[l], inv);
+  if (l + 1 < m) R[(size_t)(l + 1) * 3 + 1] = cmul(R[(size_t)(l + 1) * 3 + 1], inv);
+  if (l + 2 < m) R[(size_t)(l + 2) * 3 + 2] = cmul(R[(size_t)(l + 2) * 3 + 2], inv);
+}
+
+// The recurrence of the back substitution after k_lz_solve_prep:
+// Yc[k][l][j] = y_l (unweighted; k_lz_coef applies the pair's weight).
 __global__ void k_lz_solve(int m0, int nc, int K, const MinresState st, double2 *__restrict__ Yc) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nc * m0) return;
@@ -1099,35 +1128,31 @@ __global__ void k_lz_solve(int m0, int nc, int K, const MinresState st, double2 
   const int m = st.steps[p];
   const double2 *R = st.R + (size_t)p * K * 3;
   const double2 *g = st.g + (size_t)p * (K + 1);
-  double2 wt = st.w[k];
-  if (st.correction) wt = cdiv(wt, make_double2(st.z[k].x - st.lam[j], st.z[k].y));
   for (int l = K - 1; l >= m; --l) Yc[((size_t)k * K + l) * m0 + j] = make_double2(0.0, 0.0);
   double2 y1 = make_double2(0.0, 0.0), y2 = make_double2(0.0, 0.0);  // y_{l+1}, y_{l+2}
-  // chunks of 8 rows, bottom up; the chunk's g and band entries are loaded
-  // before the dependent recurrence runs over them
+  // chunks of 8 rows, bottom up; the chunk's coefficients are loaded before
+  // the dependent recurrence runs over them
   constexpr int CH = 8;
   for (int hi = m - 1; hi >= 0; hi -= CH) {
-    double2 gg[CH], r0[CH], r1[CH], r2[CH];
+    double2 a[CH], b[CH], c[CH];
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
       const int l = hi - u;
       if (l >= 0) {
-        gg[u] = g[l];
-        r0[u] = R[(size_t)l * 3];
-        r1[u] = (l + 1 < m) ? R[(size_t)(l + 1) * 3 + 1] : make_double2(0.0, 0.0);
-        r2[u] = (l + 2 < m) ? R[(size_t)(l + 2) * 3 + 2] : make_double2(0.0, 0.0);
+        a[u] = g[l];
+        b[u] = (l + 1 < m) ? R[(size_t)(l + 1) * 3 + 1] : make_double2(0.0, 0.0);
+        c[u] = (l + 2 < m) ? R[(size_t)(l + 2) * 3 + 2] : make_double2(0.0, 0.0);
       }
     }
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
       const int l = hi - u;
       if (l >= 0) {
-        double2 t = gg[u];
-        const double2 q1 = cmul(r1[u], y1), q2 = cmul(r2[u], y2);
-        t.x -= q1.x + q2.x;
-        t.y -= q1.y + q2.y;
-        const double2 y = cdiv(t, r0[u]);
-        Yc[((size_t)k * K + l) * m0 + j] = cmul(wt, y);
+        // y = a - b y1 - c y2
+        double2 y;
+        y.x = a[u].x - (b[u].x * y1.x - b[u].y * y1.y) - (c[u].x * y2.x - c[u].y * y2.y);
+        y.y = a[u].y - (b[u].x * y1.y + b[u].y * y1.x) - (c[u].x * y2.y + c[u].y * y2.x);
+        Yc[((size_t)k * K + l) * m0 + j] = y;
         y2 = y1;
         y1 = y;
       }
@@ -1137,16 +1162,21 @@ __global__ void k_lz_solve(int m0, int nc, int K, const MinresState st, double2 
   atomicAdd((unsigned long long *)&st.status->total_steps, (unsigned long long)m);
 }
 
-// coef[l][j] = Re sum_k Yc[k][l][j]; cx[j] = Re sum_k w_k/(z_k - lambda_j) in the
-// residual form (the filter value of the Ritz value), else 0; Sj = max_k steps.
+// coef[l][j] = Re sum_k wt[k][j] Yc[k][l][j]; cx[j] = Re sum_k w_k/(z_k - lambda_j)
+// in the residual form (the filter value of the Ritz value), else 0;
+// Sj = max_k steps.
 __global__ void k_lz_coef(int m0, int nc, int K, const MinresState st,
-                          const double2 *__restrict__ Yc, double *__restrict__ coef,
-                          double *__restrict__ cx, int *__restrict__ Sj) {
+                          const double2 *__restrict__ Yc, const double2 *__restrict__ wt,
+                          double *__restrict__ coef, double *__restrict__ cx,
+                          int *__restrict__ Sj) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < (size_t)K * m0) {
     const int l = (int)(idx / m0), j = (int)(idx % m0);
     double t = 0.0;
-    for (int k = 0; k < nc; ++k) t += Yc[((size_t)k * K + l) * m0 + j].x;
+    for (int k = 0; k < nc; ++k) {
+      const double2 w = wt[k * m0 + j], y = Yc[((size_t)k * K + l) * m0 + j];
+      t += w.x * y.x - w.y * y.y;
+    }
     coef[idx] = t;
     // FP32 copy (after the K x m0 doubles) for the FP32 quadrature
     reinterpret_cast<float *>(coef + (size_t)K * m0)[idx] = (float)t;
@@ -1454,11 +1484,13 @@ cudaError_t run_minres(const MinresArgs &a, cudaStream_t st) {
   }
   if (e != cudaSuccess) return e;
   IFEAST_PROF_BEGIN(a.prof, K_LZ_SOLVE);
-  k_lz_solve<<<(unsigned)((pc + 127) / 128), 128, 0, st>>>(a.m0, a.nc, a.K, a.ms, a.Yc);
+  k_lz_solve_prep<<<dim3((unsigned)((a.K + 127) / 128), (unsigned)pc), 128, 0, st>>>(a.m0, a.K,
+                                                                                   a.ms, a.wt);
+  k_lz_solve<<<(unsigned)((pc + 31) / 32), 32, 0, st>>>(a.m0, a.nc, a.K, a.ms, a.Yc);
   IFEAST_PROF_END(a.prof);
   const size_t kc = (size_t)a.K * a.m0;
   IFEAST_PROF_BEGIN(a.prof, K_LZ_COEF);
-  k_lz_coef<<<(unsigned)((kc + 255) / 256), 256, 0, st>>>(a.m0, a.nc, a.K, a.ms, a.Yc, a.coef,
+  k_lz_coef<<<(unsigned)((kc + 255) / 256), 256, 0, st>>>(a.m0, a.nc, a.K, a.ms, a.Yc, a.wt, a.coef,
                                                            a.cx, a.Sj);
   IFEAST_PROF_END(a.prof);
   if constexpr (sizeof(T) <= 4) {
