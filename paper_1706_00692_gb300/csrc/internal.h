@@ -272,6 +272,11 @@ cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
 bool update_resid_tc_supported(const RRArgs &a);
 cudaError_t update_resid_tc(const RRArgs &a, int blocks, cudaStream_t st);
 cudaError_t rr_tc_init();
+// Tensor-core Gram matrices A_Q = Q^T A Q, B_Q = Q^T Q (B = I, m0 <= 80):
+// gram_tc_group > 0 when supported (CTAs per 48-column chunk); gram_tc writes
+// Aq and Bq (symmetric) through the Gram partials buffer.
+int gram_tc_group(const RRArgs &a);
+cudaError_t gram_tc(const RRArgs &a, cudaStream_t st);
 cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st);
 cudaError_t column_norms(int n, int m0, const double *X, double *part, int Pr, double *beta,
                          cudaStream_t st, Profiler *prof);

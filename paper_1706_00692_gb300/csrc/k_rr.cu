@@ -1146,8 +1146,14 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
       IFEAST_PROF_END(a.prof);
     }
   }
-  // Gram partials
-  {
+  // Gram matrices: on the tensor cores (BF16 digit products, FP64-accurate,
+  // k_rr_tc.cu) when the shape allows, else FP64 partials and their reduction
+  if (gram_tc_group(a) > 0) {
+    IFEAST_PROF_BEGIN(a.prof, K_RR_GRAM);
+    cudaError_t e = gram_tc(a, st);
+    IFEAST_PROF_END(a.prof);
+    if (e != cudaSuccess) return e;
+  } else {
     const int nt = mp / 4;
     const int ntiles = nt * (nt + 1) / 2;
     const int gy = (ntiles + kThreads - 1) / kThreads;

@@ -41,6 +41,7 @@
 // own outstanding MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -531,6 +532,346 @@ k_tc_update(int n, int m, int kp, int nchunks, const double *__restrict__ Q,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Gram matrices on the tensor cores (Algorithm 2, step 3: B_Q = Q^T Q and
+// A_Q = Q^T (A Q), B = I), FP64-accurate.
+//
+// The contraction runs over the n rows, so FP32 accumulation of digit
+// products is exact only over a bounded number of rows: the rows go in slabs
+// of kGramSlab = 96, and every value of a slab is written as eight signed
+// 7-bit digits (56-bit fixed point) below a per-slab, per-column power of two
+// 2^e (2^e > the column's largest magnitude in the slab). Level d = a + b of
+// digit pairs (2 <= d <= 9; at most 8 pairs of 96 products below 2^14 each,
+// < 2^24) is an exact FP32 sum; the slab's entry is 2^{e_i + e_j - 63} T with
+// T = sum_d acc_d 2^{7(9 - d)} formed in integers and rounded once to FP64,
+// and the slabs are added in FP64 in a fixed order. The dropped pairs
+// (a + b > 9) and the 56-bit truncation weigh below 2^-48 ||q_i|| ||q_j|| in
+// all (2^-55 of the slab maxima per product, times the 96 rows of a slab,
+// bounded through sum over slabs of max_i max_j <= ||q_i|| ||q_j||), against
+// the ~sqrt(n) 2^-53 ||q_i|| ||q_j|| a sequential FP64 dot product reaches.
+//
+// MMA shapes: M = 128 rows = the columns i of Q (rows i >= m of the A operand
+// are whatever follows in shared memory: they only reach TMEM lanes that are
+// never read), N = a chunk of wc <= 48 output columns j, K = the 96 rows of
+// the slab. TMEM holds the 8 levels of one output (8 wc <= 384 columns), so
+// B_Q's MMAs (B operand = the chunk's rows of Q's own digit planes, one MMA per
+// digit pair) and A_Q's (B operand = the digit planes of the chunk's columns of
+// A Q, stacked along N as in the update) run one after the other per slab.
+// CTA (chunk c, member g) takes the slabs g, g + G, ... and keeps 2 x wc/4
+// FP64 sums per thread; per-CTA partials are then summed in CTA order.
+constexpr int kGramSlab = 96;
+constexpr int kGramDigits = 8;
+constexpr int kGramLevels = 8;     // levels d = 2..9
+constexpr int kGramChunk = 48;     // output columns per chunk (8 x 48 <= 512 TMEM columns)
+constexpr int kGramColsPerThread = kGramChunk / 4;
+// digit units (column, 8 rows) of a slab per thread: (80 + 48) x 96 / 8 / 512
+constexpr int kGramUnits = ((kTcMaxK + kGramChunk) * (kGramSlab / 8) + kTcThreads - 1) / kTcThreads;
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+
+// 8 consecutive slab rows of one column as the 16-byte core-matrix rows of the
+// eight digit planes (plane stride `pstride` elements, offset `off` in a plane)
+__device__ __forceinline__ void gram_digits8(const double (&x)[8], int e, __nv_bfloat16 *planes,
+                                             size_t pstride, int off) {
+  unsigned long long f[8];
+  uint32_t sg[4];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    f[q] = fixed56(x[q], e);
+    if (q & 1)
+      sg[q >> 1] |= sign_bit(x[q]) ? 0x80000000u : 0u;
+    else
+      sg[q >> 1] = sign_bit(x[q]) ? 0x8000u : 0u;
+  }
+#pragma unroll
+  for (int t = 1; t <= kGramDigits; ++t) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q2 = 0; q2 < 4; ++q2) {
+      const uint32_t d0 = (uint32_t)(f[2 * q2] >> (56 - 7 * t)) & 0x7Fu;
+      const uint32_t d1 = (uint32_t)(f[2 * q2 + 1] >> (56 - 7 * t)) & 0x7Fu;
+      const uint32_t sm = sg[q2] & ((d0 ? 0x8000u : 0u) | (d1 ? 0x80000000u : 0u));
+      w[q2] = (digit_bits(d0) | (digit_bits(d1) << 16)) | sm;
+    }
+    *reinterpret_cast<uint4 *>(planes + (size_t)(t - 1) * pstride + off) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_tc_gram(int n, int m, int mrows, int nch, int G, const double *__restrict__ Q,
+          const double *__restrict__ AQ, double *__restrict__ part,
+          DevStatus *__restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // A planes: 9 x (mrows x 64), then a tail so that the 128 rows an MMA reads
+  // stay inside the allocation; then the 9 planes of the chunk's A Q columns
+  const size_t pa = (size_t)mrows * kGramSlab;  // elements per A plane
+  __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+  __nv_bfloat16 *sB = sA + kGramDigits * pa + (size_t)(kTcRows - mrows) * kGramSlab;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  __shared__ int eA[kTcMaxK], eB[kGramChunk];  // per-slab column exponents
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.x / G, g = blockIdx.x % G;  // chunk, member
+  const int j0 = c * kGramChunk;
+  const int kp = (m + 15) / 16 * 16;
+  const int wc = min(kGramChunk, kp - j0);       // output columns of the chunk (multiple of 16)
+  const size_t pb = (size_t)wc * kGramSlab;    // elements per B plane
+  const int nslab = (n + kGramSlab - 1) / kGramSlab;
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tbase)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // the tail rows (read by the last plane's MMAs into unused lanes): zero
+  for (size_t e = tid; e < (size_t)(kTcRows - mrows) * kGramSlab; e += kTcThreads)
+    sA[kGramDigits * pa + e] = __ushort_as_bfloat16((unsigned short)0);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tbase;
+  const uint32_t sbo = (uint32_t)(kGramSlab >> 3) * 128u;
+  uint32_t commits = 0, waited = 0;
+  bool fail = false;
+  // drain mapping: warp w -> TMEM lanes (rows i) 32 (w & 3) + lane, columns cg * wc/4 ..
+  const int ei = 32 * (warp & 3) + lane, cg = warp >> 2, cpt = wc / 4;
+  double acc0[kGramColsPerThread], acc1[kGramColsPerThread];  // B_Q and A_Q sums
+#pragma unroll
+  for (int q = 0; q < kGramColsPerThread; ++q) acc0[q] = acc1[q] = 0.0;
+  for (int sl = g; sl < nslab && !fail; sl += G) {
+    const int r0 = sl * kGramSlab;
+    // digit planes: unit = (column, 8 consecutive slab rows); consecutive
+    // threads take consecutive columns (coalesced loads, 128-byte stores). A
+    // thread holds the values of its (at most kGramUnits) units in registers:
+    // their largest exponents set the per-slab column scales (shared-memory
+    // maxima), and the digits are cut from the same registers after a barrier.
+    for (int i = tid; i < kTcMaxK + kGramChunk; i += kTcThreads) {
+      if (i < kTcMaxK)
+        eA[i] = kNoExp;
+      else
+        eB[i - kTcMaxK] = kNoExp;
+    }
+    __syncthreads();  // (the previous slab's MMAs completed before its drain)
+    const int unitsA = mrows * (kGramSlab / 8), unitsB = wc * (kGramSlab / 8);
+    double xs[kGramUnits][8];
+#pragma unroll
+    for (int t = 0; t < kGramUnits; ++t) {
+      const int u = tid + t * kTcThreads;
+      const bool isA = u < unitsA;
+      const int v = isA ? u : u - unitsA;
+      const int rows = isA ? mrows : wc;
+      const int col = v % rows, rg = v / rows;
+      const int j = isA ? col : j0 + col;
+      const double *M = isA ? Q : AQ;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = r0 + 8 * rg + q;
+        xs[t][q] = (u < unitsA + unitsB && r < n && j < m) ? M[(size_t)r * m + j] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kGramUnits; ++t) {
+      const int u = tid + t * kTcThreads;
+      if (u >= unitsA + unitsB) continue;
+      const bool isA = u < unitsA;
+      const int v = isA ? u : u - unitsA;
+      const int col = v % (isA ? mrows : wc);
+      int ex = kNoExp;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ex = max(ex, scale_exp(xs[t][q]));
+      if (ex != kNoExp) atomicMax(isA ? &eA[col] : &eB[col], ex);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kGramUnits; ++t) {
+      const int u = tid + t * kTcThreads;
+      if (u >= unitsA + unitsB) continue;
+      const bool isA = u < unitsA;
+      const int v = isA ? u : u - unitsA;
+      const int rows = isA ? mrows : wc;
+      const int col = v % rows, rg = v / rows;
+      int e = isA ? (col < m ? eA[col] : kNoExp) : eB[col];
+      if (e == kNoExp) e = 0;
+      gram_digits8(xs[t], e, isA ? sA : sB, isA ? pa : pb, core_off(col, 8 * rg, kGramSlab));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    for (int o = 0; o < 2 && !fail; ++o) {
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t abase = smem_u32(sA), bbase = smem_u32(sB);
+        if (o == 0) {  // B_Q: B operand = rows j0 .. j0 + wc of Q's own planes
+          const uint32_t idesc = idesc_bf16(wc);
+          for (int a = 1; a <= kGramDigits; ++a)
+            for (int b = 1; a + b <= kGramLevels + 1; ++b) {
+              const uint32_t dcol = tmem + (uint32_t)((a + b - 2) * wc);
+              const uint32_t ap = abase + (uint32_t)((a - 1) * pa * 2);
+              const uint32_t bp = abase + (uint32_t)((b - 1) * pa * 2) + (uint32_t)(j0 / 8) * sbo;
+              for (int kk = 0; kk < kGramSlab / 16; ++kk)
+                mma_bf16(dcol, smem_desc(ap + kk * 256u, sbo), smem_desc(bp + kk * 256u, sbo),
+                         idesc, (a > 1 || kk > 0) ? 1u : 0u);
+            }
+        } else {  // A_Q: planes b of the chunk's A Q columns, stacked along N
+          const int per = 256 / wc;  // planes per MMA (N <= 256)
+          for (int a = 1; a <= kGramDigits; ++a)
+            for (int b0 = 1; a + b0 <= kGramLevels + 1; b0 += per) {
+              const int nb = min(per, kGramLevels + 1 - a - b0 + 1);
+              const uint32_t idesc = idesc_bf16(wc * nb);
+              const uint32_t dcol = tmem + (uint32_t)((a + b0 - 2) * wc);
+              const uint32_t ap = abase + (uint32_t)((a - 1) * pa * 2);
+              const uint32_t bp = bbase + (uint32_t)((b0 - 1) * pb * 2);
+              for (int kk = 0; kk < kGramSlab / 16; ++kk)
+                mma_bf16(dcol, smem_desc(ap + kk * 256u, sbo), smem_desc(bp + kk * 256u, sbo),
+                         idesc, (a > 1 || kk > 0) ? 1u : 0u);
+            }
+        }
+        mma_commit(&mbar);
+      }
+      ++commits;
+      bool gave_up = false;
+      if (waited < commits) {
+        gave_up = !mbar_wait(&mbar, waited & 1u);
+        waited = commits;
+      }
+      fail = __syncthreads_or(gave_up) != 0;
+      if (fail) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // drain: T = S1 2^28 + S2, S1 = levels 2..5, S2 = levels 6..9; warps whose
+      // 32 TMEM lanes hold no row i < m skip it (a warp-uniform condition)
+      long long S1[kGramColsPerThread], S2[kGramColsPerThread];
+#pragma unroll
+      for (int q = 0; q < kGramColsPerThread; ++q) S1[q] = S2[q] = 0;
+      const int dlevels = 32 * (warp & 3) < m ? kGramLevels + 1 : 1;
+      for (int d = 2; d <= dlevels; ++d) {
+        uint32_t uu[kGramColsPerThread];
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                            (uint32_t)((d - 2) * wc + cg * cpt);
+        if (cpt == 12) {
+          uint32_t v8[8], v4[4];
+          tmem_ld8(ta, v8);
+          tmem_ld4(ta + 8, v4);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 8; ++q) uu[q] = v8[q];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) uu[8 + q] = v4[q];
+        } else if (cpt == 8) {
+          uint32_t v8[8];
+          tmem_ld8(ta, v8);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 8; ++q) uu[q] = v8[q];
+#pragma unroll
+          for (int q = 8; q < kGramColsPerThread; ++q) uu[q] = 0u;
+        } else {  // cpt == 4
+          uint32_t v4[4];
+          tmem_ld4(ta, v4);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 4; ++q) uu[q] = v4[q];
+#pragma unroll
+          for (int q = 4; q < kGramColsPerThread; ++q) uu[q] = 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kGramColsPerThread; ++q) {
+          const long long v = (long long)__float2int_rn(__uint_as_float(uu[q]));
+          if (d <= 5)
+            S1[q] += v << (7 * (5 - d));
+          else
+            S2[q] += v << (7 * (9 - d));
+        }
+      }
+      if (ei < m) {
+#pragma unroll
+        for (int q = 0; q < kGramColsPerThread; ++q) {
+          const int jj = cg * cpt + q, j = j0 + jj;
+          if (q >= cpt || j >= m) continue;
+          const unsigned long long s1lo = (unsigned long long)S1[q] << 28;
+          unsigned long long lo = s1lo + (unsigned long long)S2[q];
+          const unsigned long long carry = lo < s1lo ? 1ull : 0ull;
+          unsigned long long hi = (unsigned long long)(S1[q] >> 36) +
+                                  (unsigned long long)(S2[q] >> 63) + carry;
+          const bool neg = (long long)hi < 0;
+          if (neg) {
+            lo = ~lo + 1ull;
+            hi = ~hi + (lo == 0 ? 1ull : 0ull);
+          }
+          const int ej = o == 0 ? eA[j] : eB[jj];
+          const int e2 = (eA[ei] == kNoExp ? 0 : eA[ei]) + (ej == kNoExp ? 0 : ej) - 63;
+          const double v = int128_to_double(hi, lo, neg, e2);
+          if (o == 0)
+            acc0[q] += v;
+          else
+            acc1[q] += v;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();  // TMEM free for the next pass
+    }
+  }
+  // this CTA's partial sums: part[cta][o][i][jj] (mrows x kGramChunk per output)
+  if (!fail && ei < m) {
+    double *P = part + (size_t)blockIdx.x * 2 * mrows * kGramChunk;
+#pragma unroll
+    for (int q = 0; q < kGramColsPerThread; ++q)
+      if (q < cpt) {
+        P[(size_t)ei * kGramChunk + cg * cpt + q] = acc0[q];
+        P[((size_t)mrows + ei) * kGramChunk + cg * cpt + q] = acc1[q];
+      }
+  }
+  if (fail) {
+    if (tid == 0) atomicExch(&status->tc_timeout, 1);
+    if (waited < commits) mbar_wait(&mbar, waited & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// B_Q, A_Q from the per-CTA partials: entry (i, j) of output o is the sum over
+// the G CTAs of chunk j / 48 in CTA order; each output is symmetrised as the
+// mean of (i, j) and (j, i).
+__global__ void k_tc_gram_reduce(int m, int mrows, int G, const double *__restrict__ part,
+                                 double *__restrict__ Aq, double *__restrict__ Bq) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  const int i = idx / m, j = idx % m;
+  if (i > j) return;
+  double v[2][2];
+  for (int o = 0; o < 2; ++o)
+    for (int t = 0; t < 2; ++t) {
+      const int r = t ? j : i, cc = t ? i : j;  // entry (r, cc)
+      const int ch = cc / kGramChunk, jj = cc % kGramChunk;
+      double sum = 0.0;
+      for (int g = 0; g < G; ++g)
+        sum += part[(((size_t)(ch * G + g) * 2 + o) * mrows + r) * kGramChunk + jj];
+      v[o][t] = sum;
+    }
+  const double b = 0.5 * (v[0][0] + v[0][1]), a = 0.5 * (v[1][0] + v[1][1]);
+  Bq[(size_t)i * m + j] = b;
+  Bq[(size_t)j * m + i] = b;
+  Aq[(size_t)i * m + j] = a;
+  Aq[(size_t)j * m + i] = a;
+}
+
+size_t tc_gram_smem_bytes(int mrows) {
+  const size_t need = ((size_t)kGramDigits * mrows * kGramSlab +
+                       (size_t)(kTcRows - mrows) * kGramSlab +
+                       (size_t)kGramDigits * kGramChunk * kGramSlab) * 2;
+  // over half of the SM's shared memory: one CTA (holding all 512 TMEM columns) per SM
+  const size_t floor_bytes = 120 * 1024;
+  return need > floor_bytes ? need : floor_bytes;
+}
+
 size_t tc_smem_bytes(int kp) {
   const size_t need = (size_t)kTcDigits * kTcRows * kp * 2 + (size_t)kTcDigits * kTcChunk * kp * 2;
   // at least 16 x 32 x 9 doubles for the partials, and over half of the SM's
@@ -547,6 +888,35 @@ size_t tc_scratch_bytes(int64_t n, int m0) {
 }
 
 }  // namespace
+
+// CTAs per column chunk of the tensor-core Gram (0: not supported)
+int gram_tc_group(const RRArgs &a) {
+  if (a.m0 > kTcMaxK || a.rowptrB != nullptr || a.n < (int64_t)kGramSlab * 4) return 0;
+  const int mrows = (a.m0 + 7) / 8 * 8;
+  const int kp = (a.m0 + 15) / 16 * 16;
+  const int nch = (kp + kGramChunk - 1) / kGramChunk;
+  const size_t gram_bytes = (size_t)a.Pg * 2 * ((a.m0 + 3) / 4 * 4) * ((a.m0 + 3) / 4 * 4) * 8;
+  const size_t per_cta = (size_t)2 * mrows * kGramChunk * sizeof(double);
+  const int nslab = (int)((a.n + kGramSlab - 1) / kGramSlab);
+  int G = (a.num_sms > 0 ? a.num_sms : 1) / nch;
+  G = std::min<int>(G, (int)(gram_bytes / (per_cta * nch)));
+  G = std::min(G, nslab);
+  return G >= 1 ? G : 0;
+}
+
+cudaError_t gram_tc(const RRArgs &a, cudaStream_t st) {
+  const int G = gram_tc_group(a);
+  if (G < 1) return cudaErrorInvalidValue;
+  const int m = a.m0;
+  const int mrows = (m + 7) / 8 * 8;
+  const int kp = (m + 15) / 16 * 16;
+  const int nch = (kp + kGramChunk - 1) / kGramChunk;
+  k_tc_gram<<<nch * G, kTcThreads, tc_gram_smem_bytes(mrows), st>>>((int)a.n, m, mrows, nch, G,
+                                                                     a.Q, a.AQ, a.gram_part,
+                                                                     a.status);
+  k_tc_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(m, mrows, G, a.gram_part, a.Aq, a.Bq);
+  return cudaGetLastError();
+}
 
 bool update_resid_tc_supported(const RRArgs &a) {
   const size_t gram_bytes = (size_t)a.Pg * 2 * ((a.m0 + 3) / 4 * 4) * ((a.m0 + 3) / 4 * 4) * 8;
@@ -574,8 +944,11 @@ cudaError_t update_resid_tc(const RRArgs &a, int blocks, cudaStream_t st) {
 }
 
 cudaError_t rr_tc_init() {
-  return cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes(kTcMaxK));
+  cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes(kTcMaxK));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_gram_smem_bytes(kTcMaxK));
 }
 
 }  // namespace ifeast
