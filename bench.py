@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--rate", type=float, default=8.0, help="serving arrivals per second")
     p.add_argument("--n-max", type=float, default=1e6, help="largest serving request size")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--two-pass-gb", type=float, default=80.0,
+                   help="serving: a request whose stored FP32 Lanczos basis would exceed this "
+                        "many GB runs in the two-pass mode")
     p.add_argument("--rate-sweep", default="",
                    help="serving: comma-separated multiples of the one-at-a-time service rate "
                         "(e.g. 0.5,0.8,1.2); each runs the stream with Poisson arrivals at that rate")
@@ -486,8 +489,8 @@ def run_serve(args):
     """Serving stream: Poisson arrivals of eigen-requests (2D/3D Laplacians with a
     potential, n log-uniform 1e3..n_max, m0 16..128), submitted at their arrival
     times to one server (memory budget 160 GB, 8 running at once). A request
-    whose stored Lanczos basis would exceed 8 GB runs in the two-pass mode
-    (three basis vectors). Reports converged eigenpairs/s over the makespan and
+    whose stored Lanczos basis would exceed --two-pass-gb (80 GB) runs in the
+    two-pass mode (three basis vectors). Reports converged eigenpairs/s over the makespan and
     p50/p99 request latency, and the same stream served one request at a time
     for comparison. A second, smaller stream (16 requests, n up to 5e4) is run
     three ways: served (mixed precision, 8 at once), one at a time in the same
@@ -503,8 +506,10 @@ def run_serve(args):
     build()
     reqs = inputs.serving_requests(args.requests, seed=1234, rate=args.rate, n_max=args.n_max)
     K = 300
-    # FP32 basis of K + 1 vectors over 8 GB: keep three vectors and rebuild in a second pass
-    two_pass = [(K + 1) * r.A.n * r.m0 * 4 > (8 << 30) for r in reqs]
+    # FP32 basis of K + 1 vectors over --two-pass-gb (default half the 160 GB budget, so
+    # that two such requests can be resident at once): keep three vectors and rebuild
+    # them in a second pass
+    two_pass = [(K + 1) * r.A.n * r.m0 * 4 > args.two_pass_gb * 2**30 for r in reqs]
     warm = inputs.serving_requests(3, seed=999, n_max=2e4)
 
     mixed = dict(inner="minres", inner_iters=K, alpha=3e-2, precision="fp32")
@@ -528,16 +533,27 @@ def run_serve(args):
         span = time.perf_counter() - t0
         srv.close()
         lat = np.array([o[4]["submit_to_done_ms"] for o in outs])
+        svc = np.array([o[4]["submit_to_done_ms"] - o[4]["submit_to_start_ms"] for o in outs])
         pairs = sum(int((o[3] <= 1e-10).sum()) for o in outs if o[0] == 0)
         failed = {}
         for r, o in zip(reqs, outs):
             if o[0] != 0:
                 failed[str(o[0])] = failed.get(str(o[0]), 0) + 1
+        serve.svc = svc  # start-to-done time of each request (its service time when alone)
         return pairs, span, lat, failed
 
     with ClockSampler(local) as clk:
         pairs, span, lat, failed = serve(8, True)
     pairs1, span1, lat1, failed1 = serve(1, False)
+    # share of the one-at-a-time service time by request size class
+    sizes = np.array([r.A.n for r in reqs])
+    svc1 = serve.svc
+    share = {name: float(svc1[(sizes >= lo) & (sizes < hi)].sum() / svc1.sum())
+             for name, lo, hi in [("n<1e4", 0, 1e4), ("1e4<=n<1e5", 1e4, 1e5),
+                                  ("n>=1e5", 1e5, np.inf)]}
+    count = {name: int(((sizes >= lo) & (sizes < hi)).sum())
+             for name, lo, hi in [("n<1e4", 0, 1e4), ("1e4<=n<1e5", 1e4, 1e5),
+                                  ("n>=1e5", 1e5, np.inf)]}
     # arrival-rate sweep: multiples f of the one-at-a-time service rate mu (requests/s);
     # the stream's exponential inter-arrival times are rescaled from rate args.rate to f mu
     sweep = []
@@ -573,12 +589,15 @@ def run_serve(args):
                            "max_active": 8, "budget_gb": 160, "inner": "minres",
                            "inner_precision": "fp32", "contour": "trap_half",
                            "two_pass_requests": int(sum(two_pass)),
+                           "two_pass_above_gb": args.two_pass_gb,
                            "n_max_seen": int(max(r.A.n for r in reqs))},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                "p99": float(np.percentile(lat, 99))},
                 "failed": failed, "pairs": pairs, "requests": len(reqs),
                 "one_at_a_time": {"value": pairs1 / span1, "makespan_s": span1,
-                                  "failed": failed1, "service_rate_per_s": mu},
+                                  "failed": failed1, "service_rate_per_s": mu,
+                                  "service_time_share_by_size": share,
+                                  "requests_by_size": count},
                 "rate_sweep": sweep,
                 "vs_plain_fp64": {"stream": "16 requests, n 1e3-5e4, m0 16-128, seed 1234",
                                   "plain_form": "per-node GMRES FP64, <= 32 steps, alpha 1e-2",
