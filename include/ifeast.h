@@ -172,6 +172,12 @@ typedef struct {
                            columns of workspace instead of nc * m0. The result
                            equals the all-nodes filter (same kernels, same
                            arithmetic per system). 0: all nodes at once.      */
+  int plain_loads;      /* IFEAST_INNER_GMRES with IFEAST_FP32: 1 reads the
+                           basis in the dot, Gram-Schmidt and finish kernels
+                           with plain loads; 0 (default) streams it through
+                           shared memory by TMA tile copies when the system
+                           count of a pass is even (same arithmetic, same
+                           results bit for bit).                              */
 } ifeast_opts;
 
 typedef struct {
@@ -187,7 +193,7 @@ typedef struct {
 
 /* Fills *o with the defaults: GMRES, k = 10, alpha = 0 (fixed k), max_outer =
  * 100, tol = 1e-10, FP64, verbose = 0, correction_rf = 1e-3, no time limit,
- * node_chunk = 0. */
+ * node_chunk = 0, plain_loads = 0. */
 void ifeast_default_opts(ifeast_opts *o);
 
 /* Contour nodes and weights (Eq. contour_int_quad with the rules above) on the

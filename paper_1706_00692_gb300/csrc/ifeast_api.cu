@@ -371,6 +371,7 @@ int validate_opts(const ifeast_opts *o) {
   if (o->nonsymmetric && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (o->minres_two_pass != 0 && o->minres_two_pass != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->node_chunk < 0) return IFEAST_ERR_INVALID_ARG;
+  if (o->plain_loads != 0 && o->plain_loads != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->node_chunk > 0 && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (o->minres_two_pass &&
       (o->inner_solver != IFEAST_INNER_MINRES || o->precision == IFEAST_FP64))
@@ -454,7 +455,8 @@ int ensure_device_init() {
   if (cudaGetDevice(&dev) != cudaSuccess) return IFEAST_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_init_mu);
   if (dev >= 0 && dev < 64 && !g_init_done[dev]) {
-    if (rr_init() != cudaSuccess || minres_init() != cudaSuccess) return IFEAST_ERR_CUDA;
+    if (rr_init() != cudaSuccess || minres_init() != cudaSuccess || gmres_init() != cudaSuccess)
+      return IFEAST_ERR_CUDA;
     g_init_done[dev] = true;
   }
   return IFEAST_OK;
@@ -473,6 +475,7 @@ int ensure_device_init() {
 GmresArgs gmres_args(ifeast_ctx *h, const double *X, double *Q, int correction = 0) {
   GmresArgs a{};
   a.fp32 = h->fp32 ? 1 : 0;
+  a.stream_tma = h->opts.plain_loads ? 0 : 1;
   a.val32 = h->val32;
   a.valB32 = h->valB32;
   a.b_same_pattern = h->b_same_pattern ? 1 : 0;
@@ -686,6 +689,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->correction_rf = 1e-3;
   o->time_limit_ms = 0.0;
   o->node_chunk = 0;
+  o->plain_loads = 0;
 }
 
 const char *ifeast_strerror(int code) {

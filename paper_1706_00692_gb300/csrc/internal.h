@@ -131,12 +131,14 @@ struct GmresArgs {
   // beta), y = (x_j + e) / (z_k - lambda_j), Q = cx X + Re sum_k w_k e_k / (z_k - lambda_j)
   int correction;
   int accumulate;           // 1: Q += this pass's sum (later node chunks)
+  int stream_tma;           // 1: FP32 basis kernels stream the basis by TMA (when C is even)
   const double *lam;        // [m0] Ritz values
   const double *xnorm;      // [m0] ||B x_j||
   const double *Xr;         // n x m0 the Ritz vectors x_j
   double *cx;               // [m0] Re sum_k w_k / (z_k - lambda_j)
 };
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st);
+cudaError_t gmres_init();  // once per device: opt-in shared-memory sizes
 cudaError_t spmm_shift_only(int n, const int32_t *rowptr, const int32_t *colidx,
                             const double *val, const double2 *V, double2 *W, int ncols,
                             int m0, const double2 *z, RowTiling tl, cudaStream_t st,

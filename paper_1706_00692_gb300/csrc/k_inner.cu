@@ -25,6 +25,11 @@
 // result does not depend on scheduling. With the FP32 basis the products, the
 // updates and each thread's dot sums are FP32; block partials, Hessenberg
 // columns, rotations and least-squares solutions stay FP64.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "internal.h"
 
 namespace ifeast {
@@ -287,6 +292,185 @@ k_orth_update_dot(int n, int C, const CT *__restrict__ V, size_t vstride, int s,
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 basis kernels streamed through shared memory by TMA (the dots, the
+// first Gram-Schmidt pass with its dots, and the finish). The arithmetic and
+// its order per (row, column) are those of k_dots, k_orth_update_dot and
+// k_orth_finish above; only the way the basis reaches the threads differs.
+// A block owns the rows [r0, r1) of one 32-column tile; the rows go in stages
+// of kTmaRows (one per warp), and for every stage one thread issues one 2D
+// tile copy (kTmaRows rows x 32 complex columns, 2 kB) per basis vector and one
+// for W, completing on the stage's mbarrier. Two stages are in flight, so the
+// loads in flight no longer occupy registers: up to 2 x 33 x 2 kB per block.
+// Every wait is bounded: a wait that runs out sets status->tc_timeout, the
+// block waits (bounded) for its own copies still in flight and returns, and
+// the host reports IFEAST_ERR_TIMEOUT.
+constexpr int kTmaRows = kWarps;            // rows per stage: one per warp
+constexpr int kTmaTileBytes = kTmaRows * 32 * 8;
+constexpr long kTmaSpin = 1L << 24;
+
+enum { kStreamDots = 0, kStreamUpdate = 1, kStreamFinish = 2 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity) {
+  for (long it = 0; it < kTmaSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Issue the copies of stage st (rows r0 + st * kTmaRows ..) into buffer buf:
+// vectors l0 .. l0 + nl - 1 of V, then W. Rows past n are filled with zeros.
+__device__ __forceinline__ void issue_stage(const CUtensorMap *mapV, const CUtensorMap *mapW,
+                                            float2 *buf, uint64_t *mbar, int tile, int row,
+                                            int l0, int nl) {
+  const uint32_t bytes = (uint32_t)(nl + 1) * kTmaTileBytes;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)),
+               "r"(bytes)
+               : "memory");
+  const int x = 64 * tile;  // in floats: 32 complex columns = 256 bytes
+  for (int l = 0; l < nl; ++l)
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(buf + (size_t)l * kTmaRows * 32)),
+        "l"(mapV), "r"(x), "r"(row), "r"(l0 + l), "r"(smem_addr(mbar))
+        : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(buf + (size_t)nl * kTmaRows * 32)),
+      "l"(mapW), "r"(x), "r"(row), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// MODE kStreamDots: partials of <V_l, W> for l = l0 .. l0 + 7 (<= s), like k_dots.
+// MODE kStreamUpdate: W -= sum_l H[l] V_l, partials of <V_l, W> and ||W||^2,
+// like k_orth_update_dot. MODE kStreamFinish: V_{s+1} = (W - sum_l H[l] V_l) *
+// inv_h, like k_orth_finish.
+template <int MODE, int LMAX>
+__global__ void __launch_bounds__(kThreads)
+k_gm_stream(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapW,
+            int n, int C, int s, const double2 *__restrict__ H, const double *__restrict__ inv_h,
+            const int *__restrict__ done, float2 *__restrict__ W, float2 *__restrict__ Vn,
+            double2 *__restrict__ part, int rows, int K2, DevStatus *__restrict__ status) {
+  constexpr int NACC = MODE == kStreamDots ? kDotChunk : LMAX + 1;
+  extern __shared__ __align__(128) unsigned char gm_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ float2 hs[LMAX][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = blockIdx.y;
+  const int c = tile * 32 + lane;
+  const int l0 = MODE == kStreamDots ? blockIdx.z * kDotChunk : 0;
+  const int nl = MODE == kStreamDots ? min(kDotChunk, s + 1 - l0) : s + 1;
+  const size_t stage_elems = (size_t)(nl + 1) * kTmaRows * 32;
+  float2 *sbuf = reinterpret_cast<float2 *>(gm_smem);
+  const bool active = c < C && done[c] == 0;
+  if (MODE != kStreamDots)
+    for (int l = warp; l <= s; l += kWarps)
+      hs[l][lane] = (c < C) ? make_float2((float)H[(size_t)l * C + c].x,
+                                          (float)H[(size_t)l * C + c].y)
+                            : make_float2(0.f, 0.f);
+  const int r0 = blockIdx.x * rows;
+  const int r1 = min(n, r0 + rows);
+  const int nst = r1 > r0 ? (r1 - r0 + kTmaRows - 1) / kTmaRows : 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int st = 0; st < 2 && st < nst; ++st)
+      issue_stage(&mapV, &mapW, sbuf + st * stage_elems, &mbar[st], tile, r0 + st * kTmaRows, l0,
+                  nl);
+  }
+  __syncthreads();
+  float2 acc[NACC];
+#pragma unroll
+  for (int l = 0; l < NACC; ++l) acc[l] = make_float2(0.f, 0.f);
+  float nrm = 0.f;
+  bool fail = false;
+  const float ih = (MODE == kStreamFinish && c < C) ? (float)inv_h[c] : 0.f;
+  float2 *Vnext = MODE == kStreamFinish ? Vn : nullptr;
+  int st = 0;
+  for (; st < nst; ++st) {
+    const int b = st & 1;
+    const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((st >> 1) & 1));
+    fail = __syncthreads_or(!ok) != 0;
+    if (fail) break;
+    const float2 *buf = sbuf + b * stage_elems;
+    const int r = r0 + st * kTmaRows + warp;
+    if (active && r < r1) {
+      const size_t rc = (size_t)r * C + c;
+      const float2 *vrow = buf + (size_t)warp * 32 + lane;  // vector l at vrow[l * kTmaRows * 32]
+      float2 w = buf[(size_t)nl * kTmaRows * 32 + warp * 32 + lane];
+      if (MODE == kStreamDots) {
+#pragma unroll
+        for (int l = 0; l < kDotChunk; ++l)
+          if (l < nl) cjfma(acc[l], vrow[(size_t)l * kTmaRows * 32], w);
+      } else {
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l)
+          if (l <= s) cfms(w, hs[l][lane], vrow[(size_t)l * kTmaRows * 32]);
+        if (MODE == kStreamUpdate) {
+#pragma unroll
+          for (int l = 0; l < LMAX; ++l)
+            if (l <= s) cjfma(acc[l], vrow[(size_t)l * kTmaRows * 32], w);
+          nrm = fmaf(w.x, w.x, fmaf(w.y, w.y, nrm));
+          W[rc] = w;
+        } else {
+          Vnext[rc] = make_float2(w.x * ih, w.y * ih);
+        }
+      }
+    }
+    __syncthreads();  // every thread is done with buffer b
+    if (threadIdx.x == 0 && st + 2 < nst) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_stage(&mapV, &mapW, sbuf + b * stage_elems, &mbar[b], tile,
+                  r0 + (st + 2) * kTmaRows, l0, nl);
+    }
+  }
+  if (fail) {
+    if (threadIdx.x == 0) {
+      atomicExch(&status->tc_timeout, 1);
+      // the copies of stages st and st + 1 may still be in flight
+      for (int q = st; q < st + 2 && q < nst; ++q)
+        mbar_wait_bounded(&mbar[q & 1], (uint32_t)((q >> 1) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+  if (MODE == kStreamFinish) return;
+  // fixed-order block sums (warp order) in FP64, one slot at a time
+  __shared__ double2 red[kWarps][32];
+  const int nslots = MODE == kStreamDots ? nl : s + 2;
+#pragma unroll
+  for (int l = 0; l < NACC + (MODE == kStreamUpdate ? 1 : 0); ++l) {
+    if (l < nslots) {  // uniform over the block
+      if (MODE == kStreamUpdate && l == s + 1)
+        red[warp][lane] = make_double2((double)nrm, 0.0);
+      else
+        red[warp][lane] = make_double2((double)acc[l < NACC ? l : 0].x,
+                                       (double)acc[l < NACC ? l : 0].y);
+      __syncthreads();
+      if (warp == 0) {
+        double2 t = red[0][lane];
+#pragma unroll
+        for (int q = 1; q < kWarps; ++q) t = cadd(t, red[q][lane]);
+        if (c < C) part[((size_t)blockIdx.x * K2 + l0 + l) * C + c] = t;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Per system c: Hessenberg column h_{l,s} = h1_l + h2_l, h_{s+1,s} from
 // Pythagoras, previous Givens rotations, new rotation, rotated right-hand side
 // and the stop test |g_{s+1}| <= tolc[c]. h_{s+1,s} <= brk * ||b|| is a
@@ -496,8 +680,55 @@ __global__ void k_quadrature(int n, int m0, int nc, int C, const CT *__restrict_
   Q[idx] = accumulate ? Q[idx] + t : t;  // later node chunks add their part
 }
 
+// Tensor maps of the FP32 basis (a 3D view: 2C floats x n rows x K+1 vectors)
+// and of W (2C floats x n rows), boxes of 64 floats x kTmaRows rows.
+struct TmaMaps {
+  CUtensorMap V, W;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// The streamed kernels need the FP32 basis, rows of 8 C bytes that are a
+// multiple of 16 (C even), 16-byte aligned buffers and the encoder.
+bool make_tma_maps(const GmresArgs &a, TmaMaps *m) {
+  if (!a.fp32 || (a.C & 1) || a.n < 1) return false;
+  if ((reinterpret_cast<uintptr_t>(a.V) | reinterpret_cast<uintptr_t>(a.W)) & 15) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+  if (!enc) return false;
+  const cuuint64_t row_bytes = (cuuint64_t)a.C * 8;
+  const cuuint64_t dimV[3] = {(cuuint64_t)a.C * 2, (cuuint64_t)a.n, (cuuint64_t)a.K + 1};
+  const cuuint64_t strV[2] = {row_bytes, row_bytes * (cuuint64_t)a.n};
+  const cuuint32_t boxV[3] = {64, (cuuint32_t)kTmaRows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  if (enc(&m->V, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.V, dimV, strV, boxV, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t dimW[2] = {(cuuint64_t)a.C * 2, (cuuint64_t)a.n};
+  const cuuint64_t strW[1] = {row_bytes};
+  const cuuint32_t boxW[2] = {64, (cuuint32_t)kTmaRows};
+  return enc(&m->W, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.W, dimW, strW, boxW, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 template <int LMAX, typename CT>
-cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
+cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st, const TmaMaps *tma) {
   using R = typename Cx<CT>::R;
   const dim3 grid(a.tl.P, a.tl.tiles);
   const size_t vstride = (size_t)a.n * a.C;
@@ -525,15 +756,38 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
     IFEAST_SPMM_LAUNCH(1);
 #undef IFEAST_SPMM_LAUNCH
   const dim3 gdots(a.tl.P, a.tl.tiles, (s + 1 + kDotChunk - 1) / kDotChunk);
-  k_dots<CT><<<gdots, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.done, W, a.part,
-                                                a.tl.rows, K2);
+  if constexpr (sizeof(R) == 4) {
+    if (tma) {
+      const size_t smem = 2 * (size_t)(kDotChunk + 1) * kTmaTileBytes;
+      k_gm_stream<kStreamDots, 8><<<gdots, kThreads, smem, st>>>(
+          tma->V, tma->W, a.n, a.C, s, nullptr, nullptr, a.done, nullptr, nullptr, a.part,
+          a.tl.rows, K2, a.status);
+    } else {
+      k_dots<CT><<<gdots, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.done, W, a.part,
+                                             a.tl.rows, K2);
+    }
+  } else {
+    k_dots<CT><<<gdots, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.done, W, a.part,
+                                           a.tl.rows, K2);
+  }
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 1, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H1);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_ORTH);
-  k_orth_update_dot<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.H1, a.done,
-                                                         W, a.part, a.tl.rows, K2);
+  bool streamed = false;
+  if constexpr (sizeof(R) == 4) {
+    if (tma) {
+      const size_t smem = 2 * (size_t)(s + 2) * kTmaTileBytes;
+      k_gm_stream<kStreamUpdate, LMAX><<<grid, kThreads, smem, st>>>(
+          tma->V, tma->W, a.n, a.C, s, a.H1, nullptr, a.done, W, nullptr, a.part, a.tl.rows, K2,
+          a.status);
+      streamed = true;
+    }
+  }
+  if (!streamed)
+    k_orth_update_dot<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.H1,
+                                                           a.done, W, a.part, a.tl.rows, K2);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_REDUCE);
   k_reduce_partials<<<dim3(s + 2, a.tl.tiles), kThreads, 0, st>>>(a.tl.P, a.C, K2, a.part, a.H2);
@@ -546,15 +800,26 @@ cudaError_t launch_step(const GmresArgs &a, int s, cudaStream_t st) {
   IFEAST_PROF_END(a.prof);
   if (s + 1 < a.K) {  // the last step's basis vector is never used
     IFEAST_PROF_BEGIN(a.prof, K_GM_FINISH);
-    k_orth_finish<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.H2, a.inv_h,
-                                                       a.done, W, a.tl.rows);
+    bool fstreamed = false;
+    if constexpr (sizeof(R) == 4) {
+      if (tma) {
+        const size_t smem = 2 * (size_t)(s + 2) * kTmaTileBytes;
+        k_gm_stream<kStreamFinish, LMAX><<<grid, kThreads, smem, st>>>(
+            tma->V, tma->W, a.n, a.C, s, a.H2, a.inv_h, a.done, nullptr,
+            V + (size_t)(s + 1) * vstride, nullptr, a.tl.rows, K2, a.status);
+        fstreamed = true;
+      }
+    }
+    if (!fstreamed)
+      k_orth_finish<LMAX, CT><<<grid, kThreads, 0, st>>>(a.n, a.C, V, vstride, s, a.H2,
+                                                         a.inv_h, a.done, W, a.tl.rows);
     IFEAST_PROF_END(a.prof);
   }
   return cudaGetLastError();
 }
 
 template <typename CT>
-cudaError_t run_gmres(const GmresArgs &a, cudaStream_t st) {
+cudaError_t run_gmres(const GmresArgs &a, cudaStream_t st, const TmaMaps *tma) {
   const size_t total = (size_t)a.n * a.C;
   CT *V = static_cast<CT *>(a.V);
   IFEAST_PROF_BEGIN(a.prof, K_PREP);
@@ -565,11 +830,11 @@ cudaError_t run_gmres(const GmresArgs &a, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   for (int s = 0; s < a.K && e == cudaSuccess; ++s) {
     if (s + 1 <= 8)
-      e = launch_step<8, CT>(a, s, st);
+      e = launch_step<8, CT>(a, s, st, tma);
     else if (s + 1 <= 16)
-      e = launch_step<16, CT>(a, s, st);
+      e = launch_step<16, CT>(a, s, st, tma);
     else
-      e = launch_step<32, CT>(a, s, st);
+      e = launch_step<32, CT>(a, s, st, tma);
   }
   if (e != cudaSuccess) return e;
   IFEAST_PROF_BEGIN(a.prof, K_GM_SOLVE);
@@ -587,6 +852,32 @@ cudaError_t run_gmres(const GmresArgs &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t gmres_init() {
+  const int most = 2 * (kMaxInner + 1) * kTmaTileBytes;  // s + 2 <= kMaxInner + 1 tiles per stage
+  cudaError_t e = cudaFuncSetAttribute(k_gm_stream<kStreamDots, 8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       2 * (kDotChunk + 1) * kTmaTileBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gm_stream<kStreamUpdate, 8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gm_stream<kStreamUpdate, 16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gm_stream<kStreamUpdate, 32>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gm_stream<kStreamFinish, 8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gm_stream<kStreamFinish, 16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gm_stream<kStreamFinish, 32>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  return e;
+}
 
 RowTiling make_tiling(int64_t n, int ncols, int num_sms) {
   RowTiling t;
@@ -610,6 +901,9 @@ cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
   // passes over chunks of ncc nodes: the same kernels on the chunk's nodes and
   // weights, each pass's step counts in its slice, Q summed over the passes
   // (the first pass writes it; cx of the residual form is summed likewise)
+  // the basis and W buffers are the same for every pass: one pair of maps
+  TmaMaps maps;
+  const bool use_tma = a.stream_tma && make_tma_maps(a, &maps);
   cudaError_t e = cudaSuccess;
   for (int k0 = 0; k0 < a.nc && e == cudaSuccess; k0 += a.ncc) {
     GmresArgs b = a;
@@ -618,7 +912,8 @@ cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
     b.w = a.w + k0;
     b.steps = a.steps + (size_t)k0 * a.m0;
     b.accumulate = k0 > 0 ? 1 : 0;
-    e = a.fp32 ? run_gmres<float2>(b, st) : run_gmres<double2>(b, st);
+    e = a.fp32 ? run_gmres<float2>(b, st, use_tma ? &maps : nullptr)
+               : run_gmres<double2>(b, st, nullptr);
   }
   return e;
 }

@@ -323,3 +323,24 @@ def test_node_chunk_option(lib):
                                       ct.byref(_opts(lib, inner_solver=1, inner_max_iters=50,
                                                      precision=1, node_chunk=2)),
                                       ct.byref(part)) == _lib.IFEAST_ERR_UNSUPPORTED
+
+
+def test_plain_loads_option(lib):
+    """plain_loads: 0 (default, TMA-streamed FP32 GMRES basis) or 1; anything
+    else is rejected; it does not change the workspace."""
+    o = _lib.Opts()
+    lib.ifeast_default_opts(ct.byref(o))
+    assert o.plain_loads == 0
+    c = _lib.Contour(0, 8, 0.0, 1.0)
+    a, b = ct.c_size_t(), ct.c_size_t()
+    assert lib.ifeast_workspace_bytes(5000, 30000, 12, ct.byref(c),
+                                      ct.byref(_opts(lib, precision=1, inner_max_iters=20)),
+                                      ct.byref(a)) == 0
+    assert lib.ifeast_workspace_bytes(5000, 30000, 12, ct.byref(c),
+                                      ct.byref(_opts(lib, precision=1, inner_max_iters=20,
+                                                     plain_loads=1)),
+                                      ct.byref(b)) == 0
+    assert a.value == b.value
+    assert lib.ifeast_workspace_bytes(5000, 30000, 12, ct.byref(c),
+                                      ct.byref(_opts(lib, plain_loads=2)),
+                                      ct.byref(b)) == _lib.IFEAST_ERR_INVALID_ARG

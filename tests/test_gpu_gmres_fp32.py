@@ -145,3 +145,48 @@ def test_fp32_plain_form_floors_above_fp64_accuracy(torch):
     _, _, _, _, _, _, rc, lam, X, res, it = _fem_solve(torch, (30, 25), 6, 12, 32, 1e-2, 0.0)
     assert rc != 0
     assert res.size == 0 or res.max() > 1e-10
+
+
+@pytest.mark.parametrize("name,m0,nc", [("fem", 9, 8), ("standard", 8, 5), ("own_pattern", 14, 6)])
+@pytest.mark.parametrize("k,alpha", [(5, 0.0), (20, 0.0), (32, 1e-2)])
+def test_tma_streamed_basis_equals_plain_loads(torch, name, m0, nc, k, alpha):
+    """The FP32 dot, Gram-Schmidt and finish kernels that stream the basis
+    through shared memory by TMA compute the same sums in the same order as
+    the plain-load kernels: Q and the step counts agree bit for bit (C = nc m0
+    even; 72, 40 and 84 columns span two or three 32-column tiles with a ragged
+    last tile; n = 340 or 1001 rows end in a partial stage of 8 rows)."""
+    from paper_1706_00692_gb300 import Solver
+    A, B, emin, emax, _, _ = _case(name)
+    X = inputs.initial_subspace(A.n, m0, 17)
+    out = []
+    for plain in (False, True):
+        S = Solver(A, emin, emax, m0, B=B, nc=nc, inner_iters=k, alpha=alpha, precision="fp32",
+                   plain_loads=plain)
+        Q, steps = S.apply_filter(torch.as_tensor(X, device="cuda"), RF=1.0)
+        out.append((Q.cpu().numpy(), steps.cpu().numpy()))
+        S.close()
+    assert (nc * m0) % 2 == 0
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_tma_streamed_solve_equals_plain_loads(torch):
+    """A full FP32 generalized solve (residual form from ||R_F|| <= 1e-3) gives
+    the same eigenpairs bit for bit with the streamed and the plain kernels."""
+    from paper_1706_00692_gb300 import Solver
+    K, M = inputs.fem_q1((30, 25))
+    ev = inputs.fem_q1_eigs((30, 25))
+    emin, emax = 0.0, 0.5 * (ev[5] + ev[6])
+    X0 = inputs.initial_subspace(K.n, 12, 0)
+    res = []
+    for plain in (False, True):
+        S = Solver(K, emin, emax, 12, B=M, nc=8, inner_iters=32, alpha=1e-2, max_outer=40,
+                   precision="fp32", plain_loads=plain)
+        rc = S.solve(X0)
+        lam, X, r = S.eigenpairs()
+        res.append((rc, lam, X, r, S.stats()["outer_iters"]))
+        S.close()
+    assert res[0][0] == 0 and res[1][0] == 0
+    assert res[0][4] == res[1][4]
+    for a, b in zip(res[0][1:4], res[1][1:4]):
+        assert np.array_equal(a, b)
