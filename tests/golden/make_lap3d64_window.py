@@ -7,11 +7,11 @@ shifted matrix in nested-dissection order, then shift-invert Lanczos):
 
     python tests/golden/make_lap3d64_window.py
 
-Window rule: the survey's recipe places the ~50-eigenvalue window at
+Window rule: a first window of ~50 eigenvalues is
 [lam_L(1001) + 0.5, lam_L(1051) + 0.5] from the pure Laplacian's closed-form
 spectrum shifted by the potential's mean; each endpoint is moved to the
 midpoint of the widest spectral gap of A whose midpoint lies within 1e-3 of
-the recipe's endpoint, so that Ritz values of the eigenvectors just outside
+that first endpoint, so that Ritz values of the eigenvectors just outside
 stay clear of the endpoints.
 """
 import os
@@ -58,7 +58,7 @@ def main():
         f.write("# oracle's shift-invert Lanczos (tests/golden/make_lap3d64_window.py). Column 1:\n")
         f.write("# eigenvalue, column 2: residual ||A x - lam x|| (an exact eigenvalue lies within it),\n")
         f.write("# column 3: 1 if inside the window. The window endpoints are the midpoints of the\n")
-        f.write("# widest gaps within 1e-3 of the recipe's [lam_L(1001) + 0.5, lam_L(1051) + 0.5].\n")
+        f.write("# widest gaps within 1e-3 of the first window [lam_L(1001) + 0.5, lam_L(1051) + 0.5].\n")
         f.write(f"# window {emin:.17e} {emax:.17e}\n")
         f.write(f"# inside {int(inside.sum())}\n")
         for v, r, i in zip(lam, res, inside):
