@@ -252,3 +252,23 @@ def test_rayleigh_ritz_update_fp64_accurate(torch, m0, scaled):
     assert (np.abs(res - r) <= 64 * np.finfo(float).eps * M / nAX + 1e-14).all()
     lr, _ = orc.rayleigh_ritz(Q, As @ Q)
     assert np.abs(lam - lr).max() <= 1e-9 * np.abs(lr).max()
+
+
+@pytest.mark.parametrize("m0", [1, 5, 17, 31, 32, 47, 63, 64, 79, 80])
+def test_rayleigh_ritz_tensor_core_shapes(torch, m0):
+    """Every chunk shape of the tensor-core Gram (48- and 32-column chunks,
+    8-row groups of the M = 128 operand) and update (32- and 16-column chunks)
+    on n = 2,011 rows (a partial last 96-row slab and 128-row tile): eigenvalues
+    as the oracle's to 1e-12 relative, X^T X = I to 1e-10, and the residuals as
+    a CPU FP64 recomputation from the returned X and lambda."""
+    A = inputs.add_diagonal(inputs.laplacian((2011,)), inputs.random_potential(2011, 8))
+    Q = inputs.initial_subspace(A.n, m0, 31)
+    S = _solver(A, 0.0, 2.0, m0)
+    X, lam, res = S.rayleigh_ritz(torch.as_tensor(Q, device="cuda"))
+    X, lam, res = X.cpu().numpy(), lam.cpu().numpy(), res.cpu().numpy()
+    S.close()
+    As = A.to_scipy()
+    lr, XQ = orc.rayleigh_ritz(Q, As @ Q)
+    assert np.abs(lam - lr).max() <= 1e-12 * np.abs(lr).max()
+    assert np.abs(X.T @ X - np.eye(m0)).max() <= 1e-10
+    assert np.abs(res - orc.eigen_residuals(As @ X, X, lam)).max() <= 1e-10
