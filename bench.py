@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--rate", type=float, default=8.0, help="serving arrivals per second")
     p.add_argument("--n-max", type=float, default=1e6, help="largest serving request size")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64-form", action="store_true",
+                   help="lap3d_64: skip the one timed solve of the same workload with FP64 "
+                        "inner arithmetic and storage (about 13 s)")
     p.add_argument("--two-pass-gb", type=float, default=80.0,
                    help="serving: a request whose stored FP32 Lanczos basis would exceed this "
                         "many GB runs in the two-pass mode")
@@ -321,6 +324,46 @@ def error_vs_reference(wl, lam, res):
     return out
 
 
+def fp64_form_solve(args, dev):
+    """One solve of the 64^3 workload with FP64 Krylov vectors and arithmetic
+    (stored basis ~250 GB), timed with CUDA events on its stream after an L2
+    flush; the eigenvalues are compared with the oracle's like the main line's."""
+    import gc
+    import torch
+    from paper_1706_00692_gb300 import Solver
+    gc.collect()
+    torch.cuda.empty_cache()  # the FP32 solvers' workspaces go back to the device
+    wl = make_workload("lap3d_64_fp64")
+    X0 = torch.as_tensor(wl.X0(), device=dev)
+    S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
+               inner_iters=wl.inner_iters, alpha=wl.alpha, precision=wl.precision,
+               two_pass=wl.two_pass, B=wl.B, node_chunk=wl.node_chunk, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    flush.fill_(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = S.solve(X0)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    if rc != 0:
+        S.close()
+        return {"status": int(rc)}
+    st = S.stats()
+    lam, _, res = S.eigenpairs()
+    S.close()
+    del flush
+    torch.cuda.empty_cache()
+    pairs = int((res <= 1e-10).sum())
+    return {"workload": wl.name, "value": pairs / (ms / 1e3), "unit": "eigenpairs/s",
+            "ms_per_solve": ms, "pairs": pairs, "outer_iters": st["outer_iters"],
+            "krylov_steps_total": st["total_matvecs"], "dtype": "f64",
+            "timing": "one solve after the timed FP32 steps, CUDA events, L2 flushed before it",
+            "error_vs_reference": error_vs_reference(wl, lam, res)}
+
+
 def inputs_subspace(n, m0, seed):
     from paper_1706_00692_gb300 import inputs
     return inputs.initial_subspace(n, m0, seed)
@@ -442,6 +485,12 @@ def run_ours(args):
     _, _, e2e_value = job_throughput(e2e_pairs * len(e2e_times), float(sum(e2e_times)), device=dev)
     d2h = l2.nbytes + x2.nbytes + r2.nbytes
 
+    # the same workload with FP64 Krylov arithmetic and storage (the plain-precision
+    # form of the same algorithm): one solve, timed on the device like the steps above
+    fp64_form = None
+    if args.workload == "lap3d_64" and not args.no_fp64_form and world == 1:
+        fp64_form = fp64_form_solve(args, dev)
+
     # roofline of the dominant kernel class, from the live event timings
     peak, peak_kind = measured_peaks()
     roofline = lanczos_roofline(kstat, wl, peak, peak_kind)
@@ -475,6 +524,8 @@ def run_ours(args):
                                  f"{PROFILE_EVERY}",
                 "error_vs_reference": accuracy,
                 "clocks": clk.summary()}
+        if fp64_form is not None:
+            line["fp64_form"] = fp64_form
         if not args.no_cpu_baseline and world == 1:
             v, sample = oracle_sample(wl)
             line["cpu_baseline"] = {"value": v, "unit": "eigenpairs/s", "cores": cpu_threads(),

@@ -21,8 +21,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libifeast.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["k_inner.cu", "k_minres.cu", "k_rr.cu", "k_rr_tc.cu", "k_noalloc.cu", "ifeast_api.cu",
-           "serve.cu"]
+SOURCES = ["k_inner.cu", "k_minres.cu", "k_rr.cu", "k_rr_tc.cu", "k_eig_cluster.cu", "k_noalloc.cu",
+           "ifeast_api.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -274,6 +274,12 @@ cudaError_t rr_init();  // once per device: opt-in shared-memory sizes
 bool update_resid_tc_supported(const RRArgs &a);
 cudaError_t update_resid_tc(const RRArgs &a, int blocks, cudaStream_t st);
 cudaError_t rr_tc_init();
+// FP64 Jacobi sweeps of the reduced eigenproblem on a thread-block cluster
+// (k_eig_cluster.cu): C (m x m, row-major) in place -> its eigenvectors V,
+// unsorted eigenvalues in evals
+bool eig_cluster_supported(int m);
+cudaError_t eig_cluster_init();
+cudaError_t eig_sweeps_launch(int m, double *C, double *evals, cudaStream_t st);
 // Tensor-core Gram matrices A_Q = Q^T A Q, B_Q = Q^T Q (B = I, m0 <= 80):
 // gram_tc_group > 0 when supported (CTAs per 48-column chunk); gram_tc writes
 // Aq and Bq (symmetric) through the Gram partials buffer.

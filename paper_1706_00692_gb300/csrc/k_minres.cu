@@ -475,10 +475,11 @@ constexpr int kGivensBatch = 16;
 // One block of kCoefThreads per 32-column tile, lane = column j: warp w sums
 // the partial rows b = w (mod NW) with compensated (Kahan) FP32 sums, all of
 // its rows' loads in flight first; warp 0 adds the warp sums and their
-// compensations in warp order, again compensated, converts once to FP64 and
-// forms alpha_s = <v,w>/<v,v>, beta_{s+1}^2 = <w,w> - alpha_s <v,w> (0 below the
-// breakdown threshold, which finishes the column), plus the FP32 copies
-// {alpha_s, beta_{s+1}, 1/beta_{s+1}} the next step kernel loads. Only columns
+// compensations in warp order, again compensated, and forms in FP32
+// alpha_s = <v,w>/<v,v>, beta_{s+1}^2 = <w,w> - alpha_s <v,w> (0 below the
+// breakdown threshold, which finishes the column); alpha and beta are stored
+// widened to FP64 for the Givens batches, and {alpha_s, beta_{s+1},
+// 1/beta_{s+1}} as the float4 the next step kernel loads. Only columns
 // still running (coldone[j] == 0) get coefficients. active_reset (Givens batch
 // steps): cleared so that the batch that follows can raise it.
 constexpr int kCoefThreads = 512;
@@ -522,7 +523,7 @@ k_lanczos_coef_f(int P, int m0, int s, const float *__restrict__ part, double *_
   }
   __syncthreads();
   if (warp != 0 || j >= m0 || coldone[j]) return;
-  double tot[3];
+  float tot[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     float S = 0.f, Cc = 0.f;
@@ -534,17 +535,19 @@ k_lanczos_coef_f(int P, int m0, int s, const float *__restrict__ part, double *_
       Cc = (t - S) - y;
       S = t;
     }
-    tot[q] = (double)S - (double)Cc;
+    tot[q] = S - Cc;
   }
-  const double vv = tot[0], vw = tot[1], ww = tot[2];
-  const double a = vv > 0.0 ? vw / vv : 0.0;
-  const double b2 = ww - a * vw;
-  const double b1 = b2 > brk2 * ww ? sqrt(b2) : 0.0;  // 0: invariant subspace reached
+  // FP32 arithmetic: the three sums carry the FP32 rounding of the stored
+  // vectors already, and this chain gates the next step (FP64 division and
+  // square root take ~1 us on this GPU's FP64 pipe)
+  const float vv = tot[0], vw = tot[1], ww = tot[2];
+  const float a = vv > 0.f ? vw / vv : 0.f;
+  const float b2 = fmaf(-a, vw, ww);
+  const float b1 = b2 > (float)brk2 * ww ? sqrtf(b2) : 0.f;  // 0: invariant subspace reached
   alpha[(size_t)s * m0 + j] = a;
   beta[(size_t)(s + 1) * m0 + j] = b1;
-  cf[(size_t)(s + 1) * m0 + j] =
-      make_float4((float)a, (float)b1, b1 != 0.0 ? (float)(1.0 / b1) : 0.f, 0.f);
-  if (b1 == 0.0) coldone[j] = 1;
+  cf[(size_t)(s + 1) * m0 + j] = make_float4(a, b1, b1 != 0.f ? 1.f / b1 : 0.f, 0.f);
+  if (b1 == 0.f) coldone[j] = 1;
 }
 
 // Givens QR of the shifted tridiagonals (z_k I - Tbar) for steps s0 .. s1 - 1
@@ -556,6 +559,16 @@ k_lanczos_coef_f(int P, int m0, int s, const float *__restrict__ part, double *_
 // A pair stops at its tolerance (|g_{s+1}|^2 <= tol^2) or at a breakdown
 // (beta_{s+1} = 0); the last pair of a column to stop finishes the column.
 // Any pair still running raises *active.
+// The coefficients of FP32 Lanczos vectors carry FP32 rounding, so the
+// rotations and the factor R are formed in FP32 (this GPU's FP64 pipe issues
+// one warp instruction per 64 cycles, and the batch is a dependent chain);
+// the rotated right-hand side g, whose magnitude falls by the solve's whole
+// reduction, and the stop test stay in FP64. The batch's alpha and beta are
+// loaded before the chain starts.
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
 __global__ void __launch_bounds__(32)
 k_lanczos_givens_batch(int m0, int nc, int K, int s0, int s1, const double *__restrict__ alpha,
                        const double *__restrict__ beta, const MinresState st) {
@@ -565,65 +578,81 @@ k_lanczos_givens_batch(int m0, int nc, int K, int s0, int s1, const double *__re
   pdl_launch_next();
   if (j >= m0 || st.done[p]) return;
   // the last two rotations [cs, sn] by step parity, in registers
-  double2 c0 = st.rot[(size_t)p * 4 + 0], s0r = st.rot[(size_t)p * 4 + 1];
-  double2 c1 = st.rot[(size_t)p * 4 + 2], s1r = st.rot[(size_t)p * 4 + 3];
+  const double2 r0 = st.rot[(size_t)p * 4 + 0], r1 = st.rot[(size_t)p * 4 + 1];
+  const double2 r2 = st.rot[(size_t)p * 4 + 2], r3 = st.rot[(size_t)p * 4 + 3];
+  float2 c0 = make_float2((float)r0.x, (float)r0.y), s0r = make_float2((float)r1.x, (float)r1.y);
+  float2 c1 = make_float2((float)r2.x, (float)r2.y), s1r = make_float2((float)r3.x, (float)r3.y);
   double2 *g = st.g + (size_t)p * (K + 1);
   double2 gs = g[s0];
   const double tol = st.tol[p];
-  const double2 zk = st.z[k];
+  const float2 zk = make_float2((float)st.z[k].x, (float)st.z[k].y);
   bool fin = false;
-  for (int s = s0; s < s1 && !fin; ++s) {
-    const double a = alpha[(size_t)s * m0 + j];
-    const double b0 = beta[(size_t)s * m0 + j], b1 = beta[(size_t)(s + 1) * m0 + j];
-    double2 e2 = make_double2(0.0, 0.0);
-    double2 e1 = make_double2(-b0, 0.0);
-    double2 e0 = make_double2(zk.x - a, zk.y);
-    // rotation of step s - 2 sits in the parity slot of s, that of step s - 1 in the other
-    const bool odd = s & 1;
-    if (s >= 2) {
-      const double2 cs = odd ? c1 : c0, sn = odd ? s1r : s0r;
-      e2 = make_double2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
-      e1 = cmul(cs, e1);
+  for (int c = s0; c < s1 && !fin; c += kGivensBatch) {
+    const int nb = min(kGivensBatch, s1 - c);
+    float av[kGivensBatch], b0v[kGivensBatch], b1v[kGivensBatch];
+#pragma unroll
+    for (int i = 0; i < kGivensBatch; ++i) {
+      const size_t o = (size_t)(c + i) * m0 + j;
+      av[i] = i < nb ? (float)alpha[o] : 0.f;
+      b0v[i] = i < nb ? (float)beta[o] : 0.f;
+      b1v[i] = i < nb ? (float)beta[o + m0] : 0.f;
     }
-    if (s >= 1) {
-      const double2 cs = odd ? c0 : c1, sn = odd ? s0r : s1r;
-      const double2 x = e1, y = e0;
-      e1 = make_double2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
-                        cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
-      const double2 sx = cmul(sn, x), cy = cmul(cs, y);
-      e0 = make_double2(cy.x - sx.x, cy.y - sx.y);
+#pragma unroll
+    for (int i = 0; i < kGivensBatch; ++i) {
+      if (i >= nb || fin) break;
+      const int s = c + i;
+      const float a = av[i], b0 = b0v[i], b1 = b1v[i];
+      float2 e2 = make_float2(0.f, 0.f);
+      float2 e1 = make_float2(-b0, 0.f);
+      float2 e0 = make_float2(zk.x - a, zk.y);
+      // rotation of step s - 2 sits in the parity slot of s, that of step s - 1 in the other
+      const bool odd = s & 1;
+      if (s >= 2) {
+        const float2 cs = odd ? c1 : c0, sn = odd ? s1r : s0r;
+        e2 = make_float2(sn.x * e1.x + sn.y * e1.y, sn.x * e1.y - sn.y * e1.x);
+        e1 = cmulf(cs, e1);
+      }
+      if (s >= 1) {
+        const float2 cs = odd ? c0 : c1, sn = odd ? s0r : s1r;
+        const float2 x = e1, y = e0;
+        e1 = make_float2(cs.x * x.x + cs.y * x.y + sn.x * y.x + sn.y * y.y,
+                         cs.x * x.y - cs.y * x.x + sn.x * y.y - sn.y * y.x);
+        const float2 sx = cmulf(sn, x), cy = cmulf(cs, y);
+        e0 = make_float2(cy.x - sx.x, cy.y - sx.y);
+      }
+      const float rho2 = e0.x * e0.x + e0.y * e0.y + b1 * b1;
+      if (!(rho2 > 0.f)) {
+        fin = true;
+        break;
+      }
+      const float inv = rsqrtf(rho2);
+      const float rho = rho2 * inv;
+      const float2 cs = make_float2(e0.x * inv, e0.y * inv);
+      const float2 sn = make_float2(-b1 * inv, 0.f);
+      double2 *R = st.R + ((size_t)p * K + s) * 3;
+      R[0] = make_double2(rho, 0.0);
+      R[1] = make_double2(e1.x, e1.y);
+      R[2] = make_double2(e2.x, e2.y);
+      if (odd) {
+        c1 = cs;
+        s1r = sn;
+      } else {
+        c0 = cs;
+        s0r = sn;
+      }
+      const double snd = sn.x, csx = cs.x, csy = cs.y;  // sn is real
+      const double2 gn = make_double2(-snd * gs.x, -snd * gs.y);
+      g[s + 1] = gn;
+      g[s] = make_double2(csx * gs.x + csy * gs.y, csx * gs.y - csy * gs.x);
+      gs = gn;
+      fin = b1 == 0.f || (tol > 0.0 && cabs2(gn) <= tol * tol);
+      st.steps[p] = s + 1;
     }
-    const double rho2 = cabs2(e0) + b1 * b1;
-    if (!(rho2 > 0.0)) {
-      fin = true;
-      break;
-    }
-    const double inv = rsqrt(rho2);
-    const double rho = rho2 * inv;
-    const double2 cs = make_double2(e0.x * inv, e0.y * inv);
-    const double2 sn = make_double2(-b1 * inv, 0.0);
-    double2 *R = st.R + ((size_t)p * K + s) * 3;
-    R[0] = make_double2(rho, 0.0);
-    R[1] = e1;
-    R[2] = e2;
-    if (odd) {
-      c1 = cs;
-      s1r = sn;
-    } else {
-      c0 = cs;
-      s0r = sn;
-    }
-    const double2 gn = make_double2(-sn.x * gs.x, -sn.x * gs.y);  // sn is real
-    g[s + 1] = gn;
-    g[s] = make_double2(cs.x * gs.x + cs.y * gs.y, cs.x * gs.y - cs.y * gs.x);
-    gs = gn;
-    st.steps[p] = s + 1;
-    fin = b1 == 0.0 || (tol > 0.0 && cabs2(gn) <= tol * tol);
   }
-  st.rot[(size_t)p * 4 + 0] = c0;
-  st.rot[(size_t)p * 4 + 1] = s0r;
-  st.rot[(size_t)p * 4 + 2] = c1;
-  st.rot[(size_t)p * 4 + 3] = s1r;
+  st.rot[(size_t)p * 4 + 0] = make_double2(c0.x, c0.y);
+  st.rot[(size_t)p * 4 + 1] = make_double2(s0r.x, s0r.y);
+  st.rot[(size_t)p * 4 + 2] = make_double2(c1.x, c1.y);
+  st.rot[(size_t)p * 4 + 3] = make_double2(s1r.x, s1r.y);
   if (fin) {
     st.done[p] = 1;
     if (atomicAdd(&st.ndone[j], 1) == nc - 1) st.coldone[j] = 1;

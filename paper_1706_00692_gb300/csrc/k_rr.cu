@@ -287,18 +287,23 @@ __device__ void jacobi_rr(T *Cm, T *U, int m, int ld, int max_sweeps, double sto
 }
 
 // Generalised symmetric eigenproblem A_Q X = B_Q X Lambda in one CTA.
+// stage 0: the whole solve. With the cluster sweeps (k_eig_cluster.cu):
+// stage 1 stops once C = L^-1 A_Q L^-T is formed and leaves C in Cg and L in
+// Lg (row-major, leading dimension m); stage 2 takes the unsorted eigenvalues
+// from lam and the eigenvectors V of C from Cg, sorts them and forms
+// X_Q = L^-T V (launched with smem_mats = 0).
 __global__ void __launch_bounds__(512)
 k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ Bq,
               double *__restrict__ Lg, double *__restrict__ Cg, double *__restrict__ Ug,
               double *__restrict__ XQ, double *__restrict__ lam, DevStatus *__restrict__ status,
-              int smem_mats) {
+              int smem_mats, int stage) {
   // smem_mats = how many of (C, U, L) live in shared memory (in that order)
   extern __shared__ double smem[];
   // each matrix in shared memory takes m x (m | 1) doubles (room for the odd
   // leading dimension of the mixed-precision path)
   const size_t mm_ = (size_t)m * (m | 1);
   double *Cm = smem_mats >= 1 ? smem : Cg;
-  double *U = smem_mats >= 2 ? smem + mm_ : Ug;
+  double *U = smem_mats >= 2 ? smem + mm_ : (stage == 2 ? Cg : Ug);
   double *L = smem_mats >= 3 ? smem + 2 * mm_ : Lg;
   __shared__ double red[32];
   __shared__ int flag;
@@ -308,6 +313,11 @@ k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ B
   __shared__ int rank[kMaxM0];
   const int tid = threadIdx.x, nth = blockDim.x;
   const size_t mm = (size_t)m * m;
+  if (stage == 2) {
+    if (status->breakdown) return;  // stage 1 found B_Q not positive definite
+    for (int i = tid; i < m; i += nth) evals[i] = lam[i];
+    __syncthreads();
+  } else {
 
   // ---- Cholesky of B_Q, with one shifted retry --------------------------
   double fro2 = 0.0;
@@ -365,6 +375,13 @@ k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ B
   }
   for (size_t e = tid; e < mm; e += nth) U[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
   __syncthreads();
+  if (stage == 1) {  // C and L to global memory for the cluster sweeps
+    if (smem_mats >= 1)
+      for (size_t e = tid; e < mm; e += nth) Cg[e] = Cm[e];
+    if (smem_mats >= 3)
+      for (size_t e = tid; e < mm; e += nth) Lg[e] = L[e];
+    return;
+  }
 
   if (smem_mats >= 3) {
     // ---- mixed precision: FP32 sweeps, FP64 re-orthonormalisation and finish
@@ -480,6 +497,7 @@ k_reduced_eig(int m, const double *__restrict__ Aq, const double *__restrict__ B
   jacobi_rr<double>(Cm, U, m, m, 60, 1e-28, red, rot_c, rot_s, rot_a, rot_b);
   for (int i = tid; i < m; i += nth) evals[i] = Cm[(size_t)i * m + i];
   __syncthreads();
+  }
   // ---- X_Q = L^-T U (back substitution per column), ascending order -------
   for (int i = tid; i < m; i += nth) {
     int r = 0;
@@ -1117,6 +1135,8 @@ cudaError_t rr_init() {
   if (e != cudaSuccess) return e;
   e = rr_tc_init();
   if (e != cudaSuccess) return e;
+  e = eig_cluster_init();
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_reduced_eig_nonsym, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kNsEigSmem);
   if (e != cudaSuccess) return e;
@@ -1170,12 +1190,11 @@ cudaError_t rayleigh_ritz(const RRArgs &a, cudaStream_t st) {
   }
   // reduced eigenproblem
   {
-    const size_t mat = (size_t)m * (m | 1) * sizeof(double);
-    const int nmat = (int)std::min<size_t>(3, kEigSmem / mat);
     IFEAST_PROF_BEGIN(a.prof, K_RR_EIG);
-    k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, a.Aq, a.Bq, a.L, a.Cm, a.U, a.XQ, a.lam,
-                                              a.status, nmat);
+    const cudaError_t e =
+        reduced_eig_launch(m, a.Aq, a.Bq, a.L, a.Cm, a.U, a.XQ, a.lam, a.status, st);
     IFEAST_PROF_END(a.prof);
+    if (e != cudaSuccess) return e;
   }
   // X = Q X_Q and residual partials: on the tensor cores (BF16 digit products,
   // FP64-accurate, k_rr_tc.cu) when the shape allows, else in FP64
@@ -1227,7 +1246,15 @@ cudaError_t reduced_eig_launch(int m, const double *Aq, const double *Bq, double
   if (m < 1 || m > kMaxM0) return cudaErrorInvalidValue;
   const size_t mat = (size_t)m * (m | 1) * sizeof(double);
   const int nmat = (int)std::min<size_t>(3, kEigSmem / mat);
-  k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, Aq, Bq, L, Cm, U, XQ, lam, status, nmat);
+  if (!eig_cluster_supported(m)) {
+    k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, Aq, Bq, L, Cm, U, XQ, lam, status, nmat, 0);
+    return cudaGetLastError();
+  }
+  // C formed by one CTA, the FP64 sweeps on a cluster, the sort and X_Q by one CTA
+  k_reduced_eig<<<1, 512, nmat * mat, st>>>(m, Aq, Bq, L, Cm, U, XQ, lam, status, nmat, 1);
+  cudaError_t e = eig_sweeps_launch(m, Cm, lam, st);
+  if (e != cudaSuccess) return e;
+  k_reduced_eig<<<1, 512, 0, st>>>(m, Aq, Bq, L, Cm, U, XQ, lam, status, 0, 2);
   return cudaGetLastError();
 }
 
