@@ -10,7 +10,9 @@
 // pairing:
 //   1. every CTA forms all of the round's rotations from C[a][a], C[b][b] and
 //      C[a][b], read from the owners' shared memory (distributed shared
-//      memory), with the rule of the single-CTA solver;
+//      memory), with the rule of the single-CTA solver (while the
+//      off-diagonal part is still large, tan(theta) in FP32 and c, s made
+//      orthonormal in FP64 by Newton-Raphson steps for 1/sqrt(1 + t^2));
 //   2. C <- J^T C: each new row combines the CTA's old row with its partner
 //      row (read from the partner's owner) into the second buffer;
 //   3. cluster barrier;
@@ -35,6 +37,10 @@ namespace {
 constexpr int kEigCtas = 8;       // CTAs of the cluster (portable size)
 constexpr int kEigThreads = 256;  // threads per CTA
 constexpr int kEigMinM = 24;     // below this one CTA is as fast
+constexpr int kRowBatch = 4;     // partner-row elements a thread loads at once
+// squared off-diagonal / whole norm above which a sweep forms its rotation
+// angles in FP32
+constexpr double kCoarseAngles = 1e-10;
 
 // Dynamic shared memory of k_eig_sweeps for an m x m problem: two buffers of
 // the CTA's rows of C (the row phase writes the other one) and its rows of V.
@@ -118,6 +124,9 @@ k_eig_sweeps(int m, double *__restrict__ Cg, double *__restrict__ evals, int max
     }
     cl.sync();  // norms read everywhere before they change or a CTA exits
     if (!(totals[0] > stop * totals[1])) break;
+    // rotation angles in FP32 while the off-diagonal part is large, exact FP64
+    // angles for the final sweeps (their quadratic convergence)
+    const bool coarse = totals[0] > kCoarseAngles * totals[1];
     for (int round = 0; round < mp - 1; ++round) {
       const double *Cc = Cbuf + (size_t)cur * R * ld;
       double *Cn = Cbuf + (size_t)(cur ^ 1) * R * ld;
@@ -137,12 +146,29 @@ k_eig_sweeps(int m, double *__restrict__ Cg, double *__restrict__ evals, int max
           const double *cb = cl.map_shared_rank(Cc, b / R) + (size_t)(b % R) * ld;
           const double apq = ca[b], app = ca[a], aqq = cb[b];
           if (fabs(apq) > 1e-300 && fabs(apq) > DBL_EPSILON * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) /
-                             (fabs(tau) + (fabs(tau) < 1e150 ? sqrt(1.0 + tau * tau) : fabs(tau)));
-            c = 1.0 / sqrt(1.0 + t * t);
+            double t;
+            if (coarse) {
+              // t = tan(theta) in FP32 (~1e-7 relative: the rotation then leaves
+              // ~1e-7 of C[a][b], far below the off-diagonal mass of a coarse
+              // sweep); c = (1 + t^2)^-1/2 from rsqrtf and two FP64 Newton
+              // steps, so that c^2 + s^2 = 1 to FP64 rounding
+              const float tau = (float)(aqq - app) / (2.f * (float)apq);
+              const float tf = (tau >= 0.f ? 1.f : -1.f) /
+                               (fabsf(tau) + (fabsf(tau) < 1e18f ? sqrtf(1.f + tau * tau) : fabsf(tau)));
+              t = tf;
+              const double x = 1.0 + t * t;
+              double y = rsqrtf((float)x);
+              y = y * (1.5 - 0.5 * x * y * y);
+              y = y * (1.5 - 0.5 * x * y * y);
+              c = y;
+            } else {
+              const double tau = (aqq - app) / (2.0 * apq);
+              t = (tau >= 0.0 ? 1.0 : -1.0) /
+                  (fabs(tau) + (fabs(tau) < 1e150 ? sqrt(1.0 + tau * tau) : fabs(tau)));
+              c = 1.0 / sqrt(1.0 + t * t);
+            }
             s = t * c;
-            any_rot = 1;  // every writer stores the same value
+            if (s != 0.0) any_rot = 1;  // every writer stores the same value
           }
         }
         ra[p] = a;
@@ -160,17 +186,28 @@ k_eig_sweeps(int m, double *__restrict__ Cg, double *__restrict__ evals, int max
         }
       }
       __syncthreads();
-      // 2. rows: C <- J^T C into the other buffer (partner rows from their owners)
-      for (int e = tid; e < nr * m; e += kEigThreads) {
-        const int li = e / m, k = e % m, i = r0 + li;
-        const double x = Cc[(size_t)li * ld + k];
-        const int pr = partner[i];
-        double y = x;
-        if (pr >= 0) {
-          const double xp = cl.map_shared_rank(Cc, pr / R)[(size_t)(pr % R) * ld + k];
-          y = self_c[i] * x + part_c[i] * xp;
+      // 2. rows: C <- J^T C into the other buffer (partner rows from their
+      // owners; a thread's remote loads are all issued before they are used)
+      for (int e0 = 0; e0 < nr * m; e0 += kRowBatch * kEigThreads) {
+        double xp[kRowBatch];
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+          const int e = e0 + u * kEigThreads + tid;
+          xp[u] = 0.0;
+          if (e < nr * m) {
+            const int li = e / m, k = e % m, pr = partner[r0 + li];
+            if (pr >= 0) xp[u] = cl.map_shared_rank(Cc, pr / R)[(size_t)(pr % R) * ld + k];
+          }
         }
-        Cn[(size_t)li * ld + k] = y;
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+          const int e = e0 + u * kEigThreads + tid;
+          if (e < nr * m) {
+            const int li = e / m, k = e % m, i = r0 + li;
+            const double x = Cc[(size_t)li * ld + k];
+            Cn[(size_t)li * ld + k] = partner[i] >= 0 ? self_c[i] * x + part_c[i] * xp[u] : x;
+          }
+        }
       }
       cl.sync();  // all new rows written, all reads of the old buffer done
       // 3. columns: C <- C J, V <- V J on this CTA's rows
