@@ -113,8 +113,11 @@ def measured_peaks():
 # kernel changes (None: not measured for the workload).
 ELL_STEP_TRAFFIC_LAP3D64 = 312.7e6
 
-# the Lanczos step and Givens kernels are timed in one step of PROFILE_EVERY
-PROFILE_EVERY = 8
+# the per-step kernels of the Lanczos loop (step, coefficients) are timed in one
+# step of PROFILE_EVERY: an event pair around a launch stops it from overlapping
+# the previous kernel (programmatic dependent launch), which costs the solve
+# ~10 us per sampled step; 1 in 32 still samples ~290 launches per solve
+PROFILE_EVERY = 32
 
 
 def step_bytes(wl, elem):
@@ -432,7 +435,7 @@ def run_ours(args):
     times = []
     stats = []
     # kernel timing with CUDA events on the handle's stream: every launch, except
-    # that the Lanczos step and Givens kernels are timed one step in PROFILE_EVERY
+    # that the per-step Lanczos kernels are timed one step in PROFILE_EVERY
     # (events between them would stop their programmatic overlap in every step)
     S.set_profiling(PROFILE_EVERY)
     S.kernel_times(reset=True)

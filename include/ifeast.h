@@ -378,8 +378,9 @@ int ifeast_rayleigh_ritz_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr,
  * CUDA events on the handle's stream (a few microseconds of overhead per
  * launch); the durations are summed per kernel class when the library next
  * synchronises its stream. on = N >= 2: the same, except that only launches
- * 1, 1 + N, 1 + 2N, ... of the per-step Lanczos kernels (the step kernel and
- * the kernel that reduces its partials to alpha_s, beta_{s+1}) are timed: an
+ * 1, 1 + N, 1 + 2N, ... of the chained Lanczos-loop kernels (the step
+ * kernel, the kernel that reduces its partials to alpha_s, beta_{s+1}, and the
+ * batched Givens QR) are timed, each class counted on its own: an
  * event between two of those kernels stops the second from launching while the
  * first runs (programmatic dependent launch), so timing all of them slows the
  * solve being timed. on = 0: off. A negative on returns IFEAST_ERR_INVALID_ARG.

@@ -3,7 +3,7 @@
     python -m paper_1706_00692_gb300.cli [--workload lap3d_64|lap3d_64_fp16|lap3d_64_bf16|
                                                      lap3d_64_twopass|lap3d_64_fp64|lap2d_50|
                                                      fem3d_64|fem3d_64_fp64|fem3d_48|fem3d_128]
-                                         [--max-outer M] [--inner-iters K] [--verbose]
+                                         [--max-outer M] [--inner-iters K] [--alpha A] [--verbose]
                                          [--rr-calls R] [--plain-loads]
 
 Prints one JSON line: status, eigenpairs found, largest residual, outer
@@ -55,6 +55,8 @@ def main(argv=None) -> int:
     p.add_argument("--workload", default="lap3d_64")
     p.add_argument("--max-outer", type=int, default=100)
     p.add_argument("--inner-iters", type=int, default=0, help="override the workload's cap")
+    p.add_argument("--alpha", type=float, default=-1.0,
+                   help="override the workload's inner tolerance factor (alpha of Algorithm 2)")
     p.add_argument("--verbose", action="store_true")
     p.add_argument("--plain-loads", action="store_true",
                    help="FP32 per-node GMRES: read the basis with plain loads, not TMA")
@@ -66,8 +68,9 @@ def main(argv=None) -> int:
     if a.rr_calls > 0:
         return rr_calls(wl, a.rr_calls)
     k = a.inner_iters or wl.inner_iters
+    alpha = a.alpha if a.alpha >= 0.0 else wl.alpha
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
-               inner_iters=k, alpha=wl.alpha, precision=wl.precision, two_pass=wl.two_pass,
+               inner_iters=k, alpha=alpha, precision=wl.precision, two_pass=wl.two_pass,
                max_outer=a.max_outer, B=wl.B, node_chunk=wl.node_chunk,
                verbose=a.verbose, plain_loads=a.plain_loads)
     X0 = torch.as_tensor(wl.X0(), device="cuda")

@@ -52,8 +52,9 @@ struct Profiler {
   double ms[K_COUNT] = {0};
   long long count[K_COUNT] = {0};     // timed launches
   long long launches[K_COUNT] = {0};  // all launches
-  // > 1: only every sample_every-th launch of the Lanczos step and Givens
-  // kernels is timed (events between them stop their programmatic overlap)
+  // > 1: only every sample_every-th launch of the Lanczos step, coefficient
+  // and Givens kernels is timed (events between them stop their programmatic
+  // overlap)
   int sample_every = 1;
   bool skipping = false;
   void begin(int k);

@@ -1281,8 +1281,8 @@ cudaError_t spmm_block(int n, int m, const int32_t *rowptr, const int32_t *colid
 
 void Profiler::begin(int k) {
   ++launches[k];
-  // sampling: time launch 1, 1 + N, 1 + 2N, ... of the per-step Lanczos kernels
-  skipping = sample_every > 1 && (k == K_LZ_STEP || k == K_LZ_REDUCE) &&
+  // sampling: time launch 1, 1 + N, 1 + 2N, ... of the chained Lanczos-loop kernels
+  skipping = sample_every > 1 && (k == K_LZ_STEP || k == K_LZ_REDUCE || k == K_LZ_GIVENS) &&
              (launches[k] - 1) % sample_every != 0;
   if (skipping || used >= cap) return;  // pool full: the launch goes untimed
   kid[used] = k;

@@ -273,11 +273,11 @@ def test_two_pass_solve_is_bit_identical(torch):
 
 
 def test_sampled_profiling_counts(torch):
-    """set_profiling(N): the per-step Lanczos kernels (the step kernel and the
-    reduction of its partials to alpha_s, beta_{s+1}) are timed in one step of
-    N (launches 1, 1 + N, ...), every other kernel (the Givens batches too) at
-    every launch, and all launches are counted; one Givens batch covers at most
-    16 steps."""
+    """set_profiling(N): the chained Lanczos-loop kernels (the step kernel, the
+    reduction of its partials to alpha_s, beta_{s+1}, and the Givens batches)
+    are timed at launches 1, 1 + N, ... of each class, every other kernel at
+    every launch, and all launches are counted; one Givens batch covers at
+    most 16 steps."""
     from paper_1706_00692_gb300 import Solver
     A, ev, emin, emax, i0, cnt = _interior_problem()
     S = Solver(A, emin, emax, 2 * cnt, nc=8, rule="trap_half", inner="minres", inner_iters=300,
@@ -291,7 +291,7 @@ def test_sampled_profiling_counts(torch):
     S.set_profiling(False)
     for k, n in launches.items():
         c = timed[k][0]
-        if k in ("lanczos_step", "lanczos_reduce"):
+        if k in ("lanczos_step", "lanczos_reduce", "lanczos_givens"):
             assert c == (n + 3) // 4, (k, n, c)
         else:
             assert c == n, (k, n, c)
