@@ -272,3 +272,24 @@ def test_rayleigh_ritz_tensor_core_shapes(torch, m0):
     assert np.abs(lam - lr).max() <= 1e-12 * np.abs(lr).max()
     assert np.abs(X.T @ X - np.eye(m0)).max() <= 1e-10
     assert np.abs(res - orc.eigen_residuals(As @ X, X, lam)).max() <= 1e-10
+
+
+@pytest.mark.parametrize("m0", [23, 24, 25, 41, 57, 80, 150, 223, 256])
+def test_reduced_eig_cluster_sizes(torch, m0):
+    """The reduced eigenproblem for m0 >= 24 runs its Jacobi sweeps on an 8-CTA
+    cluster (rows of C split ceil(m0 / 8) per CTA; 41 leaves the last CTA
+    without rows, 57 with one); 23 stays on one CTA, 256 is the largest m0.
+    Eigenvalues as the oracle's Rayleigh-Ritz to 1e-12 relative, X^T X = I to
+    1e-10, residuals as a CPU FP64 recomputation from the returned X and lambda."""
+    A = inputs.add_diagonal(inputs.laplacian((50, 50)), inputs.random_potential(2500, 12))
+    Q = inputs.initial_subspace(A.n, m0, 41)
+    S = _solver(A, 0.0, 8.0, m0)
+    X, lam, res = S.rayleigh_ritz(torch.as_tensor(Q, device="cuda"))
+    X, lam, res = X.cpu().numpy(), lam.cpu().numpy(), res.cpu().numpy()
+    S.close()
+    As = A.to_scipy()
+    lr, _ = orc.rayleigh_ritz(Q, As @ Q)
+    assert np.all(np.diff(lam) >= 0)
+    assert np.abs(lam - lr).max() <= 1e-12 * np.abs(lr).max()
+    assert np.abs(X.T @ X - np.eye(m0)).max() <= 1e-10
+    assert np.abs(res - orc.eigen_residuals(As @ X, X, lam)).max() <= 1e-10
