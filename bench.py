@@ -522,9 +522,9 @@ def run_ours(args):
                 "roofline": roofline,
                 "kernel_ms": {k: {"launches": n, "timed": c, "ms_per_launch": round(e, 6),
                                   "ms": round(n * e, 3)} for k, (n, c, e) in kstat.items()},
-                "kernel_timing": f"CUDA events per launch; the per-step Lanczos kernels "
-                                 f"(step, coefficient reduction) timed in one step of "
-                                 f"{PROFILE_EVERY}",
+                "kernel_timing": f"CUDA events per launch; the chained Lanczos-loop kernels "
+                                 f"(step, coefficient reduction, Givens batch) timed at one "
+                                 f"launch in {PROFILE_EVERY} of each",
                 "error_vs_reference": accuracy,
                 "clocks": clk.summary()}
         if fp64_form is not None:
