@@ -147,7 +147,8 @@ k_eig_sweeps(int m, double *__restrict__ Cg, double *__restrict__ evals, int max
           const double apq = ca[b], app = ca[a], aqq = cb[b];
           if (fabs(apq) > 1e-300 && fabs(apq) > DBL_EPSILON * sqrt(fabs(app * aqq))) {
             double t;
-            if (coarse) {
+            // (FP32 only where tau stays a normal FP32 number)
+            if (coarse && fabs(apq) > 1e-30 && fabs(aqq - app) < 1e30) {
               // t = tan(theta) in FP32 (~1e-7 relative: the rotation then leaves
               // ~1e-7 of C[a][b], far below the off-diagonal mass of a coarse
               // sweep); c = (1 + t^2)^-1/2 from rsqrtf and two FP64 Newton
