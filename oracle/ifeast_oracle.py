@@ -466,8 +466,39 @@ def in_circle(theta, c, r):
     return np.abs(theta - c) < r
 
 
+def _filtered_subspace_gmres_correction_nonsym(A, X, C, z, w, half, k, tol_rel, stats):
+    """The non-symmetric filter from a real basis X and a square C (the Galerkin
+    matrix X^T A X of the previous Rayleigh-Ritz): with R = A X - X C,
+        (z I - A)^{-1} X = [X + (z I - A)^{-1} R] (z I - C)^{-1}
+    holds exactly for any X and any C with z I - C invertible, since
+    (z I - A)^{-1} X (z I - C) = (z I - A)^{-1} ((z I - A) X + R). GMRES (zero
+    initial guess, at most k steps) runs on (z_k I - A) e = r_j only, stopped
+    at |g_{s+1}| <= tol_rel ||x_j|| (Alg. 2's bound with the correction's
+    right-hand side), and
+        Q = sum_k w_k (X + E_k) (z_k I - C)^{-1}
+    (real part for a half rule). The inner error is then relative to ||R||,
+    which falls with the outer iteration, not to ||X||."""
+    n, m0 = X.shape
+    R = A @ X - X @ C
+    Q = np.zeros(X.shape, np.complex128)
+    for zk, wk in zip(z, w):
+        op = lambda v, zk=zk: shifted_apply(A, zk, v)
+        E = np.zeros(X.shape, np.complex128)
+        for j in range(m0):
+            rn = np.linalg.norm(R[:, j])
+            if rn == 0.0:
+                stats["inner_steps"].append(0)
+                continue
+            tol_j = tol_rel * np.linalg.norm(X[:, j]) / rn if tol_rel > 0.0 else 0.0
+            out = gmres(op, R[:, j], k, tol_j)
+            stats["inner_steps"].append(out["steps"])
+            E[:, j] = out["y"]
+        Q += wk * np.linalg.solve((zk * np.eye(m0) - C).T, (X + E).T).T
+    return Q.real if half else Q
+
+
 def ifeast_nonsym(A, X0, c, r, z, w, *, half=True, inner="gmres", k=10, alpha=0.0,
-                  tol=1e-10, max_outer=100):
+                  tol=1e-10, max_outer=100, correction=False):
     """IFEAST (Algorithm 2; Algorithm 1 with inner="exact") for a real
     non-symmetric A, eigenvalues inside the circle |lambda - c| < r.
 
@@ -482,7 +513,11 @@ def ifeast_nonsym(A, X0, c, r, z, w, *, half=True, inner="gmres", k=10, alpha=0.
       eigensolver; residuals ||A x_j - theta_j x_j|| / ||A x_j|| of the unit
       Ritz vectors x_j = X u_j; ||R_F|| is their maximum over theta_j inside
       the circle;
-    * inner stop ||x_j - (z_k I - A) y|| <= alpha ||R_F|| ||x_j|| (||x_j|| = 1).
+    * inner stop ||x_j - (z_k I - A) y|| <= alpha ||R_F|| ||x_j|| (||x_j|| = 1);
+    * correction=True: from the second outer iteration on the filter runs on
+      the residual block R = A X - X C of the previous Rayleigh-Ritz
+      (_filtered_subspace_gmres_correction_nonsym), whose inner error falls
+      with ||R||; the first iteration is the plain form.
 
     Returns dict(theta, V (Ritz vectors, n x m0 complex), res, inside, iters,
     history, converged)."""
@@ -491,10 +526,13 @@ def ifeast_nonsym(A, X0, c, r, z, w, *, half=True, inner="gmres", k=10, alpha=0.
     RF = 1.0
     history = []
     A_dense = None
+    C = None  # Galerkin matrix X^T A X of the last Rayleigh-Ritz
     for it in range(1, max_outer + 1):
         stats = {"inner_steps": []}
         tol_rel = alpha * RF if alpha > 0 else 0.0
-        if inner == "exact":
+        if correction and C is not None and inner == "gmres":
+            Q = _filtered_subspace_gmres_correction_nonsym(A, X, C, z, w, half, k, tol_rel, stats)
+        elif inner == "exact":
             if A_dense is None:
                 A_dense = A.toarray() if sp.issparse(A) else np.asarray(A)
             Q = _filtered_subspace_exact(A_dense, X, z, w, half)
@@ -508,6 +546,7 @@ def ifeast_nonsym(A, X0, c, r, z, w, *, half=True, inner="gmres", k=10, alpha=0.
         theta, U, Linv_T = rayleigh_ritz_nonsym(Q, AQ)
         X = Q @ Linv_T
         AX = AQ @ Linv_T
+        C = X.T @ AX
         V = X @ U
         res = eigen_residuals(AX @ U, V, theta)
         inside = in_circle(theta, c, r)

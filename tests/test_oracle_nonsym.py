@@ -104,3 +104,67 @@ def test_ifeast_nonsym_gmres_converges_to_closed_form():
     th = out["theta"][out["inside"]]
     assert th.size == cnt
     assert np.abs(np.sort(th.real) - cf[:cnt]).max() <= 60.0 * 1e-10 * cf[cnt - 1]
+
+
+def _orthonormal_block(n, m0, seed):
+    return np.linalg.qr(inputs.initial_subspace(n, m0, seed))[0]
+
+
+@pytest.mark.parametrize("perturb", [0.0, 0.3])
+def test_correction_filter_equals_exact_filter(perturb):
+    """(zI - A)^{-1} X = [X + (zI - A)^{-1} R](zI - C)^{-1} with R = A X - X C
+    holds for any C: with GMRES run to the full dimension the correction form
+    reproduces the exact filter, for the Galerkin C = X^T A X and for a
+    perturbed one."""
+    A, cf, emax, z, w, _ = _problem()
+    Ad = A.to_scipy().toarray()
+    As = A.to_scipy()
+    X = _orthonormal_block(A.n, 9, 4)
+    C = X.T @ (As @ X)
+    if perturb:
+        C = C + perturb * np.random.default_rng(7).standard_normal(C.shape) * np.abs(C).max()
+    stats = {"inner_steps": []}
+    Q = orc._filtered_subspace_gmres_correction_nonsym(As, X, C, z, w, True, A.n, 0.0, stats)
+    Qe = orc._filtered_subspace_exact(Ad, X, z, w, True)
+    assert np.abs(Q - Qe).max() <= 1e-9 * np.abs(Qe).max()
+
+
+def test_correction_filter_planted_mistakes_are_caught():
+    """A residual with X and C in the wrong order, or (zI - C) applied instead
+    of its inverse, moves the exactly solved filter away from the exact one."""
+    A, cf, emax, z, w, _ = _problem()
+    Ad = A.to_scipy().toarray()
+    X = _orthonormal_block(A.n, 9, 4)
+    C = X.T @ Ad @ X
+    Qe = orc._filtered_subspace_exact(Ad, X, z, w, True)
+    I = np.eye(A.n)
+    bad1 = np.zeros(X.shape)
+    bad2 = np.zeros(X.shape)
+    for zk, wk in zip(z, w):
+        Rw = Ad @ X - X @ C.T                                     # C transposed
+        Ew = np.linalg.solve(zk * I - Ad, Rw.astype(complex))
+        bad1 += (wk * np.linalg.solve((zk * np.eye(9) - C).T, (X + Ew).T).T).real
+        E = np.linalg.solve(zk * I - Ad, (Ad @ X - X @ C).astype(complex))
+        bad2 += (wk * (X + E) @ (zk * np.eye(9) - C)).real          # no inverse
+    assert np.abs(bad1 - Qe).max() > 1e-3 * np.abs(Qe).max()
+    assert np.abs(bad2 - Qe).max() > 1e-3 * np.abs(Qe).max()
+
+
+def test_correction_form_converges_where_plain_form_stalls():
+    """On the 30 x 24 upwind problem (Pe = 10, the 10 lowest eigenvalues, m0 =
+    20, GMRES(32), 8 trapezoid nodes) the plain form's inner error, relative to
+    ||x_j||, holds ||R_F|| near 1e-4; solved for the correction from the second
+    iteration on, the iteration reaches 1e-10 and the closed-form eigenvalues."""
+    grid, Pe, cnt, m0 = (30, 24), 10.0, 10, 20
+    A = inputs.upwind_convection_diffusion(grid, Pe)
+    cf = inputs.upwind_convection_diffusion_eigs(grid, Pe)
+    emax = 0.5 * (cf[cnt - 1] + cf[cnt])
+    z, w = orc.contour_nodes("trap_half", 8, 0.0, emax)
+    X0 = inputs.initial_subspace(A.n, m0, 0)
+    out = orc.ifeast_nonsym(A.to_scipy(), X0, emax / 2, emax / 2, z, w, k=32, max_outer=25,
+                            correction=True)
+    assert out["converged"] and out["iters"] <= 20
+    th = np.sort(out["theta"][out["inside"]].real)
+    assert th.size == cnt
+    # eigenvector condition number (1 + Pe h)^(N/2) times the residual target
+    assert np.abs(th - cf[:cnt]).max() <= 1e4 * 1e-10 * cf[cnt - 1]
