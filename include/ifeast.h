@@ -178,6 +178,17 @@ typedef struct {
                            shared memory by TMA tile copies when the system
                            count of a pass is even (same arithmetic, same
                            results bit for bit).                              */
+  int nonsym_correction; /* nonsymmetric == 1: 1 solves, from the second outer
+                           iteration on, the shifted systems for the block
+                           residual R = A X - X C of the orthonormal basis X
+                           and its Galerkin matrix C = X^T A X, and forms
+                           Q = Re sum_k w_k (X + E_k)(z_k I - C)^-1 with
+                           (z_k I - A) E_k = R: the identity
+                           (zI - A)^-1 X = [X + (zI - A)^-1 R](zI - C)^-1 is
+                           exact, and the inner error then falls with ||R||
+                           (plain form: with ||X||). Inner stop |g_{s+1}| <=
+                           alpha ||R_F||. 0 (default): the plain form. Needs
+                           m0 <= 64 and the FP64 basis.                       */
 } ifeast_opts;
 
 typedef struct {

@@ -43,7 +43,8 @@ class Opts(ct.Structure):
                 ("max_outer", ct.c_int), ("tol", ct.c_double), ("precision", ct.c_int),
                 ("verbose", ct.c_int), ("nonsymmetric", ct.c_int), ("minres_two_pass", ct.c_int),
                 ("correction_rf", ct.c_double), ("time_limit_ms", ct.c_double),
-                ("node_chunk", ct.c_int), ("plain_loads", ct.c_int)]
+                ("node_chunk", ct.c_int), ("plain_loads", ct.c_int),
+                ("nonsym_correction", ct.c_int)]
 
 
 class Stats(ct.Structure):

@@ -47,6 +47,8 @@ def workload(name: str):
         return inputs.workload_fem3d_128()
     if name == "lap3d_64_bf16":
         return inputs.workload_lap3d_64_interior(seed=0, precision="bf16")
+    if name.startswith("convdiff_"):  # convdiff_N: N x N upwind convection-diffusion
+        return inputs.workload_convdiff(int(name.split("_")[1]))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -72,7 +74,8 @@ def main(argv=None) -> int:
     S = Solver(wl.A, wl.emin, wl.emax, wl.m0, nc=wl.nc, rule=wl.rule, inner=wl.inner,
                inner_iters=k, alpha=alpha, precision=wl.precision, two_pass=wl.two_pass,
                max_outer=a.max_outer, B=wl.B, node_chunk=wl.node_chunk,
-               verbose=a.verbose, plain_loads=a.plain_loads)
+               verbose=a.verbose, plain_loads=a.plain_loads, nonsymmetric=wl.nonsym,
+               nonsym_correction=wl.nonsym_correction)
     X0 = torch.as_tensor(wl.X0(), device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -83,7 +86,18 @@ def main(argv=None) -> int:
     out = {"workload": wl.name, "status": rc, "seconds": dt, "outer_iters": st["outer_iters"],
            "found": st["found"], "RF": st["RF"], "krylov_steps_total": st["total_matvecs"],
            "krylov_steps_seq": st["seq_matvecs"]}
-    if rc in (0, 4):
+    if rc in (0, 4) and wl.nonsym:  # complex Ritz pairs; the upwind spectrum is real
+        lam, X, res = S.eigenpairs_complex()
+        out["max_residual"] = float(res.max()) if res.size else None
+        N = round(wl.A.n ** 0.5)
+        ref = inputs.upwind_convection_diffusion_eigs((N, N), 10.0)
+        ref = ref[(ref > wl.emin) & (ref < wl.emax)]
+        out["reference_pairs"] = int(ref.size)
+        if ref.size == lam.size and ref.size:
+            out["max_rel_eig_err_vs_closed_form"] = float(
+                np.max(np.abs(np.sort(lam.real) - ref)) / ref.max())
+            out["max_abs_imag_rel"] = float(np.abs(lam.imag).max() / ref.max())
+    elif rc in (0, 4):
         lam, X, res = S.eigenpairs()
         out["max_residual"] = float(res.max()) if res.size else None
         if wl.B is not None and wl.name.startswith("fem3d_"):  # closed-form Q1 spectrum

@@ -39,6 +39,8 @@ struct ifeast_ctx {
   bool nonsym = false;
   double *LinvT = nullptr;
   double2 *theta = nullptr, *Uc = nullptr;
+  double2 *nsM = nullptr;             // block correction: [nc][m0][m0] (z_k I - C)^-1
+  double *nsG = nullptr, *nsP = nullptr;  // Re sum_k w_k M_k; L^-T C
   int *ridx = nullptr;
   double2 *z = nullptr, *w = nullptr;
   void *V = nullptr, *W = nullptr;  // double2, or float2 for the FP32 basis
@@ -193,7 +195,7 @@ struct Offsets {
   size_t val32, LV, LW0, LW1, lpart, lalpha, lcf32, lbeta, ltol, lg, lR, lrot, lYc, lwt, lsteps, ldone,
       lcoldone, lndone, lactive, lSj, lcoef, lcx, Rres, rnorm, colE, valE;
   size_t rowptrB, colidxB, valB, BQ, BX;
-  size_t LinvT, theta, Uc, ridx;
+  size_t LinvT, theta, Uc, ridx, nsM, nsG, nsP;
   size_t Qf;
   size_t valB32, tolc, Yf, gcx;
 };
@@ -303,6 +305,13 @@ Offsets plan(int64_t n, int64_t nnz, int m0, int nc, int ncc, int K, const RowTi
     o.theta = L.take<double2>(m0);
     o.Uc = L.take<double2>((size_t)m0 * m0);
     o.ridx = L.take<int>(m0);
+    o.nsM = L.take<double2>((size_t)nc * m0 * m0);  // block correction: M_k = (z_k I - C)^-1
+    o.nsG = L.take<double>((size_t)m0 * m0);
+    o.nsP = L.take<double>((size_t)m0 * m0);
+    if (!o.Rres) {  // block residual R = A X - X C and its column norms (FP64 basis)
+      o.Rres = L.take<double>((size_t)n * m0);
+      o.rnorm = L.take<double>(m0);
+    }
   }
   if (nnzB >= 0) {  // generalized problem
     o.rowptrB = L.take<int32_t>(n + 1);
@@ -372,6 +381,7 @@ int validate_opts(const ifeast_opts *o) {
   if (o->minres_two_pass != 0 && o->minres_two_pass != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->node_chunk < 0) return IFEAST_ERR_INVALID_ARG;
   if (o->plain_loads != 0 && o->plain_loads != 1) return IFEAST_ERR_INVALID_ARG;
+  if (o->nonsym_correction != 0 && o->nonsym_correction != 1) return IFEAST_ERR_INVALID_ARG;
   if (o->node_chunk > 0 && o->inner_solver != IFEAST_INNER_GMRES) return IFEAST_ERR_UNSUPPORTED;
   if (o->minres_two_pass &&
       (o->inner_solver != IFEAST_INNER_MINRES || o->precision == IFEAST_FP64))
@@ -591,6 +601,82 @@ int prepare_rhs(ifeast_ctx *h, const double *X, const double **rhs) {
   return IFEAST_OK;
 }
 
+// Block correction of the non-symmetric iteration (opts.nonsym_correction).
+// From the last Rayleigh-Ritz (L^{-T} and A_Q = Q^T A Q on the device) the
+// Galerkin matrix of the carried basis X = Q L^{-T} is C = L^{-1} A_Q L^{-T}. On
+// the host: P = L^{-T} C, M_k = (z_k I - C)^{-1} for every node (complex
+// Gauss-Jordan with partial pivoting) and Re sum_k w_k M_k; on the device the
+// right-hand sides R = A X - X C = (A Q) L^{-T} - Q P and their column norms.
+int ns_block_correction_setup(ifeast_ctx *h) {
+  const int m = h->m0;
+  const size_t mm = (size_t)m * m;
+  std::vector<double> Lt(mm), Aq(mm), T(mm, 0.0), C(mm, 0.0), P(mm, 0.0), G(mm, 0.0);
+  CK(cudaMemcpyAsync(Lt.data(), h->LinvT, mm * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(Aq.data(), h->Aq, mm * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < m; ++i)  // T = A_Q L^{-T}
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < m; ++k) T[(size_t)i * m + k] += Aq[(size_t)i * m + j] * Lt[(size_t)j * m + k];
+  for (int i = 0; i < m; ++i)  // C = (L^{-T})^T T
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < m; ++k) C[(size_t)i * m + k] += Lt[(size_t)j * m + i] * T[(size_t)j * m + k];
+  for (int i = 0; i < m; ++i)  // P = L^{-T} C
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < m; ++k) P[(size_t)i * m + k] += Lt[(size_t)i * m + j] * C[(size_t)j * m + k];
+  std::vector<double2> M((size_t)h->nc * mm), aug((size_t)m * 2 * m);
+  auto cm = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+  for (int k = 0; k < h->nc; ++k) {
+    const double2 z = h->zh[k], w = h->wh[k];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < 2 * m; ++j) {
+        double2 v = make_double2(0.0, 0.0);
+        if (j < m) v = make_double2((i == j ? z.x : 0.0) - C[(size_t)i * m + j], i == j ? z.y : 0.0);
+        else v = make_double2(j - m == i ? 1.0 : 0.0, 0.0);
+        aug[(size_t)i * 2 * m + j] = v;
+      }
+    for (int c = 0; c < m; ++c) {  // Gauss-Jordan, pivot = largest |entry| of column c
+      int p = c;
+      double best = -1.0;
+      for (int i = c; i < m; ++i) {
+        const double2 v = aug[(size_t)i * 2 * m + c];
+        const double a = v.x * v.x + v.y * v.y;
+        if (a > best) { best = a; p = i; }
+      }
+      if (!(best > 0.0)) return IFEAST_ERR_BREAKDOWN;  // a node on a Ritz value
+      if (p != c)
+        for (int j = 0; j < 2 * m; ++j) std::swap(aug[(size_t)p * 2 * m + j], aug[(size_t)c * 2 * m + j]);
+      const double2 d = aug[(size_t)c * 2 * m + c];
+      const double2 inv = make_double2(d.x / best, -d.y / best);
+      for (int j = 0; j < 2 * m; ++j) aug[(size_t)c * 2 * m + j] = cm(aug[(size_t)c * 2 * m + j], inv);
+      for (int i = 0; i < m; ++i) {
+        if (i == c) continue;
+        const double2 f = aug[(size_t)i * 2 * m + c];
+        if (f.x == 0.0 && f.y == 0.0) continue;
+        for (int j = 0; j < 2 * m; ++j) {
+          const double2 t = cm(f, aug[(size_t)c * 2 * m + j]);
+          aug[(size_t)i * 2 * m + j].x -= t.x;
+          aug[(size_t)i * 2 * m + j].y -= t.y;
+        }
+      }
+    }
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        const double2 v = aug[(size_t)i * 2 * m + m + j];
+        M[(size_t)k * mm + (size_t)i * m + j] = v;
+        G[(size_t)i * m + j] += w.x * v.x - w.y * v.y;
+      }
+  }
+  CK(cudaMemcpyAsync(h->nsM, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->nsG, G.data(), mm * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->nsP, P.data(), mm * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  // the host arrays are read by the copies: wait before they go out of scope
+  CK(cudaStreamSynchronize(h->stream));
+  CK(ns_block_residual((int)h->n, m, h->AQ, h->Q, h->LinvT, h->nsP, h->Rres, h->stream));
+  Profiler *pf = h->profiling ? &h->prof : nullptr;
+  CK(column_norms((int)h->n, m, h->Rres, h->res_part, h->Pr, h->rnorm, h->stream, pf));
+  return IFEAST_OK;
+}
+
 // Shared-basis inner solve. correction = 0: right-hand sides X (norms in
 // h->beta); correction = 1: right-hand sides h->Rres = A X - X Lambda of the
 // current X (norms h->rnorm, Ritz values h->lam, ||x_j|| in h->beta).
@@ -690,6 +776,7 @@ void ifeast_default_opts(ifeast_opts *o) {
   o->time_limit_ms = 0.0;
   o->node_chunk = 0;
   o->plain_loads = 0;
+  o->nonsym_correction = 0;
 }
 
 const char *ifeast_strerror(int code) {
@@ -901,6 +988,11 @@ int ifeast_create(const ifeast_csr *A, const ifeast_csr *B, const ifeast_contour
     h->theta = (double2 *)(b + off.theta);
     h->Uc = (double2 *)(b + off.Uc);
     h->ridx = (int *)(b + off.ridx);
+    h->nsM = (double2 *)(b + off.nsM);
+    h->nsG = (double *)(b + off.nsG);
+    h->nsP = (double *)(b + off.nsP);
+    h->Rres = (double *)(b + off.Rres);
+    h->rnorm = (double *)(b + off.rnorm);
   }
   if (B) {
     h->nnzB = nnzB;
@@ -1073,6 +1165,16 @@ int ifeast_solve(ifeast_t h, const double *X0, int x0_on_device, uint64_t seed, 
       CK(minres_filter(ma, h->stream));
     } else if (h->fp32 && it > 1 && h->stats.RF <= h->opts.correction_rf) {  // FP32: residual form
       CK(gmres_filter(gmres_args(h, h->Rres, h->Q, 1), h->stream));
+    } else if (h->nonsym && h->opts.nonsym_correction && it > 1) {  // block correction
+      rc = ns_block_correction_setup(h);
+      if (rc) return rc;
+      GmresArgs ga = gmres_args(h, h->Rres, h->Q, 0);
+      ga.correction = 2;
+      ga.beta = h->rnorm;
+      ga.ns_M = h->nsM;
+      ga.ns_Gre = h->nsG;
+      ga.ns_X = h->X;
+      CK(gmres_filter(ga, h->stream));
     } else {  // right-hand sides X, or B X (norms in beta) from the previous Rayleigh-Ritz
       CK(gmres_filter(gmres_args(h, h->rowptrB ? h->BX : h->X, h->Q), h->stream));
     }

@@ -130,7 +130,14 @@ struct GmresArgs {
   int b_same_pattern;       // 1: B has A's rowptr/colidx (valB indexed like val)
   // residual form: right-hand sides r_j = A x_j - lambda_j B x_j (in X, norms in
   // beta), y = (x_j + e) / (z_k - lambda_j), Q = cx X + Re sum_k w_k e_k / (z_k - lambda_j)
+  // (correction = 1). Block correction for non-symmetric A (correction = 2):
+  // right-hand sides R = A X - X C (C = X^T A X, X orthonormal), E_k the
+  // weighted solutions w_k (z_k I - A)^{-1} R, and
+  // Q = X Re(sum_k w_k M_k) + Re sum_k E_k M_k with M_k = (z_k I - C)^{-1}
   int correction;
+  const double2 *ns_M;      // correction = 2: [nc][m0][m0] M_k (row-major)
+  const double *ns_Gre;     // correction = 2: m0 x m0 Re sum_k w_k M_k
+  const double *ns_X;       // correction = 2: n x m0 the orthonormal basis X
   int accumulate;           // 1: Q += this pass's sum (later node chunks)
   int stream_tma;           // 1: FP32 basis kernels stream the basis by TMA (when C is even)
   const double *lam;        // [m0] Ritz values
@@ -265,6 +272,10 @@ struct NonsymArgs {
   double2 *Uc;              // m0 x m0 unit eigenvectors of C = L^{-1} Q^T A Q L^{-T}
 };
 cudaError_t rayleigh_ritz_nonsym(const RRArgs &a, const NonsymArgs &ns, cudaStream_t st);
+// R = (A Q) L^{-T} - Q P (m0 <= 64): the block residual A X - X C of X = Q L^{-T}
+// with P = L^{-T} C, right-hand sides of the non-symmetric block correction
+cudaError_t ns_block_residual(int n, int m0, const double *AQ, const double *Q,
+                              const double *LinvT, const double *P, double *R, cudaStream_t st);
 cudaError_t ritz_vectors_nonsym(int n, int m, const double *X, const double2 *Uc, const int *idx,
                                 int cnt, int cap, double2 *out, cudaStream_t st);
 constexpr int kNonsymMaxM0 = 64;

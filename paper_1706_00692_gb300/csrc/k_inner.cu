@@ -591,9 +591,11 @@ __global__ void k_prep(int n, int m0, int C, int K, const double *__restrict__ X
     const double tol_rel = status->tol_rel;
     double t = 0.0;
     if (tol_rel > 0.0) {
-      if (correction) {
+      if (correction == 1) {
         const double2 d = make_double2(z[k].x - lam[j], z[k].y);
         t = tol_rel * xnorm[j] * sqrt(cabs2(d));
+      } else if (correction == 2) {
+        t = tol_rel;  // Alg. 2's bound tol_rel ||x_j|| with ||x_j|| = 1
       } else {
         t = tol_rel * b;
       }
@@ -630,7 +632,7 @@ __global__ void k_solve_y(int C, int m0, int nc, int K, const double2 *__restric
   }
   const int k = c / m0, j = c % m0;
   double2 wk = wq[k];
-  if (correction) wk = cdiv(wk, make_double2(z[k].x - lam[j], z[k].y));
+  if (correction == 1) wk = cdiv(wk, make_double2(z[k].x - lam[j], z[k].y));
   for (int l = 0; l < K; ++l) {
     const double2 v = (l < m) ? cmul(wk, y[l]) : make_double2(0.0, 0.0);
     Y[(size_t)l * C + c] = v;
@@ -638,7 +640,7 @@ __global__ void k_solve_y(int C, int m0, int nc, int K, const double2 *__restric
   }
   if (cx && c < m0) {
     double t = 0.0;
-    if (correction)
+    if (correction == 1)
       for (int kk = 0; kk < nc; ++kk)
         t += cdiv(wq[kk], make_double2(z[kk].x - lam[c], z[kk].y)).x;
     cx[c] = t;
@@ -678,6 +680,81 @@ __global__ void k_quadrature(int n, int m0, int nc, int C, const CT *__restrict_
   }
   const double t = cx ? cx[j] * Xr[idx] + (double)q : (double)q;
   Q[idx] = accumulate ? Q[idx] + t : t;  // later node chunks add their part
+}
+
+// Block correction for non-symmetric A (FP64 basis): E[r][c] = sum_{l <
+// steps[c]} Y[l][c] V_l[r][c], the weighted solution w_k e of system c = (node
+// k, column j) on row r.
+__global__ void k_ns_solutions(int n, int C, const double2 *__restrict__ V, size_t vstride,
+                               const double2 *__restrict__ Y, const int *__restrict__ steps,
+                               double2 *__restrict__ E) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * C) return;
+  const int c = (int)(idx % C);
+  const int m = steps[c];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int l = 0; l < m; ++l) {
+    const double2 y = Y[(size_t)l * C + c], v = V[(size_t)l * vstride + idx];
+    acc.x = fma(y.x, v.x, fma(-y.y, v.y, acc.x));
+    acc.y = fma(y.x, v.y, fma(y.y, v.x, acc.y));
+  }
+  E[idx] = acc;
+}
+
+// Q = X Gre + Re(E M) (add_x = 0: without the first term; accumulate: Q +=),
+// X n x m0 real, Gre m0 x m0, E n x C complex, M C x m0 complex (row c =
+// k m0 + j holds row j of M_k). A block computes 32 rows x m0 columns: thread
+// (i, ty) owns column i of rows ty, ty + 4, ...; chunks of 16 contraction
+// indices of E and M are staged in shared memory.
+constexpr int kNsRows = 32;
+constexpr int kNsChunk = 16;
+__global__ void __launch_bounds__(256)
+k_ns_combine(int n, int m0, int C, const double *__restrict__ X, const double *__restrict__ Gre,
+             const double2 *__restrict__ E, const double2 *__restrict__ M, int add_x,
+             int accumulate, double *__restrict__ Q) {
+  __shared__ double2 sE[kNsRows][kNsChunk + 1];
+  __shared__ double2 sM[kNsChunk][64];
+  const int i = threadIdx.x, ty = threadIdx.y;  // blockDim (64, 4)
+  const int r0 = blockIdx.x * kNsRows;
+  const int tid = ty * 64 + i;
+  double acc[kNsRows / 4];
+#pragma unroll
+  for (int u = 0; u < kNsRows / 4; ++u) acc[u] = 0.0;
+  // Re(E M) = E.x M.x - E.y M.y
+  for (int c0 = 0; c0 < C; c0 += kNsChunk) {
+    for (int e = tid; e < kNsRows * kNsChunk; e += 256) {
+      const int rr = e / kNsChunk, cc = e % kNsChunk;
+      const int r = r0 + rr, c = c0 + cc;
+      sE[rr][cc] = (r < n && c < C) ? E[(size_t)r * C + c] : make_double2(0.0, 0.0);
+    }
+    for (int e = tid; e < kNsChunk * 64; e += 256) {
+      const int cc = e / 64, ii = e % 64;
+      const int c = c0 + cc;
+      sM[cc][ii] = (c < C && ii < m0) ? M[(size_t)c * m0 + ii] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int cc = 0; cc < kNsChunk; ++cc) {
+      const double2 mm = sM[cc][i];
+#pragma unroll
+      for (int u = 0; u < kNsRows / 4; ++u) {
+        const double2 ee = sE[ty + 4 * u][cc];
+        acc[u] = fma(ee.x, mm.x, fma(-ee.y, mm.y, acc[u]));
+      }
+    }
+    __syncthreads();
+  }
+  if (i >= m0) return;
+#pragma unroll
+  for (int u = 0; u < kNsRows / 4; ++u) {
+    const int r = r0 + ty + 4 * u;
+    if (r >= n) continue;
+    double t = acc[u];
+    if (add_x)
+      for (int j = 0; j < m0; ++j) t = fma(X[(size_t)r * m0 + j], Gre[(size_t)j * m0 + i], t);
+    const size_t o = (size_t)r * m0 + i;
+    Q[o] = accumulate ? Q[o] + t : t;
+  }
 }
 
 // Tensor maps of the FP32 basis (a 3D view: 2C floats x n rows x K+1 vectors)
@@ -839,10 +916,23 @@ cudaError_t run_gmres(const GmresArgs &a, cudaStream_t st, const TmaMaps *tma) {
   if (e != cudaSuccess) return e;
   IFEAST_PROF_BEGIN(a.prof, K_GM_SOLVE);
   k_solve_y<<<(a.C + 127) / 128, 128, 0, st>>>(
-      a.C, a.m0, a.nc, a.K, a.R, a.G, a.w, a.z, a.correction ? a.lam : nullptr, a.correction,
-      a.steps, a.Y, a.fp32 ? a.Yf : nullptr, a.correction ? a.cx : nullptr, a.status);
+      a.C, a.m0, a.nc, a.K, a.R, a.G, a.w, a.z, a.correction == 1 ? a.lam : nullptr,
+      a.correction, a.steps, a.Y, a.fp32 ? a.Yf : nullptr, a.correction == 1 ? a.cx : nullptr,
+      a.status);
   IFEAST_PROF_END(a.prof);
   IFEAST_PROF_BEGIN(a.prof, K_GM_QUAD);
+  if constexpr (std::is_same_v<CT, double2>) {
+    if (a.correction == 2) {  // block correction: E_k, then Q from M_k (the work vector holds E)
+      const size_t nc_tot = (size_t)a.n * a.C;
+      double2 *E = static_cast<double2 *>(a.W);
+      k_ns_solutions<<<(unsigned)((nc_tot + 255) / 256), 256, 0, st>>>(
+          a.n, a.C, V, (size_t)a.n * a.C, a.Y, a.steps, E);
+      k_ns_combine<<<(unsigned)((a.n + kNsRows - 1) / kNsRows), dim3(64, 4), 0, st>>>(
+          a.n, a.m0, a.C, a.ns_X, a.ns_Gre, E, a.ns_M, a.accumulate ? 0 : 1, a.accumulate, a.Q);
+      IFEAST_PROF_END(a.prof);
+      return cudaGetLastError();
+    }
+  }
   const size_t nq = (size_t)a.n * a.m0;
   k_quadrature<CT><<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
       a.n, a.m0, a.nc, a.C, V, (size_t)a.n * a.C, a.Y, a.Yf, a.steps,
@@ -895,7 +985,9 @@ RowTiling make_tiling(int64_t n, int ncols, int num_sms) {
 
 cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
   if (a.K < 1 || a.K > kMaxInner) return cudaErrorInvalidValue;
-  if (a.correction && (!a.lam || !a.xnorm || !a.Xr || !a.cx)) return cudaErrorInvalidValue;
+  if (a.correction == 1 && (!a.lam || !a.xnorm || !a.Xr || !a.cx)) return cudaErrorInvalidValue;
+  if (a.correction == 2 && (a.fp32 || a.m0 > 64 || !a.ns_M || !a.ns_Gre || !a.ns_X))
+    return cudaErrorInvalidValue;
   if (a.fp32 && (!a.val32 || !a.Yf || (a.rowptrB && !a.valB32))) return cudaErrorInvalidValue;
   if (a.ncc < 1 || a.nc % a.ncc != 0 || a.C != a.ncc * a.m0) return cudaErrorInvalidValue;
   // passes over chunks of ncc nodes: the same kernels on the chunk's nodes and
@@ -912,6 +1004,7 @@ cudaError_t gmres_filter(const GmresArgs &a, cudaStream_t st) {
     b.w = a.w + k0;
     b.steps = a.steps + (size_t)k0 * a.m0;
     b.accumulate = k0 > 0 ? 1 : 0;
+    if (a.ns_M) b.ns_M = a.ns_M + (size_t)k0 * a.m0 * a.m0;
     e = a.fp32 ? run_gmres<float2>(b, st, use_tma ? &maps : nullptr)
                : run_gmres<double2>(b, st, nullptr);
   }

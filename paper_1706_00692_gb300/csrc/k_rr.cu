@@ -1127,6 +1127,27 @@ __global__ void k_ritz_vectors_nonsym(int n, int m, const double *__restrict__ X
   out[(size_t)i * cap + q] = t;
 }
 
+// R = A X - X C for the carried basis X = Q L^{-T} of the non-symmetric
+// iteration, from A Q of the last Rayleigh-Ritz: R = (A Q) L^{-T} - Q P with
+// P = L^{-T} C (both m0 x m0, row-major). Thread (i, ty) of a (64, 4) block owns
+// column i of rows blockIdx.x * 32 + ty, ty + 4, ...
+__global__ void __launch_bounds__(256)
+k_ns_block_residual(int n, int m0, const double *__restrict__ AQ, const double *__restrict__ Q,
+                    const double *__restrict__ LinvT, const double *__restrict__ P,
+                    double *__restrict__ R) {
+  const int i = threadIdx.x, ty = threadIdx.y;
+  if (i >= m0) return;
+  for (int u = 0; u < 8; ++u) {
+    const int r = blockIdx.x * 32 + ty + 4 * u;
+    if (r >= n) return;
+    double t = 0.0;
+    for (int j = 0; j < m0; ++j)
+      t = fma(AQ[(size_t)r * m0 + j], LinvT[(size_t)j * m0 + i],
+              fma(-Q[(size_t)r * m0 + j], P[(size_t)j * m0 + i], t));
+    R[(size_t)r * m0 + i] = t;
+  }
+}
+
 }  // namespace
 
 cudaError_t rr_init() {
@@ -1379,6 +1400,13 @@ cudaError_t rayleigh_ritz_nonsym(const RRArgs &a, const NonsymArgs &ns, cudaStre
                                              a.alpha, a.res, a.beta, a.lam, a.status);
     IFEAST_PROF_END(a.prof);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t ns_block_residual(int n, int m0, const double *AQ, const double *Q,
+                              const double *LinvT, const double *P, double *R, cudaStream_t st) {
+  if (m0 < 1 || m0 > 64) return cudaErrorInvalidValue;
+  k_ns_block_residual<<<(unsigned)((n + 31) / 32), dim3(64, 4), 0, st>>>(n, m0, AQ, Q, LinvT, P, R);
   return cudaGetLastError();
 }
 

@@ -252,9 +252,28 @@ class Workload:
     two_pass: bool = False  # shared-basis solver without the stored basis
     B: CSR | None = None  # generalized problem A x = lambda B x (None: B = I)
     node_chunk: int = 0   # per-node GMRES: nodes per inner pass (0: all)
+    nonsym: bool = False  # real non-symmetric A (per-node GMRES, complex Ritz pairs)
+    nonsym_correction: bool = False  # non-symmetric block correction of the shifted systems
 
     def X0(self) -> np.ndarray:
         return initial_subspace(self.A.n, self.m0, self.seed)
+
+
+def workload_convdiff(N: int = 512, count: int = 40, m0: int = 64, Pe: float = 10.0) -> Workload:
+    """2D convection-diffusion, 5-point upwind, on an N x N grid (n = N^2, Peclet
+    Pe): real non-symmetric A with a closed-form real spectrum. The circle
+    through 0 and emax, emax in the gap after the count-th lowest eigenvalue,
+    holds count eigenvalues; m0 = 64, 16 trapezoid nodes on the circle (8 on the
+    upper half: conjugate nodes pair up for real A), GMRES(32) in FP64, solved
+    for the block correction from the second outer iteration on."""
+    cf = upwind_convection_diffusion_eigs((N, N), Pe)
+    emax = 0.5 * (cf[count - 1] + cf[count])
+    wl = Workload(f"convdiff_{N}x{N}_pe{int(Pe)}_lowest{count}_m0_{m0}_trap16_gmres32_blockcorr",
+                  upwind_convection_diffusion((N, N), Pe), 0.0, emax, m0=m0, nc=8,
+                  rule="trap_half", inner_iters=32, alpha=0.0, seed=0, expected_count=count)
+    wl.nonsym = True
+    wl.nonsym_correction = True
+    return wl
 
 
 def workload_lap2d_50(seed: int = 0) -> Workload:

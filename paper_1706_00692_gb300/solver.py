@@ -71,7 +71,8 @@ class Solver:
                  torch_workspace: bool = True, verbose: bool = False, B: CSR | None = None,
                  nonsymmetric: bool = False, two_pass: bool = False,
                  correction_rf: float | None = None, user_nodes=None,
-                 time_limit_ms: float = 0.0, node_chunk: int = 0, plain_loads: bool = False):
+                 time_limit_ms: float = 0.0, node_chunk: int = 0, plain_loads: bool = False,
+                 nonsym_correction: bool = False):
         torch = _torch()
         self.lib = _lib.load()
         self.torch = torch
@@ -101,6 +102,7 @@ class Solver:
         self.opts.time_limit_ms = float(time_limit_ms)
         self.opts.node_chunk = int(node_chunk)
         self.opts.plain_loads = 1 if plain_loads else 0
+        self.opts.nonsym_correction = 1 if nonsym_correction else 0
         nbytes = ct.c_size_t(0)
         rc = self.lib.ifeast_workspace_bytes_generalized(
             self.n, A.nnz, -1 if B is None else B.nnz, self.m0, ct.byref(self.contour),

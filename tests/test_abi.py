@@ -344,3 +344,19 @@ def test_plain_loads_option(lib):
     assert lib.ifeast_workspace_bytes(5000, 30000, 12, ct.byref(c),
                                       ct.byref(_opts(lib, plain_loads=2)),
                                       ct.byref(b)) == _lib.IFEAST_ERR_INVALID_ARG
+
+
+def test_nonsym_correction_option(lib):
+    """nonsym_correction: 0 (default, the plain form) or 1 (block correction of
+    the non-symmetric iteration); anything else is rejected."""
+    o = _lib.Opts()
+    lib.ifeast_default_opts(ct.byref(o))
+    assert o.nonsym_correction == 0
+    c = _lib.Contour(0, 8, 0.0, 1.0)
+    b = ct.c_size_t()
+    assert lib.ifeast_workspace_bytes(5000, 30000, 12, ct.byref(c),
+                                      ct.byref(_opts(lib, nonsymmetric=1, nonsym_correction=1)),
+                                      ct.byref(b)) == 0
+    assert lib.ifeast_workspace_bytes(5000, 30000, 12, ct.byref(c),
+                                      ct.byref(_opts(lib, nonsym_correction=2)),
+                                      ct.byref(b)) == _lib.IFEAST_ERR_INVALID_ARG
