@@ -176,3 +176,24 @@ def test_block_correction_solve_matches_oracle(torch, grid, cnt, m0, max_iters):
                             correction=True)
     assert out["converged"]
     assert abs(iters - out["iters"]) <= 1
+
+
+def test_block_correction_node_chunks_equal_all_nodes(torch):
+    """The block correction with the contour nodes solved two at a time
+    (node_chunk=2: each pass adds its nodes' E_k M_k to Q, the first also
+    X Re(sum_k w_k M_k)) gives the all-nodes iteration: the same iteration
+    count and eigenvalues to rounding."""
+    grid, Pe, cnt, m0 = (16, 12), 10.0, 6, 12
+    A = inputs.upwind_convection_diffusion(grid, Pe)
+    cf = inputs.upwind_convection_diffusion_eigs(grid, Pe)
+    emax = 0.5 * (cf[cnt - 1] + cf[cnt])
+    X0 = inputs.initial_subspace(A.n, m0, 0)
+    out = []
+    for chunk in (0, 2):
+        S = _solver(A, 0.0, emax, m0, nc=8, rule="trap_half", inner_iters=32, max_outer=40,
+                    nonsym_correction=True, node_chunk=chunk)
+        assert S.solve(X0) == 0
+        out.append((S.eigenpairs_complex()[0], S.stats()["outer_iters"]))
+        S.close()
+    assert out[0][1] == out[1][1]
+    assert np.abs(np.sort(out[0][0].real) - np.sort(out[1][0].real)).max() <= 1e-12 * cf[cnt - 1]
