@@ -87,3 +87,22 @@ def test_lap3d64_window_comes_from_the_oracle_spectrum():
     assert (lam < emin).any() and (lam > emax).any()
     assert np.all(np.diff(lam) > 0)
     assert res.max() <= 1e-11 * lam.min()
+
+
+def test_convdiff_workload_interval():
+    """The 512 x 512 upwind convection-diffusion workload: the circle through 0
+    and emax holds exactly the 40 lowest closed-form eigenvalues (all real),
+    emax sits midway in the gap after the 40th, and the closed form matches a
+    dense eigensolve on a small grid of the same generator."""
+    import numpy as np
+    from paper_1706_00692_gb300 import inputs
+    wl = inputs.workload_convdiff(512)
+    cf = inputs.upwind_convection_diffusion_eigs((512, 512), 10.0)
+    assert wl.A.n == 512 * 512 and wl.m0 == 64 and wl.nonsym and wl.nonsym_correction
+    c = r = wl.emax / 2
+    assert int((np.abs(cf - c) < r).sum()) == 40 == wl.expected_count
+    assert cf[39] < wl.emax < cf[40]
+    assert abs(wl.emax - 0.5 * (cf[39] + cf[40])) <= 1e-12 * wl.emax
+    small = inputs.upwind_convection_diffusion((12, 10), 10.0).to_scipy().toarray()
+    ev = np.sort(np.linalg.eigvals(small).real)
+    assert np.abs(ev - inputs.upwind_convection_diffusion_eigs((12, 10), 10.0)).max() <= 1e-10 * ev.max()
